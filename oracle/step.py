@@ -1,0 +1,128 @@
+"""Vortex shedding and time stepping (Sec. 2.4.2-2.4.3, the paper's stepping rules).
+
+Test infrastructure only (see the package docstring).
+
+Rules taken from the paper (Sec. 2.4.2): the first vortex released from an
+edge sits 10 dt U_inf from the edge; every later one sits one third of the way
+from the edge to the last vortex released from that edge; vortices advect with
+the local velocity (forward Euler in the paper).  Readings where the paper is
+terse: the "edge" is the Kutta point pushed half a surface segment outward
+along the surface; the first offset is along the surface normal at the edge
+whose dot product with the free stream is positive; RK2 is Heun's method whose
+second stage keeps the new strengths and enforces the Kelvin condition through
+the circulation-constrained system (Eq. circsystem) with no further shedding.
+"""
+import math
+
+import numpy as np
+
+from . import body as B
+from .vic import regularize, circulation, streamfunction, node_velocity, interpolate
+
+
+class Kinematics:
+    """Rigid plate pitching about the origin: alpha(t) = alpha0 + amp sin(omega t).
+
+    The chord points along (cos alpha, -sin alpha); the body rotation angle is
+    -alpha, so Omega = -amp omega cos(omega t).  A static plate has amp = 0.
+    """
+
+    def __init__(self, ns, chord, alpha0, amp=0.0, omega=0.0, Uinf=1.0, Vinf=0.0):
+        self.ns, self.chord, self.alpha0, self.amp, self.omega = ns, chord, alpha0, amp, omega
+        self.Uinf, self.Vinf = Uinf, Vinf
+
+    def alpha(self, t):
+        return self.alpha0 + self.amp * math.sin(self.omega * t)
+
+    def surface(self, t):
+        a = self.alpha(t)
+        xi = -1.0 + (2.0 * np.arange(1, self.ns + 1) - 1.0) / self.ns
+        x = 0.5 * self.chord * xi * math.cos(a)
+        y = -0.5 * self.chord * xi * math.sin(a)
+        return x, y, np.full(self.ns, self.chord / self.ns), (0, self.ns - 1)
+
+    def Omega(self, t):
+        return -self.amp * self.omega * math.cos(self.omega * t)
+
+
+def edge_point(xs, ys, k):
+    """Geometric edge next to Kutta point k: half a segment beyond it."""
+    nb = k + 1 if k == 0 else k - 1
+    return xs[k] + 0.5 * (xs[k] - xs[nb]), ys[k] + 0.5 * (ys[k] - ys[nb])
+
+
+def new_vortex_position(xs, ys, k, last, dt, Uinf, Vinf):
+    """Placement rule of Sec. 2.4.2 for the vortex released at edge k."""
+    ex, ey = edge_point(xs, ys, k)
+    if last is None:
+        nb = k + 1 if k == 0 else k - 1
+        tx, ty = xs[k] - xs[nb], ys[k] - ys[nb]
+        nx_, ny_ = -ty, tx
+        nrm = math.hypot(nx_, ny_)
+        nx_, ny_ = nx_ / nrm, ny_ / nrm
+        if nx_ * Uinf + ny_ * Vinf < 0.0:
+            nx_, ny_ = -nx_, -ny_
+        d = 10.0 * dt * math.hypot(Uinf, Vinf)
+        return ex + d * nx_, ey + d * ny_
+    return ex + (last[0] - ex) / 3.0, ey + (last[1] - ey) / 3.0
+
+
+class BodyState:
+    def __init__(self):
+        self.X = np.zeros(0)
+        self.Y = np.zeros(0)
+        self.G = np.zeros(0)
+        self.last = [None, None]     # index of the last vortex released at each edge
+        self.t = 0.0
+
+
+def _solve_and_velocity(grid, table, kin, t, X, Y, G, shed, dt, last_pos):
+    """One stage: sheet solve (two-edge Kutta shedding or Kelvin circulation) and
+    velocities at all vortices.  Returns (u, v, newX, newY, newG, info)."""
+    xs, ys, ds, (k1, k2) = kin.surface(t)
+    st = B.SurfaceStencil(grid, xs, ys)
+    sch = B.Schur(B.schur_matrix(grid, st, ds, table), ds)
+    sbp = B.sb_prime(xs, ys, 0.0, 0.0, kin.Omega(t), kin.Uinf, kin.Vinf)
+    w = regularize(grid, X, Y, G)
+    Gw = circulation(grid, w)
+    EinvLw = -B.interp_surface(st, streamfunction(grid, w, table))
+    if shed:
+        p1 = new_vortex_position(xs, ys, k1, last_pos[0], dt, kin.Uinf, kin.Vinf)
+        p2 = new_vortex_position(xs, ys, k2, last_pos[1], dt, kin.Uinf, kin.Vinf)
+        nX, nY = np.array([p1[0], p2[0]]), np.array([p1[1], p2[1]])
+        E = B.EinvL_unit_vortex(grid, st, nX, nY, table)
+        f, ft, s0, G1, G2 = B.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+        nG = np.array([G1, G2])
+    else:
+        f, s0 = B.sheet_circulation(sch, sbp, EinvLw, -Gw)
+        nX, nY, nG = np.zeros(0), np.zeros(0), np.zeros(0)
+    AX, AY, AG = np.concatenate([X, nX]), np.concatenate([Y, nY]), np.concatenate([G, nG])
+    wt = regularize(grid, AX, AY, AG) + B.regularize_surface(grid, st, f, ds)
+    psi1 = streamfunction(grid, wt, table, pad=1)
+    u, v = node_velocity(grid, psi1, kin.Uinf, kin.Vinf)
+    info = dict(f=f, s0=s0, Gw=Gw, circ_f=sch.circ(f), psi=psi1[1:-1, 1:-1], st=st, sch=sch, sbp=sbp)
+    return interpolate(grid, u, AX, AY), interpolate(grid, v, AX, AY), nX, nY, nG, info
+
+
+def body_step(grid, table, kin, state, dt, scheme="euler"):
+    """Advance the vortex set one step with two-edge Kutta shedding (Sec. 2.4.3)."""
+    t = state.t
+    last_pos = [None if i is None else (state.X[i], state.Y[i]) for i in state.last]
+    u1, v1, nX, nY, nG, info = _solve_and_velocity(grid, table, kin, t, state.X, state.Y, state.G,
+                                                   True, dt, last_pos)
+    X = np.concatenate([state.X, nX])
+    Y = np.concatenate([state.Y, nY])
+    G = np.concatenate([state.G, nG])
+    if scheme == "euler":
+        X, Y = X + dt * u1, Y + dt * v1
+    elif scheme == "rk2":
+        Xs, Ys = X + dt * u1, Y + dt * v1
+        u2, v2, _, _, _, _ = _solve_and_velocity(grid, table, kin, t + dt, Xs, Ys, G, False, dt, None)
+        X, Y = X + 0.5 * dt * (u1 + u2), Y + 0.5 * dt * (v1 + v2)
+    else:
+        raise ValueError(scheme)
+    n_old = len(state.X)
+    state.X, state.Y, state.G = X, Y, G
+    state.last = [n_old, n_old + 1]
+    state.t = t + dt
+    return info

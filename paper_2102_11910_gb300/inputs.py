@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle tests.
+
+This module only draws and lays out inputs (grids, point vortices, surface
+points of plates, circles and ellipses); it holds none of the method's
+arithmetic.  Every generator takes an explicit seed (numpy PCG64).
+
+Workloads (shapes of the paper's synthetic experiments):
+
+* ``plate_vortices_128``: 128 x 128 nodes, dx = 0.02, grid centred on the
+  origin; flat plate of chord 1 at 20 deg in uniform flow (1, 0) with 64
+  surface points; 256 vortices uniform in [-1, 1]^2, none within 3 dx of the
+  plate, strengths normal with variance 0.01.  Seed 1000.
+* ``vic_1024``: 1024 x 1024 nodes on [-1, 1]^2 (dx = 2/1023); 1e6 vortices
+  uniform in the central 80 % of the domain, strengths normal with variance
+  1e-4; no body.  Seed 1001.
+* ``pitching_plate_512x768``: 768 (x) by 512 (y) nodes, dx = 0.01, plate of
+  chord 1, 256 points, mid-chord 1.5 chords from the upstream edge.  Seed 1002.
+"""
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class GridSpec:
+    nx: int
+    ny: int
+    dx: float
+    x0: float
+    y0: float
+
+
+@dataclass
+class SurfaceSpec:
+    x: np.ndarray
+    y: np.ndarray
+    ds: np.ndarray
+    edges: tuple          # surface-point indices of sharp edges (empty for smooth bodies)
+
+
+def centred_grid(nx, ny, dx):
+    """Grid whose node block is centred on the origin."""
+    return GridSpec(nx, ny, dx, -0.5 * (nx - 1) * dx, -0.5 * (ny - 1) * dx)
+
+
+def plate(ns, chord=1.0, alpha=0.0, xc=0.0, yc=0.0):
+    """Flat plate: points at the midpoints of ns equal segments.
+
+    xi_p = -1 + (2p - 1)/ns (p = 1..ns) runs from the leading edge (xi = -1) to
+    the trailing edge (xi = 1); the chord points along (cos a, -sin a), so the
+    leading edge is raised for a > 0.  Edges: first and last point.
+    """
+    xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+    x = xc + 0.5 * chord * xi * math.cos(alpha)
+    y = yc - 0.5 * chord * xi * math.sin(alpha)
+    return SurfaceSpec(x, y, np.full(ns, chord / ns), (0, ns - 1))
+
+
+def plate_xi(ns):
+    return -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+
+
+def circle(ns, radius=1.0, xc=0.0, yc=0.0):
+    """Circle: theta_p = 2 pi (p - 1)/ns, counter-clockwise from +x."""
+    th = 2.0 * np.pi * np.arange(ns) / ns
+    return SurfaceSpec(xc + radius * np.cos(th), yc + radius * np.sin(th),
+                       np.full(ns, 2.0 * np.pi * radius / ns), ())
+
+
+def ellipse(ns, a, b, xc=0.0, yc=0.0, rot=0.0):
+    """Ellipse with semi-axes a, b: points at equal arc length (numerical inversion)."""
+    t = np.linspace(0.0, 2.0 * np.pi, 20001)
+    sp = np.sqrt((a * np.sin(t)) ** 2 + (b * np.cos(t)) ** 2)
+    s = np.concatenate([[0.0], np.cumsum(0.5 * (sp[1:] + sp[:-1]) * np.diff(t))])
+    per = s[-1]
+    tp = np.interp(per * np.arange(ns) / ns, s, t)
+    x, y = a * np.cos(tp), b * np.sin(tp)
+    c, sn = math.cos(rot), math.sin(rot)
+    return SurfaceSpec(xc + c * x - sn * y, yc + sn * x + c * y, np.full(ns, per / ns), ())
+
+
+def uniform_vortices(rng, n, lo, hi, variance, ylo=None, yhi=None):
+    """n vortices uniform in [lo, hi] x [ylo, yhi], strengths N(0, variance)."""
+    ylo = lo if ylo is None else ylo
+    yhi = hi if yhi is None else yhi
+    X = rng.uniform(lo, hi, n)
+    Y = rng.uniform(ylo, yhi, n)
+    G = rng.normal(0.0, math.sqrt(variance), n)
+    return X, Y, G
+
+
+def _dist_to_segment(X, Y, ax, ay, bx, by):
+    vx, vy = bx - ax, by - ay
+    t = np.clip(((X - ax) * vx + (Y - ay) * vy) / (vx * vx + vy * vy), 0.0, 1.0)
+    return np.hypot(X - (ax + t * vx), Y - (ay + t * vy))
+
+
+def plate_vortices_128(seed=1000, nv=256, ns=64):
+    """The single-step plate workload (128^2 nodes, 64 surface points, 256 vortices)."""
+    rng = np.random.default_rng(seed)
+    grid = centred_grid(128, 128, 0.02)
+    alpha = math.radians(20.0)
+    body = plate(ns, 1.0, alpha)
+    ax, ay = -0.5 * math.cos(alpha), 0.5 * math.sin(alpha)
+    X, Y, G = [], [], []
+    while len(X) < nv:
+        x, y, g = uniform_vortices(rng, nv, -1.0, 1.0, 0.01)
+        keep = _dist_to_segment(x, y, ax, ay, -ax, -ay) > 3 * grid.dx
+        X += list(x[keep]); Y += list(y[keep]); G += list(g[keep])
+    return dict(grid=grid, body=body, X=np.array(X[:nv]), Y=np.array(Y[:nv]), G=np.array(G[:nv]),
+                Uinf=1.0, Vinf=0.0, dt=0.01, alpha=alpha)
+
+
+def vic_1024(seed=1001, nv=1_000_000, n=1024):
+    """The body-free VIC workload: n^2 nodes on [-1,1]^2, nv vortices in the central 80 %."""
+    rng = np.random.default_rng(seed)
+    dx = 2.0 / (n - 1)
+    grid = GridSpec(n, n, dx, -1.0, -1.0)
+    X, Y, G = uniform_vortices(rng, nv, -0.8, 0.8, 1e-4)
+    return dict(grid=grid, X=X, Y=Y, G=G)
+
+
+def vic_small(seed, n, nv, variance=1e-4, nyf=1.0):
+    """A smaller body-free case of the same recipe (n x round(n*nyf) nodes on [-1,1] in x)."""
+    rng = np.random.default_rng(seed)
+    ny = int(round(n * nyf))
+    dx = 2.0 / (n - 1)
+    grid = GridSpec(n, ny, dx, -1.0, -0.5 * (ny - 1) * dx)
+    half_y = 0.5 * (ny - 1) * dx
+    X, Y, G = uniform_vortices(rng, nv, -0.8, 0.8, variance, -0.8 * half_y, 0.8 * half_y)
+    return dict(grid=grid, X=X, Y=Y, G=G)
+
+
+def pitching_plate_512x768(ns=256):
+    """Grid and body-frame plate of the pitching-plate workload."""
+    dx = 0.01
+    grid = GridSpec(768, 512, dx, -1.5, -0.5 * 511 * dx)
+    return dict(grid=grid, ns=ns, chord=1.0, alpha0=math.radians(30.0), amp=math.radians(10.0),
+                k=0.5, Uinf=1.0, dt=0.0025)
