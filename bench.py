@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the body-free vortex-in-cell step on GB300.
+
+Workload: 1024 x 1024 nodes on [-1, 1]^2 (2048^2 padded FFT), 1e6 point
+vortices uniform in the central 80 %, strengths N(0, 1e-4), seed 1001.  One
+step = regularize (R_v), unbounded Poisson solve with the LGF (L^{-1}),
+spectral node velocity (curl) and interpolation to the vortices (E_v), i.e.
+one call of pf_vic_velocity.  Inputs are device resident; L2 is flushed
+(256 MB write) between timed steps, outside the timed events.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload per step, extrapolated to a full step.
+
+Under torchrun every rank runs an independent replica (the path does not
+shard); the reported value is the whole-job aggregate.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIC steps/s (R+L^-1+Schur+E) at <=1e-5 rel err vs FP64; p50/p99 latency"
+UNIT = "steps/s"
+WORKLOAD = ("vic_1024: 1024x1024 nodes, dx=2/1023, 2048^2 padded LGF FFT, 1e6 vortices uniform in the "
+            "central 80%, Gamma~N(0,1e-4), seed 1001; body-free step R_v + L^-1 + curl + E_v")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------ oracle timing
+ORACLE_SAMPLE = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import vic as OV
+from oracle.lgf import lgf_table
+from paper_2102_11910_gb300 import inputs
+nsub, nodes, reps = int(sys.argv[1]), int(sys.argv[2]), int(sys.argv[3])
+wl = inputs.vic_1024()
+g = wl["grid"]; og = OV.Grid(g.nx, g.ny, g.dx, g.x0, g.y0)
+X, Y, G = wl["X"], wl["Y"], wl["G"]
+nv = len(X); M = (g.nx + 2) * (g.ny + 2)
+t0 = time.perf_counter(); tab = lgf_table(g.nx + 1, g.ny + 1); t_tab = time.perf_counter() - t0
+w_full = OV.regularize(og, X, Y, G)          # source field of the sampled direct sums
+f = np.zeros((g.ny, g.nx))
+rng = np.random.default_rng(0)
+out = []
+for r in range(reps):
+    sel = rng.integers(0, nv, nsub)
+    t0 = time.perf_counter(); OV.regularize(og, X[sel], Y[sel], G[sel]); t_reg = (time.perf_counter() - t0) * nv / nsub
+    ti = rng.integers(0, g.nx, nodes); tj = rng.integers(0, g.ny, nodes)
+    t0 = time.perf_counter(); OV.inv_laplacian_at(og, w_full, ti, tj, tab); t_node = (time.perf_counter() - t0) / nodes
+    t0 = time.perf_counter(); OV.interpolate(og, f, X[sel], Y[sel]); t_int = 2 * (time.perf_counter() - t0) * nv / nsub
+    out.append(dict(step_s=t_reg + t_node * M + t_int, t_reg=t_reg, t_node=t_node, t_int=t_int))
+print(json.dumps(dict(reps=out, t_table=t_tab, nsub=nsub, nodes=nodes)))
+"""
+
+
+def run_oracle_sample(nsub, nodes, reps):
+    """Time the oracle (one thread) in a fresh process; returns the parsed JSON."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ORACLE_SAMPLE.format(root=ROOT)
+    r = subprocess.run([sys.executable, "-c", code, str(nsub), str(nodes), str(reps)], capture_output=True, text=True,
+                       env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_line_fields(res):
+    steps = [x["step_s"] for x in res["reps"]]
+    mean = statistics.mean(steps)
+    sample = ("per step: R_v of %d random vortices, direct-sum L^-1 at %d random nodes, E_v (u and v) of the same "
+              "%d vortices, each extrapolated linearly to 1e6 vortices and all 1026^2 nodes the step needs "
+              "(O(M^2) direct sum); one thread; LGF table by quadrature excluded (%.2f s, once per grid)") % (
+                  res["nsub"], res["nodes"], res["nsub"], res["t_table"])
+    return mean, sample
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != gpu_index:
+                    continue
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def csrc_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2102_11910_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_bytes(name, nx, ny, P, Q, nv, nrec, esz):
+    """Algorithmic bytes per launch: each input read once, each output written once."""
+    M = nx * ny
+    spec = (P // 2 + 1) * ny * 2 * esz
+    return {
+        "bin_count": 24 * nv,
+        "bin_scan": 0,
+        "bin_scatter": 24 * nv + 16 * nrec,
+        "regularize": 16 * nrec + esz * M,
+        "fft_rows_fwd": esz * M + spec,
+        "fft_cols_conv": spec + (P // 2 + 1) * (Q // 2 + 1) * esz + 2 * spec,
+        "fft_rows_inv": 2 * spec + 2 * esz * M,
+        "interpolate": 16 * nv + 2 * esz * M + 2 * esz * nv,
+    }.get(name)
+
+
+# ------------------------------------------------------------------ our arm
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2102_11910_gb300 as pf
+    from paper_2102_11910_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    wl = inputs.vic_1024()
+    g = wl["grid"]
+    X, Y, G = (torch.from_numpy(a).cuda() for a in (wl["X"], wl["Y"], wl["G"]))
+    nv = X.numel()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+        uq = torch.empty(nv, dtype=torch.float32, device="cuda")
+        vq = torch.empty(nv, dtype=torch.float32, device="cuda")
+
+        def step():
+            pf.pf_vic_velocity(plan, X, Y, G, 0.0, 0.0, uq, vq)
+
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        pf.pf_sync(plan)
+        K = args.steps
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        clk = ClockSampler()
+        clk.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(k & 255)
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        if world > 1:
+            dist.barrier()
+        clocks = clk.stop(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0)
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+        pf.pf_sync(plan)
+        per = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        total_ms = sum(per)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * K / (total_ms / 1e3)
+        ms_per_step = total_ms / K
+        srt = sorted(per)
+        p50 = srt[len(srt) // 2]
+        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+
+        # per-kernel CUDA-event timing pass (same stream, same flushes)
+        KT = min(K, 200)
+        pf.pf_timing_enable(plan, True)
+        for k in range(KT):
+            flush.fill_(k & 255)
+            step()
+        rep = pf.pf_timing_report(plan)
+        pf.pf_timing_enable(plan, False)
+        launches_per_step = sum(n for n, _ in rep.values()) / KT
+    # kernel roofline
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_note = "measured" if peaks else "fallback"
+    dup = 1.12   # average tiles per vortex record at 32x32 node tiles
+    nrec_est = int(nv * dup)
+    kern = {}
+    for name, (n, ms) in rep.items():
+        b = kernel_bytes(name, g.nx, g.ny, plan.P, plan.Q, nv, nrec_est, 4)
+        avg = ms / n
+        kern[name] = {"launches_per_step": n / KT, "avg_ms": avg, "share": ms / sum(v[1] for v in rep.values()),
+                      "alg_bytes": b, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
+    dom = max(kern, key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("csrc_sha") == csrc_sha() and dom in tj.get("kernels", {}):
+            traffic = tj["kernels"][dom].get("dram_bytes")
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / hbm_peak, "traffic": traffic, "peak_source": peak_note,
+            "alg_bytes_per_launch": kern[dom]["alg_bytes"]}
+    step_bytes = 36 * nv + 28 * g.nx * g.ny
+    step_roof = {"alg_bytes": step_bytes, "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
+                 "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    import torch as _t
+    hX, hY, hG = (_t.from_numpy(a).pin_memory() for a in (wl["X"], wl["Y"], wl["G"]))
+    hu = _t.empty(nv, dtype=_t.float32).pin_memory()
+    hv = _t.empty(nv, dtype=_t.float32).pin_memory()
+    KE = max(3, min(K, 30))
+    with _t.cuda.stream(stream):
+        pf.pf_vic_velocity_host(plan, hX, hY, hG, 0.0, 0.0, hu, hv)
+        t0 = time.perf_counter()
+        for _ in range(KE):
+            pf.pf_vic_velocity_host(plan, hX, hY, hG, 0.0, 0.0, hu, hv)
+        te = time.perf_counter() - t0
+    e2e = {"value": world * KE / te, "unit": UNIT, "h2d_bytes_per_step": 24 * nv, "d2h_bytes_per_step": 8 * nv}
+
+    extras = {}
+    if not args.no_extras:
+        # all-FP64 GPU path on the same workload, and the mixed path's error against it
+        with torch.cuda.stream(stream):
+            p64 = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_FP64, stream=stream)
+            u64 = torch.empty(nv, dtype=torch.float64, device="cuda")
+            v64 = torch.empty(nv, dtype=torch.float64, device="cuda")
+            pf.pf_vic_velocity(p64, X, Y, G, 0.0, 0.0, u64, v64)
+            pf.pf_sync(p64)
+            K64 = max(3, min(K, 20))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(K64):
+                pf.pf_vic_velocity(p64, X, Y, G, 0.0, 0.0, u64, v64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / K64
+            pf.pf_vic_velocity(plan, X, Y, G, 0.0, 0.0, uq, vq)
+            pf.pf_sync(plan)
+            num = torch.sqrt(torch.sum((uq.double() - u64) ** 2) + torch.sum((vq.double() - v64) ** 2))
+            den = torch.sqrt(torch.sum(u64 ** 2) + torch.sum(v64 ** 2))
+            extras["fp64_path"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64}
+            extras["mixed_rel_err_vs_fp64_gpu"] = float(num / den)
+            p64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        res = run_oracle_sample(nsub=200000, nodes=600, reps=1)
+        mean, sample = oracle_line_fields(res)
+        cpu = {"value": 1.0 / mean, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 grid path, FP64 positions and LGF setup)",
+                       "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "roofline": roof, "step_roofline": step_roof,
+            "kernels": kern, "gpu_launches": int(round(launches_per_step * K)),
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed_loop": t_wall,
+        }
+        line.update(extras)
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    # per-step sample sized so that K + W steps take about two minutes of CPU time
+    per = 120.0 / max(1, K + W)
+    nodes = max(1, int(per / 3 / 0.012))
+    nsub = max(2000, min(200000, int(per / 3 / 1.5e-6)))
+    res = run_oracle_sample(nsub=nsub, nodes=nodes, reps=K + W)
+    res["reps"] = res["reps"][W:]
+    mean, sample = oracle_line_fields(res)
+    value = 1.0 / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 leg and the CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,132 @@
+/*
+ * gridpf: grid-based planar potential flow with point vortices and an
+ * immersed body (Beckers & Eldredge, "Planar potential flow on Cartesian
+ * grids", arXiv 2102.11910), on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every entry point returns a
+ * pf_status; none throws.  Unless stated otherwise:
+ *   - array arguments are DEVICE pointers owned by the caller;
+ *   - work is enqueued asynchronously on the plan's CUDA stream, so a call
+ *     returning PF_OK means "enqueued"; errors found by kernels (out-of-domain
+ *     vortices, a timed-out wait) are recorded in a sticky device status word
+ *     and reported by pf_sync;
+ *   - node fields are row-major nx*ny arrays, index j*nx + i for node (i, j) at
+ *     (x0 + i dx, y0 + j dx);  their element type is double for PF_FP64 plans and
+ *     float for PF_MIXED plans ("real" below);
+ *   - vortex positions and strengths are always double.
+ *
+ * Operators (paper notation): L is the 5-point Laplacian scaled by 1/dx^2;
+ * L^{-1} is applied with the lattice Green's function G of the unit-spacing
+ * Laplacian (L0 G = delta, G(0,0) = 0), so L^{-1} = dx^2 (G *) on the unbounded
+ * grid (Sec. 2.1).  R_v / E_v use the M4' kernel (Eq. vortexregularization and
+ * E_v = R_v^T), R_s / E_s the smoothed three-point kernel (Sec. 2.2.1).
+ */
+#ifndef GRIDPF_H
+#define GRIDPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad mode)      */
+    PF_ERR_OOM = 2,            /* a device allocation failed                               */
+    PF_ERR_CUDA = 3,           /* a CUDA runtime call failed; pf_last_error has the text   */
+    PF_ERR_OUT_OF_DOMAIN = 4,  /* a point's 4x4 stencil left the grid; it was not used    */
+    PF_ERR_SINGULAR = 5,       /* a pivot of the Schur factorisation vanished              */
+    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                            */
+    PF_ERR_NOT_FACTORED = 7,   /* a sheet solve was asked of a body without a factor       */
+    PF_ERR_CAPACITY = 8        /* a state's vortex capacity would be exceeded              */
+} pf_status;
+
+typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
+
+typedef struct {
+    int32_t nx, ny;        /* nodes per direction, 8 <= nx, ny <= 2048                      */
+    double dx;             /* grid spacing                                                  */
+    double x0, y0;         /* coordinates of node (0, 0)                                    */
+    int32_t precision;     /* pf_precision: element type and arithmetic of the grid path    */
+} pf_grid_desc;
+
+typedef struct pf_plan_s* pf_plan;
+typedef struct pf_schur_s* pf_schur;
+typedef struct pf_state_s* pf_state;
+
+/* ------------------------------------------------------------------ plan */
+
+/* Create a plan for one grid: builds, in FP64 on the device, the LGF table
+ * G(m, n) for 0 <= m <= nx, 0 <= n <= ny (Sec. 2.1, refs. katsura71/cserti00)
+ * and the real spectrum of G on the zero-padded (P x Q) torus, P, Q the
+ * powers of two >= 2 nx, 2 ny.  `stream` is a cudaStream_t (NULL = default).
+ * The plan owns all tables and workspaces; the call synchronises the stream. */
+pf_status pf_plan_create(const pf_grid_desc* desc, void* stream, pf_plan* out);
+pf_status pf_plan_destroy(pf_plan plan);
+
+/* Padded FFT sizes chosen for the plan (host ints). */
+pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
+
+/* Copy the plan's FP64 LGF table to a host array of (nx+1)*(ny+1) doubles,
+ * index n*(nx+1) + m for G(m, n). Synchronises. */
+pf_status pf_lgf_table(pf_plan plan, double* host_out);
+
+/* Wait for the plan's stream; return and clear the sticky status.  If
+ * `out_of_domain` is non-null it receives the number of points dropped since
+ * the last pf_sync (host int64). */
+pf_status pf_sync(pf_plan plan, int64_t* out_of_domain);
+
+/* Text of the last error on this plan (static storage owned by the plan). */
+const char* pf_last_error(pf_plan plan);
+
+/* Per-kernel timing (instrumentation; not part of the method).  While on,
+ * every kernel the plan launches is bracketed by CUDA events recorded on the
+ * plan's stream.  pf_timing_enable(plan, 1) clears the records and turns it
+ * on; (plan, 0) turns it off.  pf_timing_report synchronises and writes one
+ * line per kernel name, "<name> <launches> <total milliseconds>\n", into the
+ * host buffer buf (NUL terminated, truncated to buflen), then clears the
+ * records. */
+pf_status pf_timing_enable(pf_plan plan, int32_t on);
+pf_status pf_timing_report(pf_plan plan, char* buf, int64_t buflen);
+
+/* --------------------------------------------------- body-free VIC path */
+
+/* w = R_v Gamma: w_ij = dx^-2 sum_q Gamma_q M4'((x_i-X_q)/dx) M4'((y_j-Y_q)/dx)
+ * (Eq. vortexregularization).  X, Y, Gam: nv doubles.  w: real[nx*ny], fully
+ * overwritten.  The sum is formed in 64-bit fixed point per tile, so the
+ * result is bitwise independent of scheduling.  Vortices whose stencil leaves
+ * the grid are skipped and counted (PF_ERR_OUT_OF_DOMAIN at pf_sync). */
+pf_status pf_regularize(pf_plan plan, const double* X, const double* Y, const double* Gam,
+                        int64_t nv, void* w);
+
+/* psi = -L^{-1} w (Sec. 2.1, particular solution; no homogeneous part).
+ * w, psi: real[nx*ny]; they may alias. */
+pf_status pf_poisson_solve(pf_plan plan, const void* w, void* psi);
+
+/* Node velocity of psi = -L^{-1} w plus a uniform flow: u = d psi/dy,
+ * v = -d psi/dx by centred differences (Eq. velsf with the face-to-node
+ * averages of Sec. 2.1), evaluated exactly in spectral form on the padded
+ * torus.  uv: real[2*nx*ny], interleaved (u, v) per node. */
+pf_status pf_velocity_solve(pf_plan plan, const void* w, double Uinf, double Vinf, void* uv);
+
+/* E_v: velocity at nq points from an interleaved node velocity field:
+ * uq[q] = sum_ij M4' M4' u_ij (E_v = R_v^T, Sec. 2.1).  uq, vq: real[nq]. */
+pf_status pf_interpolate(pf_plan plan, const void* uv, const double* Xq, const double* Yq,
+                         int64_t nq, void* uq, void* vq);
+
+/* The whole body-free step: R_v, psi = -L^{-1} w, curl, E_v at the vortices
+ * themselves (plus the uniform flow).  uq, vq: real[nv]. */
+pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const double* Gam,
+                          int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
+
+/* Same step with HOST input and output buffers: copies X, Y, Gam to the
+ * device, runs pf_vic_velocity, copies uq, vq (real[nv]) back, synchronises. */
+pf_status pf_vic_velocity_host(pf_plan plan, const double* X, const double* Y, const double* Gam,
+                               int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRIDPF_H */

@@ -1,0 +1,167 @@
+"""GB300 implementation of the grid potential-flow vortex method of
+Beckers & Eldredge, "Planar potential flow on Cartesian grids" (arXiv 2102.11910).
+
+The computation lives in the CUDA library ``libgridpf.so`` (C ABI declared in
+``include/gridpf.h``).  This module only marshals torch tensors to that ABI:
+each function has the C entry point's name and forwards device pointers and
+sizes.  PyTorch provides device memory and the current CUDA stream.
+"""
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import GridPfError
+
+PF_FP64 = 0
+PF_MIXED = 1
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Handle of a pf_plan (one grid, one precision, one CUDA stream)."""
+
+    def __init__(self, nx, ny, dx, x0, y0, precision=PF_MIXED, stream=None):
+        L = _native.lib()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.nx, self.ny, self.dx, self.x0, self.y0 = int(nx), int(ny), float(dx), float(x0), float(y0)
+        self.precision = int(precision)
+        self.dtype = torch.float64 if self.precision == PF_FP64 else torch.float32
+        desc = _native.PfGridDesc(self.nx, self.ny, self.dx, self.x0, self.y0, self.precision)
+        h = ctypes.c_void_p()
+        _native.check(L.pf_plan_create(ctypes.byref(desc), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+                      "pf_plan_create")
+        self.handle = h
+        P, Q = ctypes.c_int32(), ctypes.c_int32()
+        _native.check(L.pf_plan_fft_size(h, ctypes.byref(P), ctypes.byref(Q)), "pf_plan_fft_size", h)
+        self.P, self.Q = P.value, Q.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field(self, comps=1):
+        shape = (self.ny, self.nx) if comps == 1 else (self.ny, self.nx, comps)
+        return torch.empty(shape, dtype=self.dtype, device="cuda")
+
+
+def pf_plan_create(nx, ny, dx, x0, y0, precision=PF_MIXED, stream=None):
+    return Plan(nx, ny, dx, x0, y0, precision, stream)
+
+
+def pf_plan_destroy(plan):
+    plan.close()
+
+
+def pf_sync(plan):
+    """Wait for the plan's stream; raise GridPfError on a sticky error.  Returns
+    the number of out-of-domain points (0 when there were none)."""
+    n = ctypes.c_int64()
+    st = _native.lib().pf_sync(plan.handle, ctypes.byref(n))
+    if st != 0 and st != 4:
+        _native.check(st, "pf_sync", plan.handle)
+    if st == 4:
+        raise GridPfError(st, "pf_sync", "%d points out of domain" % n.value)
+    return n.value
+
+
+def pf_lgf_table(plan):
+    import numpy as np
+    out = np.empty((plan.ny + 1, plan.nx + 1), dtype=np.float64)
+    _native.check(_native.lib().pf_lgf_table(plan.handle, out.ctypes.data_as(ctypes.c_void_p)), "pf_lgf_table",
+                  plan.handle)
+    return out
+
+
+def pf_regularize(plan, X, Y, G, w=None):
+    w = plan.field() if w is None else w
+    nv = X.numel()
+    _native.check(_native.lib().pf_regularize(plan.handle, _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
+                                              _ptr(G, torch.float64, "G"), nv, _ptr(w, plan.dtype, "w")),
+                  "pf_regularize", plan.handle)
+    return w
+
+
+def pf_poisson_solve(plan, w, psi=None):
+    psi = plan.field() if psi is None else psi
+    _native.check(_native.lib().pf_poisson_solve(plan.handle, _ptr(w, plan.dtype, "w"), _ptr(psi, plan.dtype, "psi")),
+                  "pf_poisson_solve", plan.handle)
+    return psi
+
+
+def pf_velocity_solve(plan, w, Uinf=0.0, Vinf=0.0, uv=None):
+    uv = plan.field(2) if uv is None else uv
+    _native.check(_native.lib().pf_velocity_solve(plan.handle, _ptr(w, plan.dtype, "w"), float(Uinf), float(Vinf),
+                                                  _ptr(uv, plan.dtype, "uv")), "pf_velocity_solve", plan.handle)
+    return uv
+
+
+def pf_interpolate(plan, uv, Xq, Yq, uq=None, vq=None):
+    n = Xq.numel()
+    uq = torch.empty(n, dtype=plan.dtype, device="cuda") if uq is None else uq
+    vq = torch.empty(n, dtype=plan.dtype, device="cuda") if vq is None else vq
+    _native.check(_native.lib().pf_interpolate(plan.handle, _ptr(uv, plan.dtype, "uv"), _ptr(Xq, torch.float64, "Xq"),
+                                               _ptr(Yq, torch.float64, "Yq"), n, _ptr(uq, plan.dtype, "uq"),
+                                               _ptr(vq, plan.dtype, "vq")), "pf_interpolate", plan.handle)
+    return uq, vq
+
+
+def pf_vic_velocity(plan, X, Y, G, Uinf=0.0, Vinf=0.0, uq=None, vq=None):
+    n = X.numel()
+    uq = torch.empty(n, dtype=plan.dtype, device="cuda") if uq is None else uq
+    vq = torch.empty(n, dtype=plan.dtype, device="cuda") if vq is None else vq
+    _native.check(_native.lib().pf_vic_velocity(plan.handle, _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
+                                                _ptr(G, torch.float64, "G"), n, float(Uinf), float(Vinf),
+                                                _ptr(uq, plan.dtype, "uq"), _ptr(vq, plan.dtype, "vq")),
+                  "pf_vic_velocity", plan.handle)
+    return uq, vq
+
+
+def pf_vic_velocity_host(plan, X, Y, G, Uinf=0.0, Vinf=0.0, uq=None, vq=None):
+    """Host-buffer variant: X, Y, G, uq, vq are CPU tensors (pinned recommended)."""
+    n = X.numel()
+    for t, nm in ((X, "X"), (Y, "Y"), (G, "G")):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CPU float64 tensor" % nm)
+    uq = torch.empty(n, dtype=plan.dtype) if uq is None else uq
+    vq = torch.empty(n, dtype=plan.dtype) if vq is None else vq
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_vic_velocity_host(plan.handle, c(X.data_ptr()), c(Y.data_ptr()), c(G.data_ptr()), n,
+                                                     float(Uinf), float(Vinf), c(uq.data_ptr()), c(vq.data_ptr())),
+                  "pf_vic_velocity_host", plan.handle)
+    return uq, vq
+
+
+def pf_timing_enable(plan, on=True):
+    _native.check(_native.lib().pf_timing_enable(plan.handle, 1 if on else 0), "pf_timing_enable", plan.handle)
+
+
+def pf_timing_report(plan):
+    """Per-kernel CUDA-event times since timing was enabled: {name: (launches, total_ms)}."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _native.check(_native.lib().pf_timing_report(plan.handle, buf, len(buf)), "pf_timing_report", plan.handle)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out

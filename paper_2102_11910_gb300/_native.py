@@ -1,0 +1,86 @@
+"""ctypes loader of the gridpf C-ABI library (libgridpf.so).
+
+There is no fallback: if the library is missing or fails to load, every call
+raises.  Build it with ``paper_2102_11910_gb300.build.build()``.
+"""
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+_LIB = None
+
+# C signatures of the entry points declared in include/gridpf.h
+_c = ctypes
+_P = _c.c_void_p
+_D = _c.c_double
+_I64 = _c.c_int64
+_I32 = _c.c_int32
+SIGNATURES = {
+    "pf_plan_create": (_c.c_int, [_P, _P, _c.POINTER(_P)]),
+    "pf_plan_destroy": (_c.c_int, [_P]),
+    "pf_plan_fft_size": (_c.c_int, [_P, _c.POINTER(_I32), _c.POINTER(_I32)]),
+    "pf_lgf_table": (_c.c_int, [_P, _P]),
+    "pf_sync": (_c.c_int, [_P, _c.POINTER(_I64)]),
+    "pf_last_error": (_c.c_char_p, [_P]),
+    "pf_timing_enable": (_c.c_int, [_P, _I32]),
+    "pf_timing_report": (_c.c_int, [_P, _c.c_char_p, _I64]),
+    "pf_regularize": (_c.c_int, [_P, _P, _P, _P, _I64, _P]),
+    "pf_poisson_solve": (_c.c_int, [_P, _P, _P]),
+    "pf_velocity_solve": (_c.c_int, [_P, _P, _D, _D, _P]),
+    "pf_interpolate": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "pf_vic_velocity": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
+    "pf_vic_velocity_host": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
+}
+
+STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",
+          5: "PF_ERR_SINGULAR", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_NOT_FACTORED", 8: "PF_ERR_CAPACITY"}
+
+
+class GridPfError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__("%s returned %s%s" % (where, self.name, (": " + detail) if detail else ""))
+
+
+class PfGridDesc(ctypes.Structure):
+    _fields_ = [("nx", _I32), ("ny", _I32), ("dx", _D), ("x0", _D), ("y0", _D), ("precision", _I32)]
+
+
+def header_path():
+    return os.path.join(_build.ROOT, "include", "gridpf.h")
+
+
+def declared_functions():
+    """Names of the functions declared in include/gridpf.h."""
+    txt = open(header_path()).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(pf_[a-z0-9_]+)\s*\(", txt, flags=re.M)))
+
+
+def lib():
+    """Load (building first if needed) and return the ctypes library."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        try:
+            L = ctypes.CDLL(path)
+        except OSError as e:
+            raise RuntimeError("gridpf CUDA library could not be loaded from %s: %s" % (path, e))
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status, where, plan=None):
+    if status != 0:
+        detail = ""
+        if plan is not None:
+            msg = lib().pf_last_error(plan)
+            detail = msg.decode() if msg else ""
+        raise GridPfError(status, where, detail)

@@ -1,0 +1,280 @@
+// C-ABI entry points of gridpf (declared in include/gridpf.h).
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+void free_plan(pf_plan p) {
+    for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
+    void* ptrs[] = {p->G, p->H64, p->H32, p->sx64, p->sy64, p->sx32, p->sy32, p->twP64, p->twQ64, p->twP32, p->twQ32,
+                    p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->tile_cursor, p->tile_shift,
+                    p->tile_gmax, p->recs, p->stage, p->stage_out, p->d_status, p->d_oob};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+template <typename C>
+void twiddles(std::vector<C>& v, int N) {
+    v.resize(N);
+    for (int m = 0; m < N; ++m) {
+        // exp(-2 pi i m / N) with exact values at the quarter points
+        double c, s;
+        if (m == 0) { c = 1; s = 0; }
+        else if (4 * m == N) { c = 0; s = -1; }
+        else if (2 * m == N) { c = -1; s = 0; }
+        else if (4 * m == 3 * N) { c = 0; s = 1; }
+        else { c = cos(2.0 * M_PI * m / N); s = -sin(2.0 * M_PI * m / N); }
+        v[m].x = (decltype(v[m].x))c;
+        v[m].y = (decltype(v[m].y))s;
+    }
+}
+
+// sin(2 pi k / N) / dx with exact zeros at k = 0, N/2 and exact +-1 at N/4, 3N/4
+double sin_table(int k, int N, double dx) {
+    if (k == 0 || 2 * k == N) return 0.0;
+    if (4 * k == N) return 1.0 / dx;
+    if (4 * k == 3 * N) return -1.0 / dx;
+    return sin(2.0 * M_PI * k / N) / dx;
+}
+
+template <typename T>
+pf_status upload(pf_plan p, T** dst, const std::vector<T>& src) {
+    PF_CUDA(p, cudaMalloc(dst, src.size() * sizeof(T)));
+    PF_CUDA(p, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+#define PF_TRY(x)                          \
+    do {                                   \
+        pf_status s_ = (x);                \
+        if (s_ != PF_OK) return s_;        \
+    } while (0)
+
+pf_status plan_init(pf_plan p) {
+    const int nx = p->nx, ny = p->ny, P = p->P, Q = p->Q;
+    PF_CUDA(p, cudaMalloc(&p->G, (size_t)(nx + 1) * (ny + 1) * sizeof(double)));
+    const size_t hq = (size_t)(P / 2 + 1) * (Q / 2 + 1);
+    PF_CUDA(p, cudaMalloc(&p->H64, hq * sizeof(double)));
+    PF_CUDA(p, cudaMalloc(&p->H32, hq * sizeof(float)));
+    std::vector<double> sx(P / 2 + 1), sy(Q);
+    for (int k = 0; k <= P / 2; ++k) sx[k] = sin_table(k, P, p->dx);
+    for (int l = 0; l < Q; ++l) sy[l] = sin_table(l, Q, p->dx);
+    std::vector<float> sxf(sx.begin(), sx.end()), syf(sy.begin(), sy.end());
+    PF_TRY(upload(p, &p->sx64, sx));
+    PF_TRY(upload(p, &p->sy64, sy));
+    PF_TRY(upload(p, &p->sx32, sxf));
+    PF_TRY(upload(p, &p->sy32, syf));
+    std::vector<double2> tpd, tqd;
+    std::vector<float2> tpf, tqf;
+    twiddles(tpd, P); twiddles(tqd, Q); twiddles(tpf, P); twiddles(tqf, Q);
+    PF_TRY(upload(p, &p->twP64, tpd));
+    PF_TRY(upload(p, &p->twQ64, tqd));
+    PF_TRY(upload(p, &p->twP32, tpf));
+    PF_TRY(upload(p, &p->twQ32, tqf));
+    p->esz = p->prec == PF_FP64 ? 8 : 4;
+    const size_t spec = (size_t)(P / 2 + 1) * ny * 2 * p->esz;
+    PF_CUDA(p, cudaMalloc(&p->T1, spec));
+    PF_CUDA(p, cudaMalloc(&p->T2a, spec));
+    PF_CUDA(p, cudaMalloc(&p->T2b, spec));
+    PF_CUDA(p, cudaMalloc(&p->w, (size_t)nx * ny * p->esz));
+    PF_CUDA(p, cudaMalloc(&p->uv, (size_t)2 * nx * ny * p->esz));
+    p->ntx = ceil_div(nx, BIN_TILE);
+    p->nty = ceil_div(ny, BIN_TILE);
+    p->ntiles = p->ntx * p->nty;
+    PF_CUDA(p, cudaMalloc(&p->tile_count, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->tile_cursor, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->tile_shift, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->tile_gmax, p->ntiles * sizeof(unsigned long long)));
+    PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
+    PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    PF_CUDA(p, cudaMemset(p->d_oob, 0, sizeof(unsigned long long)));
+    return lgf_build(p);
+}
+
+}  // namespace
+
+cudaEvent_t tm_event(pf_plan p) {
+    if (!p->tm.pool.empty()) {
+        cudaEvent_t e = p->tm.pool.back();
+        p->tm.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+extern "C" {
+
+pf_status pf_plan_create(const pf_grid_desc* d, void* stream, pf_plan* out) {
+    if (!d || !out) return PF_ERR_ARG;
+    *out = nullptr;
+    if (d->nx < 8 || d->ny < 8 || d->nx > 2048 || d->ny > 2048 || !(d->dx > 0) || !isfinite(d->x0) ||
+        !isfinite(d->y0) || (d->precision != PF_FP64 && d->precision != PF_MIXED))
+        return PF_ERR_ARG;
+    pf_plan p = new (std::nothrow) pf_plan_s();
+    if (!p) return PF_ERR_OOM;
+    p->nx = d->nx; p->ny = d->ny; p->dx = d->dx; p->x0 = d->x0; p->y0 = d->y0; p->prec = d->precision;
+    p->P = next_pow2(2 * d->nx);
+    p->Q = next_pow2(2 * d->ny);
+    p->stream = (cudaStream_t)stream;
+    pf_status s = plan_init(p);
+    if (s != PF_OK) {
+        free_plan(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return PF_OK;
+}
+
+pf_status pf_plan_destroy(pf_plan p) {
+    if (!p) return PF_ERR_ARG;
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+    delete p;
+    return PF_OK;
+}
+
+pf_status pf_plan_fft_size(pf_plan p, int32_t* P, int32_t* Q) {
+    if (!p || !P || !Q) return PF_ERR_ARG;
+    *P = p->P;
+    *Q = p->Q;
+    return PF_OK;
+}
+
+pf_status pf_lgf_table(pf_plan p, double* host_out) {
+    if (!p || !host_out) return PF_ERR_ARG;
+    PF_CUDA(p, cudaMemcpyAsync(host_out, p->G, (size_t)(p->nx + 1) * (p->ny + 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    return PF_OK;
+}
+
+pf_status pf_sync(pf_plan p, int64_t* out_of_domain) {
+    if (!p) return PF_ERR_ARG;
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    int st = 0;
+    unsigned long long oob = 0;
+    PF_CUDA(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    PF_CUDA(p, cudaMemcpy(&oob, p->d_oob, sizeof(oob), cudaMemcpyDeviceToHost));
+    PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    PF_CUDA(p, cudaMemset(p->d_oob, 0, sizeof(unsigned long long)));
+    if (out_of_domain) *out_of_domain = (int64_t)oob;
+    if (st & ST_TIMEOUT) return PF_ERR_TIMEOUT;
+    if (st & ST_SINGULAR) return PF_ERR_SINGULAR;
+    if (st & ST_CAPACITY) return PF_ERR_CAPACITY;
+    if (st & ST_OUT_OF_DOMAIN) return PF_ERR_OUT_OF_DOMAIN;
+    return PF_OK;
+}
+
+const char* pf_last_error(pf_plan p) { return p ? p->err : "null plan"; }
+
+pf_status pf_timing_enable(pf_plan p, int32_t on) {
+    if (!p) return PF_ERR_ARG;
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    for (cudaEvent_t e : p->tm.ev) p->tm.pool.push_back(e);
+    p->tm.ev.clear();
+    p->tm.names.clear();
+    p->tm.on = on != 0;
+    return PF_OK;
+}
+
+pf_status pf_timing_report(pf_plan p, char* buf, int64_t buflen) {
+    if (!p || !buf || buflen <= 0) return PF_ERR_ARG;
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    std::vector<const char*> names;
+    std::vector<double> ms;
+    std::vector<int64_t> cnt;
+    for (size_t i = 0; i < p->tm.names.size(); ++i) {
+        float t = 0.f;
+        PF_CUDA(p, cudaEventElapsedTime(&t, p->tm.ev[2 * i], p->tm.ev[2 * i + 1]));
+        size_t k = 0;
+        while (k < names.size() && strcmp(names[k], p->tm.names[i]) != 0) ++k;
+        if (k == names.size()) { names.push_back(p->tm.names[i]); ms.push_back(0.0); cnt.push_back(0); }
+        ms[k] += t;
+        cnt[k] += 1;
+    }
+    int64_t off = 0;
+    buf[0] = 0;
+    for (size_t k = 0; k < names.size() && off < buflen - 1; ++k)
+        off += snprintf(buf + off, (size_t)(buflen - off), "%s %lld %.6f\n", names[k], (long long)cnt[k], ms[k]);
+    for (cudaEvent_t e : p->tm.ev) p->tm.pool.push_back(e);
+    p->tm.ev.clear();
+    p->tm.names.clear();
+    return PF_OK;
+}
+
+pf_status pf_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w) {
+    if (!p || !w || nv < 0 || (nv > 0 && (!X || !Y || !G))) return PF_ERR_ARG;
+    return vortex_regularize(p, X, Y, G, nv, w);
+}
+
+pf_status pf_poisson_solve(pf_plan p, const void* w, void* psi) {
+    if (!p || !w || !psi) return PF_ERR_ARG;
+    return conv_solve(p, w, psi, CONV_PSI, 0.0, 0.0);
+}
+
+pf_status pf_velocity_solve(pf_plan p, const void* w, double Uinf, double Vinf, void* uv) {
+    if (!p || !w || !uv) return PF_ERR_ARG;
+    return conv_solve(p, w, uv, CONV_UV, Uinf, Vinf);
+}
+
+pf_status pf_interpolate(pf_plan p, const void* uv, const double* Xq, const double* Yq, int64_t nq, void* uq, void* vq) {
+    if (!p || !uv || nq < 0 || (nq > 0 && (!Xq || !Yq || !uq || !vq))) return PF_ERR_ARG;
+    return vortex_interpolate(p, uv, Xq, Yq, nq, uq, vq);
+}
+
+pf_status pf_vic_velocity(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,
+                          double Vinf, void* uq, void* vq) {
+    if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
+    PF_TRY(vortex_regularize(p, X, Y, G, nv, p->w));
+    PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
+    return vortex_interpolate(p, p->uv, X, Y, nv, uq, vq);
+}
+
+pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,
+                               double Vinf, void* uq, void* vq) {
+    if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
+    if (nv == 0) return PF_OK;
+    if (nv > p->stage_cap) {
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        if (p->stage) cudaFree(p->stage);
+        if (p->stage_out) cudaFree(p->stage_out);
+        p->stage = nullptr;
+        p->stage_out = nullptr;
+        p->stage_cap = 0;
+        PF_CUDA(p, cudaMalloc(&p->stage, (size_t)3 * nv * sizeof(double)));
+        PF_CUDA(p, cudaMalloc(&p->stage_out, (size_t)2 * nv * p->esz));
+        p->stage_cap = nv;
+    }
+    double* dX = p->stage;
+    double* dY = dX + nv;
+    double* dG = dY + nv;
+    char* du = (char*)p->stage_out;
+    char* dv = du + (size_t)nv * p->esz;
+    PF_CUDA(p, cudaMemcpyAsync(dX, X, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(dY, Y, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(dG, G, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_TRY(pf_vic_velocity(p, dX, dY, dG, nv, Uinf, Vinf, du, dv));
+    PF_CUDA(p, cudaMemcpyAsync(uq, du, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(vq, dv, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    return PF_OK;
+}
+
+}  // extern "C"

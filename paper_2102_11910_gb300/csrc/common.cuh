@@ -1,0 +1,137 @@
+// Shared device/host definitions of the gridpf library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "gridpf.h"
+
+// ------------------------------------------------------------ complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using C_t = typename cplx<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C::x) r, decltype(C::x) i) { C c; c.x = r; c.y = i; return c; }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
+// multiply by +i / -i
+template <typename C> __host__ __device__ __forceinline__ C mul_i(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+template <typename C> __host__ __device__ __forceinline__ C mul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+
+// ------------------------------------------------------------ status bits
+enum : int {
+    ST_OUT_OF_DOMAIN = 1,
+    ST_TIMEOUT = 2,
+    ST_SINGULAR = 4,
+    ST_CAPACITY = 8,
+};
+
+// ------------------------------------------------------------ kernel timing
+// Optional per-kernel CUDA-event timing on the plan's stream (off by default).
+struct KTiming {
+    bool on = false;
+    std::vector<const char*> names;
+    std::vector<cudaEvent_t> ev;      // pairs: ev[2i] before, ev[2i+1] after launch i
+    std::vector<cudaEvent_t> pool;
+};
+
+// ------------------------------------------------------------ plan
+constexpr int BIN_TILE = 32;   // node tile edge used by binning and regularization
+
+struct pf_plan_s {
+    int nx = 0, ny = 0, P = 0, Q = 0, prec = PF_FP64;
+    double dx = 0, x0 = 0, y0 = 0;
+    cudaStream_t stream = nullptr;
+    // LGF and spectrum
+    double* G = nullptr;           // (nx+1)*(ny+1), index n*(nx+1)+m
+    double* H64 = nullptr;         // (P/2+1)*(Q/2+1): -dx^2 Ghat(k,l)/(P Q), index k*(Q/2+1)+l
+    float* H32 = nullptr;
+    double* sx64 = nullptr;        // sin(2 pi k / P)/dx, k in [0, P/2]
+    double* sy64 = nullptr;        // sin(2 pi l / Q)/dx, l in [0, Q)
+    float* sx32 = nullptr;
+    float* sy32 = nullptr;
+    double2* twP64 = nullptr;      // exp(-2 pi i m / P), m in [0, P)
+    double2* twQ64 = nullptr;
+    float2* twP32 = nullptr;
+    float2* twQ32 = nullptr;
+    // grid work buffers (element size depends on precision)
+    size_t esz = 8;
+    void* T1 = nullptr;            // (P/2+1)*ny complex: row spectra, column-major in k
+    void* T2a = nullptr;
+    void* T2b = nullptr;
+    void* w = nullptr;             // nx*ny real
+    void* uv = nullptr;            // 2*nx*ny real
+    // binning
+    int ntx = 0, nty = 0, ntiles = 0;
+    int* tile_count = nullptr;
+    int* tile_start = nullptr;
+    int* tile_cursor = nullptr;
+    int* tile_shift = nullptr;
+    unsigned long long* tile_gmax = nullptr;
+    void* recs = nullptr;
+    int64_t rec_cap = 0;
+    // host-input staging for the *_host entry points
+    double* stage = nullptr;
+    int64_t stage_cap = 0;
+    void* stage_out = nullptr;
+    // status
+    int* d_status = nullptr;
+    unsigned long long* d_oob = nullptr;
+    KTiming tm;
+    char err[512] = {0};
+};
+
+cudaEvent_t tm_event(pf_plan p);   // api.cu
+
+// Launch a kernel; when timing is on, bracket it with events on the plan stream.
+#define PF_KERNEL(p, name, ...)                                                   \
+    do {                                                                          \
+        cudaEvent_t a_ = nullptr;                                                 \
+        if ((p)->tm.on) {                                                         \
+            a_ = tm_event(p);                                                     \
+            cudaEventRecord(a_, (p)->stream);                                     \
+        }                                                                         \
+        __VA_ARGS__;                                                              \
+        PF_LAUNCH_CHECK(p);                                                       \
+        if ((p)->tm.on) {                                                         \
+            cudaEvent_t b_ = tm_event(p);                                         \
+            cudaEventRecord(b_, (p)->stream);                                     \
+            (p)->tm.names.push_back(name);                                        \
+            (p)->tm.ev.push_back(a_);                                             \
+            (p)->tm.ev.push_back(b_);                                             \
+        }                                                                         \
+    } while (0)
+
+#define PF_CUDA(plan, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (plan) snprintf((plan)->err, sizeof((plan)->err), "%s:%d %s: %s", __FILE__,    \
+                               __LINE__, #call, cudaGetErrorString(e_));                      \
+            return e_ == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;                \
+        }                                                                                     \
+    } while (0)
+
+#define PF_LAUNCH_CHECK(plan) PF_CUDA(plan, cudaGetLastError())
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ internal entry points
+// (defined in the .cu files, used by api.cu)
+pf_status lgf_build(pf_plan p);                                  // lgf.cu
+pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf);  // fft.cu
+enum { CONV_PSI = 0, CONV_UV = 1 };
+pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w);  // transfer.cu
+pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq);

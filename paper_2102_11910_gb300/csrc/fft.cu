@@ -1,0 +1,196 @@
+// Unbounded Poisson solve psi = -L^{-1} w by zero-padded FFT convolution with
+// the real, even LGF spectrum (Sec. 2.1), and the spectral node velocity.
+//
+// Layout of the three passes (w real, ny rows of nx nodes; torus P x Q):
+//   1. rows:    two real rows j, j+1 packed as one complex row, length-P FFT,
+//               split into the two half spectra A_j(k), k in [0, P/2];
+//               stored column-major T1[k*ny + j] so pass 2 reads contiguously.
+//   2. columns: for each k, length-Q FFT of T1[k, 0..ny) (zero padded),
+//               multiply by H(k,l) = -dx^2 Ghat(k,l)/(PQ) (and by the centred
+//               difference symbols i sin(2 pi l/Q)/dx, -i sin(2 pi k/P)/dx for
+//               velocity), inverse FFT, keep rows [0, ny).
+//   3. rows:    rebuild full Hermitian rows from the half spectra of two real
+//               outputs (psi_j + i psi_{j+1}, or u_j + i v_j), inverse FFT,
+//               keep nodes [0, nx).
+#include "fft.cuh"
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx, int ny,
+                                                  int P, const C_t<T>* __restrict__ tw) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + P;
+    const int j0 = 2 * blockIdx.x;
+    const bool has2 = (j0 + 1) < ny;
+    for (int n = threadIdx.x; n < P; n += blockDim.x) {
+        T a = 0, b = 0;
+        if (n < nx) {
+            a = w[(size_t)j0 * nx + n];
+            if (has2) b = w[(size_t)(j0 + 1) * nx + n];
+        }
+        A[n] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    C* Z = block_fft<C, false>(A, B, P, tw);
+    for (int k = threadIdx.x; k <= P / 2; k += blockDim.x) {
+        const C z1 = Z[k], z2 = conjc(Z[(P - k) & (P - 1)]);
+        T1[(size_t)k * ny + j0] = (z1 + z2) * T(0.5);
+        if (has2) T1[(size_t)k * ny + j0 + 1] = mul_mi(z1 - z2) * T(0.5);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cols(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
+                                              C_t<T>* __restrict__ T2b, int ny, int Q, int mode,
+                                              const T* __restrict__ H, int Hld, const T* __restrict__ sx,
+                                              const T* __restrict__ sy, const C_t<T>* __restrict__ tw) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + Q;
+    C* D = B + Q;
+    const int k = blockIdx.x;
+    for (int l = threadIdx.x; l < Q; l += blockDim.x)
+        A[l] = l < ny ? T1[(size_t)k * ny + l] : cmake<C>(T(0), T(0));
+    __syncthreads();
+    C* Z = block_fft<C, false>(A, B, Q, tw);
+    C* other = (Z == A) ? B : A;
+    const T* Hk = H + (size_t)k * Hld;
+    for (int l = threadIdx.x; l < Q; l += blockDim.x) {
+        const C psi = Z[l] * Hk[l <= Q / 2 ? l : Q - l];
+        Z[l] = psi;
+        if (mode == CONV_UV) D[l] = mul_i(psi) * sy[l];
+    }
+    __syncthreads();
+    if (mode == CONV_UV) {
+        C* U = block_fft<C, true>(D, other, Q, tw);
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = U[j];
+        __syncthreads();
+        C* scratch = (U == D) ? other : D;
+        C* V = block_fft<C, true>(Z, scratch, Q, tw);
+        const T c = sx[k];
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2b[(size_t)k * ny + j] = mul_mi(V[j]) * c;
+    } else {
+        C* R = block_fft<C, true>(Z, other, Q, tw);
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = R[j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_inv(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
+                                                  T* __restrict__ out, int nx, int ny, int P, int mode, T Uinf,
+                                                  T Vinf, const C_t<T>* __restrict__ tw) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + P;
+    int ja, jb;
+    const C_t<T>* Sb;
+    bool has_b = true;
+    if (mode == CONV_UV) {
+        ja = jb = blockIdx.x;
+        Sb = T2b;
+    } else {
+        ja = 2 * blockIdx.x;
+        jb = ja + 1;
+        has_b = jb < ny;
+        Sb = T2a;
+    }
+    const int h = P / 2;
+    for (int k = threadIdx.x; k <= h; k += blockDim.x) {
+        C a = T2a[(size_t)k * ny + ja];
+        C b = has_b ? Sb[(size_t)k * ny + jb] : cmake<C>(T(0), T(0));
+        if (k == 0 || k == h) { a.y = 0; b.y = 0; }
+        A[k] = a + mul_i(b);
+        if (k > 0 && k < h) A[P - k] = conjc(a) + mul_i(conjc(b));
+    }
+    __syncthreads();
+    C* Z = block_fft<C, true>(A, B, P, tw);
+    if (mode == CONV_UV) {
+        T* o = out + (size_t)2 * ja * nx;
+        for (int n = threadIdx.x; n < nx; n += blockDim.x) {
+            o[2 * n] = Z[n].x + Uinf;
+            o[2 * n + 1] = Z[n].y + Vinf;
+        }
+    } else {
+        for (int n = threadIdx.x; n < nx; n += blockDim.x) {
+            out[(size_t)ja * nx + n] = Z[n].x;
+            if (has_b) out[(size_t)jb * nx + n] = Z[n].y;
+        }
+    }
+}
+
+// generic in-place complex FFTs of a row-major (rows x len) array, used once per
+// plan to transform the LGF torus
+template <typename C>
+__global__ void __launch_bounds__(256) k_fft_rows_inplace(C* data, int len, const C* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + len;
+    C* row = data + (size_t)blockIdx.x * len;
+    for (int n = threadIdx.x; n < len; n += blockDim.x) A[n] = row[n];
+    __syncthreads();
+    C* Z = block_fft<C, false>(A, B, len, tw);
+    for (int n = threadIdx.x; n < len; n += blockDim.x) row[n] = Z[n];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_fft_cols_inplace(C* data, int width, int len, const C* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + len;
+    const int c = blockIdx.x;
+    for (int n = threadIdx.x; n < len; n += blockDim.x) A[n] = data[(size_t)n * width + c];
+    __syncthreads();
+    C* Z = block_fft<C, false>(A, B, len, tw);
+    for (int n = threadIdx.x; n < len; n += blockDim.x) data[(size_t)n * width + c] = Z[n];
+}
+
+// raise a kernel's dynamic shared-memory limit once per size (the attribute is per function)
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    static size_t done = 0;
+    if (bytes <= done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+
+pf_status fft2d_inplace_f64(pf_plan p, double2* data) {
+    const size_t sr = 2 * (size_t)p->P * sizeof(double2), sc = 2 * (size_t)p->Q * sizeof(double2);
+    PF_CUDA(p, set_smem(k_fft_rows_inplace<double2>, sr));
+    PF_CUDA(p, set_smem(k_fft_cols_inplace<double2>, sc));
+    k_fft_rows_inplace<double2><<<p->Q, 256, sr, p->stream>>>(data, p->P, p->twP64);
+    PF_LAUNCH_CHECK(p);
+    k_fft_cols_inplace<double2><<<p->P, 256, sc, p->stream>>>(data, p->P, p->Q, p->twQ64);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
+template <typename T>
+static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* sx,
+                              const T* sy, const C_t<T>* twP, const C_t<T>* twQ) {
+    using C = C_t<T>;
+    const int P = p->P, Q = p->Q, nx = p->nx, ny = p->ny;
+    const size_t sr = 2 * (size_t)P * sizeof(C), sc = 3 * (size_t)Q * sizeof(C);
+    PF_CUDA(p, set_smem(k_rows_fwd<T>, sr));
+    PF_CUDA(p, set_smem(k_cols<T>, sc));
+    PF_CUDA(p, set_smem(k_rows_inv<T>, sr));
+    C* T1 = reinterpret_cast<C*>(p->T1);
+    C* T2a = reinterpret_cast<C*>(p->T2a);
+    C* T2b = reinterpret_cast<C*>(p->T2b);
+    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, 256, sr, p->stream>>>(w, T1, nx, ny, P, twP));
+    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Q / 2 + 1, sx, sy, twQ));
+    const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
+    PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, 256, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
+    return PF_OK;
+}
+
+pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf) {
+    if (p->prec == PF_FP64)
+        return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->sx64, p->sy64,
+                                    p->twP64, p->twQ64);
+    return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->sx32,
+                               p->sy32, p->twP32, p->twQ32);
+}

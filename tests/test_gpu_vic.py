@@ -1,0 +1,183 @@
+"""GPU parity of the body-free VIC path (Sec. 2.1) against the FP64 oracle.
+
+Tolerances: the all-FP64 path must match the oracle to 1e-12 relative (L2)
+and the mixed FP32 path to 1e-5 relative in streamfunction and velocity.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2102_11910_gb300 as pf
+from oracle import vic as OV
+from oracle.lgf import lgf_table
+from paper_2102_11910_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {pf.PF_FP64: 1e-12, pf.PF_MIXED: 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _case(nx, ny, nv, seed, variance=1e-2):
+    g = inputs.centred_grid(nx, ny, 2.0 / (nx - 1))
+    rng = np.random.default_rng(seed)
+    hx, hy = 0.5 * (nx - 1) * g.dx, 0.5 * (ny - 1) * g.dx
+    X, Y, G = inputs.uniform_vortices(rng, nv, -0.8 * hx, 0.8 * hx, variance, -0.8 * hy, 0.8 * hy)
+    return g, X, Y, G
+
+
+def _plan(g, prec):
+    return pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _og(g):
+    return OV.Grid(g.nx, g.ny, g.dx, g.x0, g.y0)
+
+
+@pytest.mark.parametrize("nx,ny", [(1024, 1024), (100, 77), (768, 512)])
+def test_lgf_table_matches_oracle(nx, ny):
+    g = inputs.centred_grid(nx, ny, 0.01)
+    plan = _plan(g, pf.PF_FP64)
+    T = pf.pf_lgf_table(plan)              # [n, m]
+    ref = lgf_table(nx, ny).T              # oracle [m, n] -> [n, m]
+    assert np.abs(T - ref).max() < 2e-14
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("nx,ny,nv", [(64, 64, 300), (100, 77, 500), (37, 45, 40)])
+def test_regularize(prec, nx, ny, nv):
+    g, X, Y, G = _case(nx, ny, nv, 11)
+    plan = _plan(g, prec)
+    w = pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    pf.pf_sync(plan)
+    ref = OV.regularize(_og(g), X, Y, G)
+    assert rel(w.cpu().numpy(), ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+    # integer accumulation: bitwise reproducible run to run
+    w2 = pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    assert torch.equal(w, w2)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45), (128, 48)])
+def test_poisson_solve(prec, nx, ny):
+    g, X, Y, G = _case(nx, ny, 200, 12)
+    og = _og(g)
+    w = OV.regularize(og, X, Y, G)
+    plan = _plan(g, prec)
+    wt = torch.from_numpy(w).to(device="cuda", dtype=plan.dtype)
+    psi = pf.pf_poisson_solve(plan, wt)
+    pf.pf_sync(plan)
+    ref = OV.streamfunction(og, w, lgf_table(nx + 1, ny + 1))
+    assert rel(psi.cpu().numpy(), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45)])
+def test_velocity_solve(prec, nx, ny):
+    g, X, Y, G = _case(nx, ny, 200, 13)
+    og = _og(g)
+    w = OV.regularize(og, X, Y, G)
+    plan = _plan(g, prec)
+    wt = torch.from_numpy(w).to(device="cuda", dtype=plan.dtype)
+    uv = pf.pf_velocity_solve(plan, wt, 0.7, -0.3).cpu().numpy()
+    pf.pf_sync(plan)
+    psi1 = OV.streamfunction(og, w, lgf_table(nx + 1, ny + 1), pad=1)
+    u, v = OV.node_velocity(og, psi1, 0.7, -0.3)
+    assert rel(uv[..., 0], u) < TOL[prec]
+    assert rel(uv[..., 1], v) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_interpolate(prec):
+    g, X, Y, G = _case(80, 70, 1000, 14)
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=(g.ny, g.nx, 2))
+    plan = _plan(g, prec)
+    uq, vq = pf.pf_interpolate(plan, torch.from_numpy(f).to(device="cuda", dtype=plan.dtype).contiguous(), _dev(X), _dev(Y))
+    pf.pf_sync(plan)
+    og = _og(g)
+    assert rel(uq.cpu().numpy(), OV.interpolate(og, f[..., 0], X, Y)) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+    assert rel(vq.cpu().numpy(), OV.interpolate(og, f[..., 1], X, Y)) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("n,nv", [(64, 400), (128, 3000), (96, 0)])
+def test_vic_velocity_end_to_end(prec, n, nv):
+    g, X, Y, G = _case(n, n, nv, 15, variance=1e-4)
+    plan = _plan(g, prec)
+    uq, vq = pf.pf_vic_velocity(plan, _dev(X), _dev(Y), _dev(G), 0.25, 0.0)
+    pf.pf_sync(plan)
+    if nv == 0:
+        assert uq.numel() == 0
+        return
+    _, _, ru, rv = OV.vortex_velocity(_og(g), X, Y, G, 0.25, 0.0)
+    assert rel(uq.cpu().numpy(), ru) < TOL[prec]
+    assert rel(vq.cpu().numpy(), rv) < TOL[prec]
+    # host-buffer entry point gives the same numbers
+    hu, hv = pf.pf_vic_velocity_host(plan, torch.from_numpy(X), torch.from_numpy(Y), torch.from_numpy(G), 0.25, 0.0)
+    assert torch.equal(hu, uq.cpu()) and torch.equal(hv, vq.cpu())
+
+
+def test_out_of_domain_is_reported_not_dropped_silently():
+    g, X, Y, G = _case(64, 64, 100, 16)
+    X = X.copy()
+    X[5] = g.x0 + 0.5 * g.dx          # stencil would leave the grid
+    X[7] = g.x0 + 62.9 * g.dx
+    plan = _plan(g, pf.PF_MIXED)
+    pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_sync(plan)
+    assert e.value.name == "PF_ERR_OUT_OF_DOMAIN" and "2 points" in str(e.value)
+    assert pf.pf_sync(plan) == 0       # the status is cleared once reported
+
+
+def test_full_size_vic_sampled_against_oracle():
+    """1024^2 nodes, 1e6 vortices: w on every node, and psi / velocity at sampled
+    nodes and vortices computed one by one by the oracle's direct sums."""
+    wl = inputs.vic_1024()
+    g = wl["grid"]
+    og = _og(g)
+    X, Y, G = wl["X"], wl["Y"], wl["G"]
+    w_ref = OV.regularize(og, X, Y, G)
+    tab = lgf_table(g.nx + 1, g.ny + 1)
+    rng = np.random.default_rng(5)
+    for prec in (pf.PF_FP64, pf.PF_MIXED):
+        plan = _plan(g, prec)
+        dX, dY, dG = _dev(X), _dev(Y), _dev(G)
+        w = pf.pf_regularize(plan, dX, dY, dG)
+        psi = pf.pf_poisson_solve(plan, w).cpu().numpy()
+        uq, vq = pf.pf_vic_velocity(plan, dX, dY, dG)
+        pf.pf_sync(plan)
+        assert rel(w.cpu().numpy(), w_ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+        # psi at sampled nodes (including the corners)
+        ti = np.concatenate([[0, g.nx - 1, 0, g.nx - 1], rng.integers(0, g.nx, 12)])
+        tj = np.concatenate([[0, 0, g.ny - 1, g.ny - 1], rng.integers(0, g.ny, 12)])
+        ref = -OV.inv_laplacian_at(og, w_ref, ti, tj, tab)
+        assert rel(psi[tj, ti], ref) < TOL[prec]
+        # velocity at sampled vortices: psi on the 6x6 node block around each stencil
+        qs = rng.integers(0, len(X), 6)
+        u_s, v_s = [], []
+        for q in qs:
+            ci = int(math.floor((X[q] - g.x0) / g.dx)); cj = int(math.floor((Y[q] - g.y0) / g.dx))
+            bi, bj = np.meshgrid(np.arange(ci - 2, ci + 4), np.arange(cj - 2, cj + 4))
+            blk = -OV.inv_laplacian_at(og, w_ref, bi.ravel(), bj.ravel(), tab).reshape(6, 6)
+            sub = OV.Grid(4, 4, g.dx, g.x0 + (ci - 1) * g.dx, g.y0 + (cj - 1) * g.dx)
+            u, v = OV.node_velocity(sub, blk)
+            big = OV.Grid(8, 8, g.dx, g.x0 + (ci - 3) * g.dx, g.y0 + (cj - 3) * g.dx)
+            U = np.zeros((8, 8)); V = np.zeros((8, 8))
+            U[2:6, 2:6] = u; V[2:6, 2:6] = v
+            u_s.append(OV.interpolate(big, U, X[q:q + 1], Y[q:q + 1])[0])
+            v_s.append(OV.interpolate(big, V, X[q:q + 1], Y[q:q + 1])[0])
+        got = np.concatenate([uq.cpu().numpy()[qs], vq.cpu().numpy()[qs]])
+        assert rel(got, np.concatenate([u_s, v_s])) < TOL[prec]
