@@ -101,6 +101,29 @@ def inv_laplacian_at(grid, src, ti, tj, table):
     return grid.dx ** 2 * out
 
 
+def node_velocity_at(grid, src, ti, tj, table, Uinf=0.0, Vinf=0.0):
+    """Node velocity of psi = -L^{-1} src at individual nodes, one by one.
+
+    Same centred differences as node_velocity (Eq. velsf), applied to the
+    kernel before the sum (the operators are linear):
+    u = -(dx/2) sum src (G(i-i', j+1-j') - G(i-i', j-1-j')),
+    v = +(dx/2) sum src (G(i+1-i', j-j') - G(i-1-i', j-j')).
+    Differencing the kernel avoids cancelling two large sums.
+    """
+    J, I = np.nonzero(src)
+    vals = src[J, I]
+    u = np.empty(len(ti))
+    v = np.empty(len(ti))
+    for k in range(len(ti)):
+        di = np.abs(ti[k] - I)
+        dy = table[di, np.abs(tj[k] + 1 - J)] - table[di, np.abs(tj[k] - 1 - J)]
+        dj = np.abs(tj[k] - J)
+        dxk = table[np.abs(ti[k] + 1 - I), dj] - table[np.abs(ti[k] - 1 - I), dj]
+        u[k] = -0.5 * grid.dx * np.dot(dy, vals) + Uinf
+        v[k] = 0.5 * grid.dx * np.dot(dxk, vals) + Vinf
+    return u, v
+
+
 def laplacian_unit(field):
     """L0 applied at interior nodes: s(i+1,j)+s(i-1,j)+s(i,j+1)+s(i,j-1)-4 s(i,j)."""
     f = field

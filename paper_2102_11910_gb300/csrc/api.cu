@@ -18,7 +18,7 @@ int next_pow2(int v) {
 void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
-    void* ptrs[] = {p->G, p->H64, p->H32, p->sx64, p->sy64, p->sx32, p->sy32, p->twP64, p->twQ64, p->twP32, p->twQ32,
+    void* ptrs[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32, p->twQ32,
                     p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->tile_cursor, p->tile_shift,
                     p->tile_gmax, p->recs, p->stage, p->stage_out, p->d_status, p->d_oob};
     for (void* q : ptrs)
@@ -41,14 +41,6 @@ void twiddles(std::vector<C>& v, int N) {
     }
 }
 
-// sin(2 pi k / N) / dx with exact zeros at k = 0, N/2 and exact +-1 at N/4, 3N/4
-double sin_table(int k, int N, double dx) {
-    if (k == 0 || 2 * k == N) return 0.0;
-    if (4 * k == N) return 1.0 / dx;
-    if (4 * k == 3 * N) return -1.0 / dx;
-    return sin(2.0 * M_PI * k / N) / dx;
-}
-
 template <typename T>
 pf_status upload(pf_plan p, T** dst, const std::vector<T>& src) {
     PF_CUDA(p, cudaMalloc(dst, src.size() * sizeof(T)));
@@ -66,16 +58,8 @@ pf_status plan_init(pf_plan p) {
     const int nx = p->nx, ny = p->ny, P = p->P, Q = p->Q;
     PF_CUDA(p, cudaMalloc(&p->G, (size_t)(nx + 1) * (ny + 1) * sizeof(double)));
     const size_t hq = (size_t)(P / 2 + 1) * (Q / 2 + 1);
-    PF_CUDA(p, cudaMalloc(&p->H64, hq * sizeof(double)));
-    PF_CUDA(p, cudaMalloc(&p->H32, hq * sizeof(float)));
-    std::vector<double> sx(P / 2 + 1), sy(Q);
-    for (int k = 0; k <= P / 2; ++k) sx[k] = sin_table(k, P, p->dx);
-    for (int l = 0; l < Q; ++l) sy[l] = sin_table(l, Q, p->dx);
-    std::vector<float> sxf(sx.begin(), sx.end()), syf(sy.begin(), sy.end());
-    PF_TRY(upload(p, &p->sx64, sx));
-    PF_TRY(upload(p, &p->sy64, sy));
-    PF_TRY(upload(p, &p->sx32, sxf));
-    PF_TRY(upload(p, &p->sy32, syf));
+    for (double** h : {&p->H64, &p->Hu64, &p->Hv64}) PF_CUDA(p, cudaMalloc(h, hq * sizeof(double)));
+    for (float** h : {&p->H32, &p->Hu32, &p->Hv32}) PF_CUDA(p, cudaMalloc(h, hq * sizeof(float)));
     std::vector<double2> tpd, tqd;
     std::vector<float2> tpf, tqf;
     twiddles(tpd, P); twiddles(tqd, Q); twiddles(tpf, P); twiddles(tqf, Q);

@@ -56,12 +56,14 @@ struct pf_plan_s {
     cudaStream_t stream = nullptr;
     // LGF and spectrum
     double* G = nullptr;           // (nx+1)*(ny+1), index n*(nx+1)+m
-    double* H64 = nullptr;         // (P/2+1)*(Q/2+1): -dx^2 Ghat(k,l)/(P Q), index k*(Q/2+1)+l
+    // spectra on the padded torus, quadrant k in [0, P/2], l in [0, Q/2], index k*(Q/2+1)+l,
+    // all divided by P*Q (the inverse FFTs are unnormalised):
+    double* H64 = nullptr;         // psi:  -dx^2 Ghat (real, even in k and l)
+    double* Hu64 = nullptr;        // u:    spectrum = i * Hu, Hu = -dx/2 Im(DyG^), odd in l
+    double* Hv64 = nullptr;        // v:    spectrum = i * Hv, Hv = +dx/2 Im(DxG^), odd in k
     float* H32 = nullptr;
-    double* sx64 = nullptr;        // sin(2 pi k / P)/dx, k in [0, P/2]
-    double* sy64 = nullptr;        // sin(2 pi l / Q)/dx, l in [0, Q)
-    float* sx32 = nullptr;
-    float* sy32 = nullptr;
+    float* Hu32 = nullptr;
+    float* Hv32 = nullptr;
     double2* twP64 = nullptr;      // exp(-2 pi i m / P), m in [0, P)
     double2* twQ64 = nullptr;
     float2* twP32 = nullptr;

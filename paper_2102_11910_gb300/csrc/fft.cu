@@ -6,9 +6,10 @@
 //               split into the two half spectra A_j(k), k in [0, P/2];
 //               stored column-major T1[k*ny + j] so pass 2 reads contiguously.
 //   2. columns: for each k, length-Q FFT of T1[k, 0..ny) (zero padded),
-//               multiply by H(k,l) = -dx^2 Ghat(k,l)/(PQ) (and by the centred
-//               difference symbols i sin(2 pi l/Q)/dx, -i sin(2 pi k/P)/dx for
-//               velocity), inverse FFT, keep rows [0, ny).
+//               multiply by the kernel spectrum (psi: -dx^2 Ghat/(PQ); for the
+//               node velocity the spectra of the centred-differenced LGF,
+//               u: -dx/2 D_y G, v: +dx/2 D_x G, which is exactly the central
+//               difference of psi), inverse FFT, keep rows [0, ny).
 //   3. rows:    rebuild full Hermitian rows from the half spectra of two real
 //               outputs (psi_j + i psi_{j+1}, or u_j + i v_j), inverse FFT,
 //               keep nodes [0, nx).
@@ -43,8 +44,8 @@ __global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T
 template <typename T>
 __global__ void __launch_bounds__(256) k_cols(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
                                               C_t<T>* __restrict__ T2b, int ny, int Q, int mode,
-                                              const T* __restrict__ H, int Hld, const T* __restrict__ sx,
-                                              const T* __restrict__ sy, const C_t<T>* __restrict__ tw) {
+                                              const T* __restrict__ H, const T* __restrict__ Hu,
+                                              const T* __restrict__ Hv, int Hld, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* A = reinterpret_cast<C*>(smem_raw);
@@ -56,22 +57,26 @@ __global__ void __launch_bounds__(256) k_cols(const C_t<T>* __restrict__ T1, C_t
     __syncthreads();
     C* Z = block_fft<C, false>(A, B, Q, tw);
     C* other = (Z == A) ? B : A;
-    const T* Hk = H + (size_t)k * Hld;
-    for (int l = threadIdx.x; l < Q; l += blockDim.x) {
-        const C psi = Z[l] * Hk[l <= Q / 2 ? l : Q - l];
-        Z[l] = psi;
-        if (mode == CONV_UV) D[l] = mul_i(psi) * sy[l];
-    }
-    __syncthreads();
+    const size_t row = (size_t)k * Hld;
     if (mode == CONV_UV) {
+        for (int l = threadIdx.x; l < Q; l += blockDim.x) {
+            const bool lo = l <= Q / 2;
+            const int lq = lo ? l : Q - l;
+            const C iw = mul_i(Z[l]);
+            const T hu = Hu[row + lq];
+            D[l] = iw * (lo ? hu : -hu);      // odd in l
+            Z[l] = iw * Hv[row + lq];         // even in l
+        }
+        __syncthreads();
         C* U = block_fft<C, true>(D, other, Q, tw);
         for (int j = threadIdx.x; j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = U[j];
         __syncthreads();
         C* scratch = (U == D) ? other : D;
         C* V = block_fft<C, true>(Z, scratch, Q, tw);
-        const T c = sx[k];
-        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2b[(size_t)k * ny + j] = mul_mi(V[j]) * c;
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2b[(size_t)k * ny + j] = V[j];
     } else {
+        for (int l = threadIdx.x; l < Q; l += blockDim.x) Z[l] = Z[l] * H[row + (l <= Q / 2 ? l : Q - l)];
+        __syncthreads();
         C* R = block_fft<C, true>(Z, other, Q, tw);
         for (int j = threadIdx.x; j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = R[j];
     }
@@ -169,8 +174,8 @@ pf_status fft2d_inplace_f64(pf_plan p, double2* data) {
 }
 
 template <typename T>
-static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* sx,
-                              const T* sy, const C_t<T>* twP, const C_t<T>* twQ) {
+static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
+                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ) {
     using C = C_t<T>;
     const int P = p->P, Q = p->Q, nx = p->nx, ny = p->ny;
     const size_t sr = 2 * (size_t)P * sizeof(C), sc = 3 * (size_t)Q * sizeof(C);
@@ -181,7 +186,7 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     C* T2a = reinterpret_cast<C*>(p->T2a);
     C* T2b = reinterpret_cast<C*>(p->T2b);
     PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, 256, sr, p->stream>>>(w, T1, nx, ny, P, twP));
-    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Q / 2 + 1, sx, sy, twQ));
+    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, Q / 2 + 1, twQ));
     const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
     PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, 256, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
     return PF_OK;
@@ -189,8 +194,8 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
 
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf) {
     if (p->prec == PF_FP64)
-        return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->sx64, p->sy64,
+        return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
                                     p->twP64, p->twQ64);
-    return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->sx32,
-                               p->sy32, p->twP32, p->twQ32);
+    return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
+                               p->Hv32, p->twP32, p->twQ32);
 }

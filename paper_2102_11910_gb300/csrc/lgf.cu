@@ -63,27 +63,45 @@ __global__ void k_lgf_table(double* __restrict__ G, int nx, int ny, const double
     }
 }
 
-// even extension of G onto the P x Q torus (row-major, P fastest); offsets
-// beyond the table are never reached by a linear convolution and are zero
-__global__ void k_torus(double2* __restrict__ g, const double* __restrict__ G, int nx, int ny, int P, int Q) {
+__device__ __forceinline__ double lgf_at(const double* __restrict__ G, int nx, int m, int n) {
+    return G[(size_t)(n < 0 ? -n : n) * (nx + 1) + (m < 0 ? -m : m)];
+}
+
+// Kernels placed on the P x Q torus (row-major, P fastest) at signed offsets
+// (m, n); offsets a linear convolution over the grid never reaches are zero.
+//   which = 0: G(m, n)                                     (psi:  -dx^2 G * w)
+//   which = 1: G(m, n+1) - G(m, n-1),  |n| <= ny-1          (u:   -dx/2 D_y G * w)
+//   which = 2: G(m+1, n) - G(m-1, n),  |m| <= nx-1          (v:   +dx/2 D_x G * w)
+// The differenced kernels decay like 1/r, so their FP64 spectra carry far less
+// rounding than the derivative symbol applied to the spectrum of G.
+__global__ void k_torus(double2* __restrict__ g, const double* __restrict__ G, int nx, int ny, int P, int Q, int which) {
     const int64_t total = (int64_t)P * Q;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int m = (int)(e % P), n = (int)(e / P);
-        const int dm = m <= P - m ? m : P - m;
-        const int dn = n <= Q - n ? n : Q - n;
+        const int mt = (int)(e % P), nt = (int)(e / P);
+        const int m = mt <= P / 2 ? mt : mt - P;
+        const int n = nt <= Q / 2 ? nt : nt - Q;
+        const int am = m < 0 ? -m : m, an = n < 0 ? -n : n;
         double v = 0.0;
-        if (dm <= nx && dn <= ny) v = G[(size_t)dn * (nx + 1) + dm];
+        if (which == 0) {
+            if (am <= nx && an <= ny) v = lgf_at(G, nx, m, n);
+        } else if (which == 1) {
+            if (am <= nx && an <= ny - 1) v = lgf_at(G, nx, m, n + 1) - lgf_at(G, nx, m, n - 1);
+        } else {
+            if (am <= nx - 1 && an <= ny) v = lgf_at(G, nx, m + 1, n) - lgf_at(G, nx, m - 1, n);
+        }
         g[e] = make_double2(v, 0.0);
     }
 }
 
+// quadrant k in [0, P/2], l in [0, Q/2] of scale * (Re or Im) of the spectrum
 __global__ void k_extract(const double2* __restrict__ g, double* __restrict__ H64, float* __restrict__ H32, int P,
-                          int Q, double scale) {
+                          int Q, double scale, int imag) {
     const int hp = P / 2 + 1, hq = Q / 2 + 1;
     const int64_t total = (int64_t)hp * hq;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(e % hq), k = (int)(e / hq);
-        const double v = scale * g[(size_t)l * P + k].x;
+        const double2 c = g[(size_t)l * P + k];
+        const double v = scale * (imag ? c.y : c.x);
         H64[e] = v;
         H32[e] = (float)v;
     }
@@ -119,12 +137,19 @@ pf_status lgf_build(pf_plan p) {
 
     double2* g = nullptr;
     PF_CUDA(p, cudaMalloc(&g, (size_t)P * Q * sizeof(double2)));
-    k_torus<<<4 * 152, 256, 0, p->stream>>>(g, p->G, nx, ny, P, Q);
-    PF_LAUNCH_CHECK(p);
-    pf_status st = fft2d_inplace_f64(p, g);
-    if (st != PF_OK) return st;
-    k_extract<<<4 * 152, 256, 0, p->stream>>>(g, p->H64, p->H32, P, Q, -p->dx * p->dx / ((double)P * Q));
-    PF_LAUNCH_CHECK(p);
+    const double inv_pq = 1.0 / ((double)P * Q);
+    // psi: -dx^2 Ghat/(PQ) (real, even);  u: -dx/2 Im(DyG^)/(PQ) (odd in l);  v: +dx/2 Im(DxG^)/(PQ) (odd in k)
+    double* H64[3] = {p->H64, p->Hu64, p->Hv64};
+    float* H32[3] = {p->H32, p->Hu32, p->Hv32};
+    const double scale[3] = {-p->dx * p->dx * inv_pq, -0.5 * p->dx * inv_pq, 0.5 * p->dx * inv_pq};
+    for (int which = 0; which < 3; ++which) {
+        k_torus<<<4 * 152, 256, 0, p->stream>>>(g, p->G, nx, ny, P, Q, which);
+        PF_LAUNCH_CHECK(p);
+        pf_status st = fft2d_inplace_f64(p, g);
+        if (st != PF_OK) return st;
+        k_extract<<<4 * 152, 256, 0, p->stream>>>(g, H64[which], H32[which], P, Q, scale[which], which != 0);
+        PF_LAUNCH_CHECK(p);
+    }
     PF_CUDA(p, cudaStreamSynchronize(p->stream));
     cudaFree(g);
     cudaFree(dn);

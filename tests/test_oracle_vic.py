@@ -77,6 +77,18 @@ def test_sampled_direct_sum_matches_field():
     assert np.allclose(vic.inv_laplacian_at(g, w, ti, tj, tab), full[tj, ti], rtol=1e-14, atol=0)
 
 
+def test_sampled_node_velocity_matches_differenced_field():
+    g = _grid(30, 26)
+    rng = np.random.default_rng(8)
+    X, Y, G = inputs.uniform_vortices(rng, 40, -0.5, 0.5, 0.01)
+    w = vic.regularize(g, X, Y, G)
+    tab = lgf_table(g.nx + 1, g.ny + 1)
+    u, v = vic.node_velocity(g, vic.streamfunction(g, w, tab, pad=1), 0.2, -0.1)
+    ti, tj = np.array([0, 29, 5, 17]), np.array([0, 25, 13, 2])
+    us, vs = vic.node_velocity_at(g, w, ti, tj, tab, 0.2, -0.1)
+    assert np.abs(us - u[tj, ti]).max() < 1e-12 and np.abs(vs - v[tj, ti]).max() < 1e-12
+
+
 def _psi_error(n):
     """Fig. 2 experiment: random vortices in the lower-left quadrant of
     [-1,1]^2; relative L2 error of psi over the upper-right quadrant."""
