@@ -125,6 +125,36 @@ pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const 
 pf_status pf_vic_velocity_host(pf_plan plan, const double* X, const double* Y, const double* Gam,
                                int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* Regularization for callers that cannot allocate device memory: code running
+ * where cudaMalloc is not allowed or not wanted (inside a host callback, under
+ * a memory budget that forbids new allocations, or in a process whose
+ * allocator is owned by someone else).  It computes exactly what
+ * pf_regularize computes, with the same kernels, but needs no plan and makes
+ * no allocation: its scratch (tile counters and up to 4 * 65536 binned vortex
+ * records) is one static device array of about 8.1 MiB inside this library,
+ * which every GPU that loads the library holds until the process exits.  The
+ * paper has no counterpart; it is an interface convenience.
+ *
+ *   desc          grid and precision, as for pf_plan_create (host pointer)
+ *   X, Y, Gam     nv doubles each (device); nv <= 65536, larger nv returns
+ *                 PF_ERR_CAPACITY without doing anything
+ *   w             real[nx*ny] output (device), fully overwritten
+ *   out_of_domain optional device int64: receives the number of vortices whose
+ *                 stencil left the grid (they are skipped); may be NULL
+ *   stream        cudaStream_t to enqueue on (NULL = default stream)
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture on the device.  All calls share the one array and
+ * it keeps the previous call's contents, so calls whose work overlaps on the
+ * GPU (different streams, or different host threads on one device) race and
+ * must be serialised by the caller. */
+pf_status pf_regularize_noalloc(const pf_grid_desc* desc, const double* X, const double* Y,
+                                const double* Gam, int64_t nv, void* w, int64_t* out_of_domain,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

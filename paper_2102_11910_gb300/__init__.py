@@ -165,3 +165,20 @@ def pf_timing_report(plan):
         name, n, ms = line.split()
         out[name] = (int(n), float(ms))
     return out
+
+
+def pf_regularize_noalloc(nx, ny, dx, x0, y0, precision, X, Y, G, w, out_of_domain=None, stream=None):
+    """Allocation-free regularization (no plan; static device scratch, nv <= 65536).
+
+    `w` must be a preallocated CUDA tensor of ny*nx elements of the precision's
+    dtype; `out_of_domain` an optional CUDA int64 tensor of one element."""
+    desc = _native.PfGridDesc(int(nx), int(ny), float(dx), float(x0), float(y0), int(precision))
+    dtype = torch.float64 if int(precision) == PF_FP64 else torch.float32
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = _native.lib().pf_regularize_noalloc(ctypes.byref(desc), _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
+                                             _ptr(G, torch.float64, "G"), X.numel(), _ptr(w, dtype, "w"),
+                                             _ptr(out_of_domain, torch.int64, "out_of_domain"),
+                                             ctypes.c_void_p(stream.cuda_stream))
+    _native.check(st, "pf_regularize_noalloc")
+    return w

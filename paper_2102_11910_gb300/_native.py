@@ -32,6 +32,7 @@ SIGNATURES = {
     "pf_interpolate": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
     "pf_vic_velocity": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
     "pf_vic_velocity_host": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
+    "pf_regularize_noalloc": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P]),
 }
 
 STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",

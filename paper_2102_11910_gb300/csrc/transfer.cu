@@ -268,3 +268,93 @@ pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const d
                                                         inv_dx, p->nx, p->ny, (float*)uq, (float*)vq, p->d_status, p->d_oob));
     return PF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free regularization.
+//
+// Same binned fixed-point kernels as pf_regularize, but every piece of scratch
+// (tile counters, fixed-point exponents, status words and the binned vortex
+// records) lives in one file-scope device array, so the entry point needs no
+// plan and makes no allocation.  The array is part of the library image: each
+// GPU that loads the library holds NOALLOC_SCRATCH_BYTES of it until exit.
+namespace {
+
+constexpr int64_t NOALLOC_MAX_VORTICES = 65536;
+constexpr int NOALLOC_MAX_TILES = (2048 / BIN_TILE) * (2048 / BIN_TILE);
+constexpr size_t NOALLOC_HEADER = 256;   // status int + out-of-domain counter, padded
+constexpr size_t NOALLOC_TILE_BYTES = (size_t)NOALLOC_MAX_TILES * (4 * sizeof(int) + sizeof(unsigned long long));
+constexpr size_t NOALLOC_SCRATCH_BYTES =
+    NOALLOC_HEADER + NOALLOC_TILE_BYTES + (size_t)4 * NOALLOC_MAX_VORTICES * sizeof(Rec<double>);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Resolve the array's device address for the current device (first call per
+// device only).  The host-side name g_noalloc_scratch is not a device address.
+cudaError_t noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = (unsigned char*)ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+pf_status regularize_noalloc_t(const pf_grid_desc* d, const double* X, const double* Y, const double* G, int64_t nv,
+                               T* w, int64_t* out_of_domain, cudaStream_t s, unsigned char* base) {
+    const int ntx = ceil_div(d->nx, BIN_TILE), nty = ceil_div(d->ny, BIN_TILE), ntiles = ntx * nty;
+    int* status = (int*)base;
+    unsigned long long* oob = (unsigned long long*)(base + 8);
+    int* tile_count = (int*)(base + NOALLOC_HEADER);
+    int* tile_start = tile_count + NOALLOC_MAX_TILES;
+    int* tile_cursor = tile_start + NOALLOC_MAX_TILES;
+    int* tile_shift = tile_cursor + NOALLOC_MAX_TILES;
+    unsigned long long* tile_gmax = (unsigned long long*)(tile_shift + NOALLOC_MAX_TILES);
+    Rec<T>* recs = (Rec<T>*)(base + NOALLOC_HEADER + NOALLOC_TILE_BYTES);
+    const double inv_dx = 1.0 / d->dx;
+    // the array keeps the previous call's contents: clear what accumulates
+    if (cudaMemsetAsync(base, 0, NOALLOC_HEADER, s) != cudaSuccess) return PF_ERR_CUDA;
+    if (cudaMemsetAsync(tile_count, 0, ntiles * sizeof(int), s) != cudaSuccess) return PF_ERR_CUDA;
+    if (cudaMemsetAsync(tile_gmax, 0, ntiles * sizeof(unsigned long long), s) != cudaSuccess) return PF_ERR_CUDA;
+    const int nb = nv > 0 ? (int)std::min<int64_t>(ceil_div(nv, 256), 152 * 16) : 0;
+    if (nb > 0)
+        k_bin_count<<<nb, 256, 0, s>>>(X, Y, G, nv, d->x0, d->y0, inv_dx, d->nx, d->ny, ntx, tile_count, tile_gmax,
+                                       status, oob);
+    k_bin_scan<<<1, 1024, 0, s>>>(tile_count, tile_gmax, tile_start, tile_cursor, tile_shift, ntiles);
+    if (nb > 0)
+        k_bin_scatter<T><<<nb, 256, 0, s>>>(X, Y, G, nv, d->x0, d->y0, inv_dx, d->nx, d->ny, ntx, tile_start,
+                                            tile_cursor, recs);
+    k_regularize<T><<<ntiles, 256, 0, s>>>(recs, tile_start, tile_count, tile_shift, d->nx, d->ny, ntx,
+                                           inv_dx * inv_dx, w);
+    if (cudaGetLastError() != cudaSuccess) return PF_ERR_CUDA;
+    if (out_of_domain &&
+        cudaMemcpyAsync(out_of_domain, oob, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return PF_ERR_CUDA;
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* X, const double* Y, const double* G,
+                                           int64_t nv, void* w, int64_t* out_of_domain, void* stream) {
+    if (!d || !w || nv < 0 || (nv > 0 && (!X || !Y || !G))) return PF_ERR_ARG;
+    if (d->nx < 8 || d->ny < 8 || d->nx > 2048 || d->ny > 2048 || !(d->dx > 0) || !isfinite(d->x0) ||
+        !isfinite(d->y0) || (d->precision != PF_FP64 && d->precision != PF_MIXED))
+        return PF_ERR_ARG;
+    if (nv > NOALLOC_MAX_VORTICES) return PF_ERR_CAPACITY;
+    unsigned char* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return PF_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d->precision == PF_FP64)
+        return regularize_noalloc_t<double>(d, X, Y, G, nv, (double*)w, out_of_domain, s, base);
+    return regularize_noalloc_t<float>(d, X, Y, G, nv, (float*)w, out_of_domain, s, base);
+}
