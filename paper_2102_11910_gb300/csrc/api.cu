@@ -18,9 +18,9 @@ int next_pow2(int v) {
 void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
-    void* ptrs[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32, p->twQ32,
-                    p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->tile_cursor, p->tile_shift,
-                    p->tile_gmax, p->recs, p->stage, p->stage_out, p->d_status, p->d_oob};
+    void* ptrs[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32, p->twQ32, p->tw256_64, p->tw256_32,
+                    p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start,
+                    p->pos, p->recs, p->ridx, p->stage, p->stage_out, p->d_status, p->d_oob};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -67,8 +67,15 @@ pf_status plan_init(pf_plan p) {
     PF_TRY(upload(p, &p->twQ64, tqd));
     PF_TRY(upload(p, &p->twP32, tpf));
     PF_TRY(upload(p, &p->twQ32, tqf));
+    std::vector<double2> t256d;
+    std::vector<float2> t256f;
+    twiddles(t256d, 256);
+    twiddles(t256f, 256);
+    PF_TRY(upload(p, &p->tw256_64, t256d));
+    PF_TRY(upload(p, &p->tw256_32, t256f));
     p->esz = p->prec == PF_FP64 ? 8 : 4;
-    const size_t spec = (size_t)(P / 2 + 1) * ny * 2 * p->esz;
+    p->ldT = (ny + 3) / 4 * 4;
+    const size_t spec = (size_t)(P / 2 + 1) * p->ldT * 2 * p->esz;
     PF_CUDA(p, cudaMalloc(&p->T1, spec));
     PF_CUDA(p, cudaMalloc(&p->T2a, spec));
     PF_CUDA(p, cudaMalloc(&p->T2b, spec));
@@ -77,11 +84,11 @@ pf_status plan_init(pf_plan p) {
     p->ntx = ceil_div(nx, BIN_TILE);
     p->nty = ceil_div(ny, BIN_TILE);
     p->ntiles = p->ntx * p->nty;
-    PF_CUDA(p, cudaMalloc(&p->tile_count, p->ntiles * sizeof(int)));
+    // count, gmax and cursor are contiguous so one memset clears them
+    PF_CUDA(p, cudaMalloc(&p->tile_count, 3 * (size_t)p->ntiles * sizeof(unsigned)));
+    p->tile_gmax = p->tile_count + p->ntiles;
+    p->tile_cursor = p->tile_count + 2 * p->ntiles;
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
-    PF_CUDA(p, cudaMalloc(&p->tile_cursor, p->ntiles * sizeof(int)));
-    PF_CUDA(p, cudaMalloc(&p->tile_shift, p->ntiles * sizeof(int)));
-    PF_CUDA(p, cudaMalloc(&p->tile_gmax, p->ntiles * sizeof(unsigned long long)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
     PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
@@ -228,7 +235,7 @@ pf_status pf_vic_velocity(pf_plan p, const double* X, const double* Y, const dou
     if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
     PF_TRY(vortex_regularize(p, X, Y, G, nv, p->w));
     PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
-    return vortex_interpolate(p, p->uv, X, Y, nv, uq, vq);
+    return vortex_interpolate_located(p, p->uv, nv, uq, vq);
 }
 
 pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,

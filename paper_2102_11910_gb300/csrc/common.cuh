@@ -68,21 +68,26 @@ struct pf_plan_s {
     double2* twQ64 = nullptr;
     float2* twP32 = nullptr;
     float2* twQ32 = nullptr;
+    double2* tw256_64 = nullptr;   // exp(-2 pi i m / 256), m in [0, 256)
+    float2* tw256_32 = nullptr;
     // grid work buffers (element size depends on precision)
     size_t esz = 8;
-    void* T1 = nullptr;            // (P/2+1)*ny complex: row spectra, column-major in k
+    int ldT = 0;                   // leading dimension of T1/T2 (ny rounded up to 4)
+    void* T1 = nullptr;            // (P/2+1)*ldT complex: row spectra, k-major
     void* T2a = nullptr;
     void* T2b = nullptr;
     void* w = nullptr;             // nx*ny real
     void* uv = nullptr;            // 2*nx*ny real
     // binning
     int ntx = 0, nty = 0, ntiles = 0;
-    int* tile_count = nullptr;
+    unsigned* tile_count = nullptr;    // one allocation: count | gmax | cursor
+    unsigned* tile_gmax = nullptr;     // bits of the largest |Gamma| (FP32, rounded up) per tile
+    unsigned* tile_cursor = nullptr;
     int* tile_start = nullptr;
-    int* tile_cursor = nullptr;
-    int* tile_shift = nullptr;
-    unsigned long long* tile_gmax = nullptr;
-    void* recs = nullptr;
+    void* pos = nullptr;               // per-vortex cell records of the last located set
+    int64_t pos_cap = 0;
+    void* recs = nullptr;              // records binned by tile
+    int* ridx = nullptr;               // original vortex index of each binned record
     int64_t rec_cap = 0;
     // host-input staging for the *_host entry points
     double* stage = nullptr;
@@ -101,13 +106,14 @@ cudaEvent_t tm_event(pf_plan p);   // api.cu
 #define PF_KERNEL(p, name, ...)                                                   \
     do {                                                                          \
         cudaEvent_t a_ = nullptr;                                                 \
-        if ((p)->tm.on) {                                                         \
+        const bool t_ = (p) != nullptr && (p)->tm.on;                             \
+        if (t_) {                                                                 \
             a_ = tm_event(p);                                                     \
             cudaEventRecord(a_, (p)->stream);                                     \
         }                                                                         \
         __VA_ARGS__;                                                              \
         PF_LAUNCH_CHECK(p);                                                       \
-        if ((p)->tm.on) {                                                         \
+        if (t_) {                                                                 \
             cudaEvent_t b_ = tm_event(p);                                         \
             cudaEventRecord(b_, (p)->stream);                                     \
             (p)->tm.names.push_back(name);                                        \
@@ -137,3 +143,4 @@ pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf,
 enum { CONV_PSI = 0, CONV_UV = 1 };
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w);  // transfer.cu
 pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq);
+pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void* uq, void* vq);

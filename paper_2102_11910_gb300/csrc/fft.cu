@@ -14,6 +14,7 @@
 //               outputs (psi_j + i psi_{j+1}, or u_j + i v_j), inverse FFT,
 //               keep nodes [0, nx).
 #include "fft.cuh"
+#include "fft_reg.cuh"
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx, int ny,
@@ -173,6 +174,220 @@ pf_status fft2d_inplace_f64(pf_plan p, double2* data) {
     return PF_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Register-resident variants for P, Q = 256 * R3 (256 <= P, Q <= 4096).  Row
+// spectra are stored with leading dimension ldT (ny rounded up to 4) so that
+// the pair of rows a group writes per k is one aligned vector store.
+
+template <typename T, int R3>
+__global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx,
+                                                        int ny, int ldT, const C_t<T>* __restrict__ tw256,
+                                                        const C_t<T>* __restrict__ twP) {
+    using C = C_t<T>;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / TP, t = threadIdx.x % TP;
+    C* buf = reinterpret_cast<C*>(smem_raw) + g * SB;
+    const int j0 = 4 * blockIdx.x + 2 * g;
+    const bool h0 = j0 < ny, h1 = j0 + 1 < ny;
+    C v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int n = t + TP * r;
+        T a = 0, b = 0;
+        if (n < nx) {
+            if (h0) a = w[(size_t)j0 * nx + n];
+            if (h1) b = w[(size_t)(j0 + 1) * nx + n];
+        }
+        v[r] = cmake<C>(a, b);
+    }
+    fft_strided<C, false, R3>(v, buf, t, tw256, twP);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[spad(t + TP * r)] = v[r];
+    __syncthreads();
+    if (h0) {
+        for (int k = t; k <= P / 2; k += TP) {
+            const C z1 = buf[spad(k)], z2 = conjc(buf[spad((P - k) & (P - 1))]);
+            const C A = (z1 + z2) * T(0.5);
+            const C B = mul_mi(z1 - z2) * T(0.5);
+            C* dst = T1 + (size_t)k * ldT + j0;
+            dst[0] = A;
+            if (h1) dst[1] = B;
+        }
+    }
+}
+
+template <typename T, int R3>
+__global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_r(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
+                                                    C_t<T>* __restrict__ T2b, int ny, int ldT, int mode,
+                                                    const T* __restrict__ H, const T* __restrict__ Hu,
+                                                    const T* __restrict__ Hv, int Hld,
+                                                    const C_t<T>* __restrict__ tw256, const C_t<T>* __restrict__ twQ) {
+    using C = C_t<T>;
+    constexpr int Q = 256 * R3, TQ = Q / 16, SB = SBuf<Q>::size;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* keep = buf + SB;
+    const int k = blockIdx.x, t = threadIdx.x;
+    const C* src = T1 + (size_t)k * ldT;
+    C v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int l = t + TQ * r;
+        v[r] = l < ny ? src[l] : cmake<C>(T(0), T(0));
+    }
+    fft_strided<C, false, R3>(v, buf, t, tw256, twQ);
+    const size_t row = (size_t)k * Hld;
+    C* outa = T2a + (size_t)k * ldT;
+    if (mode == CONV_UV) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int l = t + TQ * r;
+            const bool lo = l <= Q / 2;
+            const int lq = lo ? l : Q - l;
+            const C iw = mul_i(v[r]);
+            const T hu = Hu[row + lq];
+            keep[spad(l)] = iw * Hv[row + lq];     // even in l
+            v[r] = iw * (lo ? hu : -hu);            // odd in l
+        }
+        fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int l = t + TQ * r;
+            if (l < ny) outa[l] = v[r];
+            v[r] = keep[spad(l)];                    // written by this thread
+        }
+        fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
+        C* outb = T2b + (size_t)k * ldT;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int l = t + TQ * r;
+            if (l < ny) outb[l] = v[r];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int l = t + TQ * r;
+            v[r] = v[r] * H[row + (l <= Q / 2 ? l : Q - l)];
+        }
+        fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int l = t + TQ * r;
+            if (l < ny) outa[l] = v[r];
+        }
+    }
+}
+
+template <typename T, int R3>
+__global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
+                                                        T* __restrict__ out, int nx, int ny, int ldT, int mode, T Uinf,
+                                                        T Vinf, const C_t<T>* __restrict__ tw256,
+                                                        const C_t<T>* __restrict__ twP) {
+    using C = C_t<T>;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / TP, t = threadIdx.x % TP;
+    C* buf = reinterpret_cast<C*>(smem_raw) + g * SB;
+    int ja, jb;
+    const C* Sb;
+    bool ha, hb;
+    if (mode == CONV_UV) {
+        ja = jb = 2 * blockIdx.x + g;
+        Sb = T2b;
+        ha = hb = ja < ny;
+    } else {
+        ja = 4 * blockIdx.x + 2 * g;
+        jb = ja + 1;
+        Sb = T2a;
+        ha = ja < ny;
+        hb = jb < ny;
+    }
+    const int h = P / 2;
+    for (int k = t; k <= h; k += TP) {
+        C a = ha ? T2a[(size_t)k * ldT + ja] : cmake<C>(T(0), T(0));
+        C b = hb ? Sb[(size_t)k * ldT + jb] : cmake<C>(T(0), T(0));
+        if (k == 0 || k == h) { a.y = 0; b.y = 0; }
+        buf[spad(k)] = a + mul_i(b);
+        if (k > 0 && k < h) buf[spad(P - k)] = conjc(a) + mul_i(conjc(b));
+    }
+    __syncthreads();
+    C v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[spad(t + TP * r)];
+    __syncthreads();
+    fft_strided<C, true, R3>(v, buf, t, tw256, twP);
+    if (mode == CONV_UV) {
+        if (ha) {
+            C* o = reinterpret_cast<C*>(out) + (size_t)ja * nx;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int n = t + TP * r;
+                if (n < nx) o[n] = cmake<C>(v[r].x + Uinf, v[r].y + Vinf);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + TP * r;
+            if (n < nx) {
+                if (ha) out[(size_t)ja * nx + n] = v[r].x;
+                if (hb) out[(size_t)jb * nx + n] = v[r].y;
+            }
+        }
+    }
+}
+
+template <typename T, int R3P, int R3Q>
+static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
+                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+    using C = C_t<T>;
+    constexpr int P = 256 * R3P, Q = 256 * R3Q;
+    const int nx = p->nx, ny = p->ny, ldT = p->ldT;
+    const size_t sr = 2 * (size_t)SBuf<P>::size * sizeof(C), sc = 2 * (size_t)SBuf<Q>::size * sizeof(C);
+    PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sr));
+    PF_CUDA(p, set_smem(k_cols_r<T, R3Q>, sc));
+    PF_CUDA(p, set_smem(k_rows_inv_r<T, R3P>, sr));
+    C* T1 = reinterpret_cast<C*>(p->T1);
+    C* T2a = reinterpret_cast<C*>(p->T2a);
+    C* T2b = reinterpret_cast<C*>(p->T2b);
+    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd_r<T, R3P><<<(ny + 3) / 4, 32 * R3P, sr, p->stream>>>(w, T1, nx, ny, ldT,
+                                                                                                 tw256, twP));
+    PF_KERNEL(p, "fft_cols_conv", k_cols_r<T, R3Q><<<P / 2 + 1, 16 * R3Q, sc, p->stream>>>(
+                                      T1, T2a, T2b, ny, ldT, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ));
+    const int nb = mode == CONV_UV ? (ny + 1) / 2 : (ny + 3) / 4;
+    PF_KERNEL(p, "fft_rows_inv", k_rows_inv_r<T, R3P><<<nb, 32 * R3P, sr, p->stream>>>(T2a, T2b, out, nx, ny, ldT, mode,
+                                                                                       Uinf, Vinf, tw256, twP));
+    return PF_OK;
+}
+
+template <typename T, int R3P>
+static pf_status conv_dispatch_q(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
+                                 const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+    switch (p->Q) {
+        case 256: return conv_solve_r<T, R3P, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 512: return conv_solve_r<T, R3P, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 1024: return conv_solve_r<T, R3P, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 2048: return conv_solve_r<T, R3P, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 4096: return conv_solve_r<T, R3P, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+    }
+    return PF_ERR_ARG;
+}
+
+template <typename T>
+static pf_status conv_dispatch(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
+                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+    switch (p->P) {
+        case 256: return conv_dispatch_q<T, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 512: return conv_dispatch_q<T, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 1024: return conv_dispatch_q<T, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 2048: return conv_dispatch_q<T, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 4096: return conv_dispatch_q<T, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+    }
+    return PF_ERR_ARG;
+}
+
 template <typename T>
 static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ) {
@@ -193,9 +408,17 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
 }
 
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf) {
-    if (p->prec == PF_FP64)
+    const bool reg = p->P >= 256 && p->Q >= 256;   // register-resident kernels; small grids use the generic ones
+    if (p->prec == PF_FP64) {
+        if (reg)
+            return conv_dispatch<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
+                                         p->twP64, p->twQ64, p->tw256_64);
         return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
                                     p->twP64, p->twQ64);
+    }
+    if (reg)
+        return conv_dispatch<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
+                                    p->Hv32, p->twP32, p->twQ32, p->tw256_32);
     return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
                                p->Hv32, p->twP32, p->twQ32);
 }

@@ -69,7 +69,7 @@ def test_regularize(prec, nx, ny, nv):
 
 
 @pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
-@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45), (128, 48)])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45), (128, 48), (300, 200), (600, 100)])
 def test_poisson_solve(prec, nx, ny):
     g, X, Y, G = _case(nx, ny, 200, 12)
     og = _og(g)
@@ -83,7 +83,7 @@ def test_poisson_solve(prec, nx, ny):
 
 
 @pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
-@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45)])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45), (300, 200), (600, 100)])
 def test_velocity_solve(prec, nx, ny):
     g, X, Y, G = _case(nx, ny, 200, 13)
     og = _og(g)
