@@ -125,6 +125,67 @@ pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const 
 pf_status pf_vic_velocity_host(pf_plan plan, const double* X, const double* Y, const double* Gam,
                                int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 
+/* ------------------------------------------------------- immersed body */
+
+#define PF_MAX_SURFACE_POINTS 4096
+
+/* Surface points of one body (HOST arrays of ns doubles): coordinates and
+ * the length dS_p of the segment each point represents (Sec. 2.2.1). */
+typedef struct {
+    int32_t ns;
+    const double* x;
+    const double* y;
+    const double* ds;
+} pf_body_desc;
+
+/* Rigid motion of the body and the free stream: translation (U, V), rotation
+ * Omega about the origin; (Uinf, Vinf) is the uniform flow whose
+ * streamfunction psi_inf = Uinf y - Vinf x is the homogeneous part of the
+ * solution (Sec. 2.1, Eqs. velsurf, sfsurf). */
+typedef struct {
+    double U, V, Omega;
+    double Uinf, Vinf;
+} pf_motion;
+
+typedef enum {
+    PF_SHEET_GIVEN_S0 = 0,     /* Eq. vsheet: f = S^-1 (s'_b - s0 1 + E L^-1 w); param = s0          */
+    PF_SHEET_CIRCULATION = 1,  /* Eq. circsystem: bound circulation <1, f> = param; s0 solved for    */
+    PF_SHEET_KUTTA_STEADY = 2, /* Eq. kuttasystem: ftilde = P_k Stilde^-1 (P^Gamma s'_b + E L^-1 w),
+                                  one edge k = edges[0]; param unused                              */
+    PF_SHEET_KUTTA_SHED = 3    /* Eq. kuttasystem2 (one edge) / Eq. twovortex (two edges): new
+                                  vortices at (Xnew, Ynew) take the strengths that null ftilde at
+                                  the edges and keep the total circulation zero; param = Gamma_w,
+                                  the circulation of the existing free vorticity                   */
+} pf_sheet_mode;
+
+/* Schur complement S = -E L^-1 R_s of a body on the plan's grid (Eq. vsheet),
+ * its FP64 inverse by Gauss-Jordan with partial pivoting, f0 = S^-1 1 and
+ * Gamma0 = <1, f0> (Eqs. f0, circ0).  Synchronous.  Every surface point's
+ * stencil must lie inside the grid (else PF_ERR_OUT_OF_DOMAIN); a vanishing
+ * pivot gives PF_ERR_SINGULAR.  The factor owns its device memory. */
+pf_status pf_schur_factor(pf_plan plan, const pf_body_desc* body, pf_schur* out);
+pf_status pf_schur_destroy(pf_schur schur);
+
+/* Host copies: Gamma0 (scalar), f0 (ns doubles) and S (ns*ns, row-major); any
+ * may be NULL.  Synchronises. */
+pf_status pf_schur_info(pf_schur schur, double* gamma0, double* f0, double* S);
+
+/* Bound vortex sheet for the free vorticity w (device real[nx*ny], e.g. from
+ * pf_regularize), body motion m and mode (pf_sheet_mode).  E_s L^-1 w, the
+ * free vorticity's streamfunction seen by the surface (Eq. intermedsoln), is
+ * summed directly with the FP64 LGF over the nonzero nodes of w rather than
+ * read from an FFT solve: S is ill-conditioned (Sec. 2.2.2), and FFT rounding,
+ * white on psi, would be amplified into the sheet.  edges: n_edges (1 or 2) surface-point indices of the Kutta
+ * edges (host), used by the Kutta modes.  Xnew, Ynew: host positions of the
+ * n_edges new vortices (mode PF_SHEET_KUTTA_SHED).  Outputs: f (device,
+ * ns doubles: the sheet strength gamma, Sec. 2.2.2), gamma_new (host,
+ * n_edges: new vortex strengths), s0 (host: the uniform streamfunction value).
+ * The sheet solve runs in FP64 for both precisions.  Synchronises. */
+pf_status pf_sheet_solve(pf_plan plan, pf_schur schur, const void* w, const pf_motion* m,
+                         int32_t mode, double param, int32_t n_edges, const int32_t* edges,
+                         const double* Xnew, const double* Ynew, double* f, double* gamma_new,
+                         double* s0);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* Regularization for callers that cannot allocate device memory: code running

@@ -182,3 +182,74 @@ def pf_regularize_noalloc(nx, ny, dx, x0, y0, precision, X, Y, G, w, out_of_doma
                                              ctypes.c_void_p(stream.cuda_stream))
     _native.check(st, "pf_regularize_noalloc")
     return w
+
+
+PF_SHEET_GIVEN_S0 = 0
+PF_SHEET_CIRCULATION = 1
+PF_SHEET_KUTTA_STEADY = 2
+PF_SHEET_KUTTA_SHED = 3
+
+
+class Schur:
+    """Handle of a pf_schur (factorised Schur complement of one body on a plan's grid)."""
+
+    def __init__(self, plan, handle, ns):
+        self.plan, self.handle, self.ns = plan, handle, ns
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_schur_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_f64(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def pf_schur_factor(plan, x, y, ds):
+    """Factor S = -E L^-1 R_s for surface points (x, y) with segment lengths ds (host arrays)."""
+    x, y, ds = _host_f64(x), _host_f64(y), _host_f64(ds)
+    c = ctypes.c_void_p
+    desc = _native.PfBodyDesc(len(x), c(x.ctypes.data), c(y.ctypes.data), c(ds.ctypes.data))
+    h = ctypes.c_void_p()
+    _native.check(_native.lib().pf_schur_factor(plan.handle, ctypes.byref(desc), ctypes.byref(h)), "pf_schur_factor",
+                  plan.handle)
+    return Schur(plan, h, len(x))
+
+
+def pf_schur_info(schur):
+    """(Gamma0, f0, S) as host numpy arrays."""
+    import numpy as np
+    g = ctypes.c_double()
+    f0 = np.empty(schur.ns)
+    S = np.empty((schur.ns, schur.ns))
+    _native.check(_native.lib().pf_schur_info(schur.handle, ctypes.byref(g), f0.ctypes.data_as(ctypes.c_void_p),
+                                              S.ctypes.data_as(ctypes.c_void_p)), "pf_schur_info", schur.plan.handle)
+    return g.value, f0, S
+
+
+def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None, Ynew=None, f=None):
+    """Bound sheet for free vorticity w (device field).  motion = (U, V, Omega, Uinf, Vinf).
+    Returns (f device float64 tensor, gamma_new host list, s0)."""
+    import numpy as np
+    f = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if f is None else f
+    ed = np.ascontiguousarray(edges, dtype=np.int32)
+    ne = len(ed)
+    xn = _host_f64(Xnew if Xnew is not None else np.zeros(max(ne, 1)))
+    yn = _host_f64(Ynew if Ynew is not None else np.zeros(max(ne, 1)))
+    gn = np.zeros(max(ne, 1))
+    s0 = ctypes.c_double()
+    m = _native.PfMotion(*[float(v) for v in motion])
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_sheet_solve(plan.handle, schur.handle, _ptr(w, plan.dtype, "w"), ctypes.byref(m),
+                                               int(mode), float(param), ne, c(ed.ctypes.data) if ne else None,
+                                               c(xn.ctypes.data), c(yn.ctypes.data), _ptr(f, torch.float64, "f"),
+                                               c(gn.ctypes.data), ctypes.byref(s0)), "pf_sheet_solve", plan.handle)
+    return f, list(gn[:ne]), s0.value

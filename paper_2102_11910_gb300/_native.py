@@ -33,6 +33,10 @@ SIGNATURES = {
     "pf_vic_velocity": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
     "pf_vic_velocity_host": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
     "pf_regularize_noalloc": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P]),
+    "pf_schur_factor": (_c.c_int, [_P, _P, _c.POINTER(_P)]),
+    "pf_schur_destroy": (_c.c_int, [_P]),
+    "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
+    "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
 }
 
 STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",
@@ -48,6 +52,14 @@ class GridPfError(RuntimeError):
 
 class PfGridDesc(ctypes.Structure):
     _fields_ = [("nx", _I32), ("ny", _I32), ("dx", _D), ("x0", _D), ("y0", _D), ("precision", _I32)]
+
+
+class PfBodyDesc(ctypes.Structure):
+    _fields_ = [("ns", _I32), ("x", _P), ("y", _P), ("ds", _P)]
+
+
+class PfMotion(ctypes.Structure):
+    _fields_ = [("U", _D), ("V", _D), ("Omega", _D), ("Uinf", _D), ("Vinf", _D)]
 
 
 def header_path():

@@ -1,0 +1,610 @@
+// Immersed body: surface transfer, Schur complement and the constrained sheet
+// solves of Sec. 2.2-2.4, in FP64.
+//
+//   E_s / R_s       smoothed three-point kernel (Sec. 2.2.1), E weights carry no
+//                   dx factor, R_s carries dS/dx^2 (so R_s = E_s^T in the node and
+//                   surface inner products)
+//   S = -E L^-1 R_s (Eq. vsheet): S[p,q] = -dS_q sum_{16 x 16 node pairs} d_p G d_q,
+//                   from the plan's FP64 LGF table (L^-1 = dx^2 G*)
+//   S^-1            Gauss-Jordan with partial pivoting, one pivot per pair of
+//                   kernel launches (no device-side waiting)
+//   f0 = S^-1 1, f0hat = dS o f0, Gamma0 = <1, f0>  (Eqs. f0, circ0)
+//   solves          given s0 (Eq. vsheet), circulation (Eq. circsystem), steady
+//                   Kutta (Eqs. kuttasystem, s0), shedding at one edge
+//                   (Eq. kuttasystem2) or two edges (Eq. twovortex)
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "body.cuh"
+
+namespace {
+
+// smoothed three-point delta of Yang et al. (2009), support |r| < 2
+__device__ double yang3(double r) {
+    const double a = fabs(r);
+    const double s3 = 1.7320508075688772;
+    if (a <= 1.0) {
+        const double q = -12.0 * a * a + 12.0 * a + 1.0;
+        return 17.0 / 48.0 + s3 * M_PI / 108.0 + a / 4.0 - a * a / 4.0 + (1.0 - 2.0 * a) / 16.0 * sqrt(q > 0 ? q : 0.0) -
+               s3 / 12.0 * asin(s3 / 2.0 * (2.0 * a - 1.0));
+    }
+    if (a < 2.0) {
+        const double q = -12.0 * a * a + 36.0 * a - 23.0;
+        return 55.0 / 48.0 - s3 * M_PI / 108.0 - 13.0 * a / 12.0 + a * a / 4.0 +
+               (2.0 * a - 3.0) / 48.0 * sqrt(q > 0 ? q : 0.0) + s3 / 36.0 * asin(s3 / 2.0 * (2.0 * a - 3.0));
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double m4p(double r) {
+    const double a = fabs(r);
+    if (a <= 1.0) return 1.0 - 2.5 * a * a + 1.5 * a * a * a;
+    if (a <= 2.0) return 0.5 * (2.0 - a) * (2.0 - a) * (1.0 - a);
+    return 0.0;
+}
+
+__device__ __forceinline__ double lgf(const double* __restrict__ G, int nx, int m, int n) {
+    return G[(size_t)(n < 0 ? -n : n) * (nx + 1) + (m < 0 ? -m : m)];
+}
+
+// four-node stencil of a point: nodes floor(g)-1 .. floor(g)+2, g = (x - x0)/dx
+__device__ __forceinline__ bool stencil(double x, double x0, double dx, int n, int* idx, double* wt, bool surface) {
+    const double g = (x - x0) / dx;
+    const double c = floor(g);
+    if (!(c >= 1.0 && c <= n - 3.0)) return false;
+    const int ci = (int)c;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        idx[a] = ci - 1 + a;
+        wt[a] = surface ? yang3((double)(ci - 1 + a) - g) : m4p((double)(ci - 1 + a) - g);
+    }
+    return true;
+}
+
+__global__ void k_surface_stencil(const double* __restrict__ x, const double* __restrict__ y, int ns, double x0,
+                                  double y0, double dx, int nx, int ny, int* __restrict__ six, int* __restrict__ siy,
+                                  double* __restrict__ swx, double* __restrict__ swy, int* __restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    int ix[4], iy[4];
+    double wx[4], wy[4];
+    const bool ok = stencil(x[p], x0, dx, nx, ix, wx, true) && stencil(y[p], y0, dx, ny, iy, wy, true);
+    if (!ok) {
+        atomicOr(status, ST_OUT_OF_DOMAIN);
+        for (int a = 0; a < 4; ++a) { ix[a] = 1; iy[a] = 1; wx[a] = 0.0; wy[a] = 0.0; }
+    }
+    for (int a = 0; a < 4; ++a) {
+        six[4 * p + a] = ix[a];
+        siy[4 * p + a] = iy[a];
+        swx[4 * p + a] = wx[a];
+        swy[4 * p + a] = wy[a];
+    }
+}
+
+// S[p, q] = -dS_q sum_{a,b,a',b'} wx_p[a] wy_p[b] G(ix_p[a]-ix_q[a'], iy_p[b]-iy_q[b']) wx_q[a'] wy_q[b']
+__global__ void k_schur_build(const int* __restrict__ six, const int* __restrict__ siy, const double* __restrict__ swx,
+                              const double* __restrict__ swy, const double* __restrict__ ds, int ns,
+                              const double* __restrict__ G, int nx, double* __restrict__ A, int lda) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (q >= ns) return;
+    double acc = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            const double wp = swx[4 * p + a] * swy[4 * p + b];
+            const int ip = six[4 * p + a], jp = siy[4 * p + b];
+            double s = 0.0;
+            for (int b2 = 0; b2 < 4; ++b2)
+                for (int a2 = 0; a2 < 4; ++a2)
+                    s += lgf(G, nx, ip - six[4 * q + a2], jp - siy[4 * q + b2]) * swx[4 * q + a2] * swy[4 * q + b2];
+            acc += wp * s;
+        }
+    A[(size_t)p * lda + q] = -ds[q] * acc;
+}
+
+// augmented [S | I] for Gauss-Jordan
+__global__ void k_augment(const double* __restrict__ S, double* __restrict__ A, int ns) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= 2 * ns) return;
+    A[(size_t)i * 2 * ns + j] = j < ns ? S[(size_t)i * ns + j] : (j - ns == i ? 1.0 : 0.0);
+}
+
+// pivot k: choose the row of largest |A[i,k]|, i >= k (lowest index on ties), swap
+// it into row k and scale row k by the inverse pivot (one block)
+__global__ void k_gj_pivot(double* __restrict__ A, int ns, int k, double tiny, int* __restrict__ status) {
+    __shared__ double bv[256];
+    __shared__ int bi[256];
+    __shared__ double piv_s;
+    __shared__ int p_s;
+    const int W = 2 * ns, tid = threadIdx.x;
+    double best = -1.0;
+    int bidx = k;
+    for (int i = k + tid; i < ns; i += blockDim.x) {
+        const double v = fabs(A[(size_t)i * W + k]);
+        if (v > best) { best = v; bidx = i; }
+    }
+    bv[tid] = best;
+    bi[tid] = bidx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            const double v2 = bv[tid + o];
+            const int i2 = bi[tid + o];
+            if (v2 > bv[tid] || (v2 == bv[tid] && i2 < bi[tid])) { bv[tid] = v2; bi[tid] = i2; }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        p_s = bi[0];
+        piv_s = A[(size_t)bi[0] * W + k];
+        if (!(fabs(piv_s) > tiny)) {
+            atomicOr(status, ST_SINGULAR);
+            piv_s = piv_s == 0.0 ? 1.0 : piv_s;
+        }
+    }
+    __syncthreads();
+    const int p = p_s;
+    const double inv = 1.0 / piv_s;
+    for (int j = tid; j < W; j += blockDim.x) {
+        const double ak = A[(size_t)k * W + j], ap = A[(size_t)p * W + j];
+        if (p != k) A[(size_t)p * W + j] = ak;
+        A[(size_t)k * W + j] = ap * inv;
+    }
+}
+
+// eliminate column k from every row i != k (one block per row)
+__global__ void k_gj_eliminate(double* __restrict__ A, int ns, int k) {
+    const int i = blockIdx.x;
+    if (i == k) return;
+    const int W = 2 * ns;
+    const double f = A[(size_t)i * W + k];
+    __syncthreads();     // every thread has read the factor before column k is overwritten
+    if (f == 0.0) return;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) A[(size_t)i * W + j] -= f * A[(size_t)k * W + j];
+}
+
+__global__ void k_extract_inverse(const double* __restrict__ A, double* __restrict__ Sinv, int ns) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= ns) return;
+    Sinv[(size_t)i * ns + j] = A[(size_t)i * 2 * ns + ns + j];
+}
+
+// deterministic block reduction of a double (fixed tree)
+__device__ double block_sum(double v, double* sh) {
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) sh[tid] += sh[tid + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// f0 = S^-1 1, f0hat = dS f0, Gamma0 = sum f0hat (one block of 256)
+__global__ void k_f0(const double* __restrict__ Sinv, const double* __restrict__ ds, int ns, double* __restrict__ f0,
+                     double* __restrict__ f0hat, double* __restrict__ gamma0) {
+    __shared__ double sh[256];
+    double part = 0.0;
+    for (int p = threadIdx.x; p < ns; p += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < ns; ++q) s += Sinv[(size_t)p * ns + q];
+        f0[p] = s;
+        f0hat[p] = ds[p] * s;
+        part += ds[p] * s;
+    }
+    const double g = block_sum(part, sh);
+    if (threadIdx.x == 0) *gamma0 = g;
+}
+
+// E_s L^-1 w at surface point p = dx^2 sum_nodes w_m sum_{16 stencil nodes s} d_p(s) G(s - m),
+// summed in FP64 over the nonzero nodes of w (any precision of w).  Evaluating
+// it directly keeps FFT rounding (white noise on psi, amplified by the
+// ill-conditioned S) out of the sheet strength.  One block per surface point;
+// per-thread partial sums in a fixed order and a fixed reduction tree.
+template <typename T>
+__global__ void __launch_bounds__(256) k_surface_einvlw(const T* __restrict__ w, int nx, int ny,
+                                                        const int* __restrict__ six, const int* __restrict__ siy,
+                                                        const double* __restrict__ swx, const double* __restrict__ swy,
+                                                        const double* __restrict__ G, double dx2,
+                                                        double* __restrict__ out) {
+    __shared__ double sh[256];
+    const int p = blockIdx.x;
+    int ix[4], iy[4];
+    double wx[4], wy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ix[a] = six[4 * p + a];
+        iy[a] = siy[4 * p + a];
+        wx[a] = swx[4 * p + a];
+        wy[a] = swy[4 * p + a];
+    }
+    double acc = 0.0;
+    const int M = nx * ny;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const double wm = (double)w[m];
+        if (wm == 0.0) continue;
+        const int i = m % nx, j = m / nx;
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            double r = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) r += wx[a] * lgf(G, nx, ix[a] - i, iy[b] - j);
+            s += wy[b] * r;
+        }
+        acc += wm * s;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[p] = dx2 * tot;
+}
+
+// s'_b = (U - Uinf) y - (V - Vinf) x - Omega/2 (x^2 + y^2)   (Eq. sfsurf with the uniform flow removed)
+__global__ void k_sbprime(const double* __restrict__ x, const double* __restrict__ y, int ns, pf_motion m,
+                          double* __restrict__ sb) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    sb[p] = (m.U - m.Uinf) * y[p] - (m.V - m.Vinf) * x[p] - 0.5 * m.Omega * (x[p] * x[p] + y[p] * y[p]);
+}
+
+// E_s L^-1 d_j for unit point vortices at (vx[j], vy[j]), j < nj: out[j*ns + p]
+__global__ void k_unit_vortex(const double* __restrict__ vx, const double* __restrict__ vy, int nj,
+                              const int* __restrict__ six, const int* __restrict__ siy, const double* __restrict__ swx,
+                              const double* __restrict__ swy, int ns, const double* __restrict__ G, int nx, int ny,
+                              double x0, double y0, double dx, double* __restrict__ out, int* __restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (p >= ns || j >= nj) return;
+    int vix[4], viy[4];
+    double vwx[4], vwy[4];
+    if (!(stencil(vx[j], x0, dx, nx, vix, vwx, false) && stencil(vy[j], y0, dx, ny, viy, vwy, false))) {
+        if (p == 0) atomicOr(status, ST_OUT_OF_DOMAIN);
+        out[(size_t)j * ns + p] = 0.0;
+        return;
+    }
+    // L^-1 d_j = dx^2 G * (dx^-2 M4' M4'): the dx factors cancel
+    double acc = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            const double wp = swx[4 * p + a] * swy[4 * p + b];
+            double s = 0.0;
+            for (int b2 = 0; b2 < 4; ++b2)
+                for (int a2 = 0; a2 < 4; ++a2)
+                    s += lgf(G, nx, six[4 * p + a] - vix[a2], siy[4 * p + b] - viy[b2]) * vwx[a2] * vwy[b2];
+            acc += wp * s;
+        }
+    out[(size_t)j * ns + p] = acc;
+}
+
+// y_c = S^-1 v_c for nc right-hand sides (vectors of length ns, stride ns)
+__global__ void k_gemv(const double* __restrict__ Sinv, int ns, const double* __restrict__ v, int nc,
+                       double* __restrict__ y) {
+    const int p = blockIdx.x;
+    __shared__ double sh[4][128];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+        const double s = Sinv[(size_t)p * ns + q];
+        for (int c = 0; c < nc; ++c) acc[c] += s * v[(size_t)c * ns + q];
+    }
+    for (int c = 0; c < nc; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < nc; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < nc) y[(size_t)threadIdx.x * ns + p] = sh[threadIdx.x][0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- constraint algebra
+// One block.  Inputs (device): sb = s'_b, ew = E L^-1 w, y = S^-1 applied to
+// [rhs0, e_1, e_2] (rhs0 depends on the mode, set by the host sequence).
+// Modes (Sec. 2.3-2.4), with ftilde(v) = (S^-1 v)/f0:
+//   GIVEN_S0      f = S^-1 (sb - s0 1 + ew)                      (y0 computed with that rhs)
+//   CIRCULATION   fs = S^-1 (sb + ew), s0 = (<1, fs> - Gamma_b)/Gamma0, f = fs - s0 f0
+//   KUTTA_STEADY  ft* = ftilde(P^Gamma sb + ew), s0 = ft*_k, f = f0 o (ft* - s0)
+//   KUTTA_SHED    ft* as above, ft_j = ftilde(e_j); one edge:
+//                 G1 = (-Gw - f0hat^T P_k ft*) / (1 + f0hat^T P_k ft_1), g = ft* + G1 ft_1, s0 = g_k;
+//                 two edges: 2x2 system of Eq. twovortex, g = ft* + G1 ft_1 + G2 ft_2,
+//                 s0 = (g_k1 + g_k2)/2;  f = f0 o (g - s0)
+__global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, double param, const double* __restrict__ ds,
+                              const double* __restrict__ f0, const double* __restrict__ f0hat,
+                              const double* __restrict__ gamma0p, const double* __restrict__ y,
+                              double* __restrict__ f, double* __restrict__ out_scalars) {
+    __shared__ double sh[256];
+    __shared__ double sc[8];
+    const double Gamma0 = *gamma0p;
+    const double* y0 = y;
+    const double* y1 = y + ns;
+    const double* y2 = y + 2 * ns;
+    if (mode == PF_SHEET_GIVEN_S0) {
+        for (int p = threadIdx.x; p < ns; p += blockDim.x) f[p] = y0[p];
+        if (threadIdx.x == 0) { out_scalars[0] = param; out_scalars[1] = 0.0; out_scalars[2] = 0.0; }
+        return;
+    }
+    if (mode == PF_SHEET_CIRCULATION) {
+        double part = 0.0;
+        for (int p = threadIdx.x; p < ns; p += blockDim.x) part += ds[p] * y0[p];
+        const double circ = block_sum(part, sh);
+        const double s0 = (circ - param) / Gamma0;
+        for (int p = threadIdx.x; p < ns; p += blockDim.x) f[p] = y0[p] - s0 * f0[p];
+        if (threadIdx.x == 0) { out_scalars[0] = s0; out_scalars[1] = 0.0; out_scalars[2] = 0.0; }
+        return;
+    }
+    // Kutta modes: ftilde = y / f0;  f0hat^T ftilde(y_c) = sum ds y_c (since f0hat = ds f0)
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int p = threadIdx.x; p < ns; p += blockDim.x) {
+        a0 += ds[p] * y0[p];
+        if (mode == PF_SHEET_KUTTA_SHED) {
+            a1 += ds[p] * y1[p];
+            if (nedge == 2) a2 += ds[p] * y2[p];
+        }
+    }
+    const double h0 = block_sum(a0, sh);             // f0hat^T ft*
+    const double h1 = block_sum(a1, sh);             // f0hat^T ft_1
+    const double h2 = block_sum(a2, sh);             // f0hat^T ft_2
+    if (threadIdx.x == 0) {
+        const double fs1 = y0[k1] / f0[k1];
+        double G1 = 0.0, G2 = 0.0, s0;
+        if (mode == PF_SHEET_KUTTA_STEADY) {
+            s0 = fs1;
+        } else if (nedge == 1) {
+            const double t1 = y1[k1] / f0[k1];
+            G1 = (-param - (h0 - Gamma0 * fs1)) / (1.0 + (h1 - Gamma0 * t1));
+            s0 = fs1 + G1 * t1;
+        } else {
+            const double fs2 = y0[k2] / f0[k2];
+            const double t11 = y1[k1] / f0[k1], t12 = y2[k1] / f0[k1];
+            const double t21 = y1[k2] / f0[k2], t22 = y2[k2] / f0[k2];
+            // A_ij = 1 + f0hat^T P_ki ft_j,  b_i = -(Gw + f0hat^T P_ki ft*),  f0hat^T P_k v = f0hat^T v - Gamma0 v_k
+            const double A11 = 1.0 + h1 - Gamma0 * t11, A12 = 1.0 + h2 - Gamma0 * t12;
+            const double A21 = 1.0 + h1 - Gamma0 * t21, A22 = 1.0 + h2 - Gamma0 * t22;
+            const double b1 = -(param + h0 - Gamma0 * fs1), b2 = -(param + h0 - Gamma0 * fs2);
+            const double det = A11 * A22 - A12 * A21;
+            G1 = (b1 * A22 - A12 * b2) / det;
+            G2 = (A11 * b2 - A21 * b1) / det;
+            const double g1 = fs1 + G1 * t11 + G2 * t12;
+            const double g2 = fs2 + G1 * t21 + G2 * t22;
+            s0 = 0.5 * (g1 + g2);
+        }
+        sc[0] = s0;
+        sc[1] = G1;
+        sc[2] = G2;
+        out_scalars[0] = s0;
+        out_scalars[1] = G1;
+        out_scalars[2] = G2;
+    }
+    __syncthreads();
+    const double s0 = sc[0], G1 = sc[1], G2 = sc[2];
+    for (int p = threadIdx.x; p < ns; p += blockDim.x) {
+        double g = y0[p] / f0[p];
+        if (mode == PF_SHEET_KUTTA_SHED) {
+            g += G1 * y1[p] / f0[p];
+            if (nedge == 2) g += G2 * y2[p] / f0[p];
+        }
+        f[p] = f0[p] * (g - s0);
+    }
+}
+
+namespace {
+
+// rhs0 for the mode: GIVEN_S0: sb - s0 + ew; CIRCULATION: sb + ew;
+// Kutta: P^Gamma sb + ew = sb - (f0hat^T sb / Gamma0) + ew   (one block)
+__global__ void k_rhs0(int mode, int ns, double param, const double* __restrict__ sb, const double* __restrict__ ew,
+                       const double* __restrict__ f0hat, const double* __restrict__ gamma0p, double* __restrict__ rhs) {
+    __shared__ double sh[256];
+    double shift = 0.0;
+    if (mode == PF_SHEET_GIVEN_S0) shift = param;
+    else if (mode == PF_SHEET_KUTTA_STEADY || mode == PF_SHEET_KUTTA_SHED) {
+        double part = 0.0;
+        for (int p = threadIdx.x; p < ns; p += blockDim.x) part += f0hat[p] * sb[p];
+        shift = block_sum(part, sh) / *gamma0p;
+    }
+    for (int p = threadIdx.x; p < ns; p += blockDim.x) rhs[p] = sb[p] - shift + ew[p];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+static void free_schur(pf_schur s) {
+    void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
+                    s->dgamma0, s->work, s->scal};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+pf_status schur_factor_device(pf_plan p, pf_schur s) {
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    k_surface_stencil<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
+                                                          s->siy, s->swx, s->swy, p->d_status);
+    PF_LAUNCH_CHECK(p);
+    k_schur_build<<<dim3(ceil_div(ns, 128), ns), 128, 0, st>>>(s->six, s->siy, s->swx, s->swy, s->ds, ns, p->G, p->nx,
+                                                                s->S, ns);
+    PF_LAUNCH_CHECK(p);
+    k_augment<<<dim3(ceil_div(2 * ns, 256), ns), 256, 0, st>>>(s->S, s->A, ns);
+    PF_LAUNCH_CHECK(p);
+    // pivots smaller than 1e-300 relative scale are reported as singular
+    for (int k = 0; k < ns; ++k) {
+        k_gj_pivot<<<1, 256, 0, st>>>(s->A, ns, k, 1e-300, p->d_status);
+        k_gj_eliminate<<<ns, 256, 0, st>>>(s->A, ns, k);
+    }
+    PF_LAUNCH_CHECK(p);
+    k_extract_inverse<<<dim3(ceil_div(ns, 256), ns), 256, 0, st>>>(s->A, s->Sinv, ns);
+    PF_LAUNCH_CHECK(p);
+    k_f0<<<1, 256, 0, st>>>(s->Sinv, s->ds, ns, s->f0, s->f0hat, s->dgamma0);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
+pf_status schur_create(pf_plan p, int ns, pf_schur* out) {
+    pf_schur s = new (std::nothrow) pf_schur_s();
+    if (!s) return PF_ERR_OOM;
+    s->plan = p;
+    s->ns = ns;
+    auto fail = [&](pf_status st) { free_schur(s); delete s; return st; };
+#define PF_ALLOC(ptr, bytes)                                                                      \
+    do {                                                                                          \
+        cudaError_t e_ = cudaMalloc(&(ptr), (bytes));                                             \
+        if (e_ != cudaSuccess) {                                                                  \
+            snprintf(p->err, sizeof(p->err), "cudaMalloc: %s", cudaGetErrorString(e_));           \
+            return fail(e_ == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA);               \
+        }                                                                                         \
+    } while (0)
+    const size_t v = (size_t)ns * sizeof(double);
+    PF_ALLOC(s->x, v);
+    PF_ALLOC(s->y, v);
+    PF_ALLOC(s->ds, v);
+    PF_ALLOC(s->six, 4 * (size_t)ns * sizeof(int));
+    PF_ALLOC(s->siy, 4 * (size_t)ns * sizeof(int));
+    PF_ALLOC(s->swx, 4 * v);
+    PF_ALLOC(s->swy, 4 * v);
+    PF_ALLOC(s->S, (size_t)ns * v);
+    PF_ALLOC(s->A, 2 * (size_t)ns * v);
+    PF_ALLOC(s->Sinv, (size_t)ns * v);
+    PF_ALLOC(s->f0, v);
+    PF_ALLOC(s->f0hat, v);
+    PF_ALLOC(s->dgamma0, sizeof(double));
+    PF_ALLOC(s->work, 12 * v);
+    PF_ALLOC(s->scal, 8 * sizeof(double));
+#undef PF_ALLOC
+    *out = s;
+    return PF_OK;
+}
+
+void schur_free(pf_schur s) {
+    free_schur(s);
+    delete s;
+}
+
+// Full sheet solve on device.  psi_w: real field; vx, vy: device positions of
+// the new vortices (mode KUTTA_SHED).  Results: f (device, ns) and scal[0..2] =
+// (s0, Gamma1, Gamma2) on the device.
+pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
+                             int n_edges, const int* edges, const double* vx, const double* vy, double* f) {
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    double* sb = s->work;
+    double* ew = sb + ns;
+    double* rhs = ew + ns;          // rhs0 | e_1 | e_2 contiguous
+    double* y = rhs + 3 * ns;       // S^-1 [rhs0 | e_1 | e_2]
+    k_sbprime<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, m, sb);
+    PF_LAUNCH_CHECK(p);
+    const double dx2 = p->dx * p->dx;
+    if (p->prec == PF_FP64)
+        k_surface_einvlw<double><<<ns, 256, 0, st>>>((const double*)w, p->nx, p->ny, s->six, s->siy, s->swx, s->swy,
+                                                      p->G, dx2, ew);
+    else
+        k_surface_einvlw<float><<<ns, 256, 0, st>>>((const float*)w, p->nx, p->ny, s->six, s->siy, s->swx, s->swy,
+                                                     p->G, dx2, ew);
+    PF_LAUNCH_CHECK(p);
+    k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, sb, ew, s->f0hat, s->dgamma0, rhs);
+    PF_LAUNCH_CHECK(p);
+    int nc = 1;
+    if (mode == PF_SHEET_KUTTA_SHED) {
+        nc = 1 + n_edges;
+        k_unit_vortex<<<dim3(ceil_div(ns, 128), n_edges), 128, 0, st>>>(vx, vy, n_edges, s->six, s->siy, s->swx,
+                                                                           s->swy, ns, p->G, p->nx, p->ny, p->x0, p->y0,
+                                                                           p->dx, rhs + ns, p->d_status);
+        PF_LAUNCH_CHECK(p);
+    }
+    k_gemv<<<ns, 128, 0, st>>>(s->Sinv, ns, rhs, nc, y);
+    PF_LAUNCH_CHECK(p);
+    k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, param,
+                                     s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
+extern "C" {
+
+pf_status pf_schur_factor(pf_plan p, const pf_body_desc* b, pf_schur* out) {
+    if (!p || !b || !out || b->ns < 4 || b->ns > PF_MAX_SURFACE_POINTS || !b->x || !b->y || !b->ds) return PF_ERR_ARG;
+    *out = nullptr;
+    pf_schur s = nullptr;
+    pf_status st = schur_create(p, b->ns, &s);
+    if (st != PF_OK) return st;
+    const size_t v = (size_t)b->ns * sizeof(double);
+    if (cudaMemcpyAsync(s->x, b->x, v, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->y, b->y, v, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->ds, b->ds, v, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) {
+        schur_free(s);
+        return PF_ERR_CUDA;
+    }
+    st = schur_factor_device(p, s);
+    if (st != PF_OK) {
+        schur_free(s);
+        return st;
+    }
+    if (cudaMemcpyAsync(&s->gamma0, s->dgamma0, sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess) {
+        schur_free(s);
+        return PF_ERR_CUDA;
+    }
+    int status = 0;
+    cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (status & (ST_SINGULAR | ST_OUT_OF_DOMAIN)) {
+        cudaMemset(p->d_status, 0, sizeof(int));
+        schur_free(s);
+        return (status & ST_OUT_OF_DOMAIN) ? PF_ERR_OUT_OF_DOMAIN : PF_ERR_SINGULAR;
+    }
+    *out = s;
+    return PF_OK;
+}
+
+pf_status pf_schur_destroy(pf_schur s) {
+    if (!s) return PF_ERR_ARG;
+    cudaStreamSynchronize(s->plan->stream);
+    schur_free(s);
+    return PF_OK;
+}
+
+pf_status pf_schur_info(pf_schur s, double* gamma0, double* f0, double* S) {
+    if (!s) return PF_ERR_ARG;
+    pf_plan p = s->plan;
+    if (gamma0) *gamma0 = s->gamma0;
+    if (f0) PF_CUDA(p, cudaMemcpyAsync(f0, s->f0, (size_t)s->ns * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    if (S)
+        PF_CUDA(p, cudaMemcpyAsync(S, s->S, (size_t)s->ns * s->ns * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    return PF_OK;
+}
+
+pf_status pf_sheet_solve(pf_plan p, pf_schur s, const void* w, const pf_motion* m, int32_t mode, double param,
+                         int32_t n_edges, const int32_t* edges, const double* Xnew, const double* Ynew, double* f,
+                         double* gamma_new, double* s0) {
+    if (!p || !w || !m || !f || mode < PF_SHEET_GIVEN_S0 || mode > PF_SHEET_KUTTA_SHED) return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    const bool kutta = mode == PF_SHEET_KUTTA_STEADY || mode == PF_SHEET_KUTTA_SHED;
+    if (kutta && (n_edges < 1 || n_edges > 2 || !edges || (mode == PF_SHEET_KUTTA_STEADY && n_edges != 1)))
+        return PF_ERR_ARG;
+    if (!kutta) n_edges = 0;
+    for (int e = 0; e < n_edges; ++e)
+        if (edges[e] < 0 || edges[e] >= s->ns) return PF_ERR_ARG;
+    if (mode == PF_SHEET_KUTTA_SHED && (!Xnew || !Ynew)) return PF_ERR_ARG;
+    double* vxy = s->scal + 4;   // device slots for up to two new vortices: x at [4,5], y at [6,7]
+    if (mode == PF_SHEET_KUTTA_SHED) {
+        PF_CUDA(p, cudaMemcpyAsync(vxy, Xnew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(vxy + 2, Ynew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    }
+    pf_status st = sheet_solve_device(p, s, w, *m, mode, param, n_edges, edges, vxy, vxy + 2, f);
+    if (st != PF_OK) return st;
+    double sc[3];
+    PF_CUDA(p, cudaMemcpyAsync(sc, s->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (s0) *s0 = sc[0];
+    if (gamma_new)
+        for (int e = 0; e < (mode == PF_SHEET_KUTTA_SHED ? n_edges : 0); ++e) gamma_new[e] = sc[1 + e];
+    return PF_OK;
+}
+
+}  // extern "C"

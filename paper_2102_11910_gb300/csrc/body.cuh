@@ -1,0 +1,30 @@
+// Internal definitions of the immersed-body path (body.cu).
+#pragma once
+#include "common.cuh"
+
+struct pf_schur_s {
+    pf_plan plan = nullptr;
+    int ns = 0;
+    double* x = nullptr;      // surface points (device, ns)
+    double* y = nullptr;
+    double* ds = nullptr;
+    int* six = nullptr;       // smoothed three-point stencils: node indices and weights (ns x 4)
+    int* siy = nullptr;
+    double* swx = nullptr;
+    double* swy = nullptr;
+    double* S = nullptr;      // Schur complement, row-major ns x ns
+    double* A = nullptr;      // Gauss-Jordan workspace ns x 2 ns
+    double* Sinv = nullptr;   // S^-1
+    double* f0 = nullptr;     // S^-1 1
+    double* f0hat = nullptr;  // dS o f0
+    double* dgamma0 = nullptr;
+    double gamma0 = 0.0;      // host copy of Gamma0
+    double* work = nullptr;   // 12 ns doubles of solve scratch
+    double* scal = nullptr;   // device scalars: s0, Gamma1, Gamma2, -, new-vortex x[2], y[2]
+};
+
+pf_status schur_create(pf_plan p, int ns, pf_schur* out);
+void schur_free(pf_schur s);
+pf_status schur_factor_device(pf_plan p, pf_schur s);
+pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
+                             int n_edges, const int* edges, const double* vx, const double* vy, double* f);

@@ -1,0 +1,152 @@
+"""GPU parity of the immersed-body path (Sec. 2.2-2.4) against the FP64 oracle.
+
+Workload: 128^2 nodes, dx = 0.02, flat plate of chord 1 at 20 deg, 64 surface
+points, 256 vortices (the single-step plate case).  cond(S) is ~6e5 here
+(dS/dx = 0.78 is below the 1-4 range Sec. 2.2.2 recommends), so tolerances on
+the sheet scale with it: FP64 results agree to ~cond * 1e-16; the mixed path,
+whose vorticity field is FP32, must stay within 1e-4 in sheet strength.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2102_11910_gb300 as pf
+from oracle import body as OB
+from oracle import vic as OV
+from oracle.lgf import lgf_table
+from paper_2102_11910_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def case():
+    wl = inputs.plate_vortices_128()
+    gs = wl["grid"]
+    g = OV.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    b = wl["body"]
+    tab = lgf_table(g.nx + 1, g.ny + 1)
+    st = OB.SurfaceStencil(g, b.x, b.y)
+    S = OB.schur_matrix(g, st, b.ds, tab)
+    sch = OB.Schur(S, b.ds)
+    w = OV.regularize(g, wl["X"], wl["Y"], wl["G"])
+    X1 = np.array([b.x[0] - 0.06, b.x[-1] + 0.06])
+    Y1 = np.array([b.y[0] + 0.03, b.y[-1] - 0.03])
+    return dict(wl=wl, gs=gs, g=g, b=b, tab=tab, st=st, S=S, sch=sch, w=w, X1=X1, Y1=Y1,
+                E=OB.EinvL_unit_vortex(g, st, X1, Y1, tab), cond=np.linalg.cond(S))
+
+
+def _oracle_sheet(c, w, mode, motion):
+    """Oracle sheet for vorticity field w (FP64 numpy)."""
+    g, st, b, sch = c["g"], c["st"], c["b"], c["sch"]
+    EinvLw = -OB.interp_surface(st, OV.streamfunction(g, w, c["tab"]))
+    U, V, Om, Ui, Vi = motion
+    sbp = OB.sb_prime(b.x, b.y, U, V, Om, Ui, Vi)
+    Gw = OV.circulation(g, w)
+    k1, k2 = b.edges
+    E = c["E"]
+    if mode == "given":
+        return OB.sheet_given_s0(sch, sbp, EinvLw, 0.3), 0.3, []
+    if mode == "circ":
+        f, s0 = OB.sheet_circulation(sch, sbp, EinvLw, -0.5)
+        return f, s0, []
+    if mode == "steady":
+        f, ft, s0 = OB.sheet_kutta_steady(sch, sbp, EinvLw, k2)
+        return f, s0, []
+    if mode == "shed1":
+        f, ft, s0, G1 = OB.sheet_kutta_shed1(sch, sbp, EinvLw, k2, E[:, 1], Gw)
+        return f, s0, [G1]
+    f, ft, s0, G1, G2 = OB.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+    return f, s0, [G1, G2]
+
+
+def _gpu_sheet(c, plan, schur, w_dev, mode, motion, Gw):
+    b = c["b"]
+    k1, k2 = b.edges
+    if mode == "given":
+        return pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_GIVEN_S0, 0.3)
+    if mode == "circ":
+        return pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_CIRCULATION, -0.5)
+    if mode == "steady":
+        return pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_KUTTA_STEADY, 0.0, [k2])
+    if mode == "shed1":
+        return pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k2],
+                                 c["X1"][1:], c["Y1"][1:])
+    return pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2], c["X1"], c["Y1"])
+
+
+def _plan(c, prec):
+    gs = c["gs"]
+    return pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, prec)
+
+
+def test_schur_factor_matches_oracle(case):
+    c = case
+    plan = _plan(c, pf.PF_FP64)
+    schur = pf.pf_schur_factor(plan, c["b"].x, c["b"].y, c["b"].ds)
+    gamma0, f0, S = pf.pf_schur_info(schur)
+    assert np.abs(S - c["S"]).max() < 1e-13 * np.abs(c["S"]).max()
+    tol = c["cond"] * 1e-15
+    assert rel(f0, c["sch"].f0) < tol
+    assert abs(gamma0 - c["sch"].Gamma0) < tol * abs(c["sch"].Gamma0)
+
+
+@pytest.mark.parametrize("mode", ["given", "circ", "steady", "shed1", "shed2"])
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_sheet_solve_matches_oracle(case, prec, mode):
+    """Same vorticity field on both sides (rounded to the plan's precision)."""
+    c = case
+    plan = _plan(c, prec)
+    schur = pf.pf_schur_factor(plan, c["b"].x, c["b"].y, c["b"].ds)
+    w_dev = torch.from_numpy(c["w"]).to(device="cuda", dtype=plan.dtype).contiguous()
+    w_used = w_dev.double().cpu().numpy()
+    motion = (0.1, -0.2, 0.3, c["wl"]["Uinf"], 0.0)
+    f_ref, s0_ref, g_ref = _oracle_sheet(c, w_used, mode, motion)
+    f, g, s0 = _gpu_sheet(c, plan, schur, w_dev, mode, motion, OV.circulation(c["g"], w_used))
+    tol = c["cond"] * 1e-15
+    assert rel(f.cpu().numpy(), f_ref) < tol
+    assert abs(s0 - s0_ref) < tol * max(1.0, abs(s0_ref))
+    for a, r in zip(g, g_ref):
+        assert abs(a - r) < tol * abs(r)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_two_edge_shedding_from_gpu_vorticity(case, prec):
+    """End to end on the GPU (regularize + sheet) against the oracle from FP64 positions:
+    sheet strength within 1e-4 (mixed) and the Kutta / Kelvin identities hold."""
+    c = case
+    wl = c["wl"]
+    plan = _plan(c, prec)
+    schur = pf.pf_schur_factor(plan, c["b"].x, c["b"].y, c["b"].ds)
+    dev = [torch.from_numpy(a).cuda() for a in (wl["X"], wl["Y"], wl["G"])]
+    w_dev = pf.pf_regularize(plan, *dev)
+    pf.pf_sync(plan)
+    Gw = float(wl["G"].sum())
+    motion = (0.0, 0.0, 0.0, wl["Uinf"], 0.0)
+    f, g, s0 = _gpu_sheet(c, plan, schur, w_dev, "shed2", motion, Gw)
+    f_ref, s0_ref, g_ref = _oracle_sheet(c, c["w"], "shed2", motion)
+    tol = 1e-4 if prec == pf.PF_MIXED else c["cond"] * 1e-15
+    assert rel(f.cpu().numpy(), f_ref) < tol
+    assert rel(g, g_ref) < tol
+    fn = f.cpu().numpy()
+    # Kelvin: bound + new + free circulation = 0 (Eq. kuttasystem3, last row)
+    assert abs(np.dot(c["b"].ds, fn) + sum(g) + Gw) < 1e-9
+    # Kutta: ftilde = f / f0 vanishes at both edges
+    _, f0, _ = pf.pf_schur_info(schur)
+    k1, k2 = c["b"].edges
+    assert abs(fn[k1] / f0[k1]) < 1e-9 * np.abs(fn / f0).max() and abs(fn[k2] / f0[k2]) < 1e-9 * np.abs(fn / f0).max()
+
+
+def test_out_of_grid_body_is_rejected():
+    gs = inputs.centred_grid(64, 64, 0.02)
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, pf.PF_FP64)
+    b = inputs.plate(32, 2.0, 0.0)       # chord longer than the grid
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_schur_factor(plan, b.x, b.y, b.ds)
+    assert e.value.name == "PF_ERR_OUT_OF_DOMAIN"
