@@ -186,6 +186,45 @@ pf_status pf_sheet_solve(pf_plan plan, pf_schur schur, const void* w, const pf_m
                          const double* Xnew, const double* Ynew, double* f, double* gamma_new,
                          double* s0);
 
+/* ------------------------------------------------------- time stepping */
+
+/* Device-resident vortex set (positions and strengths, FP64) with a fixed
+ * capacity; owned by the state, stepped on its plan's stream. */
+pf_status pf_state_create(pf_plan plan, int64_t capacity, pf_state* out);
+pf_status pf_state_destroy(pf_state state);
+/* Load nv vortices from HOST arrays and set the time; clears the shedding
+ * history.  PF_ERR_CAPACITY if nv exceeds the capacity.  Synchronises. */
+pf_status pf_state_set(pf_state state, const double* X, const double* Y, const double* Gam, int64_t nv,
+                       double t);
+/* Copy the current vortices to HOST arrays (each at least nv long; any may be
+ * NULL) and report nv and t.  Synchronises. */
+pf_status pf_state_get(pf_state state, double* X, double* Y, double* Gam, int64_t* nv, double* t);
+
+/* A rigid flat plate of ns points (midpoints of ns equal segments, leading
+ * edge first) and the given chord, pitching about its mid-chord at the origin:
+ * alpha(t) = alpha0 + amp sin(omega t), chord along (cos alpha, -sin alpha),
+ * in the uniform flow (Uinf, Vinf).  ns = 0 means no body. */
+typedef struct {
+    int32_t ns;
+    double chord;
+    double alpha0, amp, omega;
+    double Uinf, Vinf;
+} pf_plate_kinematics;
+
+/* Advance the vortex set by dt.  With a plate, two vortices are released per
+ * step at its edges with the two-edge Kutta condition and Kelvin's theorem
+ * (Eq. twovortex), placed by the rule of Sec. 2.4.2 (first release 10 dt |U|
+ * from the edge along the normal facing the stream, later ones one third of
+ * the way to the previous release), and every vortex is advected with the
+ * velocity of psi = -L^-1 (w + new vortices + R_s f) plus the free stream.
+ * scheme 0: forward Euler (the paper's); 1: Heun's RK2 whose second stage at
+ * t + dt keeps the new strengths and sets the bound circulation to
+ * -sum Gamma (Eq. circsystem).  The plate's S is refactored whenever its pose
+ * changes (every stage of a pitching plate); refactoring synchronises.
+ * PF_ERR_CAPACITY if two more vortices do not fit. */
+pf_status pf_step(pf_plan plan, pf_state state, const pf_plate_kinematics* plate, double dt,
+                  int32_t scheme);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* Regularization for callers that cannot allocate device memory: code running

@@ -253,3 +253,58 @@ def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None,
                                                c(xn.ctypes.data), c(yn.ctypes.data), _ptr(f, torch.float64, "f"),
                                                c(gn.ctypes.data), ctypes.byref(s0)), "pf_sheet_solve", plan.handle)
     return f, list(gn[:ne]), s0.value
+
+
+class State:
+    """Handle of a pf_state (device-resident vortex set)."""
+
+    def __init__(self, plan, capacity):
+        h = ctypes.c_void_p()
+        _native.check(_native.lib().pf_state_create(plan.handle, int(capacity), ctypes.byref(h)), "pf_state_create",
+                      plan.handle)
+        self.plan, self.handle, self.capacity = plan, h, int(capacity)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pf_state_create(plan, capacity):
+    return State(plan, capacity)
+
+
+def pf_state_set(state, X, Y, G, t=0.0):
+    X, Y, G = _host_f64(X), _host_f64(Y), _host_f64(G)
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_state_set(state.handle, c(X.ctypes.data), c(Y.ctypes.data), c(G.ctypes.data),
+                                             len(X), float(t)), "pf_state_set", state.plan.handle)
+
+
+def pf_state_get(state):
+    """(X, Y, G, t) as host numpy arrays."""
+    import numpy as np
+    X = np.empty(state.capacity)
+    Y = np.empty(state.capacity)
+    G = np.empty(state.capacity)
+    nv = ctypes.c_int64()
+    t = ctypes.c_double()
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_state_get(state.handle, c(X.ctypes.data), c(Y.ctypes.data), c(G.ctypes.data),
+                                             ctypes.byref(nv), ctypes.byref(t)), "pf_state_get", state.plan.handle)
+    n = nv.value
+    return X[:n].copy(), Y[:n].copy(), G[:n].copy(), t.value
+
+
+def pf_step(plan, state, dt, ns=0, chord=1.0, alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0, scheme=0):
+    """Advance the state by dt (scheme 0 Euler, 1 RK2) with an optional pitching plate of ns points."""
+    k = _native.PfPlateKinematics(int(ns), float(chord), float(alpha0), float(amp), float(omega), float(Uinf),
+                                  float(Vinf))
+    _native.check(_native.lib().pf_step(plan.handle, state.handle, ctypes.byref(k), float(dt), int(scheme)),
+                  "pf_step", plan.handle)

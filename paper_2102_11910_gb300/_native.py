@@ -37,6 +37,11 @@ SIGNATURES = {
     "pf_schur_destroy": (_c.c_int, [_P]),
     "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
     "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
+    "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
+    "pf_state_destroy": (_c.c_int, [_P]),
+    "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),
+    "pf_state_get": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
+    "pf_step": (_c.c_int, [_P, _P, _P, _D, _I32]),
 }
 
 STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",
@@ -60,6 +65,10 @@ class PfBodyDesc(ctypes.Structure):
 
 class PfMotion(ctypes.Structure):
     _fields_ = [("U", _D), ("V", _D), ("Omega", _D), ("Uinf", _D), ("Vinf", _D)]
+
+
+class PfPlateKinematics(ctypes.Structure):
+    _fields_ = [("ns", _I32), ("chord", _D), ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D)]
 
 
 def header_path():

@@ -315,12 +315,14 @@ __global__ void k_gemv(const double* __restrict__ Sinv, int ns, const double* __
 //                 G1 = (-Gw - f0hat^T P_k ft*) / (1 + f0hat^T P_k ft_1), g = ft* + G1 ft_1, s0 = g_k;
 //                 two edges: 2x2 system of Eq. twovortex, g = ft* + G1 ft_1 + G2 ft_2,
 //                 s0 = (g_k1 + g_k2)/2;  f = f0 o (g - s0)
-__global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, double param, const double* __restrict__ ds,
+__global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, double param_h,
+                              const double* __restrict__ param_d, const double* __restrict__ ds,
                               const double* __restrict__ f0, const double* __restrict__ f0hat,
                               const double* __restrict__ gamma0p, const double* __restrict__ y,
                               double* __restrict__ f, double* __restrict__ out_scalars) {
     __shared__ double sh[256];
     __shared__ double sc[8];
+    const double param = param_d ? *param_d : param_h;
     const double Gamma0 = *gamma0p;
     const double* y0 = y;
     const double* y1 = y + ns;
@@ -398,9 +400,11 @@ namespace {
 
 // rhs0 for the mode: GIVEN_S0: sb - s0 + ew; CIRCULATION: sb + ew;
 // Kutta: P^Gamma sb + ew = sb - (f0hat^T sb / Gamma0) + ew   (one block)
-__global__ void k_rhs0(int mode, int ns, double param, const double* __restrict__ sb, const double* __restrict__ ew,
+__global__ void k_rhs0(int mode, int ns, double param_h, const double* __restrict__ param_d,
+                       const double* __restrict__ sb, const double* __restrict__ ew,
                        const double* __restrict__ f0hat, const double* __restrict__ gamma0p, double* __restrict__ rhs) {
     __shared__ double sh[256];
+    const double param = param_d ? *param_d : param_h;
     double shift = 0.0;
     if (mode == PF_SHEET_GIVEN_S0) shift = param;
     else if (mode == PF_SHEET_KUTTA_STEADY || mode == PF_SHEET_KUTTA_SHED) {
@@ -412,6 +416,44 @@ __global__ void k_rhs0(int mode, int ns, double param, const double* __restrict_
 }
 
 }  // namespace
+
+// R_s f added into a node field: w_n += dx^-2 sum_p dS_p f_p d_p(n) (Sec. 2.2.1).
+// Deterministic: thread (p, s) handles stencil entry s of point p; the first
+// (p, s) in index order that maps to a node sums every entry mapping to it, in
+// index order, and writes the node alone.
+template <typename T>
+__global__ void k_sheet_deposit(const int* __restrict__ six, const int* __restrict__ siy, const double* __restrict__ swx,
+                                const double* __restrict__ swy, const double* __restrict__ ds,
+                                const double* __restrict__ f, int ns, double inv_dx2, int nx, T* __restrict__ w) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 16 * ns) return;
+    const int p = e >> 4, a = e & 3, b = (e >> 2) & 3;
+    const int ni = six[4 * p + a], nj = siy[4 * p + b];
+    for (int e2 = 0; e2 < e; ++e2) {
+        const int p2 = e2 >> 4;
+        if (six[4 * p2 + (e2 & 3)] == ni && siy[4 * p2 + ((e2 >> 2) & 3)] == nj) return;   // not the owner
+    }
+    double acc = 0.0;
+    for (int e2 = e; e2 < 16 * ns; ++e2) {
+        const int p2 = e2 >> 4, a2 = e2 & 3, b2 = (e2 >> 2) & 3;
+        if (six[4 * p2 + a2] == ni && siy[4 * p2 + b2] == nj) acc += ds[p2] * f[p2] * swx[4 * p2 + a2] * swy[4 * p2 + b2];
+    }
+    const size_t n = (size_t)nj * nx + ni;
+    w[n] = (T)((double)w[n] + acc * inv_dx2);
+}
+
+pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
+    const int n = 16 * s->ns;
+    const double inv_dx2 = 1.0 / (p->dx * p->dx);
+    if (p->prec == PF_FP64)
+        k_sheet_deposit<double><<<ceil_div(n, 128), 128, 0, p->stream>>>(s->six, s->siy, s->swx, s->swy, s->ds, f, s->ns,
+                                                                          inv_dx2, p->nx, (double*)w);
+    else
+        k_sheet_deposit<float><<<ceil_div(n, 128), 128, 0, p->stream>>>(s->six, s->siy, s->swx, s->swy, s->ds, f, s->ns,
+                                                                         inv_dx2, p->nx, (float*)w);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
 
 // ---------------------------------------------------------------- host side
 
@@ -490,7 +532,8 @@ void schur_free(pf_schur s) {
 // the new vortices (mode KUTTA_SHED).  Results: f (device, ns) and scal[0..2] =
 // (s0, Gamma1, Gamma2) on the device.
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
-                             int n_edges, const int* edges, const double* vx, const double* vy, double* f) {
+                             const double* param_dev, int n_edges, const int* edges, const double* vx,
+                             const double* vy, double* f) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     double* sb = s->work;
@@ -507,7 +550,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
         k_surface_einvlw<float><<<ns, 256, 0, st>>>((const float*)w, p->nx, p->ny, s->six, s->siy, s->swx, s->swy,
                                                      p->G, dx2, ew);
     PF_LAUNCH_CHECK(p);
-    k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, sb, ew, s->f0hat, s->dgamma0, rhs);
+    k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, param_dev, sb, ew, s->f0hat, s->dgamma0, rhs);
     PF_LAUNCH_CHECK(p);
     int nc = 1;
     if (mode == PF_SHEET_KUTTA_SHED) {
@@ -520,7 +563,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     k_gemv<<<ns, 128, 0, st>>>(s->Sinv, ns, rhs, nc, y);
     PF_LAUNCH_CHECK(p);
     k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, param,
-                                     s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
+                                     param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
@@ -596,7 +639,7 @@ pf_status pf_sheet_solve(pf_plan p, pf_schur s, const void* w, const pf_motion* 
         PF_CUDA(p, cudaMemcpyAsync(vxy, Xnew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
         PF_CUDA(p, cudaMemcpyAsync(vxy + 2, Ynew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     }
-    pf_status st = sheet_solve_device(p, s, w, *m, mode, param, n_edges, edges, vxy, vxy + 2, f);
+    pf_status st = sheet_solve_device(p, s, w, *m, mode, param, nullptr, n_edges, edges, vxy, vxy + 2, f);
     if (st != PF_OK) return st;
     double sc[3];
     PF_CUDA(p, cudaMemcpyAsync(sc, s->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));

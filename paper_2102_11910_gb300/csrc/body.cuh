@@ -26,5 +26,9 @@ struct pf_schur_s {
 pf_status schur_create(pf_plan p, int ns, pf_schur* out);
 void schur_free(pf_schur s);
 pf_status schur_factor_device(pf_plan p, pf_schur s);
+// param_dev (nullable): device copy of `param` read by the kernels instead
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
-                             int n_edges, const int* edges, const double* vx, const double* vy, double* f);
+                             const double* param_dev, int n_edges, const int* edges, const double* vx,
+                             const double* vy, double* f);
+// w += R_s f  (device f of ns doubles, w real[nx*ny])
+pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);

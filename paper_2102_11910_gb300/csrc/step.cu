@@ -1,0 +1,365 @@
+// Vortex state and time stepping (Sec. 2.4.2-2.4.3 of the paper's vortex model).
+//
+// A step with a body (a rigid flat plate, pitching about its mid-chord at the
+// origin) runs entirely on the device:
+//   1. surface points at time t; S factored at that pose (reused while the
+//      pose does not change);
+//   2. w = R_v Gamma of the current vortices;
+//   3. new-vortex positions by the placement rule: the first one from an edge
+//      10 dt |U_inf| from the edge along the edge normal facing the free stream,
+//      later ones one third of the way from the edge to the last one released;
+//   4. two-edge Kutta sheet solve (Eq. twovortex) with Gamma_w = sum Gamma read
+//      on the device;
+//   5. the new vortices are appended, w is rebuilt and R_s f added (Sec. 2.4.3:
+//      psi = -L^-1 (w + G1 d1 + G2 d2 + R_s f));
+//   6. node velocity, interpolation to every vortex, advection.
+// RK2 is Heun's method: stage 2 at t + dt keeps the new strengths and enforces
+// Kelvin's theorem with the circulation-constrained system (Eq. circsystem),
+// bound circulation -sum Gamma, without shedding.
+#include <math.h>
+
+#include <new>
+#include <vector>
+
+#include "body.cuh"
+#include "common.cuh"
+
+struct pf_state_s {
+    pf_plan plan = nullptr;
+    int64_t cap = 0, nv = 0;
+    double t = 0.0;
+    int64_t last[2] = {-1, -1};     // index of the last vortex released at each edge
+    double *X = nullptr, *Y = nullptr, *G = nullptr;
+    double *Xs = nullptr, *Ys = nullptr;            // RK2 predictor positions
+    void *u1 = nullptr, *v1 = nullptr, *u2 = nullptr, *v2 = nullptr;   // velocities (plan precision)
+    double* f = nullptr;            // sheet strength
+    double* red = nullptr;          // reduction scratch: [0] sum Gamma, [1] -sum Gamma, [2..] partials
+    double* newpos = nullptr;       // device x[2], y[2] of the vortices being released
+    pf_schur schur = nullptr;       // factor at the last pose
+    double schur_alpha = NAN;
+    int schur_ns = 0;
+};
+
+namespace {
+
+constexpr int RED_BLOCKS = 64;
+
+// sum of Gamma over nv vortices: fixed partition, fixed reduction tree
+__global__ void k_sum_partial(const double* __restrict__ G, int64_t nv, double* __restrict__ part) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x)
+        s += G[q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        out[0] = s;
+        out[1] = -s;
+    }
+}
+
+struct EdgeGeo {
+    double ex[2], ey[2];     // geometric edge points
+    double nx[2], ny[2];     // unit normal facing the free stream
+    double first_dist;       // 10 dt |U_inf|
+    long long last[2];
+};
+
+__global__ void k_place(const double* __restrict__ X, const double* __restrict__ Y, EdgeGeo e, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 2) return;
+    double x, y;
+    if (e.last[k] < 0) {
+        x = e.ex[k] + e.first_dist * e.nx[k];
+        y = e.ey[k] + e.first_dist * e.ny[k];
+    } else {
+        x = e.ex[k] + (X[e.last[k]] - e.ex[k]) / 3.0;
+        y = e.ey[k] + (Y[e.last[k]] - e.ey[k]) / 3.0;
+    }
+    out[k] = x;
+    out[2 + k] = y;
+}
+
+// append the released vortices: positions from pos (x[2], y[2]), strengths scal[1..2]
+__global__ void k_append(double* __restrict__ X, double* __restrict__ Y, double* __restrict__ G, int64_t nv,
+                         const double* __restrict__ pos, const double* __restrict__ scal) {
+    const int k = threadIdx.x;
+    if (k >= 2) return;
+    X[nv + k] = pos[k];
+    Y[nv + k] = pos[2 + k];
+    G[nv + k] = scal[1 + k];
+}
+
+template <typename T>
+__global__ void k_euler(double* __restrict__ X, double* __restrict__ Y, const T* __restrict__ u, const T* __restrict__ v,
+                        int64_t nv, double dt) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
+        X[q] += dt * (double)u[q];
+        Y[q] += dt * (double)v[q];
+    }
+}
+
+template <typename T>
+__global__ void k_predict(const double* __restrict__ X, const double* __restrict__ Y, const T* __restrict__ u,
+                          const T* __restrict__ v, int64_t nv, double dt, double* __restrict__ Xs,
+                          double* __restrict__ Ys) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
+        Xs[q] = X[q] + dt * (double)u[q];
+        Ys[q] = Y[q] + dt * (double)v[q];
+    }
+}
+
+template <typename T>
+__global__ void k_heun(double* __restrict__ X, double* __restrict__ Y, const T* __restrict__ u1, const T* __restrict__ v1,
+                       const T* __restrict__ u2, const T* __restrict__ v2, int64_t nv, double dt) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
+        X[q] += 0.5 * dt * ((double)u1[q] + (double)u2[q]);
+        Y[q] += 0.5 * dt * ((double)v1[q] + (double)v2[q]);
+    }
+}
+
+void free_state(pf_state s) {
+    void* ptrs[] = {s->X, s->Y, s->G, s->Xs, s->Ys, s->u1, s->v1, s->u2, s->v2, s->f, s->red, s->newpos};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (s->schur) schur_free(s->schur);
+}
+
+int nblocks(int64_t n) { return (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), 152 * 8); }
+
+// plate at time t: points, segment lengths, rotation rate
+struct PlatePose {
+    std::vector<double> x, y, ds;
+    double alpha, Omega;
+};
+
+PlatePose plate_pose(const pf_plate_kinematics& k, double t) {
+    PlatePose P;
+    P.alpha = k.alpha0 + k.amp * sin(k.omega * t);
+    P.Omega = -k.amp * k.omega * cos(k.omega * t);     // the chord direction rotates by -alpha
+    const int ns = k.ns;
+    P.x.resize(ns);
+    P.y.resize(ns);
+    P.ds.assign(ns, k.chord / ns);
+    const double ca = cos(P.alpha), sa = sin(P.alpha);
+    for (int i = 0; i < ns; ++i) {
+        const double xi = -1.0 + (2.0 * (i + 1) - 1.0) / ns;
+        P.x[i] = 0.5 * k.chord * xi * ca;
+        P.y[i] = -0.5 * k.chord * xi * sa;
+    }
+    return P;
+}
+
+pf_status ensure_schur(pf_plan p, pf_state s, const pf_plate_kinematics& k, const PlatePose& P) {
+    if (s->schur && s->schur_ns == k.ns && s->schur_alpha == P.alpha) return PF_OK;
+    if (s->schur) {
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        schur_free(s->schur);
+        s->schur = nullptr;
+    }
+    pf_body_desc b{k.ns, P.x.data(), P.y.data(), P.ds.data()};
+    pf_status st = pf_schur_factor(p, &b, &s->schur);
+    if (st != PF_OK) return st;
+    s->schur_ns = k.ns;
+    s->schur_alpha = P.alpha;
+    return PF_OK;
+}
+
+pf_status sum_gamma(pf_plan p, pf_state s, int64_t n) {
+    k_sum_partial<<<RED_BLOCKS, 256, 0, p->stream>>>(s->G, n, s->red + 2);
+    k_sum_final<<<1, 32, 0, p->stream>>>(s->red + 2, RED_BLOCKS, s->red);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
+#define PF_TRY(x)                   \
+    do {                            \
+        pf_status s_ = (x);         \
+        if (s_ != PF_OK) return s_; \
+    } while (0)
+
+// velocity (plan precision) at the n vortices (X, Y, G) of the current arrays,
+// optionally with a body sheet f added to the source
+pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, int64_t n, pf_schur sch,
+                     const double* f, double Uinf, double Vinf, void* u, void* v) {
+    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
+    if (sch) PF_TRY(sheet_deposit(p, sch, f, p->w));
+    PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
+    return vortex_interpolate_located(p, p->uv, n, u, v);
+}
+
+// one stage with the plate: shed (two-edge Kutta) or Kelvin-constrained
+pf_status body_stage(pf_plan p, pf_state s, const pf_plate_kinematics& k, double t, double dt, const double* X,
+                     const double* Y, bool shed, void* u, void* v) {
+    const PlatePose P = plate_pose(k, t);
+    PF_TRY(ensure_schur(p, s, k, P));
+    pf_schur sch = s->schur;
+    const pf_motion m{0.0, 0.0, P.Omega, k.Uinf, k.Vinf};
+    const int ns = k.ns;
+    int64_t n = s->nv;
+    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
+    PF_TRY(sum_gamma(p, s, n));
+    if (shed) {
+        EdgeGeo e;
+        const int kk[2] = {0, ns - 1};
+        const double U = hypot(k.Uinf, k.Vinf);
+        for (int j = 0; j < 2; ++j) {
+            const int kp = kk[j], nb = j == 0 ? 1 : ns - 2;
+            const double tx = P.x[kp] - P.x[nb], ty = P.y[kp] - P.y[nb];
+            e.ex[j] = P.x[kp] + 0.5 * tx;
+            e.ey[j] = P.y[kp] + 0.5 * ty;
+            double nxv = -ty, nyv = tx;
+            const double nn = hypot(nxv, nyv);
+            nxv /= nn;
+            nyv /= nn;
+            if (nxv * k.Uinf + nyv * k.Vinf < 0.0) { nxv = -nxv; nyv = -nyv; }
+            e.nx[j] = nxv;
+            e.ny[j] = nyv;
+            e.last[j] = s->last[j];
+        }
+        e.first_dist = 10.0 * dt * U;
+        k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
+        PF_LAUNCH_CHECK(p);
+        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos, s->newpos + 2,
+                                  s->f));
+        // release: the new vortices join the arrays X, Y (the caller's position
+        // arrays) and G
+        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, sch->scal);
+        PF_LAUNCH_CHECK(p);
+        n += 2;
+    } else {
+        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_CIRCULATION, 0.0, s->red + 1, 0, nullptr, nullptr, nullptr,
+                                  s->f));
+    }
+    return velocities(p, s, X, Y, n, sch, s->f, k.Uinf, k.Vinf, u, v);
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_state_create(pf_plan p, int64_t cap, pf_state* out) {
+    if (!p || !out || cap < 0) return PF_ERR_ARG;
+    *out = nullptr;
+    pf_state s = new (std::nothrow) pf_state_s();
+    if (!s) return PF_ERR_OOM;
+    s->plan = p;
+    s->cap = cap;
+    const size_t d = (size_t)(cap > 0 ? cap : 1) * sizeof(double), e = (size_t)(cap > 0 ? cap : 1) * p->esz;
+    cudaError_t err = cudaSuccess;
+    for (double** q : {&s->X, &s->Y, &s->G, &s->Xs, &s->Ys})
+        if (err == cudaSuccess) err = cudaMalloc(q, d);
+    for (void** q : {&s->u1, &s->v1, &s->u2, &s->v2})
+        if (err == cudaSuccess) err = cudaMalloc(q, e);
+    if (err == cudaSuccess) err = cudaMalloc(&s->f, PF_MAX_SURFACE_POINTS * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&s->red, (2 + RED_BLOCKS) * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&s->newpos, 4 * sizeof(double));
+    if (err != cudaSuccess) {
+        snprintf(p->err, sizeof(p->err), "pf_state_create: %s", cudaGetErrorString(err));
+        free_state(s);
+        delete s;
+        return err == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
+    }
+    *out = s;
+    return PF_OK;
+}
+
+pf_status pf_state_destroy(pf_state s) {
+    if (!s) return PF_ERR_ARG;
+    cudaStreamSynchronize(s->plan->stream);
+    free_state(s);
+    delete s;
+    return PF_OK;
+}
+
+pf_status pf_state_set(pf_state s, const double* X, const double* Y, const double* G, int64_t nv, double t) {
+    if (!s || nv < 0 || (nv > 0 && (!X || !Y || !G))) return PF_ERR_ARG;
+    if (nv > s->cap) return PF_ERR_CAPACITY;
+    pf_plan p = s->plan;
+    const size_t b = (size_t)nv * sizeof(double);
+    if (nv > 0) {
+        PF_CUDA(p, cudaMemcpyAsync(s->X, X, b, cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(s->Y, Y, b, cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(s->G, G, b, cudaMemcpyHostToDevice, p->stream));
+    }
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    s->nv = nv;
+    s->t = t;
+    s->last[0] = s->last[1] = -1;
+    return PF_OK;
+}
+
+pf_status pf_state_get(pf_state s, double* X, double* Y, double* G, int64_t* nv, double* t) {
+    if (!s) return PF_ERR_ARG;
+    pf_plan p = s->plan;
+    const size_t b = (size_t)s->nv * sizeof(double);
+    if (s->nv > 0) {
+        if (X) PF_CUDA(p, cudaMemcpyAsync(X, s->X, b, cudaMemcpyDeviceToHost, p->stream));
+        if (Y) PF_CUDA(p, cudaMemcpyAsync(Y, s->Y, b, cudaMemcpyDeviceToHost, p->stream));
+        if (G) PF_CUDA(p, cudaMemcpyAsync(G, s->G, b, cudaMemcpyDeviceToHost, p->stream));
+    }
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (nv) *nv = s->nv;
+    if (t) *t = s->t;
+    return PF_OK;
+}
+
+pf_status pf_step(pf_plan p, pf_state s, const pf_plate_kinematics* k, double dt, int32_t scheme) {
+    if (!p || !s || !k || !(dt > 0) || (scheme != 0 && scheme != 1) || k->ns < 0 || k->ns > PF_MAX_SURFACE_POINTS ||
+        (k->ns > 0 && (k->ns < 4 || !(k->chord > 0))))
+        return PF_ERR_ARG;
+    const bool body = k->ns > 0;
+    if (body && s->nv + 2 > s->cap) return PF_ERR_CAPACITY;
+    const int64_t n0 = s->nv;
+    const int nb = nblocks(n0 + 2);
+    if (!body) {
+        PF_TRY(velocities(p, s, s->X, s->Y, n0, nullptr, nullptr, k->Uinf, k->Vinf, s->u1, s->v1));
+        if (scheme == 0) {
+            if (p->prec == PF_FP64) k_euler<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n0, dt);
+            else k_euler<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n0, dt);
+        } else {
+            if (p->prec == PF_FP64) k_predict<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n0, dt, s->Xs, s->Ys);
+            else k_predict<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n0, dt, s->Xs, s->Ys);
+            PF_LAUNCH_CHECK(p);
+            PF_TRY(velocities(p, s, s->Xs, s->Ys, n0, nullptr, nullptr, k->Uinf, k->Vinf, s->u2, s->v2));
+            if (p->prec == PF_FP64) k_heun<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n0, dt);
+            else k_heun<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n0, dt);
+        }
+        PF_LAUNCH_CHECK(p);
+        s->t += dt;
+        return PF_OK;
+    }
+    // stage 1 at t: release two vortices (appended to X, Y, G) and get u1 at all n0 + 2
+    PF_TRY(body_stage(p, s, *k, s->t, dt, s->X, s->Y, true, s->u1, s->v1));
+    const int64_t n1 = n0 + 2;
+    s->nv = n1;
+    if (scheme == 0) {
+        if (p->prec == PF_FP64) k_euler<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt);
+        else k_euler<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt);
+        PF_LAUNCH_CHECK(p);
+    } else {
+        if (p->prec == PF_FP64) k_predict<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt, s->Xs, s->Ys);
+        else k_predict<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt, s->Xs, s->Ys);
+        PF_LAUNCH_CHECK(p);
+        PF_TRY(body_stage(p, s, *k, s->t + dt, dt, s->Xs, s->Ys, false, s->u2, s->v2));
+        if (p->prec == PF_FP64) k_heun<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n1, dt);
+        else k_heun<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n1, dt);
+        PF_LAUNCH_CHECK(p);
+    }
+    s->last[0] = n0;
+    s->last[1] = n0 + 1;
+    s->t += dt;
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -544,24 +544,28 @@ pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const 
 pf_status plan_bin_reserve(pf_plan p, int64_t nv) {
     const size_t psz = p->prec == PF_FP64 ? sizeof(Pos<double>) : sizeof(Pos<float>);
     const size_t rsz = p->prec == PF_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
+    // capacities grow geometrically so a slowly growing vortex set (shedding)
+    // does not reallocate every step
     if (nv > p->pos_cap) {
+        const int64_t cap = std::max<int64_t>(std::max<int64_t>(nv, 2 * p->pos_cap), 4096);
         PF_CUDA(p, cudaStreamSynchronize(p->stream));
         if (p->pos) cudaFree(p->pos);
         p->pos = nullptr;
         p->pos_cap = 0;
-        PF_CUDA(p, cudaMalloc(&p->pos, (size_t)nv * psz));
-        p->pos_cap = nv;
+        PF_CUDA(p, cudaMalloc(&p->pos, (size_t)cap * psz));
+        p->pos_cap = cap;
     }
     if (4 * nv > p->rec_cap) {   // a vortex is entered in at most four tiles
+        const int64_t cap = 4 * p->pos_cap;
         PF_CUDA(p, cudaStreamSynchronize(p->stream));
         if (p->recs) cudaFree(p->recs);
         if (p->ridx) cudaFree(p->ridx);
         p->recs = nullptr;
         p->ridx = nullptr;
         p->rec_cap = 0;
-        PF_CUDA(p, cudaMalloc(&p->recs, (size_t)4 * nv * rsz));
-        PF_CUDA(p, cudaMalloc(&p->ridx, (size_t)4 * nv * sizeof(int)));
-        p->rec_cap = 4 * nv;
+        PF_CUDA(p, cudaMalloc(&p->recs, (size_t)cap * rsz));
+        PF_CUDA(p, cudaMalloc(&p->ridx, (size_t)cap * sizeof(int)));
+        p->rec_cap = cap;
     }
     return PF_OK;
 }
