@@ -200,29 +200,36 @@ pf_status pf_state_set(pf_state state, const double* X, const double* Y, const d
  * NULL) and report nv and t.  Synchronises. */
 pf_status pf_state_get(pf_state state, double* X, double* Y, double* Gam, int64_t* nv, double* t);
 
-/* A rigid flat plate of ns points (midpoints of ns equal segments, leading
- * edge first) and the given chord, pitching about its mid-chord at the origin:
- * alpha(t) = alpha0 + amp sin(omega t), chord along (cos alpha, -sin alpha),
- * in the uniform flow (Uinf, Vinf).  ns = 0 means no body. */
+/* A rigid body given in its own frame (HOST arrays of ns points: coordinates
+ * and segment lengths), turned by the angle -alpha(t) about the origin,
+ * alpha(t) = alpha0 + amp sin(omega t) (for a plate along the body x axis the
+ * chord points along (cos alpha, -sin alpha)), in the uniform flow
+ * (Uinf, Vinf).  n_edges = 2: vortices are released at surface points
+ * edge[0], edge[1] (Kutta, Sec. 2.4.3); n_edges = 0: no release, the bound
+ * circulation is -sum Gamma (Kelvin, Eq. circsystem).  ns = 0 means no body. */
 typedef struct {
     int32_t ns;
-    double chord;
+    const double* xb;
+    const double* yb;
+    const double* ds;
+    int32_t n_edges;
+    int32_t edge[2];
     double alpha0, amp, omega;
     double Uinf, Vinf;
-} pf_plate_kinematics;
+} pf_body_kinematics;
 
-/* Advance the vortex set by dt.  With a plate, two vortices are released per
- * step at its edges with the two-edge Kutta condition and Kelvin's theorem
- * (Eq. twovortex), placed by the rule of Sec. 2.4.2 (first release 10 dt |U|
- * from the edge along the normal facing the stream, later ones one third of
- * the way to the previous release), and every vortex is advected with the
+/* Advance the vortex set by dt.  With a body that has two edges, two vortices
+ * are released per step with the two-edge Kutta condition and Kelvin's
+ * theorem (Eq. twovortex), placed by the rule of Sec. 2.4.2 (first release
+ * 10 dt |U| from the edge along the normal facing the stream, later ones one
+ * third of the way to the previous release); every vortex is advected with the
  * velocity of psi = -L^-1 (w + new vortices + R_s f) plus the free stream.
  * scheme 0: forward Euler (the paper's); 1: Heun's RK2 whose second stage at
  * t + dt keeps the new strengths and sets the bound circulation to
- * -sum Gamma (Eq. circsystem).  The plate's S is refactored whenever its pose
- * changes (every stage of a pitching plate); refactoring synchronises.
+ * -sum Gamma (Eq. circsystem).  S is refactored whenever the pose changes
+ * (every stage of a pitching body); nothing in a step waits for the host.
  * PF_ERR_CAPACITY if two more vortices do not fit. */
-pf_status pf_step(pf_plan plan, pf_state state, const pf_plate_kinematics* plate, double dt,
+pf_status pf_step(pf_plan plan, pf_state state, const pf_body_kinematics* body, double dt,
                   int32_t scheme);
 
 /* ------------------------------------------------ allocation-free variant */

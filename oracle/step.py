@@ -21,33 +21,44 @@ from .vic import regularize, circulation, streamfunction, node_velocity, interpo
 
 
 class Kinematics:
-    """Rigid plate pitching about the origin: alpha(t) = alpha0 + amp sin(omega t).
+    """Rigid body pitching about the origin: alpha(t) = alpha0 + amp sin(omega t).
 
-    The chord points along (cos alpha, -sin alpha); the body rotation angle is
-    -alpha, so Omega = -amp omega cos(omega t).  A static plate has amp = 0.
+    The body is given in its own frame (default: a flat plate of `ns` segment
+    midpoints along x, edges at both ends) and turned by -alpha, so a plate's
+    chord points along (cos alpha, -sin alpha) and Omega = -amp omega cos(omega t).
+    A body with no edges is Kelvin-constrained and releases nothing.
     """
 
-    def __init__(self, ns, chord, alpha0, amp=0.0, omega=0.0, Uinf=1.0, Vinf=0.0):
+    def __init__(self, ns, chord, alpha0, amp=0.0, omega=0.0, Uinf=1.0, Vinf=0.0, body=None):
         self.ns, self.chord, self.alpha0, self.amp, self.omega = ns, chord, alpha0, amp, omega
         self.Uinf, self.Vinf = Uinf, Vinf
+        if body is None:
+            xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+            body = (0.5 * chord * xi, np.zeros(ns), np.full(ns, chord / ns), (0, ns - 1))
+        self.xb, self.yb, self.ds, self.edges = body
 
     def alpha(self, t):
         return self.alpha0 + self.amp * math.sin(self.omega * t)
 
     def surface(self, t):
         a = self.alpha(t)
-        xi = -1.0 + (2.0 * np.arange(1, self.ns + 1) - 1.0) / self.ns
-        x = 0.5 * self.chord * xi * math.cos(a)
-        y = -0.5 * self.chord * xi * math.sin(a)
-        return x, y, np.full(self.ns, self.chord / self.ns), (0, self.ns - 1)
+        ca, sa = math.cos(a), math.sin(a)
+        x = ca * self.xb + sa * self.yb
+        y = -sa * self.xb + ca * self.yb
+        return x, y, self.ds, tuple(self.edges)
 
     def Omega(self, t):
         return -self.amp * self.omega * math.cos(self.omega * t)
 
 
+def _neighbour(k, n):
+    """The surface point next to edge point k, away from the edge."""
+    return 1 if k == 0 else (n - 2 if k == n - 1 else k + 1)
+
+
 def edge_point(xs, ys, k):
     """Geometric edge next to Kutta point k: half a segment beyond it."""
-    nb = k + 1 if k == 0 else k - 1
+    nb = _neighbour(k, len(xs))
     return xs[k] + 0.5 * (xs[k] - xs[nb]), ys[k] + 0.5 * (ys[k] - ys[nb])
 
 
@@ -55,7 +66,7 @@ def new_vortex_position(xs, ys, k, last, dt, Uinf, Vinf):
     """Placement rule of Sec. 2.4.2 for the vortex released at edge k."""
     ex, ey = edge_point(xs, ys, k)
     if last is None:
-        nb = k + 1 if k == 0 else k - 1
+        nb = _neighbour(k, len(xs))
         tx, ty = xs[k] - xs[nb], ys[k] - ys[nb]
         nx_, ny_ = -ty, tx
         nrm = math.hypot(nx_, ny_)
@@ -79,7 +90,7 @@ class BodyState:
 def _solve_and_velocity(grid, table, kin, t, X, Y, G, shed, dt, last_pos):
     """One stage: sheet solve (two-edge Kutta shedding or Kelvin circulation) and
     velocities at all vortices.  Returns (u, v, newX, newY, newG, info)."""
-    xs, ys, ds, (k1, k2) = kin.surface(t)
+    xs, ys, ds, edges = kin.surface(t)
     st = B.SurfaceStencil(grid, xs, ys)
     sch = B.Schur(B.schur_matrix(grid, st, ds, table), ds)
     sbp = B.sb_prime(xs, ys, 0.0, 0.0, kin.Omega(t), kin.Uinf, kin.Vinf)
@@ -87,6 +98,7 @@ def _solve_and_velocity(grid, table, kin, t, X, Y, G, shed, dt, last_pos):
     Gw = circulation(grid, w)
     EinvLw = -B.interp_surface(st, streamfunction(grid, w, table))
     if shed:
+        k1, k2 = edges
         p1 = new_vortex_position(xs, ys, k1, last_pos[0], dt, kin.Uinf, kin.Vinf)
         p2 = new_vortex_position(xs, ys, k2, last_pos[1], dt, kin.Uinf, kin.Vinf)
         nX, nY = np.array([p1[0], p2[0]]), np.array([p1[1], p2[1]])
@@ -105,11 +117,13 @@ def _solve_and_velocity(grid, table, kin, t, X, Y, G, shed, dt, last_pos):
 
 
 def body_step(grid, table, kin, state, dt, scheme="euler"):
-    """Advance the vortex set one step with two-edge Kutta shedding (Sec. 2.4.3)."""
+    """Advance the vortex set one step: two-edge Kutta shedding (Sec. 2.4.3) for
+    a body with two edges, the Kelvin-constrained sheet otherwise."""
     t = state.t
+    release = len(kin.edges) == 2
     last_pos = [None if i is None else (state.X[i], state.Y[i]) for i in state.last]
     u1, v1, nX, nY, nG, info = _solve_and_velocity(grid, table, kin, t, state.X, state.Y, state.G,
-                                                   True, dt, last_pos)
+                                                   release, dt, last_pos)
     X = np.concatenate([state.X, nX])
     Y = np.concatenate([state.Y, nY])
     G = np.concatenate([state.G, nG])
@@ -123,6 +137,7 @@ def body_step(grid, table, kin, state, dt, scheme="euler"):
         raise ValueError(scheme)
     n_old = len(state.X)
     state.X, state.Y, state.G = X, Y, G
-    state.last = [n_old, n_old + 1]
+    if release:
+        state.last = [n_old, n_old + 1]
     state.t = t + dt
     return info

@@ -302,9 +302,37 @@ def pf_state_get(state):
     return X[:n].copy(), Y[:n].copy(), G[:n].copy(), t.value
 
 
-def pf_step(plan, state, dt, ns=0, chord=1.0, alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0, scheme=0):
-    """Advance the state by dt (scheme 0 Euler, 1 RK2) with an optional pitching plate of ns points."""
-    k = _native.PfPlateKinematics(int(ns), float(chord), float(alpha0), float(amp), float(omega), float(Uinf),
-                                  float(Vinf))
-    _native.check(_native.lib().pf_step(plan.handle, state.handle, ctypes.byref(k), float(dt), int(scheme)),
+class BodyKinematics:
+    """A rigid body in its own frame (host arrays), pitching about the origin:
+    world = body turned by -alpha(t), alpha(t) = alpha0 + amp sin(omega t).
+    edges: () for a Kelvin-constrained body, or the two surface-point indices
+    at which vortices are released."""
+
+    def __init__(self, xb, yb, ds, edges=(), alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0):
+        self.xb, self.yb, self.ds = _host_f64(xb), _host_f64(yb), _host_f64(ds)
+        e = list(edges)
+        c = ctypes.c_void_p
+        self.struct = _native.PfBodyKinematics(len(self.xb), c(self.xb.ctypes.data), c(self.yb.ctypes.data),
+                                               c(self.ds.ctypes.data), len(e), (ctypes.c_int32 * 2)(*(e + [0, 0])[:2]),
+                                               float(alpha0), float(amp), float(omega), float(Uinf), float(Vinf))
+
+
+def plate_kinematics(ns, chord=1.0, alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0):
+    """Flat plate along the body x axis (ns segment midpoints, leading edge first),
+    releasing vortices at both ends."""
+    import numpy as np
+    xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+    return BodyKinematics(0.5 * chord * xi, np.zeros(ns), np.full(ns, chord / ns), (0, ns - 1), alpha0, amp, omega,
+                          Uinf, Vinf)
+
+
+def no_body(Uinf=0.0, Vinf=0.0):
+    k = BodyKinematics([], [], [], (), 0.0, 0.0, 0.0, Uinf, Vinf)
+    return k
+
+
+def pf_step(plan, state, dt, body=None, scheme=0):
+    """Advance the state by dt (scheme 0 Euler, 1 RK2) with an optional BodyKinematics."""
+    body = no_body() if body is None else body
+    _native.check(_native.lib().pf_step(plan.handle, state.handle, ctypes.byref(body.struct), float(dt), int(scheme)),
                   "pf_step", plan.handle)

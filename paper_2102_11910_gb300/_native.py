@@ -67,8 +67,9 @@ class PfMotion(ctypes.Structure):
     _fields_ = [("U", _D), ("V", _D), ("Omega", _D), ("Uinf", _D), ("Vinf", _D)]
 
 
-class PfPlateKinematics(ctypes.Structure):
-    _fields_ = [("ns", _I32), ("chord", _D), ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D)]
+class PfBodyKinematics(ctypes.Structure):
+    _fields_ = [("ns", _I32), ("xb", _P), ("yb", _P), ("ds", _P), ("n_edges", _I32), ("edge", _I32 * 2),
+                ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D)]
 
 
 def header_path():

@@ -1,6 +1,6 @@
 // Vortex state and time stepping (Sec. 2.4.2-2.4.3 of the paper's vortex model).
 //
-// A step with a body (a rigid flat plate, pitching about its mid-chord at the
+// A step with a body (rigid, given in its own frame, pitching about the
 // origin) runs entirely on the device:
 //   1. surface points at time t; S factored at that pose (reused while the
 //      pose does not change);
@@ -9,7 +9,7 @@
 //      10 dt |U_inf| from the edge along the edge normal facing the free stream,
 //      later ones one third of the way from the edge to the last one released;
 //   4. two-edge Kutta sheet solve (Eq. twovortex) with Gamma_w = sum Gamma read
-//      on the device;
+//      on the device (bodies without edges: circulation -sum Gamma, no release);
 //   5. the new vortices are appended, w is rebuilt and R_s f added (Sec. 2.4.3:
 //      psi = -L^-1 (w + G1 d1 + G2 d2 + R_s f));
 //   6. node velocity, interpolation to every vortex, advection.
@@ -38,7 +38,14 @@ struct pf_state_s {
     pf_schur schur = nullptr;       // factor at the last pose
     double schur_alpha = NAN;
     int schur_ns = 0;
+    const double* schur_xb = nullptr;   // body the factor belongs to
 };
+
+#define PF_TRY(x)                   \
+    do {                            \
+        pf_status s_ = (x);         \
+        if (s_ != PF_OK) return s_; \
+    } while (0)
 
 namespace {
 
@@ -137,41 +144,47 @@ void free_state(pf_state s) {
 
 int nblocks(int64_t n) { return (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), 152 * 8); }
 
-// plate at time t: points, segment lengths, rotation rate
-struct PlatePose {
-    std::vector<double> x, y, ds;
+// body at time t: world points (body frame turned by -alpha), rotation rate
+struct Pose {
+    std::vector<double> x, y;
     double alpha, Omega;
 };
 
-PlatePose plate_pose(const pf_plate_kinematics& k, double t) {
-    PlatePose P;
+Pose body_pose(const pf_body_kinematics& k, double t) {
+    Pose P;
     P.alpha = k.alpha0 + k.amp * sin(k.omega * t);
-    P.Omega = -k.amp * k.omega * cos(k.omega * t);     // the chord direction rotates by -alpha
-    const int ns = k.ns;
-    P.x.resize(ns);
-    P.y.resize(ns);
-    P.ds.assign(ns, k.chord / ns);
+    P.Omega = -k.amp * k.omega * cos(k.omega * t);     // the body turns by -alpha
     const double ca = cos(P.alpha), sa = sin(P.alpha);
-    for (int i = 0; i < ns; ++i) {
-        const double xi = -1.0 + (2.0 * (i + 1) - 1.0) / ns;
-        P.x[i] = 0.5 * k.chord * xi * ca;
-        P.y[i] = -0.5 * k.chord * xi * sa;
+    P.x.resize(k.ns);
+    P.y.resize(k.ns);
+    for (int i = 0; i < k.ns; ++i) {
+        P.x[i] = ca * k.xb[i] + sa * k.yb[i];
+        P.y[i] = -sa * k.xb[i] + ca * k.yb[i];
     }
     return P;
 }
 
-pf_status ensure_schur(pf_plan p, pf_state s, const pf_plate_kinematics& k, const PlatePose& P) {
-    if (s->schur && s->schur_ns == k.ns && s->schur_alpha == P.alpha) return PF_OK;
-    if (s->schur) {
-        PF_CUDA(p, cudaStreamSynchronize(p->stream));
-        schur_free(s->schur);
-        s->schur = nullptr;
+// factor S at the pose, asynchronously (errors surface at pf_sync); the
+// previous factor is kept while body and angle are unchanged
+pf_status ensure_schur(pf_plan p, pf_state s, const pf_body_kinematics& k, const Pose& P) {
+    if (s->schur && s->schur_ns == k.ns && s->schur_alpha == P.alpha && s->schur_xb == k.xb) return PF_OK;
+    if (!s->schur || s->schur_ns != k.ns) {
+        if (s->schur) {
+            PF_CUDA(p, cudaStreamSynchronize(p->stream));
+            schur_free(s->schur);
+            s->schur = nullptr;
+        }
+        PF_TRY(schur_create(p, k.ns, &s->schur));
     }
-    pf_body_desc b{k.ns, P.x.data(), P.y.data(), P.ds.data()};
-    pf_status st = pf_schur_factor(p, &b, &s->schur);
-    if (st != PF_OK) return st;
+    const size_t v = (size_t)k.ns * sizeof(double);
+    // pageable host sources: the copies complete before the calls return
+    PF_CUDA(p, cudaMemcpyAsync(s->schur->x, P.x.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(s->schur->y, P.y.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(s->schur->ds, k.ds, v, cudaMemcpyHostToDevice, p->stream));
+    PF_TRY(schur_factor_device(p, s->schur));
     s->schur_ns = k.ns;
     s->schur_alpha = P.alpha;
+    s->schur_xb = k.xb;
     return PF_OK;
 }
 
@@ -181,12 +194,6 @@ pf_status sum_gamma(pf_plan p, pf_state s, int64_t n) {
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
-
-#define PF_TRY(x)                   \
-    do {                            \
-        pf_status s_ = (x);         \
-        if (s_ != PF_OK) return s_; \
-    } while (0)
 
 // velocity (plan precision) at the n vortices (X, Y, G) of the current arrays,
 // optionally with a body sheet f added to the source
@@ -198,10 +205,10 @@ pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, in
     return vortex_interpolate_located(p, p->uv, n, u, v);
 }
 
-// one stage with the plate: shed (two-edge Kutta) or Kelvin-constrained
-pf_status body_stage(pf_plan p, pf_state s, const pf_plate_kinematics& k, double t, double dt, const double* X,
+// one stage with the body: shed (two-edge Kutta) or Kelvin-constrained
+pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double t, double dt, const double* X,
                      const double* Y, bool shed, void* u, void* v) {
-    const PlatePose P = plate_pose(k, t);
+    const Pose P = body_pose(k, t);
     PF_TRY(ensure_schur(p, s, k, P));
     pf_schur sch = s->schur;
     const pf_motion m{0.0, 0.0, P.Omega, k.Uinf, k.Vinf};
@@ -211,10 +218,11 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_plate_kinematics& k, double
     PF_TRY(sum_gamma(p, s, n));
     if (shed) {
         EdgeGeo e;
-        const int kk[2] = {0, ns - 1};
+        const int kk[2] = {k.edge[0], k.edge[1]};
         const double U = hypot(k.Uinf, k.Vinf);
         for (int j = 0; j < 2; ++j) {
-            const int kp = kk[j], nb = j == 0 ? 1 : ns - 2;
+            // the neighbour along the surface away from the edge
+            const int kp = kk[j], nb = kp == 0 ? 1 : (kp == ns - 1 ? ns - 2 : kp + 1);
             const double tx = P.x[kp] - P.x[nb], ty = P.y[kp] - P.y[nb];
             e.ex[j] = P.x[kp] + 0.5 * tx;
             e.ey[j] = P.y[kp] + 0.5 * ty;
@@ -314,12 +322,16 @@ pf_status pf_state_get(pf_state s, double* X, double* Y, double* G, int64_t* nv,
     return PF_OK;
 }
 
-pf_status pf_step(pf_plan p, pf_state s, const pf_plate_kinematics* k, double dt, int32_t scheme) {
-    if (!p || !s || !k || !(dt > 0) || (scheme != 0 && scheme != 1) || k->ns < 0 || k->ns > PF_MAX_SURFACE_POINTS ||
-        (k->ns > 0 && (k->ns < 4 || !(k->chord > 0))))
+pf_status pf_step(pf_plan p, pf_state s, const pf_body_kinematics* k, double dt, int32_t scheme) {
+    if (!p || !s || !k || !(dt > 0) || (scheme != 0 && scheme != 1) || k->ns < 0 || k->ns > PF_MAX_SURFACE_POINTS)
         return PF_ERR_ARG;
     const bool body = k->ns > 0;
-    if (body && s->nv + 2 > s->cap) return PF_ERR_CAPACITY;
+    if (body && (k->ns < 4 || !k->xb || !k->yb || !k->ds || (k->n_edges != 0 && k->n_edges != 2))) return PF_ERR_ARG;
+    if (body && k->n_edges == 2)
+        for (int e = 0; e < 2; ++e)
+            if (k->edge[e] < 0 || k->edge[e] >= k->ns) return PF_ERR_ARG;
+    const bool release = body && k->n_edges == 2;
+    if (release && s->nv + 2 > s->cap) return PF_ERR_CAPACITY;
     const int64_t n0 = s->nv;
     const int nb = nblocks(n0 + 2);
     if (!body) {
@@ -340,8 +352,8 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_plate_kinematics* k, double dt
         return PF_OK;
     }
     // stage 1 at t: release two vortices (appended to X, Y, G) and get u1 at all n0 + 2
-    PF_TRY(body_stage(p, s, *k, s->t, dt, s->X, s->Y, true, s->u1, s->v1));
-    const int64_t n1 = n0 + 2;
+    PF_TRY(body_stage(p, s, *k, s->t, dt, s->X, s->Y, release, s->u1, s->v1));
+    const int64_t n1 = n0 + (release ? 2 : 0);
     s->nv = n1;
     if (scheme == 0) {
         if (p->prec == PF_FP64) k_euler<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt);
@@ -356,8 +368,10 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_plate_kinematics* k, double dt
         else k_heun<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n1, dt);
         PF_LAUNCH_CHECK(p);
     }
-    s->last[0] = n0;
-    s->last[1] = n0 + 1;
+    if (release) {
+        s->last[0] = n0;
+        s->last[1] = n0 + 1;
+    }
     s->t += dt;
     return PF_OK;
 }

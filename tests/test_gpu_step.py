@@ -35,8 +35,8 @@ def test_plate_shedding_steps_match_oracle(prec, scheme, amp):
     pf.pf_state_set(state, np.zeros(0), np.zeros(0), np.zeros(0), 0.0)
     for _ in range(nsteps):
         OS.body_step(og, tab, kin, ost, dt, scheme)
-        pf.pf_step(plan, state, dt, ns=ns, chord=1.0, alpha0=math.radians(30.0), amp=math.radians(amp), omega=1.0,
-                   Uinf=1.0, scheme=0 if scheme == "euler" else 1)
+        pf.pf_step(plan, state, dt, pf.plate_kinematics(ns, 1.0, math.radians(30.0), math.radians(amp), 1.0, 1.0),
+                   scheme=0 if scheme == "euler" else 1)
     pf.pf_sync(plan)
     X, Y, G, t = pf.pf_state_get(state)
     assert len(X) == 2 * nsteps and abs(t - nsteps * dt) < 1e-14
@@ -49,6 +49,32 @@ def test_plate_shedding_steps_match_oracle(prec, scheme, amp):
     assert G[1] > 0 and G[0] < 0
 
 
+@pytest.mark.parametrize("prec,scheme", [(pf.PF_FP64, 0), (pf.PF_FP64, 1), (pf.PF_MIXED, 1)])
+def test_pitching_ellipse_with_vortices_matches_oracle(prec, scheme):
+    """Kelvin-constrained body (no edges): ellipse of aspect 3 pitching in a stream,
+    with free vortices around it."""
+    g, plan, og, tab = _setup(prec)
+    e = inputs.ellipse(60, 0.45, 0.15)
+    rng = np.random.default_rng(4)
+    ang = rng.uniform(0, 2 * np.pi, 40)
+    rad = rng.uniform(0.55, 0.8, 40)
+    X, Y, G = rad * np.cos(ang), rad * np.sin(ang), rng.normal(0, 0.03, 40)
+    kin = OS.Kinematics(60, 1.0, 0.3, amp=0.1, omega=2.0, Uinf=1.0, body=(e.x, e.y, e.ds, ()))
+    ost = OS.BodyState()
+    ost.X, ost.Y, ost.G = X.copy(), Y.copy(), G.copy()
+    state = pf.State(plan, 64)
+    pf.pf_state_set(state, X, Y, G, 0.0)
+    bk = pf.BodyKinematics(e.x, e.y, e.ds, (), 0.3, 0.1, 2.0, 1.0)
+    for _ in range(2):
+        OS.body_step(og, tab, kin, ost, 0.02, "euler" if scheme == 0 else "rk2")
+        pf.pf_step(plan, state, 0.02, bk, scheme=scheme)
+    pf.pf_sync(plan)
+    Xg, Yg, Gg, t = pf.pf_state_get(state)
+    assert len(Xg) == 40 and np.array_equal(Gg, G)
+    tx = 1e-11 if prec == pf.PF_FP64 else 1e-6
+    assert np.abs(Xg - ost.X).max() < tx and np.abs(Yg - ost.Y).max() < tx
+
+
 @pytest.mark.parametrize("prec,scheme", [(pf.PF_FP64, 0), (pf.PF_MIXED, 1)])
 def test_body_free_step_matches_oracle(prec, scheme):
     g, plan, og, tab = _setup(prec, n=64, dx=2.0 / 63)
@@ -57,7 +83,7 @@ def test_body_free_step_matches_oracle(prec, scheme):
     dt = 0.05
     state = pf.State(plan, 256)
     pf.pf_state_set(state, X, Y, G, 0.0)
-    pf.pf_step(plan, state, dt, Uinf=0.2, scheme=scheme)
+    pf.pf_step(plan, state, dt, pf.no_body(0.2), scheme=scheme)
     pf.pf_sync(plan)
     Xg, Yg, Gg, t = pf.pf_state_get(state)
     _, _, u1, v1 = OV.vortex_velocity(og, X, Y, G, 0.2, 0.0, tab)
@@ -76,5 +102,5 @@ def test_step_capacity_is_enforced():
     state = pf.State(plan, 3)
     pf.pf_state_set(state, np.zeros(2), np.zeros(2), np.zeros(2), 0.0)
     with pytest.raises(pf.GridPfError) as e:
-        pf.pf_step(plan, state, 0.01, ns=16, chord=1.0, alpha0=0.3, Uinf=1.0)
+        pf.pf_step(plan, state, 0.01, pf.plate_kinematics(16, 1.0, 0.3, Uinf=1.0))
     assert e.value.name == "PF_ERR_CAPACITY"
