@@ -65,6 +65,12 @@ typedef struct pf_state_s* pf_state;
 pf_status pf_plan_create(const pf_grid_desc* desc, void* stream, pf_plan* out);
 pf_status pf_plan_destroy(pf_plan plan);
 
+/* A plan for the same grid that shares the source's read-only tables (LGF
+ * table and spectra, reference counted) but has its own workspaces, stream
+ * and precision: many instances of one grid shape cost one set of tables.
+ * The tables live until the last plan sharing them is destroyed. */
+pf_status pf_plan_clone(pf_plan src, int32_t precision, void* stream, pf_plan* out);
+
 /* Padded FFT sizes chosen for the plan (host ints). */
 pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
 
@@ -231,6 +237,60 @@ typedef struct {
  * PF_ERR_CAPACITY if two more vortices do not fit. */
 pf_status pf_step(pf_plan plan, pf_state state, const pf_body_kinematics* body, double dt,
                   int32_t scheme);
+
+/* Independent instances, one step each: pf_step for plans[i], states[i],
+ * bodies[i] (i < n), each enqueued on its own plan's stream so instances on
+ * distinct streams overlap on the device.  Stops at the first error. */
+pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
+                        double dt, int32_t scheme);
+
+/* ------------------------------------------------------- request server */
+
+/* Continuous batching of independent time-stepping requests on one GPU.
+ * Requests are admitted in submission order while fewer than max_slots are
+ * running and the device memory of the resident instances (their grids'
+ * LGF tables and spectra, and per instance the plan workspaces, vortex bins,
+ * state and Schur factor) stays within hbm_budget_bytes; idle instances are
+ * kept for reuse by later requests of the same grid and evicted least
+ * recently used first.  Every admitted request runs on its own stream, all of
+ * its steps enqueued at admission, so requests overlap on the device.  The
+ * kernels are deterministic and instances share no mutable data: a request's
+ * result does not depend on what else is running. */
+typedef struct pf_server_s* pf_server;
+
+typedef struct {
+    int32_t max_slots;
+    int64_t hbm_budget_bytes;
+    int32_t precision;           /* pf_precision of every instance */
+} pf_server_config;
+
+typedef struct {
+    pf_grid_desc grid;           /* its precision field is ignored */
+    pf_body_kinematics body;     /* ns = 0: no body; arrays are copied at submission */
+    const double* X;             /* initial vortices (host, nv each), copied at submission */
+    const double* Y;
+    const double* Gam;
+    int64_t nv;
+    int64_t capacity;            /* >= nv (+ 2 nsteps for a body with two edges) */
+    int32_t nsteps;
+    double dt;
+    int32_t scheme;              /* as pf_step */
+} pf_request;
+
+pf_status pf_server_create(const pf_server_config* cfg, pf_server* out);
+pf_status pf_server_destroy(pf_server server);
+/* Queue a request (admitting what fits) and return its ticket. */
+pf_status pf_server_submit(pf_server server, const pf_request* req, int64_t* ticket);
+/* Non-blocking progress: retire finished requests and admit queued ones.  Up
+ * to max tickets of requests finished since the last call are written to
+ * tickets (host), their number to n_done. */
+pf_status pf_server_progress(pf_server server, int32_t max, int64_t* tickets, int32_t* n_done);
+/* A finished request's final vortices (host arrays of at least nv entries; any
+ * may be NULL), nv, and latency from submission to completion in seconds.
+ * Returns the request's status; the request is then forgotten. */
+pf_status pf_server_result(pf_server server, int64_t ticket, double* X, double* Y, double* Gam,
+                           int64_t* nv, double* latency_s);
+pf_status pf_server_stats(pf_server server, int32_t* queued, int32_t* active, int64_t* used_bytes);
 
 /* ------------------------------------------------ allocation-free variant */
 

@@ -65,6 +65,22 @@ class Plan:
         return torch.empty(shape, dtype=self.dtype, device="cuda")
 
 
+def pf_plan_clone(src, precision=None, stream=None):
+    """A plan on `stream` sharing src's LGF tables and spectra (own workspaces)."""
+    precision = src.precision if precision is None else int(precision)
+    stream = torch.cuda.current_stream() if stream is None else stream
+    p = Plan.__new__(Plan)
+    p.stream = stream
+    p.nx, p.ny, p.dx, p.x0, p.y0, p.P, p.Q = src.nx, src.ny, src.dx, src.x0, src.y0, src.P, src.Q
+    p.precision = precision
+    p.dtype = torch.float64 if precision == PF_FP64 else torch.float32
+    h = ctypes.c_void_p()
+    _native.check(_native.lib().pf_plan_clone(src.handle, precision, ctypes.c_void_p(stream.cuda_stream),
+                                              ctypes.byref(h)), "pf_plan_clone", src.handle)
+    p.handle = h
+    return p
+
+
 def pf_plan_create(nx, ny, dx, x0, y0, precision=PF_MIXED, stream=None):
     return Plan(nx, ny, dx, x0, y0, precision, stream)
 
@@ -336,3 +352,84 @@ def pf_step(plan, state, dt, body=None, scheme=0):
     body = no_body() if body is None else body
     _native.check(_native.lib().pf_step(plan.handle, state.handle, ctypes.byref(body.struct), float(dt), int(scheme)),
                   "pf_step", plan.handle)
+
+
+def pf_step_batch(plans, states, bodies, dt, scheme=0):
+    """One step of many independent instances (each on its own plan's stream)."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    S = (ctypes.c_void_p * n)(*[s.handle.value for s in states])
+    B = (_native.PfBodyKinematics * n)(*[b.struct for b in bodies])
+    _native.check(_native.lib().pf_step_batch(n, P, S, B, float(dt), int(scheme)), "pf_step_batch")
+
+
+class Server:
+    """Request server (pf_server): continuous batching of time-stepping requests."""
+
+    def __init__(self, max_slots=16, hbm_budget_bytes=8 << 30, precision=PF_MIXED):
+        cfg = _native.PfServerConfig(int(max_slots), int(hbm_budget_bytes), int(precision))
+        h = ctypes.c_void_p()
+        _native.check(_native.lib().pf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pf_server_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pf_server_submit(server, grid, X, Y, G, nsteps, dt, body=None, capacity=None, scheme=0):
+    """grid: (nx, ny, dx, x0, y0).  Returns the ticket."""
+    body = no_body() if body is None else body
+    X, Y, G = _host_f64(X), _host_f64(Y), _host_f64(G)
+    nv = len(X)
+    if capacity is None:
+        capacity = nv + (2 * nsteps if len(body.xb) and body.struct.n_edges == 2 else 0)
+    c = ctypes.c_void_p
+    req = _native.PfRequest(_native.PfGridDesc(int(grid[0]), int(grid[1]), float(grid[2]), float(grid[3]),
+                                               float(grid[4]), 0), body.struct,
+                            c(X.ctypes.data), c(Y.ctypes.data), c(G.ctypes.data), nv, int(capacity), int(nsteps),
+                            float(dt), int(scheme))
+    t = ctypes.c_int64()
+    _native.check(_native.lib().pf_server_submit(server.handle, ctypes.byref(req), ctypes.byref(t)),
+                  "pf_server_submit")
+    return t.value
+
+
+def pf_server_progress(server, max_done=1024):
+    buf = (ctypes.c_int64 * max_done)()
+    n = ctypes.c_int32()
+    _native.check(_native.lib().pf_server_progress(server.handle, max_done, buf, ctypes.byref(n)),
+                  "pf_server_progress")
+    return list(buf[:n.value])
+
+
+def pf_server_result(server, ticket, capacity):
+    """(X, Y, G, latency_s) of a finished request; raises on its error status."""
+    import numpy as np
+    X = np.empty(max(capacity, 1))
+    Y = np.empty(max(capacity, 1))
+    G = np.empty(max(capacity, 1))
+    nv = ctypes.c_int64()
+    lat = ctypes.c_double()
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_server_result(server.handle, int(ticket), c(X.ctypes.data), c(Y.ctypes.data),
+                                                 c(G.ctypes.data), ctypes.byref(nv), ctypes.byref(lat)),
+                  "pf_server_result")
+    n = nv.value
+    return X[:n].copy(), Y[:n].copy(), G[:n].copy(), lat.value
+
+
+def pf_server_stats(server):
+    q = ctypes.c_int32()
+    a = ctypes.c_int32()
+    u = ctypes.c_int64()
+    _native.check(_native.lib().pf_server_stats(server.handle, ctypes.byref(q), ctypes.byref(a), ctypes.byref(u)),
+                  "pf_server_stats")
+    return q.value, a.value, u.value

@@ -42,6 +42,14 @@ SIGNATURES = {
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),
     "pf_state_get": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
     "pf_step": (_c.c_int, [_P, _P, _P, _D, _I32]),
+    "pf_step_batch": (_c.c_int, [_I32, _P, _P, _P, _D, _I32]),
+    "pf_plan_clone": (_c.c_int, [_P, _I32, _P, _c.POINTER(_P)]),
+    "pf_server_create": (_c.c_int, [_P, _c.POINTER(_P)]),
+    "pf_server_destroy": (_c.c_int, [_P]),
+    "pf_server_submit": (_c.c_int, [_P, _P, _c.POINTER(_I64)]),
+    "pf_server_progress": (_c.c_int, [_P, _I32, _P, _c.POINTER(_I32)]),
+    "pf_server_result": (_c.c_int, [_P, _I64, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
+    "pf_server_stats": (_c.c_int, [_P, _c.POINTER(_I32), _c.POINTER(_I32), _c.POINTER(_I64)]),
 }
 
 STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",
@@ -70,6 +78,15 @@ class PfMotion(ctypes.Structure):
 class PfBodyKinematics(ctypes.Structure):
     _fields_ = [("ns", _I32), ("xb", _P), ("yb", _P), ("ds", _P), ("n_edges", _I32), ("edge", _I32 * 2),
                 ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D)]
+
+
+class PfServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", _I32), ("hbm_budget_bytes", _I64), ("precision", _I32)]
+
+
+class PfRequest(ctypes.Structure):
+    _fields_ = [("grid", PfGridDesc), ("body", PfBodyKinematics), ("X", _P), ("Y", _P), ("Gam", _P), ("nv", _I64),
+                ("capacity", _I64), ("nsteps", _I32), ("dt", _D), ("scheme", _I32)]
 
 
 def header_path():

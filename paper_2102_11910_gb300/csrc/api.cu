@@ -18,11 +18,17 @@ int next_pow2(int v) {
 void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
-    void* ptrs[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32, p->twQ32, p->tw256_64, p->tw256_32,
-                    p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start,
-                    p->pos, p->recs, p->ridx, p->stage, p->stage_out, p->d_status, p->d_oob};
-    for (void* q : ptrs)
+    void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start,
+                   p->pos, p->recs, p->ridx, p->stage, p->stage_out, p->d_status, p->d_oob};
+    for (void* q : own)
         if (q) cudaFree(q);
+    if (p->shared && --p->shared->refs == 0) {
+        void* tables[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32,
+                          p->twQ32, p->tw256_64, p->tw256_32};
+        for (void* q : tables)
+            if (q) cudaFree(q);
+        delete p->shared;
+    }
 }
 
 template <typename C>
@@ -54,8 +60,12 @@ pf_status upload(pf_plan p, T** dst, const std::vector<T>& src) {
         if (s_ != PF_OK) return s_;        \
     } while (0)
 
+pf_status plan_workspaces(pf_plan p);
+
 pf_status plan_init(pf_plan p) {
     const int nx = p->nx, ny = p->ny, P = p->P, Q = p->Q;
+    p->shared = new (std::nothrow) PlanTables();
+    if (!p->shared) return PF_ERR_OOM;
     PF_CUDA(p, cudaMalloc(&p->G, (size_t)(nx + 1) * (ny + 1) * sizeof(double)));
     const size_t hq = (size_t)(P / 2 + 1) * (Q / 2 + 1);
     for (double** h : {&p->H64, &p->Hu64, &p->Hv64}) PF_CUDA(p, cudaMalloc(h, hq * sizeof(double)));
@@ -73,6 +83,13 @@ pf_status plan_init(pf_plan p) {
     twiddles(t256f, 256);
     PF_TRY(upload(p, &p->tw256_64, t256d));
     PF_TRY(upload(p, &p->tw256_32, t256f));
+    PF_TRY(plan_workspaces(p));
+    return lgf_build(p);
+}
+
+// per-plan buffers (not shared between clones)
+pf_status plan_workspaces(pf_plan p) {
+    const int nx = p->nx, ny = p->ny, P = p->P;
     p->esz = p->prec == PF_FP64 ? 8 : 4;
     p->ldT = (ny + 3) / 4 * 4;
     const size_t spec = (size_t)(P / 2 + 1) * p->ldT * 2 * p->esz;
@@ -93,7 +110,7 @@ pf_status plan_init(pf_plan p) {
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
     PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
     PF_CUDA(p, cudaMemset(p->d_oob, 0, sizeof(unsigned long long)));
-    return lgf_build(p);
+    return PF_OK;
 }
 
 }  // namespace
@@ -124,6 +141,35 @@ pf_status pf_plan_create(const pf_grid_desc* d, void* stream, pf_plan* out) {
     p->Q = next_pow2(2 * d->ny);
     p->stream = (cudaStream_t)stream;
     pf_status s = plan_init(p);
+    if (s != PF_OK) {
+        free_plan(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return PF_OK;
+}
+
+pf_status pf_plan_clone(pf_plan src, int32_t precision, void* stream, pf_plan* out) {
+    if (!src || !out || (precision != PF_FP64 && precision != PF_MIXED)) return PF_ERR_ARG;
+    *out = nullptr;
+    pf_plan p = new (std::nothrow) pf_plan_s();
+    if (!p) return PF_ERR_OOM;
+    p->nx = src->nx; p->ny = src->ny; p->P = src->P; p->Q = src->Q; p->dx = src->dx; p->x0 = src->x0;
+    p->y0 = src->y0; p->prec = precision;
+    p->stream = (cudaStream_t)stream;
+    p->shared = src->shared;
+    p->shared->refs++;
+    p->G = src->G; p->H64 = src->H64; p->H32 = src->H32; p->Hu64 = src->Hu64; p->Hv64 = src->Hv64;
+    p->Hu32 = src->Hu32; p->Hv32 = src->Hv32; p->twP64 = src->twP64; p->twQ64 = src->twQ64; p->twP32 = src->twP32;
+    p->twQ32 = src->twQ32; p->tw256_64 = src->tw256_64; p->tw256_32 = src->tw256_32;
+    // make sure the source's tables are complete before another stream reads them
+    if (cudaStreamSynchronize(src->stream) != cudaSuccess) {
+        free_plan(p);
+        delete p;
+        return PF_ERR_CUDA;
+    }
+    pf_status s = plan_workspaces(p);
     if (s != PF_OK) {
         free_plan(p);
         delete p;

@@ -32,3 +32,8 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
                              const double* vy, double* f);
 // w += R_s f  (device f of ns doubles, w real[nx*ny])
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);
+
+// step.cu: asynchronous state transfers used by the request server
+pf_status state_load_async(pf_state s, const double* X, const double* Y, const double* G, int64_t nv, double t);
+pf_status state_store_async(pf_state s, double* X, double* Y, double* G, int64_t* nv);
+int64_t state_capacity(pf_state s);

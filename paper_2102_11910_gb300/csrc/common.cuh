@@ -50,7 +50,13 @@ struct KTiming {
 // ------------------------------------------------------------ plan
 constexpr int BIN_TILE = 32;   // node tile edge used by binning and regularization
 
+// Read-only tables of one grid shape, shared by a plan and its clones.
+struct PlanTables {
+    int refs = 1;
+};
+
 struct pf_plan_s {
+    PlanTables* shared = nullptr;  // owner of G, H*, twiddles (reference counted)
     int nx = 0, ny = 0, P = 0, Q = 0, prec = PF_FP64;
     double dx = 0, x0 = 0, y0 = 0;
     cudaStream_t stream = nullptr;

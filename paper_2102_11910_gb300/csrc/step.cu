@@ -254,6 +254,38 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
 
 }  // namespace
 
+// enqueue a state load from pinned host arrays on the plan's stream (no sync)
+pf_status state_load_async(pf_state s, const double* X, const double* Y, const double* G, int64_t nv, double t) {
+    if (nv > s->cap) return PF_ERR_CAPACITY;
+    pf_plan p = s->plan;
+    const size_t b = (size_t)nv * sizeof(double);
+    if (nv > 0) {
+        PF_CUDA(p, cudaMemcpyAsync(s->X, X, b, cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(s->Y, Y, b, cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(s->G, G, b, cudaMemcpyHostToDevice, p->stream));
+    }
+    s->nv = nv;
+    s->t = t;
+    s->last[0] = s->last[1] = -1;
+    s->schur_xb = nullptr;
+    return PF_OK;
+}
+
+// enqueue a copy of the current vortices to pinned host arrays (no sync)
+pf_status state_store_async(pf_state s, double* X, double* Y, double* G, int64_t* nv) {
+    pf_plan p = s->plan;
+    const size_t b = (size_t)s->nv * sizeof(double);
+    if (s->nv > 0) {
+        PF_CUDA(p, cudaMemcpyAsync(X, s->X, b, cudaMemcpyDeviceToHost, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(Y, s->Y, b, cudaMemcpyDeviceToHost, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(G, s->G, b, cudaMemcpyDeviceToHost, p->stream));
+    }
+    *nv = s->nv;
+    return PF_OK;
+}
+
+int64_t state_capacity(pf_state s) { return s->cap; }
+
 extern "C" {
 
 pf_status pf_state_create(pf_plan p, int64_t cap, pf_state* out) {
@@ -304,6 +336,7 @@ pf_status pf_state_set(pf_state s, const double* X, const double* Y, const doubl
     s->nv = nv;
     s->t = t;
     s->last[0] = s->last[1] = -1;
+    s->schur_xb = nullptr;          // a new history may come with a new body
     return PF_OK;
 }
 
@@ -373,6 +406,18 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_body_kinematics* k, double dt,
         s->last[1] = n0 + 1;
     }
     s->t += dt;
+    return PF_OK;
+}
+
+pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies, double dt,
+                        int32_t scheme) {
+    if (n < 0 || (n > 0 && (!plans || !states || !bodies))) return PF_ERR_ARG;
+    // every instance is enqueued on its own plan's stream; distinct streams run
+    // concurrently on the device
+    for (int32_t i = 0; i < n; ++i) {
+        const pf_status st = pf_step(plans[i], states[i], &bodies[i], dt, scheme);
+        if (st != PF_OK) return st;
+    }
     return PF_OK;
 }
 

@@ -586,6 +586,9 @@ BinWork plan_binwork(pf_plan p) {
 
 }  // namespace
 
+// size the plan's vortex buffers for nv vortices ahead of time
+pf_status plan_reserve_vortices(pf_plan p, int64_t nv) { return plan_bin_reserve(p, nv); }
+
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w) {
     pf_status st = plan_bin_reserve(p, nv);
     if (st != PF_OK) return st;
