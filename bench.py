@@ -156,14 +156,13 @@ def kernel_bytes(name, nx, ny, P, Q, nv, nrec, esz):
     M = nx * ny
     spec = (P // 2 + 1) * ny * 2 * esz
     return {
-        "bin_count": 24 * nv,
-        "bin_scan": 0,
-        "bin_scatter": 24 * nv + 16 * nrec,
+        "bin_locate": 24 * nv + 16 * nv,
+        "bin_scatter": 16 * nv + 20 * nrec,
         "regularize": 16 * nrec + esz * M,
         "fft_rows_fwd": esz * M + spec,
         "fft_cols_conv": spec + (P // 2 + 1) * (Q // 2 + 1) * esz + 2 * spec,
         "fft_rows_inv": 2 * spec + 2 * esz * M,
-        "interpolate": 16 * nv + 2 * esz * M + 2 * esz * nv,
+        "interpolate": 20 * nrec + 2 * esz * M + 2 * esz * nv,
     }.get(name)
 
 
@@ -254,7 +253,7 @@ def bench_ours(args):
         avg = ms / n
         kern[name] = {"launches_per_step": n / KT, "avg_ms": avg, "share": ms / sum(v[1] for v in rep.values()),
                       "alg_bytes": b, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
-    dom = max(kern, key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
+    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
@@ -307,6 +306,11 @@ def bench_ours(args):
             extras["fp64_path"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64}
             extras["mixed_rel_err_vs_fp64_gpu"] = float(num / den)
             p64.close()
+        if world == 1:
+            try:
+                extras["workloads"] = bench_workloads(pf, inputs, torch, stream)
+            except Exception as e:          # reported, never fatal for the main line
+                extras["workloads"] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -332,6 +336,128 @@ def bench_ours(args):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ other workloads
+def _steps_per_s(pf, plan, fn, n):
+    pf.pf_sync(plan)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        fn()
+    pf.pf_sync(plan)
+    return n / (time.perf_counter() - t0)
+
+
+def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
+    """Body workloads: single-step plate, pitching plate, uneven batch, request server."""
+    import numpy as np
+    out = {}
+    with torch.cuda.stream(stream):
+        # plate, 128^2, 64 points, 256 vortices, Euler with two-edge release
+        wl = inputs.plate_vortices_128()
+        g = wl["grid"]
+        res = {}
+        for prec, name in ((pf.PF_MIXED, "mixed"), (pf.PF_FP64, "fp64")):
+            plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec, stream=stream)
+            state = pf.State(plan, 256 + 2 * 64)
+            pf.pf_state_set(state, wl["X"], wl["Y"], wl["G"])
+            body = pf.plate_kinematics(64, 1.0, wl["alpha"], Uinf=1.0)
+            pf.pf_step(plan, state, 0.002, body)             # includes the one-off factorisation
+            res[name] = _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, 0.002, body), 20)
+        out["plate_128"] = {"unit": "steps/s", "desc": "128^2, plate 20 deg, Ns 64, 256 vortices, Euler, dt 0.002, "
+                            "two-edge release every step (factor reused)", **res}
+        # pitching plate, 768 x 512, Ns 256, RK2, S refactored at every stage
+        pw = inputs.pitching_plate_512x768()
+        g = pw["grid"]
+        plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+        state = pf.State(plan, 200)
+        pf.pf_state_set(state, np.zeros(0), np.zeros(0), np.zeros(0))
+        omega = 2.0 * pw["k"] * pw["Uinf"] / pw["chord"]
+        body = pf.plate_kinematics(pw["ns"], pw["chord"], pw["alpha0"], pw["amp"], omega, pw["Uinf"])
+        pf.pf_step(plan, state, pw["dt"], body, scheme=1)
+        out["pitching_plate_768x512"] = {"unit": "steps/s", "desc": "768x512, dx 0.01, Ns 256, 30+10 sin(t) deg, "
+                                         "RK2, two factorisations per step",
+                                         "mixed": _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, pw["dt"],
+                                                                                            body, scheme=1), 8)}
+        # uneven batch: independent instances, one step each per call
+        inst = inputs.batched_instances(n=n_batch)
+        res = {}
+        for prec, name in ((pf.PF_MIXED, "batched_mixed"), (pf.PF_FP64, "unbatched_fp64")):
+            bases, plans, states, bodies = {}, [], [], []
+            for r in inst:
+                gg = r["grid"]
+                key = (gg.nx, gg.ny)
+                if key not in bases:
+                    bases[key] = pf.Plan(gg.nx, gg.ny, gg.dx, gg.x0, gg.y0, prec, stream=stream)
+                p = pf.pf_plan_clone(bases[key], prec, torch.cuda.Stream()) if name.startswith("batched") \
+                    else bases[key]
+                st = pf.State(p, len(r["X"]) + 64)
+                pf.pf_state_set(st, r["X"], r["Y"], r["G"])
+                b = r["body"]
+                plans.append(p)
+                states.append(st)
+                bodies.append(pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"]))
+            dt = 0.002
+            if name.startswith("batched"):
+                pf.pf_step_batch(plans, states, bodies, dt)          # factorisations
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    pf.pf_step_batch(plans, states, bodies, dt)
+                torch.cuda.synchronize()
+                res[name] = 3 * len(inst) / (time.perf_counter() - t0)
+            else:
+                for p, st, b in zip(plans, states, bodies):
+                    pf.pf_step(p, st, dt, b)
+                    pf.pf_sync(p)
+                t0 = time.perf_counter()
+                for p, st, b in zip(plans, states, bodies):
+                    pf.pf_step(p, st, dt, b)
+                    pf.pf_sync(p)
+                res[name] = len(inst) / (time.perf_counter() - t0)
+            del plans, states, bases
+        out["uneven_batch"] = {"unit": "instance-steps/s", "instances": len(inst),
+                               "desc": "grids 128^2..512^2, plate or ellipse, Ns 32-256, 100-20000 vortices; "
+                                       "batched: one stream per instance, shared tables; unbatched FP64: one "
+                                       "instance at a time", **res}
+    # request server: burst, then Poisson arrivals at 70 % of the burst throughput
+    reqs = inputs.serving_requests(n=n_requests)
+    def run(rate):
+        server = pf.Server(max_slots=32, hbm_budget_bytes=32 << 30, precision=pf.PF_MIXED)
+        rng = np.random.default_rng(7)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
+        t0 = time.perf_counter()
+        pending, lats, i, steps, failed = set(), [], 0, 0, 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                r = reqs[i]
+                b = r["body"]
+                body = pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"])
+                gg = r["grid"]
+                pending.add(pf.pf_server_submit(server, (gg.nx, gg.ny, gg.dx, gg.x0, gg.y0), r["X"], r["Y"], r["G"],
+                                                r["nsteps"], 0.002, body))
+                steps += r["nsteps"]
+                i += 1
+            for t in pf.pf_server_progress(server):
+                pending.discard(t)
+                try:
+                    lats.append(pf.pf_server_result(server, t, 200000)[3])
+                except pf.GridPfError:
+                    failed += 1
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        server.close()
+        lats = sorted(lats)
+        return {"requests": len(reqs), "failed": failed, "steps": steps, "wall_s": wall, "steps_per_s": steps / wall,
+                "requests_per_s": len(reqs) / wall, "p50_ms": 1e3 * lats[len(lats) // 2],
+                "p99_ms": 1e3 * lats[min(len(lats) - 1, int(0.99 * len(lats)))]}
+    burst = run(None)
+    poisson = run(0.7 * burst["requests_per_s"])
+    out["serving"] = {"desc": "requests as the uneven batch plus 10% at 1024^2 with 1e5 vortices, 1-50 steps "
+                              "each, dt 0.002, mixed precision, 32 slots", "burst": burst,
+                      "poisson_at_0.7x": poisson}
+    return out
 
 
 # ------------------------------------------------------------------ reference arm

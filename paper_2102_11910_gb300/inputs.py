@@ -138,3 +138,74 @@ def pitching_plate_512x768(ns=256):
     grid = GridSpec(768, 512, dx, -1.5, -0.5 * 511 * dx)
     return dict(grid=grid, ns=ns, chord=1.0, alpha0=math.radians(30.0), amp=math.radians(10.0),
                 k=0.5, Uinf=1.0, dt=0.0025)
+
+
+GRID_SHAPES = ((128, 128), (256, 256), (512, 384), (512, 512))   # (nx, ny)
+
+
+def batched_instance(rng, shape=None, big=False):
+    """One instance of the uneven batch recipe.
+
+    Grid drawn from 128^2, 256^2, 384x512, 512^2 (or 1024^2 with 1e5 vortices
+    when `big`), dx = 2/(max(nx, ny) - 1), centred on the origin; one body of
+    size 1 at the origin: a flat plate at 5-30 deg releasing at both edges, or
+    an ellipse of aspect 2-10 (Kelvin-constrained); surface points 32-256 with
+    dS/dx in [1, 4] (below 1 the sheet system is so ill-conditioned that the
+    released strengths diverge within a few steps, in FP64 too); 100-20000 vortices (log-uniform) outside radius 0.55, in
+    x from -0.8 to 0.4 of the half-width and at least 0.35 from the top and bottom,
+    strengths normal with variance 0.2 / count (induced speeds of order U_inf).
+    """
+    if big:
+        nx = ny = 1024
+    else:
+        nx, ny = GRID_SHAPES[rng.integers(len(GRID_SHAPES))] if shape is None else shape
+    dx = 2.0 / (max(nx, ny) - 1)
+    grid = centred_grid(nx, ny, dx)
+    plate_body = rng.random() < 0.5
+    perim = 1.0 if plate_body else None
+    if not plate_body:
+        ar = rng.uniform(2.0, 10.0)
+        a, b = 0.5, 0.5 / ar
+        t = np.linspace(0.0, 2 * np.pi, 2001)
+        perim = float(np.sum(np.hypot(np.diff(a * np.cos(t)), np.diff(b * np.sin(t)))))
+    lo = max(32, int(math.ceil(perim / (4.0 * dx))))
+    hi = min(256, int(perim / dx))
+    ns = int(rng.integers(lo, max(lo, hi) + 1))
+    if plate_body:
+        xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+        body = dict(xb=0.5 * xi, yb=np.zeros(ns), ds=np.full(ns, 1.0 / ns), edges=(0, ns - 1),
+                    alpha0=math.radians(rng.uniform(5.0, 30.0)))
+    else:
+        e = ellipse(ns, a, b)
+        body = dict(xb=e.x, yb=e.y, ds=e.ds, edges=(), alpha0=rng.uniform(0.0, math.pi))
+    nv = 100000 if big else int(round(math.exp(rng.uniform(math.log(100), math.log(20000)))))
+    hx, hy = 0.5 * (nx - 1) * dx, 0.5 * (ny - 1) * dx - 0.35
+    X, Y = np.empty(0), np.empty(0)
+    while len(X) < nv:
+        # upstream-biased box so that 50 steps of advection stay on the grid
+        x = rng.uniform(-0.8 * hx, 0.4 * hx, 2 * nv)
+        y = rng.uniform(-hy, hy, 2 * nv)
+        keep = np.hypot(x, y) > 0.55
+        X, Y = np.concatenate([X, x[keep]]), np.concatenate([Y, y[keep]])
+    # total circulation variance fixed (that of 200 vortices of variance 1e-3), so
+    # that induced speeds stay O(U_inf) whatever the count
+    G = rng.normal(0.0, math.sqrt(1e-3 * 200.0 / nv), nv)
+    return dict(grid=grid, body=body, X=X[:nv], Y=Y[:nv], G=G, Uinf=1.0)
+
+
+def batched_instances(seed=1003, n=256):
+    """The uneven batch: n independent instances (seed 1003)."""
+    rng = np.random.default_rng(seed)
+    return [batched_instance(rng) for _ in range(n)]
+
+
+def serving_requests(seed=1004, n=4096, big_fraction=0.1):
+    """Requests of the serving workload: instances as in the batch, 10 % at
+    1024^2 with 1e5 vortices, each for 1-50 steps (uniform)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        r = batched_instance(rng, big=rng.random() < big_fraction)
+        r["nsteps"] = int(rng.integers(1, 51))
+        out.append(r)
+    return out
