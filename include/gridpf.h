@@ -299,8 +299,9 @@ pf_status pf_server_stats(pf_server server, int32_t* queued, int32_t* active, in
  * a memory budget that forbids new allocations, or in a process whose
  * allocator is owned by someone else).  It computes exactly what
  * pf_regularize computes, with the same kernels, but needs no plan and makes
- * no allocation: its scratch (tile counters, 65536 per-vortex cell records and
- * up to 4 * 65536 binned records) is one static device array of about 10.1 MiB inside this library,
+ * no allocation: its scratch (tile counters and offsets, 65536 per-vortex cell
+ * records and up to 4 * 65536 binned records) is one static device array of
+ * about 11.6 MiB inside this library,
  * which every GPU that loads the library holds until the process exits.  The
  * paper has no counterpart; it is an interface convenience.
  *

@@ -18,7 +18,7 @@ int next_pow2(int v) {
 void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
-    void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start,
+    void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->bin_off,
                    p->pos, p->recs, p->ridx, p->stage, p->stage_out, p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);
@@ -92,7 +92,8 @@ pf_status plan_workspaces(pf_plan p) {
     const int nx = p->nx, ny = p->ny, P = p->P;
     p->esz = p->prec == PF_FP64 ? 8 : 4;
     p->ldT = (ny + 3) / 4 * 4;
-    const size_t spec = (size_t)(P / 2 + 1) * p->ldT * 2 * p->esz;
+    p->ldK = (P / 2 + 1 + 3) / 4 * 4;
+    const size_t spec = (size_t)p->ldK * p->ldT * 2 * p->esz;
     PF_CUDA(p, cudaMalloc(&p->T1, spec));
     PF_CUDA(p, cudaMalloc(&p->T2a, spec));
     PF_CUDA(p, cudaMalloc(&p->T2b, spec));
@@ -101,10 +102,10 @@ pf_status plan_workspaces(pf_plan p) {
     p->ntx = ceil_div(nx, BIN_TILE);
     p->nty = ceil_div(ny, BIN_TILE);
     p->ntiles = p->ntx * p->nty;
-    // count, gmax and cursor are contiguous so one memset clears them
-    PF_CUDA(p, cudaMalloc(&p->tile_count, 3 * (size_t)p->ntiles * sizeof(unsigned)));
+    // count and gmax are contiguous so one memset clears them
+    PF_CUDA(p, cudaMalloc(&p->tile_count, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
     p->tile_gmax = p->tile_count + p->ntiles;
-    p->tile_cursor = p->tile_count + 2 * p->ntiles;
+    p->tile_rep = p->tile_count + 2 * p->ntiles;
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));

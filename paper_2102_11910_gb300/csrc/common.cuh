@@ -50,6 +50,21 @@ struct KTiming {
 // ------------------------------------------------------------ plan
 constexpr int BIN_TILE = 32;   // node tile edge used by binning and regularization
 
+// Vortex partition of the binning passes: block b owns vortices
+// [b * span, min(nv, (b + 1) * span)).  Large sets use exactly BIN_MAX_BLOCKS
+// blocks (four per SM, all resident at once, equal work per SM); small sets
+// use fewer blocks of at least 1024 vortices.
+constexpr int BIN_MAX_BLOCKS = 608;
+inline int64_t bin_span(int64_t nv) {
+    const int64_t s = (nv + BIN_MAX_BLOCKS - 1) / BIN_MAX_BLOCKS;
+    return s < 1024 ? 1024 : s;
+}
+inline int bin_blocks(int64_t nv) { return nv > 0 ? (int)((nv + bin_span(nv) - 1) / bin_span(nv)) : 0; }
+// The locate pass reduces its per-block tile counts and largest |Gamma| into
+// TILE_REP replicas per tile (block b into replica b % TILE_REP), so that no
+// address takes more than a few tens of the global reductions.
+constexpr int TILE_REP = 16;
+
 // Read-only tables of one grid shape, shared by a plan and its clones.
 struct PlanTables {
     int refs = 1;
@@ -78,18 +93,21 @@ struct pf_plan_s {
     float2* tw256_32 = nullptr;
     // grid work buffers (element size depends on precision)
     size_t esz = 8;
-    int ldT = 0;                   // leading dimension of T1/T2 (ny rounded up to 4)
-    void* T1 = nullptr;            // (P/2+1)*ldT complex: row spectra, k-major
+    int ldT = 0;                   // ny rounded up to 4
+    int ldK = 0;                   // P/2 + 1 rounded up to 4
+    void* T1 = nullptr;            // ldT*ldK complex: half spectra of the rows (layout set by the FFT kernels)
     void* T2a = nullptr;
     void* T2b = nullptr;
     void* w = nullptr;             // nx*ny real
     void* uv = nullptr;            // 2*nx*ny real
     // binning
     int ntx = 0, nty = 0, ntiles = 0;
-    unsigned* tile_count = nullptr;    // one allocation: count | gmax | cursor
+    unsigned* tile_count = nullptr;    // one allocation: count | gmax | replicas (2 TILE_REP per tile)
     unsigned* tile_gmax = nullptr;     // bits of the largest |Gamma| (FP32, rounded up) per tile
-    unsigned* tile_cursor = nullptr;
+    unsigned* tile_rep = nullptr;      // [t][r] counts, then [t][r] gmax
     int* tile_start = nullptr;
+    int* bin_off = nullptr;            // per (block, tile): histogram, then first record slot
+    int64_t bin_off_cap = 0;           // entries
     void* pos = nullptr;               // per-vortex cell records of the last located set
     int64_t pos_cap = 0;
     void* recs = nullptr;              // records binned by tile

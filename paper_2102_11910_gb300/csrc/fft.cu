@@ -3,8 +3,9 @@
 //
 // Layout of the three passes (w real, ny rows of nx nodes; torus P x Q):
 //   1. rows:    two real rows j, j+1 packed as one complex row, length-P FFT,
-//               split into the two half spectra A_j(k), k in [0, P/2];
-//               stored column-major T1[k*ny + j] so pass 2 reads contiguously.
+//               split into the two half spectra A_j(k), k in [0, P/2]; the
+//               generic kernels store them column-major T1[k*ny + j], the
+//               register-resident ones in groups of four rows (see below).
 //   2. columns: for each k, length-Q FFT of T1[k, 0..ny) (zero padded),
 //               multiply by the kernel spectrum (psi: -dx^2 Ghat/(PQ); for the
 //               node velocity the spectra of the centred-differenced LGF,
@@ -176,19 +177,26 @@ pf_status fft2d_inplace_f64(pf_plan p, double2* data) {
 
 
 // ---------------------------------------------------------------------------
-// Register-resident variants for P, Q = 256 * R3 (256 <= P, Q <= 4096).  Row
-// spectra are stored with leading dimension ldT (ny rounded up to 4) so that
-// the pair of rows a group writes per k is one aligned vector store.
+// Register-resident variants for P, Q = 256 * R3 (256 <= P, Q <= 4096).
+//
+// Half-spectrum layout shared by T1, T2a, T2b: rows in groups of four,
+// element (j, k) at ((j / 4) * nk + k) * 4 + j % 4 with nk = P/2 + 1.  The
+// forward row pass (four rows per block) then writes one contiguous run, and
+// a column k is read and written as full 32-byte sectors of four rows.
+__device__ __forceinline__ size_t spec_at(int j, int k, int nk) {
+    return ((size_t)(j >> 2) * nk + k) * 4 + (j & 3);
+}
 
 template <typename T, int R3>
 __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx,
-                                                        int ny, int ldT, const C_t<T>* __restrict__ tw256,
+                                                        int ny, const C_t<T>* __restrict__ tw256,
                                                         const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
-    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufs = reinterpret_cast<C*>(smem_raw);
     const int g = threadIdx.x / TP, t = threadIdx.x % TP;
-    C* buf = reinterpret_cast<C*>(smem_raw) + g * SB;
+    C* buf = bufs + g * SB;
     const int j0 = 4 * blockIdx.x + 2 * g;
     const bool h0 = j0 < ny, h1 = j0 + 1 < ny;
     C v[16];
@@ -206,40 +214,35 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf[spad(t + TP * r)] = v[r];
     __syncthreads();
-    if (h0) {
-        for (int k = t; k <= P / 2; k += TP) {
-            const C z1 = buf[spad(k)], z2 = conjc(buf[spad((P - k) & (P - 1))]);
-            const C A = (z1 + z2) * T(0.5);
-            const C B = mul_mi(z1 - z2) * T(0.5);
-            C* dst = T1 + (size_t)k * ldT + j0;
-            dst[0] = A;
-            if (h1) dst[1] = B;
-        }
+    // the block's four rows are one contiguous run of NK * 4 elements
+    C* dst = T1 + (size_t)blockIdx.x * NK * 4;
+    for (int e = threadIdx.x; e < NK * 4; e += blockDim.x) {
+        const int k = e >> 2, jj = e & 3;
+        const C* bz = bufs + (jj >> 1) * SB;
+        const C z1 = bz[spad(k)], z2 = conjc(bz[spad((P - k) & (P - 1))]);
+        dst[e] = (jj & 1) ? mul_mi(z1 - z2) * T(0.5) : (z1 + z2) * T(0.5);
     }
 }
 
 template <typename T, int R3>
-__global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_r(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
-                                                    C_t<T>* __restrict__ T2b, int ny, int ldT, int mode,
-                                                    const T* __restrict__ H, const T* __restrict__ Hu,
-                                                    const T* __restrict__ Hv, int Hld,
-                                                    const C_t<T>* __restrict__ tw256, const C_t<T>* __restrict__ twQ) {
+__global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_r(
+    const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a, C_t<T>* __restrict__ T2b, int ny, int nk, int mode,
+    const T* __restrict__ H, const T* __restrict__ Hu, const T* __restrict__ Hv, int Hld,
+    const C_t<T>* __restrict__ tw256, const C_t<T>* __restrict__ twQ) {
     using C = C_t<T>;
     constexpr int Q = 256 * R3, TQ = Q / 16, SB = SBuf<Q>::size;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* keep = buf + SB;
     const int k = blockIdx.x, t = threadIdx.x;
-    const C* src = T1 + (size_t)k * ldT;
     C v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int l = t + TQ * r;
-        v[r] = l < ny ? src[l] : cmake<C>(T(0), T(0));
+        v[r] = l < ny ? T1[spec_at(l, k, nk)] : cmake<C>(T(0), T(0));
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twQ);
     const size_t row = (size_t)k * Hld;
-    C* outa = T2a + (size_t)k * ldT;
     if (mode == CONV_UV) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -255,15 +258,14 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int l = t + TQ * r;
-            if (l < ny) outa[l] = v[r];
+            if (l < ny) T2a[spec_at(l, k, nk)] = v[r];
             v[r] = keep[spad(l)];                    // written by this thread
         }
         fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
-        C* outb = T2b + (size_t)k * ldT;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int l = t + TQ * r;
-            if (l < ny) outb[l] = v[r];
+            if (l < ny) T2b[spec_at(l, k, nk)] = v[r];
         }
     } else {
 #pragma unroll
@@ -275,18 +277,18 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int l = t + TQ * r;
-            if (l < ny) outa[l] = v[r];
+            if (l < ny) T2a[spec_at(l, k, nk)] = v[r];
         }
     }
 }
 
 template <typename T, int R3>
 __global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
-                                                        T* __restrict__ out, int nx, int ny, int ldT, int mode, T Uinf,
+                                                        T* __restrict__ out, int nx, int ny, int mode, T Uinf,
                                                         T Vinf, const C_t<T>* __restrict__ tw256,
                                                         const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
-    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / TP, t = threadIdx.x % TP;
     C* buf = reinterpret_cast<C*>(smem_raw) + g * SB;
@@ -306,8 +308,8 @@ __global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict
     }
     const int h = P / 2;
     for (int k = t; k <= h; k += TP) {
-        C a = ha ? T2a[(size_t)k * ldT + ja] : cmake<C>(T(0), T(0));
-        C b = hb ? Sb[(size_t)k * ldT + jb] : cmake<C>(T(0), T(0));
+        C a = ha ? T2a[spec_at(ja, k, NK)] : cmake<C>(T(0), T(0));
+        C b = hb ? Sb[spec_at(jb, k, NK)] : cmake<C>(T(0), T(0));
         if (k == 0 || k == h) { a.y = 0; b.y = 0; }
         buf[spad(k)] = a + mul_i(b);
         if (k > 0 && k < h) buf[spad(P - k)] = conjc(a) + mul_i(conjc(b));
@@ -344,7 +346,7 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
     using C = C_t<T>;
     constexpr int P = 256 * R3P, Q = 256 * R3Q;
-    const int nx = p->nx, ny = p->ny, ldT = p->ldT;
+    const int nx = p->nx, ny = p->ny;
     const size_t sr = 2 * (size_t)SBuf<P>::size * sizeof(C), sc = 2 * (size_t)SBuf<Q>::size * sizeof(C);
     PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sr));
     PF_CUDA(p, set_smem(k_cols_r<T, R3Q>, sc));
@@ -352,13 +354,13 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     C* T1 = reinterpret_cast<C*>(p->T1);
     C* T2a = reinterpret_cast<C*>(p->T2a);
     C* T2b = reinterpret_cast<C*>(p->T2b);
-    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd_r<T, R3P><<<(ny + 3) / 4, 32 * R3P, sr, p->stream>>>(w, T1, nx, ny, ldT,
-                                                                                                 tw256, twP));
+    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd_r<T, R3P><<<(ny + 3) / 4, 32 * R3P, sr, p->stream>>>(w, T1, nx, ny, tw256,
+                                                                                                 twP));
     PF_KERNEL(p, "fft_cols_conv", k_cols_r<T, R3Q><<<P / 2 + 1, 16 * R3Q, sc, p->stream>>>(
-                                      T1, T2a, T2b, ny, ldT, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ));
+                                      T1, T2a, T2b, ny, P / 2 + 1, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ));
     const int nb = mode == CONV_UV ? (ny + 1) / 2 : (ny + 3) / 4;
-    PF_KERNEL(p, "fft_rows_inv", k_rows_inv_r<T, R3P><<<nb, 32 * R3P, sr, p->stream>>>(T2a, T2b, out, nx, ny, ldT, mode,
-                                                                                       Uinf, Vinf, tw256, twP));
+    PF_KERNEL(p, "fft_rows_inv", k_rows_inv_r<T, R3P><<<nb, 32 * R3P, sr, p->stream>>>(T2a, T2b, out, nx, ny, mode, Uinf,
+                                                                                       Vinf, tw256, twP));
     return PF_OK;
 }
 

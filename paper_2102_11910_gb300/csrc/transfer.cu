@@ -5,10 +5,11 @@
 // Regularization is a binned scatter in four kernels:
 //   locate   FP64 position -> integer cell + fraction (one pass, FP64 used only
 //            for g = (X - x0)/dx), compact per-vortex record, per-block tile
-//            histogram in shared memory flushed with one reduction per tile;
-//   scan     exclusive scan of the tile counts, fixed-point exponent per tile;
-//   scatter  per-block ranks in shared memory, one cursor reservation per
-//            (block, tile), records written into their tiles; a vortex whose
+//            histogram in shared memory, written out as one row per block;
+//   offsets  column scan of the block histograms: the first record slot of
+//            every (block, tile) pair, and the first slot of every tile;
+//   scatter  per-block ranks in shared memory, records written into their
+//            tiles at the block's offsets (no global atomics); a vortex whose
 //            4x4 stencil straddles tiles is entered in every tile it touches;
 //   deposit  one block per BIN_TILE^2 node tile sums its records in shared
 //            memory as fixed-point integers with a per-tile scale chosen from
@@ -22,9 +23,8 @@
 
 namespace {
 
-constexpr int CHUNK = 2048;          // vortices per block in the locate / scatter passes
 constexpr int BIN_THREADS = 256;
-constexpr int PER_THREAD = CHUNK / BIN_THREADS;
+constexpr int BIN_UNROLL = 4;        // vortices per thread whose loads are issued together
 
 // per-vortex cell record (original order)
 template <typename T> struct Pos;
@@ -66,7 +66,8 @@ __device__ __forceinline__ void m4p_weights(T f, T w[4]) {
 // [0, n) iff 1 <= g < n - 2.  FP64 path: g = (X - x0)/dx, fraction g - floor(g)
 // exact.  Mixed path: one FMA, then the integer and fractional parts are read
 // from the bits of g (no further FP64 work); the fraction is truncated to 24 bits.
-__device__ __forceinline__ bool split(double X, double x0, double dx, double, double, int n, int& c, double& f) {
+__device__ __forceinline__ bool split(double X, double x0, double dx, double, double, int n, long long, int& c,
+                                      double& f) {
     const double g = (X - x0) / dx;
     if (!(g >= 1.0 && g < (double)(n - 2))) return false;
     const double fl = floor(g);
@@ -74,26 +75,45 @@ __device__ __forceinline__ bool split(double X, double x0, double dx, double, do
     f = g - fl;
     return true;
 }
-__device__ __forceinline__ bool split(double X, double, double, double inv_dx, double c0, int n, int& c, float& f) {
+__device__ __forceinline__ bool split(double X, double, double, double inv_dx, double c0, int, long long lim, int& c,
+                                      float& f) {
     const double g = fma(X, inv_dx, c0);
     // 1 <= g < n - 2 compared on the bit patterns (monotone for non-negative
-    // doubles; negative values and NaN fail), keeping the FP64 pipe for the FMA
+    // doubles; negative values and NaN fail; lim = bits of (double)(n - 2)),
+    // keeping the FP64 pipe for the FMA
     const long long gb = __double_as_longlong(g);
-    if (gb < 0x3FF0000000000000ll || gb >= __double_as_longlong((double)(n - 2))) return false;
-    const unsigned long long bits = (unsigned long long)gb;
-    const int sh = 52 - ((int)(bits >> 52) - 1023);                  // g >= 1: sign 0, exponent 0..10
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    c = (int)(mant >> sh);
-    const unsigned long long fr = mant & ((1ull << sh) - 1);
-    f = __uint2float_rz((unsigned)((fr << (64 - sh)) >> 32)) * 0x1p-32f;
+    if (gb < 0x3FF0000000000000ll || gb >= lim) return false;
+    // g = 2^e (1 + m 2^-52), 0 <= e <= 10 since g < 2048: the integer part is the
+    // top e fraction bits with the hidden bit, the cell fraction the next 32
+    const unsigned hi = (unsigned)((unsigned long long)gb >> 32), lo = (unsigned)gb;
+    const int e = (int)(hi >> 20) - 1023;
+    const unsigned m20 = hi & 0xFFFFFu;
+    c = (int)((m20 | 0x100000u) >> (20 - e));
+    f = __uint2float_rz(__funnelshift_l(lo, m20, 12 + e)) * 0x1p-32f;
     return true;
+}
+
+// double -> float rounded to nearest even with integer instructions only (the
+// FP64 pipe is 1/64 rate); zero, and values outside the normal FP32 range,
+// take the hardware conversion.  Bitwise equal to (float)d.
+__device__ __forceinline__ float d2f(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (e <= 0 || e >= 255) return (float)d;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;     // 52 fraction bits
+    const unsigned top = (unsigned)(m >> 29);                // the 23 kept
+    const unsigned rest = (unsigned)(m & 0x1FFFFFFFull);     // the 29 dropped
+    unsigned out = sign | ((unsigned)e << 23) | top;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ++out;   // carries into the exponent
+    return __uint_as_float(out);
 }
 
 __device__ __forceinline__ void make_pos(Pos<float>& p, int ci, int cj, float fx, float fy, double g) {
     p.cell = (unsigned)ci | ((unsigned)cj << 16);
     p.fx = fx;
     p.fy = fy;
-    p.g = (float)g;
+    p.g = d2f(g);
 }
 __device__ __forceinline__ void make_pos(Pos<double>& p, int ci, int cj, double fx, double fy, double g) {
     p.ci = ci;
@@ -107,15 +127,16 @@ struct Geo {
     double x0, y0, dx;
     double inv_dx, cx, cy;     // 1/dx, -x0/dx, -y0/dx (host computed)
     double inv_dx2;            // 1/dx^2
+    long long xlim, ylim;      // bit patterns of (double)(nx - 2), (double)(ny - 2)
     int nx, ny, ntx, ntiles;
 };
 
 template <typename T>
 __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
-                                                       const double* __restrict__ G, int64_t nv, Geo geo,
-                                                       Pos<T>* __restrict__ pos, unsigned* __restrict__ tile_count,
-                                                       unsigned* __restrict__ tile_gmax, int* __restrict__ status,
-                                                       unsigned long long* __restrict__ oob) {
+                                                       const double* __restrict__ G, int64_t nv, int64_t span, Geo geo,
+                                                       Pos<T>* __restrict__ pos, unsigned* __restrict__ tile_rep,
+                                                       int* __restrict__ hist,
+                                                       int* __restrict__ status, unsigned long long* __restrict__ oob) {
     extern __shared__ unsigned sm[];
     unsigned* cnt = sm;
     unsigned* gmx = sm + geo.ntiles;
@@ -124,58 +145,66 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
         gmx[i] = 0u;
     }
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * CHUNK;
+    const int64_t lo = (int64_t)blockIdx.x * span;
+    const int64_t hi = lo + span < nv ? lo + span : nv;
     int bad = 0;
-    // issue every load of this thread's vortices before using any of them
-    double xs[PER_THREAD], ys[PER_THREAD], gs[PER_THREAD];
+    for (int64_t base = lo; base < hi; base += BIN_THREADS * BIN_UNROLL) {
+        // issue the loads of BIN_UNROLL vortices before using any of them
+        double xs[BIN_UNROLL], ys[BIN_UNROLL], gs[BIN_UNROLL];
 #pragma unroll
-    for (int k = 0; k < PER_THREAD; ++k) {
-        const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-        xs[k] = ys[k] = gs[k] = 0.0;
-        if (q < nv) {
-            xs[k] = X[q];
-            ys[k] = Y[q];
-            gs[k] = G[q];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < PER_THREAD; ++k) {
-        const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-        if (q >= nv) break;
-        int ci = 0, cj = 0;
-        T fx = 0, fy = 0;
-        const double gq = gs[k];
-        Pos<T> p;
-        if (!split(xs[k], geo.x0, geo.dx, geo.inv_dx, geo.cx, geo.nx, ci, fx) ||
-            !split(ys[k], geo.y0, geo.dx, geo.inv_dx, geo.cy, geo.ny, cj, fy)) {
-            ++bad;
-            make_pos(p, 0xFFFF, 0xFFFF, T(0), T(0), 0.0);   // marker: skipped by scatter and interpolation
-            pos[q] = p;
-            continue;
-        }
-        make_pos(p, ci, cj, fx, fy, gq);
-        pos[q] = p;
-        // |Gamma| rounded to FP32 and widened by two ulps: an upper bound of |Gamma|
-        const unsigned gb = __float_as_uint(fabsf((float)gq) * 1.0000003f);
-        const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
-        const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                const int t = ty * geo.ntx + tx;
-                atomicAdd(&cnt[t], 1u);
-                atomicMax(&gmx[t], gb);
+        for (int k = 0; k < BIN_UNROLL; ++k) {
+            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            xs[k] = ys[k] = gs[k] = 0.0;
+            if (q < hi) {
+                xs[k] = X[q];
+                ys[k] = Y[q];
+                gs[k] = G[q];
             }
+        }
+#pragma unroll
+        for (int k = 0; k < BIN_UNROLL; ++k) {
+            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            if (q >= hi) break;
+            int ci = 0, cj = 0;
+            T fx = 0, fy = 0;
+            Pos<T> p;
+            if (!split(xs[k], geo.x0, geo.dx, geo.inv_dx, geo.cx, geo.nx, geo.xlim, ci, fx) ||
+                !split(ys[k], geo.y0, geo.dx, geo.inv_dx, geo.cy, geo.ny, geo.ylim, cj, fy)) {
+                ++bad;
+                make_pos(p, 0xFFFF, 0xFFFF, T(0), T(0), 0.0);   // marker: skipped by scatter and interpolation
+                pos[q] = p;
+                continue;
+            }
+            make_pos(p, ci, cj, fx, fy, gs[k]);
+            pos[q] = p;
+            // |Gamma| rounded to FP32 and widened by two ulps: an upper bound of |Gamma|
+            const unsigned gb = __float_as_uint(fabsf(d2f(gs[k])) * 1.0000003f);
+            const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
+            const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const int t = ty * geo.ntx + tx;
+                    atomicAdd(&cnt[t], 1u);
+                    atomicMax(&gmx[t], gb);
+                }
+        }
     }
     if (bad) {
         atomicAdd(oob, (unsigned long long)bad);
         atomicOr(status, ST_OUT_OF_DOMAIN);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS)
-        if (cnt[i]) {
-            atomicAdd(&tile_count[i], cnt[i]);
-            atomicMax(&tile_gmax[i], gmx[i]);
+    int* row = hist + (size_t)blockIdx.x * geo.ntiles;
+    unsigned* rc = tile_rep + blockIdx.x % TILE_REP;
+    unsigned* rg = rc + (size_t)geo.ntiles * TILE_REP;
+    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) {
+        const unsigned c = cnt[i];
+        row[i] = (int)c;
+        if (c) {
+            atomicAdd(&rc[i * TILE_REP], c);
+            atomicMax(&rg[i * TILE_REP], gmx[i]);
         }
+    }
 }
 
 // Fixed-point exponent of a tile: every node sum is bounded by
@@ -188,100 +217,152 @@ __device__ __forceinline__ int tile_shift_of(unsigned count, unsigned gmax_bits)
     return sh > 100 ? 100 : (sh < -60 ? -60 : sh);
 }
 
-// Exclusive scan of the tile counts by one block of BIN_THREADS threads; thread
-// tid owns tiles [tid*per, tid*per + per) and gets their first offset in *first.
-__device__ __forceinline__ void block_scan_tiles(const unsigned* __restrict__ tile_count, int ntiles, int per,
-                                                 int* __restrict__ wsum, int& first) {
-    const int lo = threadIdx.x * per, hi = min(ntiles, lo + per);
-    int s = 0;
-    for (int t = lo; t < hi; ++t) s += (int)tile_count[t];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = s;
+// k_offsets: a block covers OFF_TILES tiles; its OFF_SEGS x OFF_TILES threads
+// each own a run of at most OFF_RUN consecutive vortex blocks of one tile.
+constexpr int OFF_TILES = 8, OFF_SEGS = 128, OFF_RUN = 5;
+static_assert(OFF_SEGS * OFF_RUN >= BIN_MAX_BLOCKS, "k_offsets covers every block");
+static_assert(OFF_TILES * OFF_SEGS == 1024, "k_offsets runs 1024 threads");
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    if (lane == 31) wsum[wid] = incl;
+    return v;
+}
+
+// Record offsets: tile_count and tile_gmax (reduced over the replicas),
+// tile_start (exclusive scan of tile_count) and, in place over the block
+// histograms, off[b][t] = tile_start[t] + sum_{b' < b} hist[b'][t].
+__global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ tile_rep, int ntiles, int nb,
+                                                  int* __restrict__ hist_off, int* __restrict__ tile_start,
+                                                  unsigned* __restrict__ tile_count, unsigned* __restrict__ tile_gmax) {
+    __shared__ int part[OFF_SEGS][OFF_TILES + 1];
+    __shared__ int red[32];
+    __shared__ int tstart[OFF_TILES];
+    const int tx = threadIdx.x % OFF_TILES, ty = threadIdx.x / OFF_TILES;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int t0 = blockIdx.x * OFF_TILES, t = t0 + tx;
+    const int S = (nb + OFF_SEGS - 1) / OFF_SEGS;   // <= OFF_RUN
+    const int b0 = ty * S;
+    int v[OFF_RUN];
+    int seg = 0;
+#pragma unroll
+    for (int k = 0; k < OFF_RUN; ++k) {              // all loads in flight together
+        v[k] = 0;
+        if (k < S && b0 + k < nb && t < ntiles) v[k] = hist_off[(size_t)(b0 + k) * ntiles + t];
+        seg += v[k];
+    }
+    int s = 0;                                        // records in the tiles before t0 (all replicas)
+#pragma unroll 16
+    for (int i = threadIdx.x; i < t0 * TILE_REP; i += 1024) s += (int)tile_rep[i];
+    s = warp_sum(s);
+    if (lane == 0) red[wid] = s;
+    part[ty][tx] = seg;
     __syncthreads();
-    int wofs = 0;
-    for (int k = 0; k < wid; ++k) wofs += wsum[k];
-    first = wofs + incl - s;
+    if (wid < OFF_TILES) {                            // exclusive scan over the runs of tile t0 + wid
+        const int a0 = part[4 * lane][wid], a1 = part[4 * lane + 1][wid];
+        const int a2 = part[4 * lane + 2][wid], a3 = part[4 * lane + 3][wid];
+        const int sum4 = a0 + a1 + a2 + a3;
+        const int ex = warp_incl_scan(sum4, lane) - sum4;
+        part[4 * lane][wid] = ex;
+        part[4 * lane + 1][wid] = ex + a0;
+        part[4 * lane + 2][wid] = ex + a0 + a1;
+        part[4 * lane + 3][wid] = ex + a0 + a1 + a2;
+    } else if (wid == OFF_TILES) {                    // totals and first slots of the block's tiles
+        static_assert(OFF_TILES * 4 == 32 && TILE_REP % 4 == 0, "four lanes per tile");
+        const int before = warp_sum(red[lane]);
+        const int tl = lane / 4, q = lane % 4;          // tile t0 + tl, replicas [q R/4, (q + 1) R/4)
+        int c = 0;
+        unsigned gm = 0u;
+        if (t0 + tl < ntiles) {
+            const unsigned* rc = tile_rep + (size_t)(t0 + tl) * TILE_REP + q * (TILE_REP / 4);
+            const unsigned* rg = rc + (size_t)ntiles * TILE_REP;
+#pragma unroll
+            for (int r = 0; r < TILE_REP / 4; ++r) {
+                c += (int)rc[r];
+                gm = max(gm, rg[r]);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        }
+        // lanes 4 tl .. 4 tl + 3 hold tile tl's total: scan over the lanes q == 0
+        const int own = q == 0 ? c : 0;
+        const int ex = before + warp_incl_scan(own, lane) - own;
+        if (q == 0) {
+            tstart[tl] = ex;
+            if (t0 + tl < ntiles) {
+                tile_start[t0 + tl] = ex;
+                tile_count[t0 + tl] = (unsigned)c;
+                tile_gmax[t0 + tl] = gm;
+            }
+        }
+    }
+    __syncthreads();
+    if (t < ntiles) {
+        int run = tstart[tx] + part[ty][tx];
+#pragma unroll
+        for (int k = 0; k < OFF_RUN; ++k) {
+            if (k < S && b0 + k < nb) hist_off[(size_t)(b0 + k) * ntiles + t] = run;
+            run += v[k];
+        }
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BIN_THREADS) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, Geo geo,
-                                                        const unsigned* __restrict__ tile_count,
-                                                        int* __restrict__ tile_start,
-                                                        unsigned* __restrict__ tile_cursor, Rec<T>* __restrict__ recs,
-                                                        int* __restrict__ ridx) {
-    __shared__ int wsum[BIN_THREADS / 32];
+__global__ void __launch_bounds__(BIN_THREADS) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
+                                                        Geo geo, const int* __restrict__ off,
+                                                        Rec<T>* __restrict__ recs, int* __restrict__ ridx) {
     extern __shared__ unsigned sm[];
     unsigned* cnt = sm;
-    int* bas = (int*)(sm + geo.ntiles);
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) cnt[i] = 0u;
+    int* first = (int*)(sm + geo.ntiles);
+    const int* row = off + (size_t)blockIdx.x * geo.ntiles;
+    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) {
+        cnt[i] = 0u;
+        first[i] = row[i];
+    }
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * CHUNK;
-    unsigned long long rk[PER_THREAD];     // up to four 16-bit ranks per vortex
-    int cell[PER_THREAD][2];
+    const int64_t lo = (int64_t)blockIdx.x * span;
+    const int64_t hi = lo + span < nv ? lo + span : nv;
+    for (int64_t base = lo; base < hi; base += BIN_THREADS * BIN_UNROLL) {
+        Pos<T> p[BIN_UNROLL];
 #pragma unroll
-    for (int k = 0; k < PER_THREAD; ++k) {     // loads first
-        const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-        cell[k][0] = 0xFFFF;
-        if (q < nv) {
-            const Pos<T> p = pos[q];
-            cell[k][0] = pos_ci(p);
-            cell[k][1] = pos_cj(p);
+        for (int k = 0; k < BIN_UNROLL; ++k) {     // loads first
+            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            if (q < hi) p[k] = pos[q];
+            else make_pos(p[k], 0xFFFF, 0xFFFF, T(0), T(0), 0.0);
         }
-    }
 #pragma unroll
-    for (int k = 0; k < PER_THREAD; ++k) {
-        rk[k] = 0ull;
-        const int ci = cell[k][0], cj = cell[k][1];
-        if (ci == 0xFFFF) continue;
-        const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
-        const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
-        int s = 0;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx, ++s) {
-                const unsigned r = atomicAdd(&cnt[ty * geo.ntx + tx], 1u);
-                rk[k] |= (unsigned long long)r << (16 * s);
-            }
-    }
-    // every block scans the tile totals itself (block 0 publishes them for the
-    // deposit and interpolation kernels), then reserves its run in each tile
-    const int per = (geo.ntiles + BIN_THREADS - 1) / BIN_THREADS;
-    int first = 0;
-    block_scan_tiles(tile_count, geo.ntiles, per, wsum, first);   // contains __syncthreads
-    for (int i = threadIdx.x * per, e = min(geo.ntiles, threadIdx.x * per + per); i < e; ++i) {
-        if (blockIdx.x == 0) tile_start[i] = first;
-        if (cnt[i]) bas[i] = first + (int)atomicAdd(&tile_cursor[i], cnt[i]);
-        first += (int)tile_count[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER_THREAD; ++k) {
-        const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-        if (q >= nv) continue;
-        const Pos<T> p = pos[q];
-        const int ci = pos_ci(p), cj = pos_cj(p);
-        if (ci == 0xFFFF) continue;
-        const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
-        const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
-        Rec<T> r;
-        r.fx = p.fx;
-        r.fy = p.fy;
-        r.g = p.g;
-        int s = 0;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx, ++s) {
-                const unsigned rank = (unsigned)(rk[k] >> (16 * s)) & 0xFFFFu;
-                r.lx = (decltype(r.lx))(ci - tx * BIN_TILE);
-                r.ly = (decltype(r.ly))(cj - ty * BIN_TILE);
-                const int slot = bas[ty * geo.ntx + tx] + (int)rank;
-                recs[slot] = r;
-                if (ridx) ridx[slot] = (int)q;
-            }
+        for (int k = 0; k < BIN_UNROLL; ++k) {
+            const int ci = pos_ci(p[k]), cj = pos_cj(p[k]);
+            if (ci == 0xFFFF) continue;
+            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
+            const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
+            Rec<T> r;
+            r.fx = p[k].fx;
+            r.fy = p[k].fy;
+            r.g = p[k].g;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const int t = ty * geo.ntx + tx;
+                    const int slot = first[t] + (int)atomicAdd(&cnt[t], 1u);
+                    r.lx = (decltype(r.lx))(ci - tx * BIN_TILE);
+                    r.ly = (decltype(r.ly))(cj - ty * BIN_TILE);
+                    recs[slot] = r;
+                    if (ridx) ridx[slot] = (int)q;
+                }
+        }
     }
 }
 
@@ -290,64 +371,57 @@ template <typename T> __device__ __forceinline__ T pow2(int sh);
 template <> __device__ __forceinline__ float pow2<float>(int sh) { return __int_as_float((sh + 127) << 23); }
 template <> __device__ __forceinline__ double pow2<double>(int sh) { return __longlong_as_double((long long)(sh + 1023) << 52); }
 
-// round(x) = hi * 2^16 + lo with 0 <= lo < 2^16, for |x| < 2^46, in FP32 and
-// 32-bit integer arithmetic only: h = floor(x / 2^16) and x - h 2^16 are exact
-__device__ __forceinline__ void split_hilo(float x, int& hi, unsigned& lo) {
-    float h = floorf(x * 0x1p-16f);
-    const float l = fmaf(-h, 65536.0f, x);
-    unsigned li = __float2uint_rn(l);
-    if (li >= 65536u) {
-        li -= 65536u;
-        h += 1.0f;
-    }
-    hi = __float2int_rz(h);
-    lo = li;
+// x = hi * 2^16 + lo + e, |lo| <= 2^15, |e| <= 1/2, for |x| < 2^38, with FP32
+// adds only (no conversion instructions, which issue at 1/8 rate): adding
+// 1.5 * 2^39 rounds x to a multiple of 2^16 (h), x - h is exact, and adding
+// 1.5 * 2^23 to an integer-valued (or rounded) float of magnitude < 2^22 leaves
+// it in the low mantissa bits.
+__device__ __forceinline__ void split_hilo(float x, int& hi, int& lo) {
+    const float h = __fsub_rn(__fadd_rn(x, 0x1.8p39f), 0x1.8p39f);
+    const float l = __fsub_rn(x, h);
+    hi = __float_as_int(__fmaf_rn(h, 0x1p-16f, 0x1.8p23f)) - 0x4B400000;
+    lo = __float_as_int(__fadd_rn(l, 0x1.8p23f)) - 0x4B400000;
 }
 
 // Deposit: one block per node tile accumulates its records in shared memory as
-// fixed-point integers.  FP32 path: each term round(v 2^sh) = hi 2^16 + lo goes
-// into two native 32-bit shared adds (exact while the tile has fewer than 65536
-// records and |sum| < 2^46); otherwise, and for FP64, one 64-bit add.  Integer
-// sums are exact, so the result does not depend on the order of the adds.
-template <typename T>
-__global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs, const int* __restrict__ tile_start,
-                                                 const unsigned* __restrict__ tile_count,
-                                                 const unsigned* __restrict__ tile_gmax, Geo geo, T* __restrict__ w) {
-    __shared__ unsigned long long acc[BIN_TILE * BIN_TILE];
-    const int t = blockIdx.x;
-    const int tx = t % geo.ntx, ty = t / geo.ntx;
-    for (int i = threadIdx.x; i < BIN_TILE * BIN_TILE; i += blockDim.x) acc[i] = 0ull;
-    __syncthreads();
-    const int start = tile_start[t], cnt = (int)tile_count[t];
-    const bool split32 = sizeof(T) == 4 && cnt < 65536;
-    const int sh = tile_shift_of((unsigned)cnt, tile_gmax[t]) - (split32 ? 15 : 0);   // 2^61 -> 2^46 when split
-    const T scale = pow2<T>(sh);
+// fixed-point integers.  FP32 path: each term v 2^sh, rounded to an integer
+// hi 2^16 + lo, goes into two native 32-bit shared adds (exact while the tile
+// has fewer than 65536 records and |sum| < 2^38); otherwise, and for FP64, one
+// 64-bit add.  Integer sums are exact, so the result does not depend on the
+// order of the adds.
+//
+// A record's local cell (lx, ly) lies in [-2, 32], so its nodes lie in
+// [-3, 34]: the accumulator covers that range (ACC_W^2 nodes) and the adds
+// need no bounds tests; only the tile's own 32 x 32 nodes are written out.
+constexpr int ACC_HALO = 3, ACC_W = BIN_TILE + 6;
+
+enum { DEP_SPLIT32 = 0, DEP_F32_64 = 1, DEP_F64_64 = 2 };
+
+template <int MODE, typename T>
+__device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs, int cnt, T scale,
+                                                unsigned long long* acc) {
     int* acc_hi = reinterpret_cast<int*>(acc);
-    unsigned* acc_lo = reinterpret_cast<unsigned*>(acc) + BIN_TILE * BIN_TILE;
+    int* acc_lo = reinterpret_cast<int*>(acc) + ACC_W * ACC_W;
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-        const Rec<T> rc = recs[start + r];
+        const Rec<T> rc = recs[r];
         T wx[4], wy[4];
         m4p_weights<T>(rc.fx, wx);
         m4p_weights<T>(rc.fy, wy);
         const T gs = rc.g * scale;
+        const int base = (rc.ly - 1 + ACC_HALO) * ACC_W + (rc.lx - 1 + ACC_HALO);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int ly = rc.ly - 1 + b;
-            if (ly < 0 || ly >= BIN_TILE) continue;
             const T gy = gs * wy[b];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const int lx = rc.lx - 1 + a;
-                if (lx < 0 || lx >= BIN_TILE) continue;
-                const int node = ly * BIN_TILE + lx;
+                const int node = base + b * ACC_W + a;
                 const T x = gy * wx[a];
-                if (sizeof(T) == 4 && split32) {
-                    int hi;
-                    unsigned lo;
+                if (MODE == DEP_SPLIT32) {
+                    int hi, lo;
                     split_hilo((float)x, hi, lo);
                     atomicAdd(&acc_hi[node], hi);
                     atomicAdd(&acc_lo[node], lo);
-                } else if (sizeof(T) == 4) {
+                } else if (MODE == DEP_F32_64) {
                     atomicAdd(&acc[node], (unsigned long long)__float2ll_rn((float)x));
                 } else {
                     atomicAdd(&acc[node], (unsigned long long)__double2ll_rn((double)x));
@@ -355,18 +429,39 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs, const int* __restrict__ tile_start,
+                                                 const unsigned* __restrict__ tile_count,
+                                                 const unsigned* __restrict__ tile_gmax, Geo geo, T* __restrict__ w) {
+    __shared__ unsigned long long acc[ACC_W * ACC_W];
+    const int t = blockIdx.x;
+    const int tx = t % geo.ntx, ty = t / geo.ntx;
+    for (int i = threadIdx.x; i < ACC_W * ACC_W; i += blockDim.x) acc[i] = 0ull;
     __syncthreads();
-    const double inv_dx2 = geo.inv_dx2;
+    const int start = tile_start[t], cnt = (int)tile_count[t];
+    const bool split32 = sizeof(T) == 4 && cnt < 65536;
+    const int sh = tile_shift_of((unsigned)cnt, tile_gmax[t]) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
+    const T scale = pow2<T>(sh);
+    if (sizeof(T) == 8) deposit_records<DEP_F64_64>(recs + start, cnt, scale, acc);
+    else if (split32) deposit_records<DEP_SPLIT32>(recs + start, cnt, scale, acc);
+    else deposit_records<DEP_F32_64>(recs + start, cnt, scale, acc);
+    __syncthreads();
+    const int* acc_hi = reinterpret_cast<const int*>(acc);
+    const int* acc_lo = reinterpret_cast<const int*>(acc) + ACC_W * ACC_W;
     const float inv_dx2f = (float)geo.inv_dx2;
     for (int i = threadIdx.x; i < BIN_TILE * BIN_TILE; i += blockDim.x) {
-        const int gi = tx * BIN_TILE + (i % BIN_TILE), gj = ty * BIN_TILE + (i / BIN_TILE);
+        const int lx = i % BIN_TILE, ly = i / BIN_TILE;
+        const int gi = tx * BIN_TILE + lx, gj = ty * BIN_TILE + ly;
+        const int node = (ly + ACC_HALO) * ACC_W + lx + ACC_HALO;
         if (gi < geo.nx && gj < geo.ny) {
             long long a;
-            if (split32) a = (long long)acc_hi[i] * 65536ll + (long long)acc_lo[i];
-            else a = (long long)acc[i];
+            if (split32) a = (long long)acc_hi[node] * 65536ll + (long long)acc_lo[node];
+            else a = (long long)acc[node];
             T v;
             if (sizeof(T) == 4) v = (T)(__ll2float_rn(a) * pow2<float>(-sh) * inv_dx2f);
-            else v = (T)(ldexp((double)a, -sh) * inv_dx2);
+            else v = (T)(ldexp((double)a, -sh) * geo.inv_dx2);
             w[(size_t)gj * geo.nx + gi] = v;
         }
     }
@@ -459,6 +554,78 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
     }
 }
 
+// FP32 variant of k_interp_tiles that reads each stencil row with two 16-byte
+// shared loads: the patch is staged twice as node pairs, starting at even and
+// at odd local x, so that the four nodes px .. px + 3 of a row are the pairs
+// E[px / 2], E[px / 2 + 1] (px even) or O[(px - 1) / 2], O[(px + 1) / 2].
+constexpr int PAIRS = (PATCH + 1) / 2;   // 18 pairs per patch row
+
+__global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __restrict__ recs,
+                                                          const int* __restrict__ ridx,
+                                                          const int* __restrict__ tile_start,
+                                                          const unsigned* __restrict__ tile_count,
+                                                          const float2* __restrict__ uv, Geo geo,
+                                                          float* __restrict__ uq, float* __restrict__ vq) {
+    __shared__ float4 pe[PATCH * PAIRS];
+    __shared__ float4 po[PATCH * PAIRS];
+    const int t = blockIdx.x;
+    const int cnt = (int)tile_count[t];
+    if (cnt == 0) return;
+    const int tx = t % geo.ntx, ty = t / geo.ntx;
+    const int gi0 = tx * BIN_TILE - 1, gj0 = ty * BIN_TILE - 1;
+    // patch nodes px, py in [0, 2 PAIRS) x [0, PATCH); px = 2 PAIRS - 1 only pads
+    for (int i = threadIdx.x; i < PATCH * 2 * PAIRS; i += blockDim.x) {
+        const int px = i % (2 * PAIRS), py = i / (2 * PAIRS);
+        const int gi = gi0 + px, gj = gj0 + py;
+        float2 v = make_float2(0.f, 0.f);
+        if (px < PATCH && gi >= 0 && gi < geo.nx && gj >= 0 && gj < geo.ny) v = uv[(size_t)gj * geo.nx + gi];
+        float* e = reinterpret_cast<float*>(&pe[py * PAIRS + px / 2]) + 2 * (px & 1);
+        e[0] = v.x;
+        e[1] = v.y;
+        if (px >= 1) {
+            float* o = reinterpret_cast<float*>(&po[py * PAIRS + (px - 1) / 2]) + 2 * ((px - 1) & 1);
+            o[0] = v.x;
+            o[1] = v.y;
+        }
+    }
+    __syncthreads();
+    const int start = tile_start[t];
+    constexpr int U = 4;
+    for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
+        Rec<float> rc[U];
+        int qi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {           // loads first
+            const int r = r0 + u * blockDim.x + threadIdx.x;
+            rc[u].lx = -1;
+            if (r < cnt) {
+                rc[u] = recs[start + r];
+                qi[u] = ridx[start + r];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int lx = rc[u].lx, ly = rc[u].ly;
+            if (lx < 0 || lx >= BIN_TILE || ly < 0 || ly >= BIN_TILE) continue;  // not home
+            float wx[4], wy[4];
+            m4p_weights<float>(rc[u].fx, wx);
+            m4p_weights<float>(rc[u].fy, wy);
+            const float4* rows = (lx & 1) ? po + (lx - 1) / 2 : pe + lx / 2;   // node px = lx is the first
+            float su = 0.f, sv = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float4 p0 = rows[(ly + b) * PAIRS], p1 = rows[(ly + b) * PAIRS + 1];
+                const float ru = wx[0] * p0.x + wx[1] * p0.z + wx[2] * p1.x + wx[3] * p1.z;
+                const float rv = wx[0] * p0.y + wx[1] * p0.w + wx[2] * p1.y + wx[3] * p1.w;
+                su += wy[b] * ru;
+                sv += wy[b] * rv;
+            }
+            uq[qi[u]] = su;
+            vq[qi[u]] = sv;
+        }
+    }
+}
+
 // E_v at arbitrary points
 template <typename T>
 __global__ void k_interp_xy(const T* __restrict__ uv, const double* __restrict__ X, const double* __restrict__ Y,
@@ -468,8 +635,8 @@ __global__ void k_interp_xy(const T* __restrict__ uv, const double* __restrict__
         int ci = 0, cj = 0;
         T fx = 0, fy = 0;
         T su = 0, sv = 0;
-        if (split(X[q], geo.x0, geo.dx, geo.inv_dx, geo.cx, geo.nx, ci, fx) &&
-            split(Y[q], geo.y0, geo.dx, geo.inv_dx, geo.cy, geo.ny, cj, fy)) {
+        if (split(X[q], geo.x0, geo.dx, geo.inv_dx, geo.cx, geo.nx, geo.xlim, ci, fx) &&
+            split(Y[q], geo.y0, geo.dx, geo.inv_dx, geo.cy, geo.ny, geo.ylim, cj, fy)) {
             gather16<T>(uv, geo.nx, ci, cj, fx, fy, su, sv);
         } else {
             atomicAdd(oob, 1ull);
@@ -485,10 +652,11 @@ __global__ void k_interp_xy(const T* __restrict__ uv, const double* __restrict__
 struct BinWork {
     int* status;
     unsigned long long* oob;
-    unsigned* tile_count;
+    unsigned* tile_count;     // written by k_offsets
     unsigned* tile_gmax;
+    unsigned* tile_rep;       // 2 TILE_REP * ntiles, cleared before each locate
     int* tile_start;
-    unsigned* tile_cursor;
+    int* bin_off;             // bin_blocks(nv) * ntiles
     void* pos;
     void* recs;
     int* ridx;          // original index of every binned record (may be null)
@@ -501,6 +669,9 @@ inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
     g.cx = -x0 / dx;
     g.cy = -y0 / dx;
     g.inv_dx2 = 1.0 / (dx * dx);
+    const double lx = (double)(nx - 2), ly = (double)(ny - 2);
+    memcpy(&g.xlim, &lx, sizeof(double));
+    memcpy(&g.ylim, &ly, sizeof(double));
     g.ntx = ceil_div(nx, BIN_TILE);
     g.ntiles = g.ntx * ceil_div(ny, BIN_TILE);
     return g;
@@ -520,22 +691,24 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename T>
 pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
                             const double* G, int64_t nv, T* w, cudaStream_t s) {
-    // tile_count, tile_gmax and tile_cursor are contiguous: one clear
-    if (cudaMemsetAsync(bw.tile_count, 0, 3 * (size_t)geo.ntiles * sizeof(unsigned), s) != cudaSuccess) return PF_ERR_CUDA;
-    const int nb = nv > 0 ? ceil_div(nv, CHUNK) : 0;
+    if (cudaMemsetAsync(bw.tile_rep, 0, 2 * (size_t)TILE_REP * geo.ntiles * sizeof(unsigned), s) != cudaSuccess)
+        return PF_ERR_CUDA;
+    const int nb = bin_blocks(nv);
+    const int64_t span = bin_span(nv);
     const size_t sh = 2 * (size_t)geo.ntiles * sizeof(unsigned);
     if (set_smem(k_locate<T>, sh) != cudaSuccess || set_smem(k_scatter<T>, sh) != cudaSuccess) return PF_ERR_CUDA;
     Pos<T>* pos = (Pos<T>*)bw.pos;
     if (nb > 0) {
-        PF_KERNEL(p, "bin_locate", k_locate<T><<<nb, BIN_THREADS, sh, s>>>(X, Y, G, nv, geo, pos, bw.tile_count,
-                                                                           bw.tile_gmax, bw.status, bw.oob));
+        PF_KERNEL(p, "bin_locate", k_locate<T><<<nb, BIN_THREADS, sh, s>>>(X, Y, G, nv, span, geo, pos, bw.tile_rep,
+                                                                           bw.bin_off, bw.status, bw.oob));
     }
+    PF_KERNEL(p, "bin_offsets", k_offsets<<<ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s>>>(
+                                     bw.tile_rep, geo.ntiles, nb, bw.bin_off, bw.tile_start, bw.tile_count,
+                                     bw.tile_gmax));
     if (nb > 0) {
-        PF_KERNEL(p, "bin_scatter", k_scatter<T><<<nb, BIN_THREADS, sh, s>>>(pos, nv, geo, bw.tile_count,
-                                                                             bw.tile_start, bw.tile_cursor,
+        PF_KERNEL(p, "bin_scatter", k_scatter<T><<<nb, BIN_THREADS, sh, s>>>(pos, nv, span, geo, bw.bin_off,
                                                                              (Rec<T>*)bw.recs, bw.ridx));
     }
-    if (nb == 0 && cudaMemsetAsync(bw.tile_start, 0, geo.ntiles * sizeof(int), s) != cudaSuccess) return PF_ERR_CUDA;
     PF_KERNEL(p, "regularize", k_deposit<T><<<geo.ntiles, 256, 0, s>>>((const Rec<T>*)bw.recs, bw.tile_start,
                                                                       bw.tile_count, bw.tile_gmax, geo, w));
     return PF_OK;
@@ -544,6 +717,10 @@ pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const 
 pf_status plan_bin_reserve(pf_plan p, int64_t nv) {
     const size_t psz = p->prec == PF_FP64 ? sizeof(Pos<double>) : sizeof(Pos<float>);
     const size_t rsz = p->prec == PF_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
+    if (nv > (int64_t)1 << 29) {   // record slots are 32-bit
+        snprintf(p->err, sizeof(p->err), "%lld vortices exceed the 2^29 a plan can bin", (long long)nv);
+        return PF_ERR_CAPACITY;
+    }
     // capacities grow geometrically so a slowly growing vortex set (shedding)
     // does not reallocate every step
     if (nv > p->pos_cap) {
@@ -567,6 +744,16 @@ pf_status plan_bin_reserve(pf_plan p, int64_t nv) {
         PF_CUDA(p, cudaMalloc(&p->ridx, (size_t)cap * sizeof(int)));
         p->rec_cap = cap;
     }
+    const int64_t need = (int64_t)bin_blocks(nv) * p->ntiles;
+    if (need > p->bin_off_cap) {
+        const int64_t cap = std::max<int64_t>(need, (int64_t)bin_blocks(p->pos_cap) * p->ntiles);
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        if (p->bin_off) cudaFree(p->bin_off);
+        p->bin_off = nullptr;
+        p->bin_off_cap = 0;
+        PF_CUDA(p, cudaMalloc(&p->bin_off, (size_t)cap * sizeof(int)));
+        p->bin_off_cap = cap;
+    }
     return PF_OK;
 }
 
@@ -576,8 +763,9 @@ BinWork plan_binwork(pf_plan p) {
     b.oob = p->d_oob;
     b.tile_count = p->tile_count;
     b.tile_gmax = p->tile_gmax;
+    b.tile_rep = p->tile_rep;
     b.tile_start = p->tile_start;
-    b.tile_cursor = p->tile_cursor;
+    b.bin_off = p->bin_off;
     b.pos = p->pos;
     b.recs = p->recs;
     b.ridx = p->ridx;
@@ -607,7 +795,7 @@ pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void
                                         (const Rec<double>*)p->recs, p->ridx, p->tile_start, p->tile_count,
                                         (const double2*)uv, geo, (double*)uq, (double*)vq));
     else
-        PF_KERNEL(p, "interpolate", k_interp_tiles<float><<<geo.ntiles, 256, 0, p->stream>>>(
+        PF_KERNEL(p, "interpolate", k_interp_tiles_f32<<<geo.ntiles, 256, 0, p->stream>>>(
                                         (const Rec<float>*)p->recs, p->ridx, p->tile_start, p->tile_count,
                                         (const float2*)uv, geo, (float*)uq, (float*)vq));
     return PF_OK;
@@ -641,11 +829,13 @@ namespace {
 
 constexpr int64_t NOALLOC_MAX_VORTICES = 65536;
 constexpr int NOALLOC_MAX_TILES = (2048 / BIN_TILE) * (2048 / BIN_TILE);
+constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_VORTICES / 1024);   // bin_blocks() at the maximum
 constexpr size_t NOALLOC_HEADER = 256;   // status int + out-of-domain counter, padded
-constexpr size_t NOALLOC_TILE_BYTES = (size_t)NOALLOC_MAX_TILES * 5 * sizeof(int);
+constexpr size_t NOALLOC_TILE_BYTES = (size_t)NOALLOC_MAX_TILES * (4 + 2 * TILE_REP) * sizeof(int);
+constexpr size_t NOALLOC_OFF_BYTES = (size_t)NOALLOC_MAX_BLOCKS * NOALLOC_MAX_TILES * sizeof(int);
 constexpr size_t NOALLOC_POS_BYTES = (size_t)NOALLOC_MAX_VORTICES * sizeof(Pos<double>);
-constexpr size_t NOALLOC_SCRATCH_BYTES =
-    NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_POS_BYTES + (size_t)4 * NOALLOC_MAX_VORTICES * sizeof(Rec<double>);
+constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES +
+                                         (size_t)4 * NOALLOC_MAX_VORTICES * sizeof(Rec<double>);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -675,12 +865,13 @@ BinWork noalloc_binwork(unsigned char* base, int ntiles) {
     b.oob = (unsigned long long*)(base + 8);
     unsigned* t = (unsigned*)(base + NOALLOC_HEADER);
     const int nt = ntiles;         // <= NOALLOC_MAX_TILES
-    b.tile_count = t;              // count, gmax and cursor contiguous for one clear
+    b.tile_count = t;
     b.tile_gmax = t + nt;
-    b.tile_cursor = t + 2 * nt;
-    b.tile_start = (int*)(t + 3 * nt);
-    b.pos = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES;
-    b.recs = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_POS_BYTES;
+    b.tile_start = (int*)(t + 2 * nt);
+    b.tile_rep = t + 3 * nt;       // 2 TILE_REP * nt
+    b.bin_off = (int*)(base + NOALLOC_HEADER + NOALLOC_TILE_BYTES);
+    b.pos = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES;
+    b.recs = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES;
     b.ridx = nullptr;   // no interpolation follows an allocation-free regularization
     return b;
 }
@@ -693,7 +884,7 @@ extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* 
     if (d->nx < 8 || d->ny < 8 || d->nx > 2048 || d->ny > 2048 || !(d->dx > 0) || !isfinite(d->x0) ||
         !isfinite(d->y0) || (d->precision != PF_FP64 && d->precision != PF_MIXED))
         return PF_ERR_ARG;
-    if (nv > NOALLOC_MAX_VORTICES) return PF_ERR_CAPACITY;
+    if (nv > NOALLOC_MAX_VORTICES || bin_blocks(nv) > NOALLOC_MAX_BLOCKS) return PF_ERR_CAPACITY;
     unsigned char* base = nullptr;
     if (noalloc_scratch(&base) != cudaSuccess) return PF_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
