@@ -110,8 +110,7 @@ struct pf_plan_s {
     int64_t bin_off_cap = 0;           // entries
     void* pos = nullptr;               // per-vortex cell records of the last located set
     int64_t pos_cap = 0;
-    void* recs = nullptr;              // records binned by tile
-    int* ridx = nullptr;               // original vortex index of each binned record
+    void* recs = nullptr;              // records binned by tile (with each vortex's original index)
     int64_t rec_cap = 0;
     // host-input staging for the *_host entry points
     double* stage = nullptr;

@@ -72,7 +72,7 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
     const int64_t grid = 3 * spec + 3 * (int64_t)s.nx * s.ny * esz;
     const int64_t c = cap > 4096 ? cap : 4096;
     const int64_t ntiles = (int64_t)((s.nx + 31) / 32) * ((s.ny + 31) / 32);
-    const int64_t bins = c * 32 + 4 * c * 36 + (4 + 2 * TILE_REP) * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
+    const int64_t bins = c * 32 + 4 * c * 32 + (4 + 2 * TILE_REP) * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
     const int64_t state = 5 * cap * 8 + 4 * cap * esz + 4096 * 8;
     const int64_t schur = (int64_t)ns * ns * 8 * 4 + (int64_t)ns * 200;
     return grid + bins + state + schur;

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -26,24 +27,31 @@ namespace {
 constexpr int BIN_THREADS = 256;
 constexpr int BIN_UNROLL = 4;        // vortices per thread whose loads are issued together
 
-// per-vortex cell record (original order)
+// Per-vortex cell record (original order).  Mixed path: packed cell and the
+// 32-bit cell fractions as fixed-point integers; FP64: cell and fractions.
 template <typename T> struct Pos;
 template <> struct __align__(16) Pos<float> {
-    unsigned cell;    // ci | cj << 16
-    float fx, fy, g;
+    unsigned cell;        // ci | cj << 16
+    unsigned fxw, fyw;    // fraction * 2^32 (truncated)
+    float g;
 };
 template <> struct __align__(16) Pos<double> {
     int ci, cj;
     double fx, fy, g;
 };
-// per-tile record
+// Per-tile record: cell relative to the tile origin (lx, ly in [-2, 32]),
+// fractions, Gamma and the vortex's original index q.  Mixed path: each
+// fraction keeps 24 bits, fixed point, with the biased local cell lx + 2 in the
+// low 8 bits of the same word (16 bytes in all, like the FP64 record's 32).
 template <typename T> struct Rec;
 template <> struct __align__(16) Rec<float> {
-    short lx, ly;     // cell index relative to the tile origin
-    float fx, fy, g;
+    unsigned xw, yw;      // (fraction * 2^32) & ~0xFF | (local cell + 2)
+    float g;
+    int q;
 };
 template <> struct __align__(16) Rec<double> {
-    int lx, ly;
+    short lx, ly;
+    int q;
     double fx, fy, g;
 };
 
@@ -51,6 +59,34 @@ __device__ __forceinline__ int pos_ci(const Pos<float>& p) { return (int)(p.cell
 __device__ __forceinline__ int pos_cj(const Pos<float>& p) { return (int)(p.cell >> 16); }
 __device__ __forceinline__ int pos_ci(const Pos<double>& p) { return p.ci; }
 __device__ __forceinline__ int pos_cj(const Pos<double>& p) { return p.cj; }
+
+__device__ __forceinline__ int rec_lx(const Rec<float>& r) { return (int)(r.xw & 0xFFu) - 2; }
+__device__ __forceinline__ int rec_ly(const Rec<float>& r) { return (int)(r.yw & 0xFFu) - 2; }
+__device__ __forceinline__ float rec_fx(const Rec<float>& r) { return __uint2float_rn(r.xw >> 8) * 0x1p-24f; }
+__device__ __forceinline__ float rec_fy(const Rec<float>& r) { return __uint2float_rn(r.yw >> 8) * 0x1p-24f; }
+__device__ __forceinline__ int rec_lx(const Rec<double>& r) { return r.lx; }
+__device__ __forceinline__ int rec_ly(const Rec<double>& r) { return r.ly; }
+__device__ __forceinline__ double rec_fx(const Rec<double>& r) { return r.fx; }
+__device__ __forceinline__ double rec_fy(const Rec<double>& r) { return r.fy; }
+
+__device__ __forceinline__ Rec<float> make_rec(const Pos<float>& p, int lx, int ly, int q) {
+    Rec<float> r;
+    r.xw = (p.fxw & ~0xFFu) | (unsigned)(lx + 2);
+    r.yw = (p.fyw & ~0xFFu) | (unsigned)(ly + 2);
+    r.g = p.g;
+    r.q = q;
+    return r;
+}
+__device__ __forceinline__ Rec<double> make_rec(const Pos<double>& p, int lx, int ly, int q) {
+    Rec<double> r;
+    r.lx = (short)lx;
+    r.ly = (short)ly;
+    r.q = q;
+    r.fx = p.fx;
+    r.fy = p.fy;
+    r.g = p.g;
+    return r;
+}
 
 // M4' weights of the four nodes floor(g)-1 .. floor(g)+2 for fractional part f
 template <typename T>
@@ -93,6 +129,20 @@ __device__ __forceinline__ bool split(double X, double, double, double inv_dx, d
     return true;
 }
 
+// Mixed path of the binning passes: as split, but the cell fraction is returned
+// as a 32-bit fixed-point integer (fraction * 2^32, truncated).
+__device__ __forceinline__ bool split_fixed(double X, double inv_dx, double c0, long long lim, int& c, unsigned& fr) {
+    const double g = fma(X, inv_dx, c0);
+    const long long gb = __double_as_longlong(g);
+    if (gb < 0x3FF0000000000000ll || gb >= lim) return false;
+    const unsigned hi = (unsigned)((unsigned long long)gb >> 32), lo = (unsigned)gb;
+    const int e = (int)(hi >> 20) - 1023;
+    const unsigned m20 = hi & 0xFFFFFu;
+    c = (int)((m20 | 0x100000u) >> (20 - e));
+    fr = __funnelshift_l(lo, m20, 12 + e);
+    return true;
+}
+
 // double -> float rounded to nearest even with integer instructions only (the
 // FP64 pipe is 1/64 rate); zero, and values outside the normal FP32 range,
 // take the hardware conversion.  Bitwise equal to (float)d.
@@ -109,10 +159,10 @@ __device__ __forceinline__ float d2f(double d) {
     return __uint_as_float(out);
 }
 
-__device__ __forceinline__ void make_pos(Pos<float>& p, int ci, int cj, float fx, float fy, double g) {
+__device__ __forceinline__ void make_pos(Pos<float>& p, int ci, int cj, unsigned fxw, unsigned fyw, double g) {
     p.cell = (unsigned)ci | ((unsigned)cj << 16);
-    p.fx = fx;
-    p.fy = fy;
+    p.fxw = fxw;
+    p.fyw = fyw;
     p.g = d2f(g);
 }
 __device__ __forceinline__ void make_pos(Pos<double>& p, int ci, int cj, double fx, double fy, double g) {
@@ -130,6 +180,15 @@ struct Geo {
     long long xlim, ylim;      // bit patterns of (double)(nx - 2), (double)(ny - 2)
     int nx, ny, ntx, ntiles;
 };
+
+// the split used by the locate pass: fixed-point fraction (mixed), exact (FP64)
+__device__ __forceinline__ bool loc_split(double X, const Geo& g, int axis, int& c, unsigned& fr) {
+    return split_fixed(X, g.inv_dx, axis ? g.cy : g.cx, axis ? g.ylim : g.xlim, c, fr);
+}
+__device__ __forceinline__ bool loc_split(double X, const Geo& g, int axis, int& c, double& f) {
+    return split(X, axis ? g.y0 : g.x0, g.dx, 0.0, 0.0, axis ? g.ny : g.nx, 0, c, f);
+}
+template <typename T> using Frac = typename std::conditional<sizeof(T) == 4, unsigned, double>::type;
 
 template <typename T>
 __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
@@ -166,12 +225,11 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
             const int64_t q = base + k * BIN_THREADS + threadIdx.x;
             if (q >= hi) break;
             int ci = 0, cj = 0;
-            T fx = 0, fy = 0;
+            Frac<T> fx = 0, fy = 0;
             Pos<T> p;
-            if (!split(xs[k], geo.x0, geo.dx, geo.inv_dx, geo.cx, geo.nx, geo.xlim, ci, fx) ||
-                !split(ys[k], geo.y0, geo.dx, geo.inv_dx, geo.cy, geo.ny, geo.ylim, cj, fy)) {
+            if (!loc_split(xs[k], geo, 0, ci, fx) || !loc_split(ys[k], geo, 1, cj, fy)) {
                 ++bad;
-                make_pos(p, 0xFFFF, 0xFFFF, T(0), T(0), 0.0);   // marker: skipped by scatter and interpolation
+                make_pos(p, 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);   // marker: skipped by scatter
                 pos[q] = p;
                 continue;
             }
@@ -238,15 +296,14 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-// Record offsets: tile_count and tile_gmax (reduced over the replicas),
-// tile_start (exclusive scan of tile_count) and, in place over the block
-// histograms, off[b][t] = tile_start[t] + sum_{b' < b} hist[b'][t].
+// Per-tile totals and per-(block, tile) offsets within the tile: tile_count
+// and tile_gmax (reduced over the replicas) and, in place over the block
+// histograms, off[b][t] = sum_{b' < b} hist[b'][t].  Blocks are independent
+// (the tiles' first slots are added by the scatter pass).
 __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ tile_rep, int ntiles, int nb,
-                                                  int* __restrict__ hist_off, int* __restrict__ tile_start,
-                                                  unsigned* __restrict__ tile_count, unsigned* __restrict__ tile_gmax) {
+                                                  int* __restrict__ hist_off, unsigned* __restrict__ tile_count,
+                                                  unsigned* __restrict__ tile_gmax) {
     __shared__ int part[OFF_SEGS][OFF_TILES + 1];
-    __shared__ int red[32];
-    __shared__ int tstart[OFF_TILES];
     const int tx = threadIdx.x % OFF_TILES, ty = threadIdx.x / OFF_TILES;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int t0 = blockIdx.x * OFF_TILES, t = t0 + tx;
@@ -260,11 +317,6 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
         if (k < S && b0 + k < nb && t < ntiles) v[k] = hist_off[(size_t)(b0 + k) * ntiles + t];
         seg += v[k];
     }
-    int s = 0;                                        // records in the tiles before t0 (all replicas)
-#pragma unroll 16
-    for (int i = threadIdx.x; i < t0 * TILE_REP; i += 1024) s += (int)tile_rep[i];
-    s = warp_sum(s);
-    if (lane == 0) red[wid] = s;
     part[ty][tx] = seg;
     __syncthreads();
     if (wid < OFF_TILES) {                            // exclusive scan over the runs of tile t0 + wid
@@ -276,18 +328,16 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
         part[4 * lane + 1][wid] = ex + a0;
         part[4 * lane + 2][wid] = ex + a0 + a1;
         part[4 * lane + 3][wid] = ex + a0 + a1 + a2;
-    } else if (wid == OFF_TILES) {                    // totals and first slots of the block's tiles
+    } else if (wid == OFF_TILES) {                    // totals of the block's tiles
         static_assert(OFF_TILES * 4 == 32 && TILE_REP % 4 == 0, "four lanes per tile");
-        const int before = warp_sum(red[lane]);
         const int tl = lane / 4, q = lane % 4;          // tile t0 + tl, replicas [q R/4, (q + 1) R/4)
-        int c = 0;
-        unsigned gm = 0u;
+        unsigned c = 0u, gm = 0u;
         if (t0 + tl < ntiles) {
             const unsigned* rc = tile_rep + (size_t)(t0 + tl) * TILE_REP + q * (TILE_REP / 4);
             const unsigned* rg = rc + (size_t)ntiles * TILE_REP;
 #pragma unroll
             for (int r = 0; r < TILE_REP / 4; ++r) {
-                c += (int)rc[r];
+                c += rc[r];
                 gm = max(gm, rg[r]);
             }
         }
@@ -296,21 +346,14 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
             c += __shfl_xor_sync(0xffffffffu, c, o);
             gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
         }
-        // lanes 4 tl .. 4 tl + 3 hold tile tl's total: scan over the lanes q == 0
-        const int own = q == 0 ? c : 0;
-        const int ex = before + warp_incl_scan(own, lane) - own;
-        if (q == 0) {
-            tstart[tl] = ex;
-            if (t0 + tl < ntiles) {
-                tile_start[t0 + tl] = ex;
-                tile_count[t0 + tl] = (unsigned)c;
-                tile_gmax[t0 + tl] = gm;
-            }
+        if (q == 0 && t0 + tl < ntiles) {
+            tile_count[t0 + tl] = c;
+            tile_gmax[t0 + tl] = gm;
         }
     }
     __syncthreads();
     if (t < ntiles) {
-        int run = tstart[tx] + part[ty][tx];
+        int run = part[ty][tx];
 #pragma unroll
         for (int k = 0; k < OFF_RUN; ++k) {
             if (k < S && b0 + k < nb) hist_off[(size_t)(b0 + k) * ntiles + t] = run;
@@ -319,48 +362,83 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
     }
 }
 
+// Every block scans the tile totals itself (block 0 publishes the tiles' first
+// slots for the deposit and interpolation passes), adds them to its offsets
+// and places its records.
+constexpr int SCAN_PER = 16;     // tiles per thread in the block scan: 256 * 16 >= 64 * 64 tiles
+template <typename T> struct ScatterUnroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+static_assert((2048 / BIN_TILE) * (2048 / BIN_TILE) <= BIN_THREADS * SCAN_PER, "scan covers every tile");
+
 template <typename T>
-__global__ void __launch_bounds__(BIN_THREADS) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
+__global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
                                                         Geo geo, const int* __restrict__ off,
-                                                        Rec<T>* __restrict__ recs, int* __restrict__ ridx) {
+                                                        const unsigned* __restrict__ tile_count,
+                                                        int* __restrict__ tile_start, Rec<T>* __restrict__ recs) {
     extern __shared__ unsigned sm[];
+    __shared__ int wsum[BIN_THREADS / 32];
     unsigned* cnt = sm;
     int* first = (int*)(sm + geo.ntiles);
-    const int* row = off + (size_t)blockIdx.x * geo.ntiles;
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) {
-        cnt[i] = 0u;
-        first[i] = row[i];
-    }
-    __syncthreads();
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
-    for (int64_t base = lo; base < hi; base += BIN_THREADS * BIN_UNROLL) {
-        Pos<T> p[BIN_UNROLL];
+    // this thread's first records (in flight during the scan)
+    Pos<T> p[ScatterUnroll<T>::value];
 #pragma unroll
-        for (int k = 0; k < BIN_UNROLL; ++k) {     // loads first
-            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-            if (q < hi) p[k] = pos[q];
-            else make_pos(p[k], 0xFFFF, 0xFFFF, T(0), T(0), 0.0);
+    for (int k = 0; k < ScatterUnroll<T>::value; ++k) {
+        const int64_t q = lo + k * BIN_THREADS + threadIdx.x;
+        if (q < hi) p[k] = pos[q];
+        else make_pos(p[k], 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);
+    }
+    // exclusive scan of tile_count: thread i owns tiles [i * per, i * per + per)
+    const int per = (geo.ntiles + BIN_THREADS - 1) / BIN_THREADS;   // <= SCAN_PER
+    const int t0 = threadIdx.x * per;
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k)
+        if (k < per && t0 + k < geo.ntiles) mine += (int)tile_count[t0 + k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int run = incl - mine;
+    for (int w = 0; w < wid; ++w) run += wsum[w];
+    const int* row = off + (size_t)blockIdx.x * geo.ntiles;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const int i = t0 + k;
+        if (k < per && i < geo.ntiles) {
+            cnt[i] = 0u;
+            first[i] = run + row[i];
+            if (blockIdx.x == 0) tile_start[i] = run;
+            run += (int)tile_count[i];
+        }
+    }
+    __syncthreads();
+    for (int64_t base = lo; base < hi; base += BIN_THREADS * ScatterUnroll<T>::value) {
+        if (base != lo) {
+#pragma unroll
+            for (int k = 0; k < ScatterUnroll<T>::value; ++k) {     // loads first
+                const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+                if (q < hi) p[k] = pos[q];
+                else make_pos(p[k], 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < BIN_UNROLL; ++k) {
+        for (int k = 0; k < ScatterUnroll<T>::value; ++k) {
             const int ci = pos_ci(p[k]), cj = pos_cj(p[k]);
             if (ci == 0xFFFF) continue;
             const int64_t q = base + k * BIN_THREADS + threadIdx.x;
             const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
             const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
-            Rec<T> r;
-            r.fx = p[k].fx;
-            r.fy = p[k].fy;
-            r.g = p[k].g;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx) {
                     const int t = ty * geo.ntx + tx;
                     const int slot = first[t] + (int)atomicAdd(&cnt[t], 1u);
-                    r.lx = (decltype(r.lx))(ci - tx * BIN_TILE);
-                    r.ly = (decltype(r.ly))(cj - ty * BIN_TILE);
-                    recs[slot] = r;
-                    if (ridx) ridx[slot] = (int)q;
+                    recs[slot] = make_rec(p[k], ci - tx * BIN_TILE, cj - ty * BIN_TILE, (int)q);
                 }
         }
     }
@@ -405,10 +483,10 @@ __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs,
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
         const Rec<T> rc = recs[r];
         T wx[4], wy[4];
-        m4p_weights<T>(rc.fx, wx);
-        m4p_weights<T>(rc.fy, wy);
+        m4p_weights<T>(rec_fx(rc), wx);
+        m4p_weights<T>(rec_fy(rc), wy);
         const T gs = rc.g * scale;
-        const int base = (rc.ly - 1 + ACC_HALO) * ACC_W + (rc.lx - 1 + ACC_HALO);
+        const int base = (rec_ly(rc) - 1 + ACC_HALO) * ACC_W + (rec_lx(rc) - 1 + ACC_HALO);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const T gy = gs * wy[b];
@@ -496,7 +574,7 @@ __device__ __forceinline__ void gather16(const T* __restrict__ uv, int nx, int c
 constexpr int PATCH = BIN_TILE + 3;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__ recs, const int* __restrict__ ridx,
+__global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__ recs,
                                                       const int* __restrict__ tile_start,
                                                       const unsigned* __restrict__ tile_count, const C_t<T>* __restrict__ uv,
                                                       Geo geo, T* __restrict__ uq, T* __restrict__ vq) {
@@ -518,26 +596,25 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<T> rc[U];
-        int qi[U];
+        bool ok[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {           // loads first
             const int r = r0 + u * blockDim.x + threadIdx.x;
-            rc[u].lx = -1;
-            if (r < cnt) {
-                rc[u] = recs[start + r];
-                qi[u] = ridx[start + r];
-            }
+            ok[u] = r < cnt;
+            if (ok[u]) rc[u] = recs[start + r];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (rc[u].lx < 0 || rc[u].lx >= BIN_TILE || rc[u].ly < 0 || rc[u].ly >= BIN_TILE) continue;  // not home
+            if (!ok[u]) continue;
+            const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
+            if (lx < 0 || lx >= BIN_TILE || ly < 0 || ly >= BIN_TILE) continue;  // not home
             T wx[4], wy[4];
-            m4p_weights<T>(rc[u].fx, wx);
-            m4p_weights<T>(rc[u].fy, wy);
+            m4p_weights<T>(rec_fx(rc[u]), wx);
+            m4p_weights<T>(rec_fy(rc[u]), wy);
             T su = 0, sv = 0;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const C* row = patch + (rc[u].ly + b) * PATCH + rc[u].lx;    // node (lx - 1 + a, ly - 1 + b)
+                const C* row = patch + (ly + b) * PATCH + lx;    // node (lx - 1 + a, ly - 1 + b)
                 T ru = 0, rv = 0;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -548,8 +625,8 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
                 su += wy[b] * ru;
                 sv += wy[b] * rv;
             }
-            uq[qi[u]] = su;
-            vq[qi[u]] = sv;
+            uq[rc[u].q] = su;
+            vq[rc[u].q] = sv;
         }
     }
 }
@@ -561,7 +638,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
 constexpr int PAIRS = (PATCH + 1) / 2;   // 18 pairs per patch row
 
 __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __restrict__ recs,
-                                                          const int* __restrict__ ridx,
                                                           const int* __restrict__ tile_start,
                                                           const unsigned* __restrict__ tile_count,
                                                           const float2* __restrict__ uv, Geo geo,
@@ -593,23 +669,21 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<float> rc[U];
-        int qi[U];
+        bool ok[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {           // loads first
             const int r = r0 + u * blockDim.x + threadIdx.x;
-            rc[u].lx = -1;
-            if (r < cnt) {
-                rc[u] = recs[start + r];
-                qi[u] = ridx[start + r];
-            }
+            ok[u] = r < cnt;
+            if (ok[u]) rc[u] = recs[start + r];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int lx = rc[u].lx, ly = rc[u].ly;
+            if (!ok[u]) continue;
+            const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
             if (lx < 0 || lx >= BIN_TILE || ly < 0 || ly >= BIN_TILE) continue;  // not home
             float wx[4], wy[4];
-            m4p_weights<float>(rc[u].fx, wx);
-            m4p_weights<float>(rc[u].fy, wy);
+            m4p_weights<float>(rec_fx(rc[u]), wx);
+            m4p_weights<float>(rec_fy(rc[u]), wy);
             const float4* rows = (lx & 1) ? po + (lx - 1) / 2 : pe + lx / 2;   // node px = lx is the first
             float su = 0.f, sv = 0.f;
 #pragma unroll
@@ -620,8 +694,8 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
                 su += wy[b] * ru;
                 sv += wy[b] * rv;
             }
-            uq[qi[u]] = su;
-            vq[qi[u]] = sv;
+            uq[rc[u].q] = su;
+            vq[rc[u].q] = sv;
         }
     }
 }
@@ -659,7 +733,6 @@ struct BinWork {
     int* bin_off;             // bin_blocks(nv) * ntiles
     void* pos;
     void* recs;
-    int* ridx;          // original index of every binned record (may be null)
 };
 
 inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
@@ -703,11 +776,13 @@ pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const 
                                                                            bw.bin_off, bw.status, bw.oob));
     }
     PF_KERNEL(p, "bin_offsets", k_offsets<<<ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s>>>(
-                                     bw.tile_rep, geo.ntiles, nb, bw.bin_off, bw.tile_start, bw.tile_count,
-                                     bw.tile_gmax));
+                                     bw.tile_rep, geo.ntiles, nb, bw.bin_off, bw.tile_count, bw.tile_gmax));
     if (nb > 0) {
         PF_KERNEL(p, "bin_scatter", k_scatter<T><<<nb, BIN_THREADS, sh, s>>>(pos, nv, span, geo, bw.bin_off,
-                                                                             (Rec<T>*)bw.recs, bw.ridx));
+                                                                             bw.tile_count, bw.tile_start,
+                                                                             (Rec<T>*)bw.recs));
+    } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
+        return PF_ERR_CUDA;
     }
     PF_KERNEL(p, "regularize", k_deposit<T><<<geo.ntiles, 256, 0, s>>>((const Rec<T>*)bw.recs, bw.tile_start,
                                                                       bw.tile_count, bw.tile_gmax, geo, w));
@@ -736,12 +811,9 @@ pf_status plan_bin_reserve(pf_plan p, int64_t nv) {
         const int64_t cap = 4 * p->pos_cap;
         PF_CUDA(p, cudaStreamSynchronize(p->stream));
         if (p->recs) cudaFree(p->recs);
-        if (p->ridx) cudaFree(p->ridx);
         p->recs = nullptr;
-        p->ridx = nullptr;
         p->rec_cap = 0;
         PF_CUDA(p, cudaMalloc(&p->recs, (size_t)cap * rsz));
-        PF_CUDA(p, cudaMalloc(&p->ridx, (size_t)cap * sizeof(int)));
         p->rec_cap = cap;
     }
     const int64_t need = (int64_t)bin_blocks(nv) * p->ntiles;
@@ -768,7 +840,6 @@ BinWork plan_binwork(pf_plan p) {
     b.bin_off = p->bin_off;
     b.pos = p->pos;
     b.recs = p->recs;
-    b.ridx = p->ridx;
     return b;
 }
 
@@ -792,11 +863,11 @@ pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void
     const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0);
     if (p->prec == PF_FP64)
         PF_KERNEL(p, "interpolate", k_interp_tiles<double><<<geo.ntiles, 256, 0, p->stream>>>(
-                                        (const Rec<double>*)p->recs, p->ridx, p->tile_start, p->tile_count,
+                                        (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
                                         (const double2*)uv, geo, (double*)uq, (double*)vq));
     else
         PF_KERNEL(p, "interpolate", k_interp_tiles_f32<<<geo.ntiles, 256, 0, p->stream>>>(
-                                        (const Rec<float>*)p->recs, p->ridx, p->tile_start, p->tile_count,
+                                        (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
                                         (const float2*)uv, geo, (float*)uq, (float*)vq));
     return PF_OK;
 }
@@ -872,7 +943,6 @@ BinWork noalloc_binwork(unsigned char* base, int ntiles) {
     b.bin_off = (int*)(base + NOALLOC_HEADER + NOALLOC_TILE_BYTES);
     b.pos = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES;
     b.recs = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES;
-    b.ridx = nullptr;   // no interpolation follows an allocation-free regularization
     return b;
 }
 
