@@ -1,40 +1,67 @@
-"""Summarise an ncu launch list (CSV of gpu__time_duration.sum) per kernel.
+"""Summaries of ncu output for the step kernels.
 
-Usage: python -m paper_2102_11910_gb300.profiling launches.csv
-Prints, per kernel, the number of launches, total device time and share.
+Usage:
+  python -m paper_2102_11910_gb300.profiling launches launches.csv
+      per kernel: launches, total device time and share, from an ncu CSV of
+      gpu__time_duration.sum (one pass; cold-cache, serialised launches);
+  python -m paper_2102_11910_gb300.profiling traffic raw.csv
+      per step kernel: DRAM bytes read + written per launch, from
+      `ncu -i report --page raw --csv`, as the JSON that bench.py reads
+      (keyed by the source hash of csrc/, so a stale capture is ignored).
 """
 import collections
 import csv
+import glob
+import hashlib
+import json
+import os
 import re
 import sys
 
+HERE = os.path.dirname(os.path.abspath(__file__))
 
-STEP_KERNELS = {"k_bin_count", "k_bin_scan", "k_bin_scatter", "k_regularize", "k_rows_fwd", "k_cols", "k_rows_inv",
-                "k_interpolate"}
+# kernel function -> name used by the per-kernel timing of the library
+STEP_KERNELS = {
+    "k_locate": "bin_locate", "k_offsets": "bin_offsets", "k_scatter": "bin_scatter", "k_deposit": "regularize",
+    "k_rows_fwd_r": "fft_rows_fwd", "k_cols_r": "fft_cols_conv", "k_rows_inv_r": "fft_rows_inv",
+    "k_interp_tiles_f32": "interpolate", "k_interp_tiles": "interpolate",
+}
+
+
+def csrc_sha():
+    """Hash of the CUDA sources; counters taken from another build do not apply."""
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(HERE, "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def kernel_name(raw):
     s = raw.replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
     s = re.sub(r"^void\s+", "", s)
-    s = s.replace("<unnamed>::", "")
     return re.split(r"[<(]", s, maxsplit=1)[0].strip()
 
 
-def main(path):
+def _rows(path):
     rows = list(csv.reader(open(path)))
     hi = [i for i, r in enumerate(rows) if "Kernel Name" in r][0]
-    h = rows[hi]
+    return rows[hi], rows[hi + 1:]
+
+
+def launches(path):
+    h, body = _rows(path)
     ki, mi, ui = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Unit")
     tot, cnt = collections.OrderedDict(), collections.Counter()
     scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3, "s": 1e6,
              "second": 1e6}
-    for r in rows[hi + 1:]:
+    for r in body:
         if len(r) <= mi or not r[mi]:
             continue
         us = float(r[mi].replace(",", "")) * scale.get(r[ui], 1.0)
         name = kernel_name(r[ki])
         tot[name] = tot.get(name, 0.0) + us
         cnt[name] += 1
+
     def table(names, title):
         T = sum(tot[k] for k in names)
         print(title)
@@ -49,5 +76,27 @@ def main(path):
         table(step, "kernels of the VIC step only (plan set-up and torch fills excluded)")
 
 
+def traffic(path):
+    rows = list(csv.reader(open(path)))
+    h, units, body = rows[0], rows[1], rows[2:]
+    ki = h.index("Kernel Name")
+    cols = {m: h.index(m) for m in ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum")}
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    acc = collections.defaultdict(lambda: [0.0, 0])
+    for r in body:
+        name = STEP_KERNELS.get(kernel_name(r[ki]))
+        if not name:
+            continue
+        b = 0.0
+        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            i = cols[m]
+            b += float(r[i].replace(",", "")) * unit.get(units[i], 1.0)
+        acc[name][0] += b
+        acc[name][1] += 1
+    out = {"csrc_sha": csrc_sha(), "source": os.path.basename(path),
+           "kernels": {k: {"dram_bytes": v[0] / v[1], "launches": v[1]} for k, v in acc.items()}}
+    print(json.dumps(out, indent=1))
+
+
 if __name__ == "__main__":
-    main(sys.argv[1])
+    {"launches": launches, "traffic": traffic}[sys.argv[1]](sys.argv[2])
