@@ -283,6 +283,22 @@ def bench_ours(args):
 
     extras = {}
     if not args.no_extras:
+        # impulse diagnostics (Sec. 2.6.2) of the step's vorticity: node reduction time
+        with torch.cuda.stream(stream):
+            w = pf.pf_regularize(plan, X, Y, G)
+            pf.pf_impulse(plan, w)
+            pf.pf_timing_enable(plan, True)
+            for _ in range(20):
+                flush.fill_(3)
+                pf.pf_impulse(plan, w)
+            rimp = pf.pf_timing_report(plan)
+            pf.pf_timing_enable(plan, False)
+        n_i, ms_i = rimp["impulse"]
+        us_i = 1e3 * ms_i / n_i
+        gbs_i = g.nx * g.ny * 4 / (us_i * 1e-6) / 1e9
+        extras["impulse"] = {"kernel_us": us_i, "alg_bytes": g.nx * g.ny * 4, "gbs": gbs_i, "frac": gbs_i / hbm_peak,
+                             "final_us": 1e3 * rimp["impulse_final"][1] / rimp["impulse_final"][0],
+                             "value": [float(v) for v in pf.pf_impulse(plan, w)]}
         # all-FP64 GPU path on the same workload, and the mixed path's error against it
         with torch.cuda.stream(stream):
             p64 = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_FP64, stream=stream)

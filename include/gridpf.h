@@ -192,6 +192,29 @@ pf_status pf_sheet_solve(pf_plan plan, pf_schur schur, const void* w, const pf_m
                          const double* Xnew, const double* Ynew, double* f, double* gamma_new,
                          double* s0);
 
+/* Linear and angular impulse of the fluid about the origin (Sec. 2.6.2,
+ * Eqs. linimpxd, linimpyd, angimpd); for a single body the force and moment
+ * are F = -rho dP/dt and M_O = -rho dPi_O/dt (Eq. FMimp):
+ *   P_x  =  <y, w>_N + <y_s, f + n_x v_y - n_y v_x>_S
+ *   P_y  = -<x, w>_N - <x_s, f + n_x v_y - n_y v_x>_S
+ *   Pi_O = -1/2 <x^2 + y^2, w>_N - 1/2 <x_s^2 + y_s^2, f + n_x v_y - n_y v_x>_S
+ * with <a, b>_N = dx^2 sum over the nodes, <a, b>_S = sum_p dS_p a_p b_p and the
+ * rigid surface velocity v = (U - Omega y_s, V + Omega x_s).
+ *   w        real[nx*ny] node vorticity of the fluid (device), e.g. from pf_regularize
+ *   body     surface points (host arrays, as for pf_schur_factor), or NULL: node
+ *            terms only
+ *   nxs, nys double[ns] unit normals into the fluid (HOST), or both NULL: the
+ *            slip term n x v is left out (a zero-thickness plate, whose two sides
+ *            cancel it)
+ *   f        double[ns] bound sheet strength (device, e.g. from pf_sheet_solve);
+ *            required when body has points
+ *   m        body motion (host; U, V, Omega used) or NULL for a body at rest
+ *   out      double[3] (host): P_x, P_y, Pi_O
+ * Sums run in FP64 in a fixed order (bitwise reproducible).  Synchronises the
+ * plan's stream. */
+pf_status pf_impulse(pf_plan plan, const void* w, const pf_body_desc* body, const double* nxs,
+                     const double* nys, const double* f, const pf_motion* m, double* out);
+
 /* ------------------------------------------------------- time stepping */
 
 /* Device-resident vortex set (positions and strengths, FP64) with a fixed

@@ -22,4 +22,6 @@ body     surface operators R_s/E_s, Schur complement S (Eq. vsheet), f0, Gamma0,
          of Sec. 2.3-2.4 (Eqs. circsystem, kuttasystem, kuttasystem2,
          kuttasystem3/twovortex).
 step     vortex shedding placement and the Euler / RK2 time step (Sec. 2.4.2).
+diagnostics  linear and angular impulse of the fluid (Sec. 2.6.2, Eqs.
+         linimpxd, linimpyd, angimpd).
 """

@@ -271,6 +271,33 @@ def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None,
     return f, list(gn[:ne]), s0.value
 
 
+def pf_impulse(plan, w, x=None, y=None, ds=None, f=None, nx=None, ny=None, motion=None):
+    """(P_x, P_y, Pi_O) of the fluid about the origin for node vorticity w (device
+    field) and, optionally, a surface (host arrays x, y, ds, normals nx, ny) with
+    its sheet strength f (device float64).  motion = (U, V, Omega) of the body."""
+    import numpy as np
+    c = ctypes.c_void_p
+    desc = None
+    keep = []
+    if x is not None:
+        x, y, ds = _host_f64(x), _host_f64(y), _host_f64(ds)
+        keep += [x, y, ds]
+        desc = _native.PfBodyDesc(len(x), c(x.ctypes.data), c(y.ctypes.data), c(ds.ctypes.data))
+    pn = [None, None]
+    if nx is not None:
+        nx, ny = _host_f64(nx), _host_f64(ny)
+        keep += [nx, ny]
+        pn = [c(nx.ctypes.data), c(ny.ctypes.data)]
+    m = _native.PfMotion(*(list(float(v) for v in motion) + [0.0, 0.0])) if motion is not None else None
+    out = np.zeros(3)
+    _native.check(_native.lib().pf_impulse(plan.handle, _ptr(w, plan.dtype, "w"),
+                                           ctypes.byref(desc) if desc is not None else None, pn[0], pn[1],
+                                           _ptr(f, torch.float64, "f") if f is not None else None,
+                                           ctypes.byref(m) if m is not None else None,
+                                           c(out.ctypes.data)), "pf_impulse", plan.handle)
+    return out
+
+
 class State:
     """Handle of a pf_state (device-resident vortex set)."""
 

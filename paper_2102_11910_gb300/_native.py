@@ -37,6 +37,7 @@ SIGNATURES = {
     "pf_schur_destroy": (_c.c_int, [_P]),
     "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
     "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
+    "pf_impulse": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),

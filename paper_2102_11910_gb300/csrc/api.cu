@@ -19,7 +19,7 @@ void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
     void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->bin_off,
-                   p->pos, p->recs, p->stage, p->stage_out, p->d_status, p->d_oob};
+                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);
     if (p->shared && --p->shared->refs == 0) {
@@ -107,6 +107,7 @@ pf_status plan_workspaces(pf_plan p) {
     p->tile_gmax = p->tile_count + p->ntiles;
     p->tile_rep = p->tile_count + 2 * p->ntiles;
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->diag, PF_DIAG_DOUBLES * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
     PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));

@@ -49,6 +49,7 @@ struct KTiming {
 
 // ------------------------------------------------------------ plan
 constexpr int BIN_TILE = 32;   // node tile edge used by binning and regularization
+constexpr int PF_DIAG_DOUBLES = 4 * 2048 + 3 + 5 * 4096;   // impulse scratch: row partials, results, surface
 
 // Vortex partition of the binning passes: block b owns vortices
 // [b * span, min(nv, (b + 1) * span)).  Large sets use exactly BIN_MAX_BLOCKS
@@ -116,6 +117,8 @@ struct pf_plan_s {
     double* stage = nullptr;
     int64_t stage_cap = 0;
     void* stage_out = nullptr;
+    // diagnostics scratch (per-block partial sums and results)
+    double* diag = nullptr;            // PF_DIAG_DOUBLES
     // status
     int* d_status = nullptr;
     unsigned long long* d_oob = nullptr;
