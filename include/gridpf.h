@@ -126,8 +126,10 @@ pf_status pf_interpolate(pf_plan plan, const void* uv, const double* Xq, const d
 pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const double* Gam,
                           int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 
-/* Same step with HOST input and output buffers: copies X, Y, Gam to the
- * device, runs pf_vic_velocity, copies uq, vq (real[nv]) back, synchronises. */
+/* Same step with HOST input and output buffers, synchronous.  Page-locked
+ * inputs (cudaHostAlloc / cudaHostRegister) are read by the first kernel
+ * directly over the host link; pageable inputs are first copied to a device
+ * staging buffer.  uq, vq (real[nv]) are copied back from the device. */
 pf_status pf_vic_velocity_host(pf_plan plan, const double* X, const double* Y, const double* Gam,
                                int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 

@@ -124,8 +124,12 @@ def test_vic_velocity_end_to_end(prec, n, nv):
     _, _, ru, rv = OV.vortex_velocity(_og(g), X, Y, G, 0.25, 0.0)
     assert rel(uq.cpu().numpy(), ru) < TOL[prec]
     assert rel(vq.cpu().numpy(), rv) < TOL[prec]
-    # host-buffer entry point gives the same numbers
+    # host-buffer entry point gives the same numbers, from pageable inputs (staged
+    # through a copy) and from page-locked ones (read in place by the first kernel)
     hu, hv = pf.pf_vic_velocity_host(plan, torch.from_numpy(X), torch.from_numpy(Y), torch.from_numpy(G), 0.25, 0.0)
+    assert torch.equal(hu, uq.cpu()) and torch.equal(hv, vq.cpu())
+    pX, pY, pG = (torch.from_numpy(a).pin_memory() for a in (X, Y, G))
+    hu, hv = pf.pf_vic_velocity_host(plan, pX, pY, pG, 0.25, 0.0)
     assert torch.equal(hu, uq.cpu()) and torch.equal(hv, vq.cpu())
 
 
