@@ -380,8 +380,18 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
             body = pf.plate_kinematics(64, 1.0, wl["alpha"], Uinf=1.0)
             pf.pf_step(plan, state, 0.002, body)             # includes the one-off factorisation
             res[name] = _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, 0.002, body), 20)
+        # the same with the generalized edge condition at the leading edge (Sec. 2.5)
+        plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+        state = pf.State(plan, 256 + 2 * 64)
+        pf.pf_state_set(state, wl["X"], wl["Y"], wl["G"])
+        xi = -1.0 + (2.0 * np.arange(1, 65) - 1.0) / 64
+        body = pf.BodyKinematics(0.5 * xi, np.zeros(64), np.full(64, 1.0 / 64), (0, 63), wl["alpha"], Uinf=1.0,
+                                 edge_bounds=((-0.5, 0.5), (0.0, 0.0)))
+        pf.pf_step(plan, state, 0.002, body)
+        res["mixed_edge_bounded"] = _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, 0.002, body), 20)
         out["plate_128"] = {"unit": "steps/s", "desc": "128^2, plate 20 deg, Ns 64, 256 vortices, Euler, dt 0.002, "
-                            "two-edge release every step (factor reused)", **res}
+                            "two-edge release every step (factor reused); edge_bounded: leading edge under "
+                            "|ftilde| <= 0.5 (generalized edge condition), trailing edge Kutta", **res}
         # pitching plate, 768 x 512, Ns 256, RK2, S refactored at every stage
         pw = inputs.pitching_plate_512x768()
         g = pw["grid"]

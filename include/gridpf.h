@@ -217,6 +217,22 @@ pf_status pf_sheet_solve(pf_plan plan, pf_schur schur, const void* w, const pf_m
 pf_status pf_impulse(pf_plan plan, const void* w, const pf_body_desc* body, const double* nxs,
                      const double* nys, const double* f, const pf_motion* m, double* out);
 
+/* Generalized edge condition (Sec. 2.5, Eq. twovortex-gen): the shedding
+ * solve of pf_sheet_solve (mode PF_SHEET_KUTTA_SHED, param = gamma_w, the
+ * circulation of w) with bounds on the edge values of the non-singular sheet
+ * ftilde.  Edge e (surface point edges[e]) sheds only when the intermediate
+ * sheet's value there, e_k^T ftilde*, lies outside [bounds[2e], bounds[2e+1]],
+ * and then with the strength that puts the final value at the bound it
+ * crossed; an edge inside its range sheds nothing (gamma_new[e] = 0).  Zero
+ * bounds are the Kutta condition.  For a flat plate of chord c the bounds
+ * follow from the edge suction parameter sigma_k through
+ * e_k^T ftilde = -(2 pi c / Gamma0) sigma_k.  bounds: host, 2 n_edges, with
+ * lo <= hi (else PF_ERR_ARG).  Other arguments and outputs as for
+ * pf_sheet_solve.  Synchronises. */
+pf_status pf_sheet_solve_edges(pf_plan plan, pf_schur schur, const void* w, const pf_motion* m, double gamma_w,
+                               int32_t n_edges, const int32_t* edges, const double* bounds, const double* Xnew,
+                               const double* Ynew, double* f, double* gamma_new, double* s0);
+
 /* ------------------------------------------------------- time stepping */
 
 /* Device-resident vortex set (positions and strengths, FP64) with a fixed
@@ -247,6 +263,8 @@ typedef struct {
     int32_t edge[2];
     double alpha0, amp, omega;
     double Uinf, Vinf;
+    int32_t edge_bounded;        /* 0: Kutta at both edges; 1: generalized edge condition  */
+    double edge_bounds[4];       /* lo_0, hi_0, lo_1, hi_1 (as pf_sheet_solve_edges)        */
 } pf_body_kinematics;
 
 /* Advance the vortex set by dt.  With a body that has two edges, two vortices
@@ -257,7 +275,9 @@ typedef struct {
  * velocity of psi = -L^-1 (w + new vortices + R_s f) plus the free stream.
  * scheme 0: forward Euler (the paper's); 1: Heun's RK2 whose second stage at
  * t + dt keeps the new strengths and sets the bound circulation to
- * -sum Gamma (Eq. circsystem).  S is refactored whenever the pose changes
+ * -sum Gamma (Eq. circsystem).  With edge_bounded the release follows the
+ * generalized edge condition of pf_sheet_solve_edges (an edge inside its
+ * bounds releases a vortex of zero strength).  S is refactored whenever the pose changes
  * (every stage of a pitching body); nothing in a step waits for the host.
  * PF_ERR_CAPACITY if two more vortices do not fit. */
 pf_status pf_step(pf_plan plan, pf_state state, const pf_body_kinematics* body, double dt,

@@ -192,6 +192,71 @@ def sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, EinvLd1, EinvLd2, Gamma_w):
     return sch.f0 * ft, ft, s0, G1, G2
 
 
+def edge_targets(fts, edges, bounds):
+    """Generalized edge condition (Sec. 2.5): for each edge k the intermediate
+    value e_k^T ftilde* is tested against [fmin_k, fmax_k]; an edge outside its
+    range is active and its target is the bound it crossed.
+    Returns [(k, active, target)]."""
+    out = []
+    for k, (lo, hi) in zip(edges, bounds):
+        v = fts[k]
+        if lo <= v <= hi:
+            out.append((k, False, 0.0))
+        else:
+            out.append((k, True, lo if v < lo else hi))
+    return out
+
+
+def sheet_edge_shed(sch, sbp, EinvLw, edges, EinvLds, Gamma_w, bounds):
+    """New vortices at one or two edges under the generalized edge condition
+    (Sec. 2.5, Eq. twovortex-gen), Kelvin over the whole flow.
+
+    Active edges solve A Gamma = b with A_ij = 1 + f0hat^T P_ki ftilde_j and
+    b_i = -(Gamma_w + f0hat^T P_ki ftilde* + Gamma0 target_i); an edge inside
+    its range sheds nothing (Gamma = 0).  Then g = ftilde* + sum Gamma_j ftilde_j
+    and s0 = g_k - target_k on the active edges (their mean for two); with no
+    active edge Kelvin alone fixes s0 = (f0hat^T ftilde* + Gamma_w)/Gamma0.
+    fmin = fmax = 0 is the Kutta condition.  Returns (f, ftilde, s0, Gammas).
+    """
+    fts = intermediate_sheet(sch, sbp, EinvLw)
+    fts_j = [sch.solve_tilde(e) for e in EinvLds]
+    tg = edge_targets(fts, edges, bounds)
+    act = [i for i, (_, a, _) in enumerate(tg) if a]
+    G = np.zeros(len(edges))
+    if act:
+        A = np.array([[1.0 + sch.f0hat_Pk(fts_j[j], tg[i][0]) for j in act] for i in act])
+        b = -np.array([Gamma_w + sch.f0hat_Pk(fts, tg[i][0]) + sch.Gamma0 * tg[i][2] for i in act])
+        G[act] = np.linalg.solve(A, b)
+    g = fts + sum(G[j] * fts_j[j] for j in range(len(edges)))
+    if act:
+        s0 = float(np.mean([g[tg[i][0]] - tg[i][2] for i in act]))
+    else:
+        s0 = (float(np.dot(sch.f0hat, fts)) + Gamma_w) / sch.Gamma0
+    ft = g - s0 * sch.ones
+    return sch.f0 * ft, ft, s0, G
+
+
+def sheet_edge_shed2_monolithic(S, f0, f0hat, PGsb, EinvLw, k1, k2, EinvLd1, EinvLd2, Gamma_w, t1, t2):
+    """Dense (Ns+3) solve of the two-edge system with edge targets t1, t2
+    (both edges active; Sec. 2.5): the rows of Eq. kuttasystem3 with
+    e_k1^T ftilde = t1, e_k2^T ftilde = t2."""
+    ns = S.shape[0]
+    A = np.zeros((ns + 3, ns + 3))
+    A[:ns, :ns] = S * f0[None, :]
+    A[:ns, ns] = 1.0
+    A[:ns, ns + 1] = -EinvLd1
+    A[:ns, ns + 2] = -EinvLd2
+    A[ns, k1] = 1.0
+    A[ns + 1, k2] = 1.0
+    A[ns + 2, :ns] = f0hat
+    A[ns + 2, ns + 1] = 1.0
+    A[ns + 2, ns + 2] = 1.0
+    rhs = np.concatenate([PGsb + EinvLw, [t1, t2, -Gamma_w]])
+    x = np.linalg.solve(A, rhs)
+    ft = x[:ns]
+    return f0 * ft, ft, x[ns], x[ns + 1], x[ns + 2]
+
+
 def sheet_kutta_shed2_schur3(sch, sbp, EinvLw, k1, k2, EinvLd1, EinvLd2, Gamma_w):
     """Same solution from the unsplit 3x3 Schur problem (Eq. schurkutta2)."""
     fts = intermediate_sheet(sch, sbp, EinvLw)

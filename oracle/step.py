@@ -29,9 +29,10 @@ class Kinematics:
     A body with no edges is Kelvin-constrained and releases nothing.
     """
 
-    def __init__(self, ns, chord, alpha0, amp=0.0, omega=0.0, Uinf=1.0, Vinf=0.0, body=None):
+    def __init__(self, ns, chord, alpha0, amp=0.0, omega=0.0, Uinf=1.0, Vinf=0.0, body=None, edge_bounds=None):
         self.ns, self.chord, self.alpha0, self.amp, self.omega = ns, chord, alpha0, amp, omega
         self.Uinf, self.Vinf = Uinf, Vinf
+        self.edge_bounds = edge_bounds      # None: Kutta at both edges; else generalized (Sec. 2.5)
         if body is None:
             xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
             body = (0.5 * chord * xi, np.zeros(ns), np.full(ns, chord / ns), (0, ns - 1))
@@ -103,8 +104,11 @@ def _solve_and_velocity(grid, table, kin, t, X, Y, G, shed, dt, last_pos):
         p2 = new_vortex_position(xs, ys, k2, last_pos[1], dt, kin.Uinf, kin.Vinf)
         nX, nY = np.array([p1[0], p2[0]]), np.array([p1[1], p2[1]])
         E = B.EinvL_unit_vortex(grid, st, nX, nY, table)
-        f, ft, s0, G1, G2 = B.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
-        nG = np.array([G1, G2])
+        if kin.edge_bounds is None:
+            f, ft, s0, G1, G2 = B.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+            nG = np.array([G1, G2])
+        else:      # an edge inside its bounds releases a vortex of zero strength
+            f, ft, s0, nG = B.sheet_edge_shed(sch, sbp, EinvLw, (k1, k2), (E[:, 0], E[:, 1]), Gw, kin.edge_bounds)
     else:
         f, s0 = B.sheet_circulation(sch, sbp, EinvLw, -Gw)
         nX, nY, nG = np.zeros(0), np.zeros(0), np.zeros(0)

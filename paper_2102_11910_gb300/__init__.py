@@ -298,6 +298,27 @@ def pf_impulse(plan, w, x=None, y=None, ds=None, f=None, nx=None, ny=None, motio
     return out
 
 
+def pf_sheet_solve_edges(plan, schur, w, motion, gamma_w, edges, bounds, Xnew, Ynew, f=None):
+    """Generalized edge condition: bounds = ((lo0, hi0)[, (lo1, hi1)]) on the edge
+    values of ftilde.  Returns (f device float64 tensor, gamma_new host list, s0)."""
+    import numpy as np
+    f = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if f is None else f
+    ed = np.ascontiguousarray(edges, dtype=np.int32)
+    ne = len(ed)
+    bd = _host_f64([v for pair in bounds for v in pair])
+    xn, yn = _host_f64(Xnew), _host_f64(Ynew)
+    gn = np.zeros(ne)
+    s0 = ctypes.c_double()
+    m = _native.PfMotion(*[float(v) for v in motion])
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_sheet_solve_edges(plan.handle, schur.handle, _ptr(w, plan.dtype, "w"),
+                                                     ctypes.byref(m), float(gamma_w), ne, c(ed.ctypes.data),
+                                                     c(bd.ctypes.data), c(xn.ctypes.data), c(yn.ctypes.data),
+                                                     _ptr(f, torch.float64, "f"), c(gn.ctypes.data), ctypes.byref(s0)),
+                  "pf_sheet_solve_edges", plan.handle)
+    return f, list(gn), s0.value
+
+
 class State:
     """Handle of a pf_state (device-resident vortex set)."""
 
@@ -351,13 +372,16 @@ class BodyKinematics:
     edges: () for a Kelvin-constrained body, or the two surface-point indices
     at which vortices are released."""
 
-    def __init__(self, xb, yb, ds, edges=(), alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0):
+    def __init__(self, xb, yb, ds, edges=(), alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0, edge_bounds=None):
+        """edge_bounds: None (Kutta) or ((lo0, hi0), (lo1, hi1)) for the generalized edge condition."""
         self.xb, self.yb, self.ds = _host_f64(xb), _host_f64(yb), _host_f64(ds)
         e = list(edges)
         c = ctypes.c_void_p
+        eb = [float(v) for pair in edge_bounds for v in pair] if edge_bounds is not None else [0.0] * 4
         self.struct = _native.PfBodyKinematics(len(self.xb), c(self.xb.ctypes.data), c(self.yb.ctypes.data),
                                                c(self.ds.ctypes.data), len(e), (ctypes.c_int32 * 2)(*(e + [0, 0])[:2]),
-                                               float(alpha0), float(amp), float(omega), float(Uinf), float(Vinf))
+                                               float(alpha0), float(amp), float(omega), float(Uinf), float(Vinf),
+                                               1 if edge_bounds is not None else 0, (ctypes.c_double * 4)(*eb))
 
 
 def plate_kinematics(ns, chord=1.0, alpha0=0.0, amp=0.0, omega=0.0, Uinf=0.0, Vinf=0.0):

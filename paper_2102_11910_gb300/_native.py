@@ -38,6 +38,7 @@ SIGNATURES = {
     "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
     "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
     "pf_impulse": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),
@@ -78,7 +79,8 @@ class PfMotion(ctypes.Structure):
 
 class PfBodyKinematics(ctypes.Structure):
     _fields_ = [("ns", _I32), ("xb", _P), ("yb", _P), ("ds", _P), ("n_edges", _I32), ("edge", _I32 * 2),
-                ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D)]
+                ("alpha0", _D), ("amp", _D), ("omega", _D), ("Uinf", _D), ("Vinf", _D),
+                ("edge_bounded", _I32), ("edge_bounds", _D * 4)]
 
 
 class PfServerConfig(ctypes.Structure):

@@ -315,7 +315,11 @@ __global__ void k_gemv(const double* __restrict__ Sinv, int ns, const double* __
 //                 G1 = (-Gw - f0hat^T P_k ft*) / (1 + f0hat^T P_k ft_1), g = ft* + G1 ft_1, s0 = g_k;
 //                 two edges: 2x2 system of Eq. twovortex, g = ft* + G1 ft_1 + G2 ft_2,
 //                 s0 = (g_k1 + g_k2)/2;  f = f0 o (g - s0)
-__global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, double param_h,
+//                 With edge bounds (Sec. 2.5, Eq. twovortex-gen) an edge whose ft*_k lies
+//                 inside [lo, hi] sheds nothing (G = 0, its row dropped) and an active
+//                 edge's row gets + Gamma0 target on the right and s0 = g_k - target;
+//                 with no active edge Kelvin alone gives s0 = (f0hat^T ft* + Gw)/Gamma0.
+__global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, EdgeBounds eb, double param_h,
                               const double* __restrict__ param_d, const double* __restrict__ ds,
                               const double* __restrict__ f0, const double* __restrict__ f0hat,
                               const double* __restrict__ gamma0p, const double* __restrict__ y,
@@ -360,22 +364,44 @@ __global__ void k_constraints(int mode, int ns, int nedge, int k1, int k2, doubl
             s0 = fs1;
         } else if (nedge == 1) {
             const double t1 = y1[k1] / f0[k1];
-            G1 = (-param - (h0 - Gamma0 * fs1)) / (1.0 + (h1 - Gamma0 * t1));
-            s0 = fs1 + G1 * t1;
+            const bool act = !eb.on || !(eb.lo[0] <= fs1 && fs1 <= eb.hi[0]);
+            const double tg = (eb.on && fs1 < eb.lo[0]) ? eb.lo[0] : (eb.on ? eb.hi[0] : 0.0);
+            if (act) {
+                G1 = (-param - (h0 - Gamma0 * fs1) - Gamma0 * tg) / (1.0 + (h1 - Gamma0 * t1));
+                s0 = fs1 + G1 * t1 - tg;
+            } else {
+                s0 = (h0 + param) / Gamma0;
+            }
         } else {
             const double fs2 = y0[k2] / f0[k2];
             const double t11 = y1[k1] / f0[k1], t12 = y2[k1] / f0[k1];
             const double t21 = y1[k2] / f0[k2], t22 = y2[k2] / f0[k2];
-            // A_ij = 1 + f0hat^T P_ki ft_j,  b_i = -(Gw + f0hat^T P_ki ft*),  f0hat^T P_k v = f0hat^T v - Gamma0 v_k
+            const bool act1 = !eb.on || !(eb.lo[0] <= fs1 && fs1 <= eb.hi[0]);
+            const bool act2 = !eb.on || !(eb.lo[1] <= fs2 && fs2 <= eb.hi[1]);
+            const double tg1 = (eb.on && fs1 < eb.lo[0]) ? eb.lo[0] : (eb.on ? eb.hi[0] : 0.0);
+            const double tg2 = (eb.on && fs2 < eb.lo[1]) ? eb.lo[1] : (eb.on ? eb.hi[1] : 0.0);
+            // A_ij = 1 + f0hat^T P_ki ft_j,  b_i = -(Gw + f0hat^T P_ki ft* + Gamma0 target_i),
+            // f0hat^T P_k v = f0hat^T v - Gamma0 v_k
             const double A11 = 1.0 + h1 - Gamma0 * t11, A12 = 1.0 + h2 - Gamma0 * t12;
             const double A21 = 1.0 + h1 - Gamma0 * t21, A22 = 1.0 + h2 - Gamma0 * t22;
-            const double b1 = -(param + h0 - Gamma0 * fs1), b2 = -(param + h0 - Gamma0 * fs2);
-            const double det = A11 * A22 - A12 * A21;
-            G1 = (b1 * A22 - A12 * b2) / det;
-            G2 = (A11 * b2 - A21 * b1) / det;
-            const double g1 = fs1 + G1 * t11 + G2 * t12;
-            const double g2 = fs2 + G1 * t21 + G2 * t22;
-            s0 = 0.5 * (g1 + g2);
+            const double b1 = -(param + h0 - Gamma0 * fs1 + Gamma0 * tg1);
+            const double b2 = -(param + h0 - Gamma0 * fs2 + Gamma0 * tg2);
+            if (act1 && act2) {
+                const double det = A11 * A22 - A12 * A21;
+                G1 = (b1 * A22 - A12 * b2) / det;
+                G2 = (A11 * b2 - A21 * b1) / det;
+                const double g1 = fs1 + G1 * t11 + G2 * t12;
+                const double g2 = fs2 + G1 * t21 + G2 * t22;
+                s0 = 0.5 * ((g1 - tg1) + (g2 - tg2));
+            } else if (act1) {
+                G1 = b1 / A11;
+                s0 = fs1 + G1 * t11 - tg1;
+            } else if (act2) {
+                G2 = b2 / A22;
+                s0 = fs2 + G2 * t22 - tg2;
+            } else {
+                s0 = (h0 + param) / Gamma0;
+            }
         }
         sc[0] = s0;
         sc[1] = G1;
@@ -533,7 +559,7 @@ void schur_free(pf_schur s) {
 // (s0, Gamma1, Gamma2) on the device.
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
-                             const double* vy, double* f) {
+                             const double* vy, double* f, const EdgeBounds& eb) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     double* sb = s->work;
@@ -562,8 +588,8 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     }
     k_gemv<<<ns, 128, 0, st>>>(s->Sinv, ns, rhs, nc, y);
     PF_LAUNCH_CHECK(p);
-    k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, param,
-                                     param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
+    k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, eb,
+                                     param, param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
@@ -647,6 +673,33 @@ pf_status pf_sheet_solve(pf_plan p, pf_schur s, const void* w, const pf_motion* 
     if (s0) *s0 = sc[0];
     if (gamma_new)
         for (int e = 0; e < (mode == PF_SHEET_KUTTA_SHED ? n_edges : 0); ++e) gamma_new[e] = sc[1 + e];
+    return PF_OK;
+}
+
+pf_status pf_sheet_solve_edges(pf_plan p, pf_schur s, const void* w, const pf_motion* m, double gamma_w,
+                               int32_t n_edges, const int32_t* edges, const double* bounds, const double* Xnew,
+                               const double* Ynew, double* f, double* gamma_new, double* s0) {
+    if (!p || !w || !m || !f || !bounds || !edges || !Xnew || !Ynew || n_edges < 1 || n_edges > 2) return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    EdgeBounds eb;
+    eb.on = 1;
+    for (int e = 0; e < n_edges; ++e) {
+        if (edges[e] < 0 || edges[e] >= s->ns || !(bounds[2 * e] <= bounds[2 * e + 1])) return PF_ERR_ARG;
+        eb.lo[e] = bounds[2 * e];
+        eb.hi[e] = bounds[2 * e + 1];
+    }
+    double* vxy = s->scal + 4;
+    PF_CUDA(p, cudaMemcpyAsync(vxy, Xnew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(vxy + 2, Ynew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    pf_status st = sheet_solve_device(p, s, w, *m, PF_SHEET_KUTTA_SHED, gamma_w, nullptr, n_edges, edges, vxy, vxy + 2,
+                                      f, eb);
+    if (st != PF_OK) return st;
+    double sc[3];
+    PF_CUDA(p, cudaMemcpyAsync(sc, s->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (s0) *s0 = sc[0];
+    if (gamma_new)
+        for (int e = 0; e < n_edges; ++e) gamma_new[e] = sc[1 + e];
     return PF_OK;
 }
 

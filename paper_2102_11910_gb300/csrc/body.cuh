@@ -26,10 +26,18 @@ struct pf_schur_s {
 pf_status schur_create(pf_plan p, int ns, pf_schur* out);
 void schur_free(pf_schur s);
 pf_status schur_factor_device(pf_plan p, pf_schur s);
+// Generalized edge condition (Sec. 2.5) for the shedding mode: with on = 0 every
+// edge sheds under the Kutta condition; otherwise edge e sheds only when its
+// intermediate value lies outside [lo[e], hi[e]], and ends at the bound crossed.
+struct EdgeBounds {
+    int on = 0;
+    double lo[2] = {0.0, 0.0};
+    double hi[2] = {0.0, 0.0};
+};
 // param_dev (nullable): device copy of `param` read by the kernels instead
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
-                             const double* vy, double* f);
+                             const double* vy, double* f, const EdgeBounds& eb = EdgeBounds());
 // w += R_s f  (device f of ns doubles, w real[nx*ny])
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);
 

@@ -238,8 +238,14 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
         e.first_dist = 10.0 * dt * U;
         k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
         PF_LAUNCH_CHECK(p);
+        EdgeBounds eb;
+        eb.on = k.edge_bounded ? 1 : 0;
+        for (int j = 0; j < 2; ++j) {
+            eb.lo[j] = k.edge_bounds[2 * j];
+            eb.hi[j] = k.edge_bounds[2 * j + 1];
+        }
         PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos, s->newpos + 2,
-                                  s->f));
+                                  s->f, eb));
         // release: the new vortices join the arrays X, Y (the caller's position
         // arrays) and G
         k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, sch->scal);
@@ -362,7 +368,9 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_body_kinematics* k, double dt,
     if (body && (k->ns < 4 || !k->xb || !k->yb || !k->ds || (k->n_edges != 0 && k->n_edges != 2))) return PF_ERR_ARG;
     if (body && k->n_edges == 2)
         for (int e = 0; e < 2; ++e)
-            if (k->edge[e] < 0 || k->edge[e] >= k->ns) return PF_ERR_ARG;
+            if (k->edge[e] < 0 || k->edge[e] >= k->ns ||
+                (k->edge_bounded && !(k->edge_bounds[2 * e] <= k->edge_bounds[2 * e + 1])))
+                return PF_ERR_ARG;
     const bool release = body && k->n_edges == 2;
     if (release && s->nv + 2 > s->cap) return PF_ERR_CAPACITY;
     const int64_t n0 = s->nv;
