@@ -106,6 +106,7 @@ pf_status plan_workspaces(pf_plan p) {
     PF_CUDA(p, cudaMalloc(&p->tile_count, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
     p->tile_gmax = p->tile_count + p->ntiles;
     p->tile_rep = p->tile_count + 2 * p->ntiles;
+    PF_CUDA(p, cudaMemset(p->tile_count, 0, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->diag, PF_DIAG_DOUBLES * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));

@@ -160,6 +160,31 @@ cudaEvent_t tm_event(pf_plan p);   // api.cu
 
 #define PF_LAUNCH_CHECK(plan) PF_CUDA(plan, cudaGetLastError())
 
+// Programmatic dependent launch.  A kernel launched by pf_launch may begin
+// while the kernel before it on the stream is finishing: it runs only
+// shared-memory set-up before pdl_wait(), which returns once that kernel has
+// completed and its writes are visible (immediately for an ordinary launch).
+// pdl_trigger() is called by every block after its main work, so the next
+// kernel is launched only once all blocks of this one are running.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------ internal entry points

@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
     C* buf = bufs + g * SB;
     const int j0 = 4 * blockIdx.x + 2 * g;
     const bool h0 = j0 < ny, h1 = j0 + 1 < ny;
+    pdl_wait();
     C v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
         v[r] = cmake<C>(a, b);
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twP);
+    pdl_trigger();
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf[spad(t + TP * r)] = v[r];
     __syncthreads();
@@ -235,6 +237,7 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* keep = buf + SB;
     const int k = blockIdx.x, t = threadIdx.x;
+    pdl_wait();
     C v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
         v[r] = l < ny ? T1[spec_at(l, k, nk)] : cmake<C>(T(0), T(0));
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twQ);
+    pdl_trigger();
     const size_t row = (size_t)k * Hld;
     if (mode == CONV_UV) {
 #pragma unroll
@@ -307,6 +311,7 @@ __global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict
         hb = jb < ny;
     }
     const int h = P / 2;
+    pdl_wait();
     for (int k = t; k <= h; k += TP) {
         C a = ha ? T2a[spec_at(ja, k, NK)] : cmake<C>(T(0), T(0));
         C b = hb ? Sb[spec_at(jb, k, NK)] : cmake<C>(T(0), T(0));
@@ -320,6 +325,7 @@ __global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict
     for (int r = 0; r < 16; ++r) v[r] = buf[spad(t + TP * r)];
     __syncthreads();
     fft_strided<C, true, R3>(v, buf, t, tw256, twP);
+    pdl_trigger();
     if (mode == CONV_UV) {
         if (ha) {
             C* o = reinterpret_cast<C*>(out) + (size_t)ja * nx;
@@ -354,13 +360,13 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     C* T1 = reinterpret_cast<C*>(p->T1);
     C* T2a = reinterpret_cast<C*>(p->T2a);
     C* T2b = reinterpret_cast<C*>(p->T2b);
-    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd_r<T, R3P><<<(ny + 3) / 4, 32 * R3P, sr, p->stream>>>(w, T1, nx, ny, tw256,
-                                                                                                 twP));
-    PF_KERNEL(p, "fft_cols_conv", k_cols_r<T, R3Q><<<P / 2 + 1, 16 * R3Q, sc, p->stream>>>(
-                                      T1, T2a, T2b, ny, P / 2 + 1, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ));
+    PF_KERNEL(p, "fft_rows_fwd", PF_CUDA(p, pf_launch(k_rows_fwd_r<T, R3P>, (ny + 3) / 4, 32 * R3P, sr, p->stream, w, T1,
+                                                      nx, ny, tw256, twP)));
+    PF_KERNEL(p, "fft_cols_conv", PF_CUDA(p, pf_launch(k_cols_r<T, R3Q>, P / 2 + 1, 16 * R3Q, sc, p->stream, T1, T2a,
+                                                       T2b, ny, P / 2 + 1, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ)));
     const int nb = mode == CONV_UV ? (ny + 1) / 2 : (ny + 3) / 4;
-    PF_KERNEL(p, "fft_rows_inv", k_rows_inv_r<T, R3P><<<nb, 32 * R3P, sr, p->stream>>>(T2a, T2b, out, nx, ny, mode, Uinf,
-                                                                                       Vinf, tw256, twP));
+    PF_KERNEL(p, "fft_rows_inv", PF_CUDA(p, pf_launch(k_rows_inv_r<T, R3P>, nb, 32 * R3P, sr, p->stream, T2a, T2b, out,
+                                                      nx, ny, mode, Uinf, Vinf, tw256, twP)));
     return PF_OK;
 }
 

@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
         cnt[i] = 0u;
         gmx[i] = 0u;
     }
+    pdl_wait();
     __syncthreads();
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
                 }
         }
     }
+    pdl_trigger();
     if (bad) {
         atomicAdd(oob, (unsigned long long)bad);
         atomicOr(status, ST_OUT_OF_DOMAIN);
@@ -300,7 +302,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // and tile_gmax (reduced over the replicas) and, in place over the block
 // histograms, off[b][t] = sum_{b' < b} hist[b'][t].  Blocks are independent
 // (the tiles' first slots are added by the scatter pass).
-__global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ tile_rep, int ntiles, int nb,
+__global__ void __launch_bounds__(1024) k_offsets(unsigned* __restrict__ tile_rep, int ntiles, int nb,
                                                   int* __restrict__ hist_off, unsigned* __restrict__ tile_count,
                                                   unsigned* __restrict__ tile_gmax) {
     __shared__ int part[OFF_SEGS][OFF_TILES + 1];
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
     const int t0 = blockIdx.x * OFF_TILES, t = t0 + tx;
     const int S = (nb + OFF_SEGS - 1) / OFF_SEGS;   // <= OFF_RUN
     const int b0 = ty * S;
+    pdl_wait();
     int v[OFF_RUN];
     int seg = 0;
 #pragma unroll
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
         if (k < S && b0 + k < nb && t < ntiles) v[k] = hist_off[(size_t)(b0 + k) * ntiles + t];
         seg += v[k];
     }
+    pdl_trigger();
     part[ty][tx] = seg;
     __syncthreads();
     if (wid < OFF_TILES) {                            // exclusive scan over the runs of tile t0 + wid
@@ -333,12 +337,14 @@ __global__ void __launch_bounds__(1024) k_offsets(const unsigned* __restrict__ t
         const int tl = lane / 4, q = lane % 4;          // tile t0 + tl, replicas [q R/4, (q + 1) R/4)
         unsigned c = 0u, gm = 0u;
         if (t0 + tl < ntiles) {
-            const unsigned* rc = tile_rep + (size_t)(t0 + tl) * TILE_REP + q * (TILE_REP / 4);
-            const unsigned* rg = rc + (size_t)ntiles * TILE_REP;
+            unsigned* rc = tile_rep + (size_t)(t0 + tl) * TILE_REP + q * (TILE_REP / 4);
+            unsigned* rg = rc + (size_t)ntiles * TILE_REP;
 #pragma unroll
             for (int r = 0; r < TILE_REP / 4; ++r) {
                 c += rc[r];
                 gm = max(gm, rg[r]);
+                rc[r] = 0u;          // cleared for the next locate pass
+                rg[r] = 0u;
             }
         }
 #pragma unroll
@@ -380,6 +386,7 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
     int* first = (int*)(sm + geo.ntiles);
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
+    pdl_wait();
     // this thread's first records (in flight during the scan)
     Pos<T> p[ScatterUnroll<T>::value];
 #pragma unroll
@@ -417,6 +424,7 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
             run += (int)tile_count[i];
         }
     }
+    pdl_trigger();
     __syncthreads();
     for (int64_t base = lo; base < hi; base += BIN_THREADS * ScatterUnroll<T>::value) {
         if (base != lo) {
@@ -517,6 +525,7 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
     const int t = blockIdx.x;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     for (int i = threadIdx.x; i < ACC_W * ACC_W; i += blockDim.x) acc[i] = 0ull;
+    pdl_wait();
     __syncthreads();
     const int start = tile_start[t], cnt = (int)tile_count[t];
     const bool split32 = sizeof(T) == 4 && cnt < 65536;
@@ -525,6 +534,7 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
     if (sizeof(T) == 8) deposit_records<DEP_F64_64>(recs + start, cnt, scale, acc);
     else if (split32) deposit_records<DEP_SPLIT32>(recs + start, cnt, scale, acc);
     else deposit_records<DEP_F32_64>(recs + start, cnt, scale, acc);
+    pdl_trigger();
     __syncthreads();
     const int* acc_hi = reinterpret_cast<const int*>(acc);
     const int* acc_lo = reinterpret_cast<const int*>(acc) + ACC_W * ACC_W;
@@ -581,6 +591,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
     using C = C_t<T>;
     __shared__ C patch[PATCH * PATCH];
     const int t = blockIdx.x;
+    pdl_wait();
     const int cnt = (int)tile_count[t];
     if (cnt == 0) return;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
@@ -592,6 +603,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
         patch[i] = v;
     }
     __syncthreads();
+    pdl_trigger();
     const int start = tile_start[t];
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
@@ -645,6 +657,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     __shared__ float4 pe[PATCH * PAIRS];
     __shared__ float4 po[PATCH * PAIRS];
     const int t = blockIdx.x;
+    pdl_wait();
     const int cnt = (int)tile_count[t];
     if (cnt == 0) return;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
@@ -665,6 +678,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         }
     }
     __syncthreads();
+    pdl_trigger();
     const int start = tile_start[t];
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
@@ -728,7 +742,7 @@ struct BinWork {
     unsigned long long* oob;
     unsigned* tile_count;     // written by k_offsets
     unsigned* tile_gmax;
-    unsigned* tile_rep;       // 2 TILE_REP * ntiles, cleared before each locate
+    unsigned* tile_rep;       // 2 TILE_REP * ntiles, zero on entry (k_offsets leaves it zero)
     int* tile_start;
     int* bin_off;             // bin_blocks(nv) * ntiles
     void* pos;
@@ -764,28 +778,26 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename T>
 pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
                             const double* G, int64_t nv, T* w, cudaStream_t s) {
-    if (cudaMemsetAsync(bw.tile_rep, 0, 2 * (size_t)TILE_REP * geo.ntiles * sizeof(unsigned), s) != cudaSuccess)
-        return PF_ERR_CUDA;
+    // the replicas are zero here: cleared when allocated and by every k_offsets pass
     const int nb = bin_blocks(nv);
     const int64_t span = bin_span(nv);
     const size_t sh = 2 * (size_t)geo.ntiles * sizeof(unsigned);
     if (set_smem(k_locate<T>, sh) != cudaSuccess || set_smem(k_scatter<T>, sh) != cudaSuccess) return PF_ERR_CUDA;
     Pos<T>* pos = (Pos<T>*)bw.pos;
     if (nb > 0) {
-        PF_KERNEL(p, "bin_locate", k_locate<T><<<nb, BIN_THREADS, sh, s>>>(X, Y, G, nv, span, geo, pos, bw.tile_rep,
-                                                                           bw.bin_off, bw.status, bw.oob));
+        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T>, nb, BIN_THREADS, sh, s, X, Y, G, nv, span, geo, pos,
+                                                       bw.tile_rep, bw.bin_off, bw.status, bw.oob)));
     }
-    PF_KERNEL(p, "bin_offsets", k_offsets<<<ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s>>>(
-                                     bw.tile_rep, geo.ntiles, nb, bw.bin_off, bw.tile_count, bw.tile_gmax));
+    PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s, bw.tile_rep,
+                                                     geo.ntiles, nb, bw.bin_off, bw.tile_count, bw.tile_gmax)));
     if (nb > 0) {
-        PF_KERNEL(p, "bin_scatter", k_scatter<T><<<nb, BIN_THREADS, sh, s>>>(pos, nv, span, geo, bw.bin_off,
-                                                                             bw.tile_count, bw.tile_start,
-                                                                             (Rec<T>*)bw.recs));
+        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T>, nb, BIN_THREADS, sh, s, pos, nv, span, geo,
+                                                         bw.bin_off, bw.tile_count, bw.tile_start, (Rec<T>*)bw.recs)));
     } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
         return PF_ERR_CUDA;
     }
-    PF_KERNEL(p, "regularize", k_deposit<T><<<geo.ntiles, 256, 0, s>>>((const Rec<T>*)bw.recs, bw.tile_start,
-                                                                      bw.tile_count, bw.tile_gmax, geo, w));
+    PF_KERNEL(p, "regularize", PF_CUDA(p, pf_launch(k_deposit<T>, geo.ntiles, 256, 0, s, (const Rec<T>*)bw.recs,
+                                                    bw.tile_start, bw.tile_count, bw.tile_gmax, geo, w)));
     return PF_OK;
 }
 
@@ -862,13 +874,13 @@ pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void
     if (nq == 0) return PF_OK;
     const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0);
     if (p->prec == PF_FP64)
-        PF_KERNEL(p, "interpolate", k_interp_tiles<double><<<geo.ntiles, 256, 0, p->stream>>>(
-                                        (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
-                                        (const double2*)uv, geo, (double*)uq, (double*)vq));
+        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles<double>, geo.ntiles, 256, 0, p->stream,
+                                                         (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
+                                                         (const double2*)uv, geo, (double*)uq, (double*)vq)));
     else
-        PF_KERNEL(p, "interpolate", k_interp_tiles_f32<<<geo.ntiles, 256, 0, p->stream>>>(
-                                        (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
-                                        (const float2*)uv, geo, (float*)uq, (float*)vq));
+        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32, geo.ntiles, 256, 0, p->stream,
+                                                         (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
+                                                         (const float2*)uv, geo, (float*)uq, (float*)vq)));
     return PF_OK;
 }
 
@@ -960,8 +972,11 @@ extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* 
     cudaStream_t s = (cudaStream_t)stream;
     const Geo geo = make_geo(d->nx, d->ny, d->dx, d->x0, d->y0);
     const BinWork bw = noalloc_binwork(base, geo.ntiles);
-    // the array keeps the previous call's contents: clear the status words
+    // the array keeps the previous call's contents: clear the status words and
+    // the tile replicas (a call that stopped early may have left them dirty)
     if (cudaMemsetAsync(base, 0, NOALLOC_HEADER, s) != cudaSuccess) return PF_ERR_CUDA;
+    if (cudaMemsetAsync(bw.tile_rep, 0, 2 * (size_t)TILE_REP * geo.ntiles * sizeof(unsigned), s) != cudaSuccess)
+        return PF_ERR_CUDA;
     pf_status st = d->precision == PF_FP64
                        ? regularize_launch<double>(nullptr, geo, bw, X, Y, G, nv, (double*)w, s)
                        : regularize_launch<float>(nullptr, geo, bw, X, Y, G, nv, (float*)w, s);
