@@ -160,6 +160,14 @@ cudaEvent_t tm_event(pf_plan p);   // api.cu
 
 #define PF_LAUNCH_CHECK(plan) PF_CUDA(plan, cudaGetLastError())
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (once per
+// device, kernel and size; safe to call from several host threads).
+cudaError_t ensure_smem(const void* kernel, size_t bytes);   // api.cu
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+    return ensure_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 // Programmatic dependent launch.  A kernel launched by pf_launch may begin
 // while the kernel before it on the stream is finishing: it runs only
 // shared-memory set-up before pdl_wait(), which returns once that kernel has

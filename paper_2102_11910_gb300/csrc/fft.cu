@@ -154,16 +154,6 @@ __global__ void __launch_bounds__(256) k_fft_cols_inplace(C* data, int width, in
     for (int n = threadIdx.x; n < len; n += blockDim.x) data[(size_t)n * width + c] = Z[n];
 }
 
-// raise a kernel's dynamic shared-memory limit once per size (the attribute is per function)
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    static size_t done = 0;
-    if (bytes <= done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done = bytes;
-    return e;
-}
-
 pf_status fft2d_inplace_f64(pf_plan p, double2* data) {
     const size_t sr = 2 * (size_t)p->P * sizeof(double2), sc = 2 * (size_t)p->Q * sizeof(double2);
     PF_CUDA(p, set_smem(k_fft_rows_inplace<double2>, sr));

@@ -764,15 +764,6 @@ inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
     return g;
 }
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
-    static size_t done = 0;
-    if (bytes <= done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done = bytes;
-    return e;
-}
-
 // Launch the four regularization kernels; `p` (may be null) only supplies the
 // timing records and the error text.
 template <typename T>
