@@ -392,6 +392,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
         out["plate_128"] = {"unit": "steps/s", "desc": "128^2, plate 20 deg, Ns 64, 256 vortices, Euler, dt 0.002, "
                             "two-edge release every step (factor reused); edge_bounded: leading edge under "
                             "|ftilde| <= 0.5 (generalized edge condition), trailing edge Kutta", **res}
+        print("workload done: %s" % 'plate_128', file=sys.stderr, flush=True)
         # pitching plate, 768 x 512, Ns 256, RK2, S refactored at every stage
         pw = inputs.pitching_plate_512x768()
         g = pw["grid"]
@@ -405,6 +406,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                          "RK2, two factorisations per step",
                                          "mixed": _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, pw["dt"],
                                                                                             body, scheme=1), 8)}
+        print("workload done: %s" % 'pitching_plate_768x512', file=sys.stderr, flush=True)
         # uneven batch: independent instances, one step each per call
         inst = inputs.batched_instances(n=n_batch)
         res = {}
@@ -446,6 +448,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                "desc": "grids 128^2..512^2, plate or ellipse, Ns 32-256, 100-20000 vortices; "
                                        "batched: one stream per instance, shared tables; unbatched FP64: one "
                                        "instance at a time", **res}
+        print("workload done: %s" % 'uneven_batch', file=sys.stderr, flush=True)
     # request server: burst, then Poisson arrivals at 70 % of the burst throughput
     reqs = inputs.serving_requests(n=n_requests)
     def run(rate):
@@ -454,8 +457,13 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
         arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
         t0 = time.perf_counter()
         pending, lats, i, steps, failed = set(), [], 0, 0, 0
+        last_done = time.perf_counter()
         while i < len(reqs) or pending:
             now = time.perf_counter() - t0
+            if pending and time.perf_counter() - last_done > 120.0:
+                q, a, u = pf.pf_server_stats(server)
+                raise RuntimeError("serving stalled: no request finished for 120 s (queued %d, running %d, "
+                                   "%d bytes resident)" % (q, a, u))
             while i < len(reqs) and arrivals[i] <= now:
                 r = reqs[i]
                 b = r["body"]
@@ -466,6 +474,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                 steps += r["nsteps"]
                 i += 1
             for t in pf.pf_server_progress(server):
+                last_done = time.perf_counter()
                 pending.discard(t)
                 try:
                     lats.append(pf.pf_server_result(server, t, 200000)[3])

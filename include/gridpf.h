@@ -39,7 +39,9 @@ typedef enum {
     PF_ERR_SINGULAR = 5,       /* a pivot of the Schur factorisation vanished              */
     PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                            */
     PF_ERR_NOT_FACTORED = 7,   /* a sheet solve was asked of a body without a factor       */
-    PF_ERR_CAPACITY = 8        /* a state's vortex capacity would be exceeded              */
+    PF_ERR_CAPACITY = 8,       /* a state's vortex capacity would be exceeded              */
+    PF_ERR_INTERNAL = 9        /* a device-side consistency check of the vortex binning
+                                  failed (the offending records were skipped): a bug     */
 } pf_status;
 
 typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
@@ -73,6 +75,19 @@ pf_status pf_plan_clone(pf_plan src, int32_t precision, void* stream, pf_plan* o
 
 /* Padded FFT sizes chosen for the plan (host ints). */
 pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
+
+/* How the sheet solves of this plan obtain E_s L^-1 w, the streamfunction of
+ * the free vorticity at the surface stencils (Sec. 2.2.2):
+ *   PF_RHS_DIRECT  the FP64 lattice-Green's-function sum over every nonzero
+ *                  node of w (16 ns nx ny multiply-adds);
+ *   PF_RHS_FFT     an FP64 zero-padded FFT solve psi = -L^-1 w (FP64 for
+ *                  either precision; needs P, Q >= 256), read at the stencils;
+ *   PF_RHS_AUTO    (default) the FFT when ns nx ny > 2^22 and P, Q >= 256.
+ * Both are FP64; they differ by rounding only.  Mixed-precision plans that
+ * take the FFT route allocate 2 nx ny doubles and two FP64 spectra once.
+ * PF_ERR_ARG for an unknown route or PF_RHS_FFT on a grid with P or Q < 256. */
+enum { PF_RHS_AUTO = 0, PF_RHS_DIRECT = 1, PF_RHS_FFT = 2 };
+pf_status pf_plan_set_rhs_route(pf_plan plan, int32_t route);
 
 /* Copy the plan's FP64 LGF table to a host array of (nx+1)*(ny+1) doubles,
  * index n*(nx+1) + m for G(m, n). Synchronises. */
@@ -300,7 +315,11 @@ pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_bo
  * recently used first.  Every admitted request runs on its own stream, all of
  * its steps enqueued at admission, so requests overlap on the device.  The
  * kernels are deterministic and instances share no mutable data: a request's
- * result does not depend on what else is running. */
+ * result does not depend on what else is running.  A request waits in the
+ * queue only while running requests hold what it needs: one that does not
+ * fit the budget with nothing else resident finishes with PF_ERR_OOM, and a
+ * CUDA error while admitting finishes the request at the head of the queue
+ * with PF_ERR_CUDA and is returned by the call that met it. */
 typedef struct pf_server_s* pf_server;
 
 typedef struct {

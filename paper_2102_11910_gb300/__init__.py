@@ -271,6 +271,14 @@ def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None,
     return f, list(gn[:ne]), s0.value
 
 
+PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT = 0, 1, 2
+
+
+def pf_plan_set_rhs_route(plan, route):
+    """Route of E_s L^-1 w in the sheet solves: PF_RHS_AUTO, PF_RHS_DIRECT or PF_RHS_FFT."""
+    _native.check(_native.lib().pf_plan_set_rhs_route(plan.handle, int(route)), "pf_plan_set_rhs_route", plan.handle)
+
+
 def pf_impulse(plan, w, x=None, y=None, ds=None, f=None, nx=None, ny=None, motion=None):
     """(P_x, P_y, Pi_O) of the fluid about the origin for node vorticity w (device
     field) and, optionally, a surface (host arrays x, y, ds, normals nx, ny) with

@@ -38,6 +38,7 @@ SIGNATURES = {
     "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
     "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
     "pf_impulse": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pf_plan_set_rhs_route": (_c.c_int, [_P, _I32]),
     "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
@@ -55,7 +56,8 @@ SIGNATURES = {
 }
 
 STATUS = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_OUT_OF_DOMAIN",
-          5: "PF_ERR_SINGULAR", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_NOT_FACTORED", 8: "PF_ERR_CAPACITY"}
+          5: "PF_ERR_SINGULAR", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_NOT_FACTORED", 8: "PF_ERR_CAPACITY",
+          9: "PF_ERR_INTERNAL"}
 
 
 class GridPfError(RuntimeError):

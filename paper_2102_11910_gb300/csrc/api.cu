@@ -22,7 +22,7 @@ void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
     void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->bin_off,
-                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->d_status, p->d_oob};
+                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);
     if (p->shared && --p->shared->refs == 0) {
@@ -57,11 +57,6 @@ pf_status upload(pf_plan p, T** dst, const std::vector<T>& src) {
     return PF_OK;
 }
 
-#define PF_TRY(x)                          \
-    do {                                   \
-        pf_status s_ = (x);                \
-        if (s_ != PF_OK) return s_;        \
-    } while (0)
 
 pf_status plan_workspaces(pf_plan p);
 
@@ -109,13 +104,19 @@ pf_status plan_workspaces(pf_plan p) {
     PF_CUDA(p, cudaMalloc(&p->tile_count, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
     p->tile_gmax = p->tile_count + p->ntiles;
     p->tile_rep = p->tile_count + 2 * p->ntiles;
-    PF_CUDA(p, cudaMemset(p->tile_count, 0, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->diag, PF_DIAG_DOUBLES * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
-    PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
-    PF_CUDA(p, cudaMemset(p->d_oob, 0, sizeof(unsigned long long)));
+    // The first binning pass adds into the tile replicas, so they must be zero
+    // before any kernel of this plan runs.  A plain cudaMemset goes to the
+    // legacy stream, which a non-blocking plan stream does not wait for; zero
+    // on the plan's stream and wait, so that the plan is ready whatever stream
+    // it is later used on.
+    PF_CUDA(p, cudaMemsetAsync(p->tile_count, 0, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned), p->stream));
+    PF_CUDA(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+    PF_CUDA(p, cudaMemsetAsync(p->d_oob, 0, sizeof(unsigned long long), p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
     return PF_OK;
 }
 
@@ -207,6 +208,13 @@ pf_status pf_plan_destroy(pf_plan p) {
     return PF_OK;
 }
 
+pf_status pf_plan_set_rhs_route(pf_plan p, int32_t route) {
+    if (!p || route < PF_RHS_AUTO || route > PF_RHS_FFT) return PF_ERR_ARG;
+    if (route == PF_RHS_FFT && (p->P < 256 || p->Q < 256)) return PF_ERR_ARG;
+    p->rhs_route = route;
+    return PF_OK;
+}
+
 pf_status pf_plan_fft_size(pf_plan p, int32_t* P, int32_t* Q) {
     if (!p || !P || !Q) return PF_ERR_ARG;
     *P = p->P;
@@ -224,14 +232,16 @@ pf_status pf_lgf_table(pf_plan p, double* host_out) {
 
 pf_status pf_sync(pf_plan p, int64_t* out_of_domain) {
     if (!p) return PF_ERR_ARG;
-    PF_CUDA(p, cudaStreamSynchronize(p->stream));
     int st = 0;
     unsigned long long oob = 0;
-    PF_CUDA(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    PF_CUDA(p, cudaMemcpy(&oob, p->d_oob, sizeof(oob), cudaMemcpyDeviceToHost));
-    PF_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
-    PF_CUDA(p, cudaMemset(p->d_oob, 0, sizeof(unsigned long long)));
+    // read and clear on the plan's stream: work enqueued after this call sees the cleared flags
+    PF_CUDA(p, cudaMemcpyAsync(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(&oob, p->d_oob, sizeof(oob), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+    PF_CUDA(p, cudaMemsetAsync(p->d_oob, 0, sizeof(unsigned long long), p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
     if (out_of_domain) *out_of_domain = (int64_t)oob;
+    if (st & ST_INTERNAL) return PF_ERR_INTERNAL;
     if (st & ST_TIMEOUT) return PF_ERR_TIMEOUT;
     if (st & ST_SINGULAR) return PF_ERR_SINGULAR;
     if (st & ST_CAPACITY) return PF_ERR_CAPACITY;

@@ -245,6 +245,28 @@ __global__ void __launch_bounds__(256) k_surface_einvlw(const T* __restrict__ w,
     if (threadIdx.x == 0) out[p] = dx2 * tot;
 }
 
+// The same quantity from an FP64 psi = -L^-1 w on the grid: E_s L^-1 w = -E_s psi.
+__global__ void k_surface_from_psi(const double* __restrict__ psi, int nx, int ns, const int* __restrict__ six,
+                                   const int* __restrict__ siy, const double* __restrict__ swx,
+                                   const double* __restrict__ swy, double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        double r = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) r += swx[4 * p + a] * psi[(size_t)siy[4 * p + b] * nx + six[4 * p + a]];
+        s += swy[4 * p + b] * r;
+    }
+    out[p] = -s;
+}
+
+__global__ void k_widen(const float* __restrict__ w, int64_t n, double* __restrict__ w64) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w64[i] = (double)w[i];
+}
+
 // s'_b = (U - Uinf) y - (V - Vinf) x - Omega/2 (x^2 + y^2)   (Eq. sfsurf with the uniform flow removed)
 __global__ void k_sbprime(const double* __restrict__ x, const double* __restrict__ y, int ns, pf_motion m,
                           double* __restrict__ sb) {
@@ -557,6 +579,57 @@ void schur_free(pf_schur s) {
 // Full sheet solve on device.  psi_w: real field; vx, vy: device positions of
 // the new vortices (mode KUTTA_SHED).  Results: f (device, ns) and scal[0..2] =
 // (s0, Gamma1, Gamma2) on the device.
+// E_s L^-1 w into ew (ns doubles).  The direct FP64 sum costs 16 ns nx ny
+// multiply-adds at the GPU's low FP64 rate; on larger grids the same quantity
+// comes from an FP64 FFT solve psi = -L^-1 w (FP64 rounding, far below what
+// the ill-conditioned S amplifies into the sheet) read at the stencils.
+pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew) {
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    const int64_t M = (int64_t)p->nx * p->ny;
+    const bool fft_ok = p->P >= 256 && p->Q >= 256;
+    const bool fft = fft_ok && (p->rhs_route == PF_RHS_FFT ||
+                                (p->rhs_route == PF_RHS_AUTO && (int64_t)ns * M > ((int64_t)1 << 22)));
+    if (!fft) {
+        const double dx2 = p->dx * p->dx;
+        if (p->prec == PF_FP64)
+            k_surface_einvlw<double><<<ns, 256, 0, st>>>((const double*)w, p->nx, p->ny, s->six, s->siy, s->swx,
+                                                          s->swy, p->G, dx2, ew);
+        else
+            k_surface_einvlw<float><<<ns, 256, 0, st>>>((const float*)w, p->nx, p->ny, s->six, s->siy, s->swx,
+                                                         s->swy, p->G, dx2, ew);
+        PF_LAUNCH_CHECK(p);
+        return PF_OK;
+    }
+    const size_t spec = (size_t)p->ldK * p->ldT * 2 * sizeof(double);
+    const double* w64;
+    double* psi;
+    void *T1, *T2;
+    if (p->prec == PF_FP64) {      // the plan's own buffers are free during a sheet solve
+        w64 = (const double*)w;
+        psi = (double*)p->uv;
+        T1 = p->T1;
+        T2 = p->T2a;
+    } else {
+        if (!p->rhs64) {
+            PF_CUDA(p, cudaStreamSynchronize(st));
+            PF_CUDA(p, cudaMalloc(&p->rhs64, 2 * (size_t)M * sizeof(double) + 2 * spec));
+        }
+        double* b = (double*)p->rhs64;
+        double* wd = b;
+        psi = b + M;
+        T1 = b + 2 * M;
+        T2 = (char*)T1 + spec;
+        k_widen<<<152 * 4, 256, 0, st>>>((const float*)w, M, wd);
+        PF_LAUNCH_CHECK(p);
+        w64 = wd;
+    }
+    PF_TRY(conv_psi_f64(p, w64, psi, T1, T2));
+    k_surface_from_psi<<<ceil_div(ns, 128), 128, 0, st>>>(psi, p->nx, ns, s->six, s->siy, s->swx, s->swy, ew);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
                              const double* vy, double* f, const EdgeBounds& eb) {
@@ -568,14 +641,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     double* y = rhs + 3 * ns;       // S^-1 [rhs0 | e_1 | e_2]
     k_sbprime<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, m, sb);
     PF_LAUNCH_CHECK(p);
-    const double dx2 = p->dx * p->dx;
-    if (p->prec == PF_FP64)
-        k_surface_einvlw<double><<<ns, 256, 0, st>>>((const double*)w, p->nx, p->ny, s->six, s->siy, s->swx, s->swy,
-                                                      p->G, dx2, ew);
-    else
-        k_surface_einvlw<float><<<ns, 256, 0, st>>>((const float*)w, p->nx, p->ny, s->six, s->siy, s->swx, s->swy,
-                                                     p->G, dx2, ew);
-    PF_LAUNCH_CHECK(p);
+    PF_TRY(surface_rhs(p, s, w, ew));
     k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, param_dev, sb, ew, s->f0hat, s->dgamma0, rhs);
     PF_LAUNCH_CHECK(p);
     int nc = 1;
@@ -614,15 +680,16 @@ pf_status pf_schur_factor(pf_plan p, const pf_body_desc* b, pf_schur* out) {
         schur_free(s);
         return st;
     }
+    int status = 0;
     if (cudaMemcpyAsync(&s->gamma0, s->dgamma0, sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
         cudaStreamSynchronize(p->stream) != cudaSuccess) {
         schur_free(s);
         return PF_ERR_CUDA;
     }
-    int status = 0;
-    cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (status & (ST_SINGULAR | ST_OUT_OF_DOMAIN)) {
-        cudaMemset(p->d_status, 0, sizeof(int));
+        cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream);
+        cudaStreamSynchronize(p->stream);
         schur_free(s);
         return (status & ST_OUT_OF_DOMAIN) ? PF_ERR_OUT_OF_DOMAIN : PF_ERR_SINGULAR;
     }

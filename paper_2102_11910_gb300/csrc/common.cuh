@@ -36,6 +36,7 @@ enum : int {
     ST_TIMEOUT = 2,
     ST_SINGULAR = 4,
     ST_CAPACITY = 8,
+    ST_INTERNAL = 16,           // a binning consistency check failed; the work was skipped
 };
 
 // ------------------------------------------------------------ kernel timing
@@ -117,6 +118,11 @@ struct pf_plan_s {
     double* stage = nullptr;
     int64_t stage_cap = 0;
     void* stage_out = nullptr;
+    // FP64 surface right-hand side by FFT (sheet solves on large grids): the
+    // route (PF_RHS_AUTO / PF_RHS_DIRECT / PF_RHS_FFT) and, for mixed plans,
+    // lazily allocated FP64 buffers: w, psi (nx*ny each), two spectra
+    int rhs_route = 0;
+    void* rhs64 = nullptr;
     // diagnostics scratch (per-block partial sums and results)
     double* diag = nullptr;            // PF_DIAG_DOUBLES
     // status
@@ -160,6 +166,12 @@ cudaEvent_t tm_event(pf_plan p);   // api.cu
 
 #define PF_LAUNCH_CHECK(plan) PF_CUDA(plan, cudaGetLastError())
 
+#define PF_TRY(x)                   \
+    do {                            \
+        pf_status s_ = (x);         \
+        if (s_ != PF_OK) return s_; \
+    } while (0)
+
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (once per
 // device, kernel and size; safe to call from several host threads).
 cudaError_t ensure_smem(const void* kernel, size_t bytes);   // api.cu
@@ -199,6 +211,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // (defined in the .cu files, used by api.cu)
 pf_status lgf_build(pf_plan p);                                  // lgf.cu
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf);  // fft.cu
+pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2);           // fft.cu
 enum { CONV_PSI = 0, CONV_UV = 1 };
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w);  // transfer.cu
 pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq);

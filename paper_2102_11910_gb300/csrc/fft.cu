@@ -337,9 +337,16 @@ __global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict
     }
 }
 
+// workspaces of one convolution (half spectra of the rows, column outputs)
+struct ConvWs {
+    void* T1;
+    void* T2a;
+    void* T2b;
+};
+
 template <typename T, int R3P, int R3Q>
 static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
-                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256, ConvWs ws) {
     using C = C_t<T>;
     constexpr int P = 256 * R3P, Q = 256 * R3Q;
     const int nx = p->nx, ny = p->ny;
@@ -347,9 +354,9 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sr));
     PF_CUDA(p, set_smem(k_cols_r<T, R3Q>, sc));
     PF_CUDA(p, set_smem(k_rows_inv_r<T, R3P>, sr));
-    C* T1 = reinterpret_cast<C*>(p->T1);
-    C* T2a = reinterpret_cast<C*>(p->T2a);
-    C* T2b = reinterpret_cast<C*>(p->T2b);
+    C* T1 = reinterpret_cast<C*>(ws.T1);
+    C* T2a = reinterpret_cast<C*>(ws.T2a);
+    C* T2b = reinterpret_cast<C*>(ws.T2b);
     PF_KERNEL(p, "fft_rows_fwd", PF_CUDA(p, pf_launch(k_rows_fwd_r<T, R3P>, (ny + 3) / 4, 32 * R3P, sr, p->stream, w, T1,
                                                       nx, ny, tw256, twP)));
     PF_KERNEL(p, "fft_cols_conv", PF_CUDA(p, pf_launch(k_cols_r<T, R3Q>, P / 2 + 1, 16 * R3Q, sc, p->stream, T1, T2a,
@@ -362,26 +369,26 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
 
 template <typename T, int R3P>
 static pf_status conv_dispatch_q(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
-                                 const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+                                 const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256, ConvWs ws) {
     switch (p->Q) {
-        case 256: return conv_solve_r<T, R3P, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 512: return conv_solve_r<T, R3P, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 1024: return conv_solve_r<T, R3P, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 2048: return conv_solve_r<T, R3P, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 4096: return conv_solve_r<T, R3P, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 256: return conv_solve_r<T, R3P, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 512: return conv_solve_r<T, R3P, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 1024: return conv_solve_r<T, R3P, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 2048: return conv_solve_r<T, R3P, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 4096: return conv_solve_r<T, R3P, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
     }
     return PF_ERR_ARG;
 }
 
 template <typename T>
 static pf_status conv_dispatch(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
-                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256) {
+                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, const C_t<T>* tw256, ConvWs ws) {
     switch (p->P) {
-        case 256: return conv_dispatch_q<T, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 512: return conv_dispatch_q<T, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 1024: return conv_dispatch_q<T, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 2048: return conv_dispatch_q<T, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
-        case 4096: return conv_dispatch_q<T, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256);
+        case 256: return conv_dispatch_q<T, 1>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 512: return conv_dispatch_q<T, 2>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 1024: return conv_dispatch_q<T, 4>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 2048: return conv_dispatch_q<T, 8>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
+        case 4096: return conv_dispatch_q<T, 16>(p, w, out, mode, Uinf, Vinf, H, Hu, Hv, twP, twQ, tw256, ws);
     }
     return PF_ERR_ARG;
 }
@@ -407,16 +414,26 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
 
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf) {
     const bool reg = p->P >= 256 && p->Q >= 256;   // register-resident kernels; small grids use the generic ones
+    const ConvWs ws{p->T1, p->T2a, p->T2b};
     if (p->prec == PF_FP64) {
         if (reg)
             return conv_dispatch<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
-                                         p->twP64, p->twQ64, p->tw256_64);
+                                         p->twP64, p->twQ64, p->tw256_64, ws);
         return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
                                     p->twP64, p->twQ64);
     }
     if (reg)
         return conv_dispatch<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
-                                    p->Hv32, p->twP32, p->twQ32, p->tw256_32);
+                                    p->Hv32, p->twP32, p->twQ32, p->tw256_32, ws);
     return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
                                p->Hv32, p->twP32, p->twQ32);
+}
+
+// psi = -L^-1 w in FP64 for either precision of plan, on the register-resident
+// path (P, Q >= 256), with caller-given FP64 workspaces T1, T2 (ldT x ldK
+// complex each): the surface right-hand side of the sheet solves.
+pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2) {
+    if (p->P < 256 || p->Q < 256) return PF_ERR_ARG;
+    return conv_dispatch<double>(p, w, psi, CONV_PSI, 0.0, 0.0, p->H64, p->Hu64, p->Hv64, p->twP64, p->twQ64,
+                                 p->tw256_64, ConvWs{T1, T2, T2});
 }

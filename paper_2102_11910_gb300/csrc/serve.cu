@@ -75,7 +75,12 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
     const int64_t bins = c * 32 + 4 * c * 32 + (4 + 2 * TILE_REP) * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
     const int64_t state = 5 * cap * 8 + 4 * cap * esz + 4096 * 8;
     const int64_t schur = (int64_t)ns * ns * 8 * 4 + (int64_t)ns * 200;
-    return grid + bins + state + schur;
+    // FP64 buffers of the FFT route of the surface right-hand side (mixed plans)
+    const int64_t M = (int64_t)s.nx * s.ny;
+    const int Q = 1 << (32 - __builtin_clz(2 * s.ny - 1));
+    const bool fft = P >= 256 && Q >= 256 && (int64_t)ns * M > ((int64_t)1 << 22);
+    const int64_t rhs = (fft && prec != PF_FP64) ? 2 * M * 8 + 2 * (int64_t)ldK * ldT * 16 : 0;
+    return grid + bins + state + schur + rhs;
 }
 
 int64_t table_bytes(int nx, int ny) {
@@ -143,10 +148,12 @@ pf_status new_slot(pf_server s, int shape, int64_t cap, int ns, Slot** out) {
     sl->bytes = bytes;
     s->used += bytes;
     pf_status st = PF_OK;
-    if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&sl->pinned, 3 * (size_t)(cap > 0 ? cap : 1) * sizeof(double)) != cudaSuccess)
-        st = PF_ERR_OOM;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl->pinned, 3 * (size_t)(cap > 0 ? cap : 1) * sizeof(double));
+    // only a failed allocation is worth waiting on; any other error (a lost
+    // context, for one) fails the request
+    if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
     if (st == PF_OK) st = pf_plan_clone(h.base, s->cfg.precision, sl->stream, &sl->plan);
     if (st == PF_OK) st = pf_state_create(sl->plan, cap, &sl->state);
     if (st == PF_OK) st = plan_reserve_vortices(sl->plan, cap);
@@ -201,42 +208,75 @@ void retire(pf_server s) {
     }
 }
 
+// finish the request at the head of the queue without running it
+void reject(pf_server s, pf_status st) {
+    Request* r = s->queue.front();
+    s->queue.pop_front();
+    r->status = st;
+    r->latency = now_s() - r->t_submit;
+    r->nv_out = 0;
+    r->done = true;
+    s->finished.push_back(r->ticket);
+}
+
+// Admit queued requests in order.  A request waits while running requests
+// hold the slots or the memory it needs; one that cannot be admitted with
+// nothing running never will be, and fails with PF_ERR_OOM.  A CUDA error
+// fails the request and is returned.
 pf_status admit(pf_server s) {
     while (!s->queue.empty()) {
         Request* r = s->queue.front();
+        int busy = 0;
+        for (Slot* c : s->slots) busy += c->req != nullptr;
         int shape = find_shape(s, r->grid);
         if (shape < 0) {
             const int64_t tb = table_bytes(r->grid.nx, r->grid.ny);
-            if (!make_room(s, tb)) return PF_OK;
+            if (!make_room(s, tb)) {
+                if (busy > 0) return PF_OK;
+                reject(s, PF_ERR_OOM);
+                continue;
+            }
             Shape h;
             h.nx = r->grid.nx; h.ny = r->grid.ny; h.dx = r->grid.dx; h.x0 = r->grid.x0; h.y0 = r->grid.y0;
             h.table_bytes = tb;
-            if (cudaStreamCreateWithFlags(&h.stream, cudaStreamNonBlocking) != cudaSuccess) return PF_ERR_CUDA;
+            if (cudaStreamCreateWithFlags(&h.stream, cudaStreamNonBlocking) != cudaSuccess) {
+                reject(s, PF_ERR_CUDA);
+                return PF_ERR_CUDA;
+            }
             pf_grid_desc g = r->grid;
             g.precision = s->cfg.precision;
             const pf_status st = pf_plan_create(&g, h.stream, &h.base);
             if (st != PF_OK) {
                 cudaStreamDestroy(h.stream);
+                if (st == PF_ERR_OOM && busy > 0) return PF_OK;   // wait for memory to free up
+                reject(s, st);
+                if (st == PF_ERR_OOM || st == PF_ERR_ARG) continue;
                 return st;
             }
             s->used += tb;
             s->shapes.push_back(h);
             shape = (int)s->shapes.size() - 1;
         }
+        if (busy >= s->cfg.max_slots) return PF_OK;
         Slot* sl = nullptr;
-        int busy = 0;
-        for (Slot* c : s->slots) {
-            if (c->req) { ++busy; continue; }
-            if (!sl && c->shape == shape && c->cap >= r->capacity) sl = c;
-        }
+        for (Slot* c : s->slots)
+            if (!c->req && c->shape == shape && c->cap >= r->capacity) {
+                sl = c;
+                break;
+            }
         if (!sl) {
-            if (busy >= s->cfg.max_slots) return PF_OK;
-            if (!make_room(s, slot_bytes(s->shapes[shape], s->cfg.precision, r->capacity, r->kin.ns))) return PF_OK;
+            if (!make_room(s, slot_bytes(s->shapes[shape], s->cfg.precision, r->capacity, r->kin.ns))) {
+                if (busy > 0) return PF_OK;
+                reject(s, PF_ERR_OOM);
+                continue;
+            }
             const pf_status st = new_slot(s, shape, r->capacity, r->kin.ns, &sl);
-            if (st == PF_ERR_OOM) return PF_OK;    // wait for memory to free up
-            if (st != PF_OK) return st;
-        } else if (busy >= s->cfg.max_slots) {
-            return PF_OK;
+            if (st == PF_ERR_OOM && busy > 0) return PF_OK;    // wait for memory to free up
+            if (st != PF_OK) {
+                reject(s, st);
+                if (st == PF_ERR_OOM) continue;
+                return st;
+            }
         }
         s->queue.pop_front();
         launch(sl, r);

@@ -41,11 +41,6 @@ struct pf_state_s {
     const double* schur_xb = nullptr;   // body the factor belongs to
 };
 
-#define PF_TRY(x)                   \
-    do {                            \
-        pf_status s_ = (x);         \
-        if (s_ != PF_OK) return s_; \
-    } while (0)
 
 namespace {
 

@@ -379,7 +379,8 @@ template <typename T>
 __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
                                                         Geo geo, const int* __restrict__ off,
                                                         const unsigned* __restrict__ tile_count,
-                                                        int* __restrict__ tile_start, Rec<T>* __restrict__ recs) {
+                                                        int* __restrict__ tile_start, Rec<T>* __restrict__ recs,
+                                                        int64_t rec_cap, int* __restrict__ status) {
     extern __shared__ unsigned sm[];
     __shared__ int wsum[BIN_THREADS / 32];
     unsigned* cnt = sm;
@@ -446,6 +447,10 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
                 for (int tx = tx0; tx <= tx1; ++tx) {
                     const int t = ty * geo.ntx + tx;
                     const int slot = first[t] + (int)atomicAdd(&cnt[t], 1u);
+                    if (slot < 0 || slot >= rec_cap) {      // counts and histograms disagree
+                        atomicOr(status, ST_INTERNAL);
+                        continue;
+                    }
                     recs[slot] = make_rec(p[k], ci - tx * BIN_TILE, cj - ty * BIN_TILE, (int)q);
                 }
         }
@@ -520,14 +525,19 @@ __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs,
 template <typename T>
 __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs, const int* __restrict__ tile_start,
                                                  const unsigned* __restrict__ tile_count,
-                                                 const unsigned* __restrict__ tile_gmax, Geo geo, T* __restrict__ w) {
+                                                 const unsigned* __restrict__ tile_gmax, Geo geo, T* __restrict__ w,
+                                                 int64_t rec_cap, int* __restrict__ status) {
     __shared__ unsigned long long acc[ACC_W * ACC_W];
     const int t = blockIdx.x;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     for (int i = threadIdx.x; i < ACC_W * ACC_W; i += blockDim.x) acc[i] = 0ull;
     pdl_wait();
     __syncthreads();
-    const int start = tile_start[t], cnt = (int)tile_count[t];
+    int start = tile_start[t], cnt = (int)tile_count[t];
+    if (start < 0 || cnt < 0 || (int64_t)start + cnt > rec_cap) {     // block-uniform
+        if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+        start = cnt = 0;
+    }
     const bool split32 = sizeof(T) == 4 && cnt < 65536;
     const int sh = tile_shift_of((unsigned)cnt, tile_gmax[t]) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
     const T scale = pow2<T>(sh);
@@ -587,13 +597,19 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__ recs,
                                                       const int* __restrict__ tile_start,
                                                       const unsigned* __restrict__ tile_count, const C_t<T>* __restrict__ uv,
-                                                      Geo geo, T* __restrict__ uq, T* __restrict__ vq) {
+                                                      Geo geo, T* __restrict__ uq, T* __restrict__ vq, int64_t rec_cap,
+                                                      int64_t nq, int* __restrict__ status) {
     using C = C_t<T>;
     __shared__ C patch[PATCH * PATCH];
     const int t = blockIdx.x;
     pdl_wait();
     const int cnt = (int)tile_count[t];
     if (cnt == 0) return;
+    const int start = tile_start[t];
+    if (start < 0 || cnt < 0 || (int64_t)start + cnt > rec_cap) {     // block-uniform
+        if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+        return;
+    }
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     const int gi0 = tx * BIN_TILE - 1, gj0 = ty * BIN_TILE - 1;
     for (int i = threadIdx.x; i < PATCH * PATCH; i += blockDim.x) {
@@ -604,7 +620,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
     }
     __syncthreads();
     pdl_trigger();
-    const int start = tile_start[t];
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<T> rc[U];
@@ -637,6 +652,10 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
                 su += wy[b] * ru;
                 sv += wy[b] * rv;
             }
+            if (rc[u].q < 0 || rc[u].q >= nq) {
+                atomicOr(status, ST_INTERNAL);
+                continue;
+            }
             uq[rc[u].q] = su;
             vq[rc[u].q] = sv;
         }
@@ -653,13 +672,19 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
                                                           const int* __restrict__ tile_start,
                                                           const unsigned* __restrict__ tile_count,
                                                           const float2* __restrict__ uv, Geo geo,
-                                                          float* __restrict__ uq, float* __restrict__ vq) {
+                                                          float* __restrict__ uq, float* __restrict__ vq,
+                                                          int64_t rec_cap, int64_t nq, int* __restrict__ status) {
     __shared__ float4 pe[PATCH * PAIRS];
     __shared__ float4 po[PATCH * PAIRS];
     const int t = blockIdx.x;
     pdl_wait();
     const int cnt = (int)tile_count[t];
     if (cnt == 0) return;
+    const int start = tile_start[t];
+    if (start < 0 || cnt < 0 || (int64_t)start + cnt > rec_cap) {     // block-uniform
+        if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+        return;
+    }
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     const int gi0 = tx * BIN_TILE - 1, gj0 = ty * BIN_TILE - 1;
     // patch nodes px, py in [0, 2 PAIRS) x [0, PATCH); px = 2 PAIRS - 1 only pads
@@ -679,7 +704,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     }
     __syncthreads();
     pdl_trigger();
-    const int start = tile_start[t];
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<float> rc[U];
@@ -707,6 +731,10 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
                 const float rv = wx[0] * p0.y + wx[1] * p0.w + wx[2] * p1.y + wx[3] * p1.w;
                 su += wy[b] * ru;
                 sv += wy[b] * rv;
+            }
+            if (rc[u].q < 0 || rc[u].q >= nq) {
+                atomicOr(status, ST_INTERNAL);
+                continue;
             }
             uq[rc[u].q] = su;
             vq[rc[u].q] = sv;
@@ -747,6 +775,7 @@ struct BinWork {
     int* bin_off;             // bin_blocks(nv) * ntiles
     void* pos;
     void* recs;
+    int64_t rec_cap;          // record slots in recs
 };
 
 inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
@@ -783,12 +812,14 @@ pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const 
                                                      geo.ntiles, nb, bw.bin_off, bw.tile_count, bw.tile_gmax)));
     if (nb > 0) {
         PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T>, nb, BIN_THREADS, sh, s, pos, nv, span, geo,
-                                                         bw.bin_off, bw.tile_count, bw.tile_start, (Rec<T>*)bw.recs)));
+                                                         bw.bin_off, bw.tile_count, bw.tile_start, (Rec<T>*)bw.recs,
+                                                         bw.rec_cap, bw.status)));
     } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
         return PF_ERR_CUDA;
     }
     PF_KERNEL(p, "regularize", PF_CUDA(p, pf_launch(k_deposit<T>, geo.ntiles, 256, 0, s, (const Rec<T>*)bw.recs,
-                                                    bw.tile_start, bw.tile_count, bw.tile_gmax, geo, w)));
+                                                    bw.tile_start, bw.tile_count, bw.tile_gmax, geo, w, bw.rec_cap,
+                                                    bw.status)));
     return PF_OK;
 }
 
@@ -843,6 +874,7 @@ BinWork plan_binwork(pf_plan p) {
     b.bin_off = p->bin_off;
     b.pos = p->pos;
     b.recs = p->recs;
+    b.rec_cap = p->rec_cap;
     return b;
 }
 
@@ -867,11 +899,13 @@ pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void
     if (p->prec == PF_FP64)
         PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles<double>, geo.ntiles, 256, 0, p->stream,
                                                          (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
-                                                         (const double2*)uv, geo, (double*)uq, (double*)vq)));
+                                                         (const double2*)uv, geo, (double*)uq, (double*)vq, p->rec_cap,
+                                                         nq, p->d_status)));
     else
         PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32, geo.ntiles, 256, 0, p->stream,
                                                          (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
-                                                         (const float2*)uv, geo, (float*)uq, (float*)vq)));
+                                                         (const float2*)uv, geo, (float*)uq, (float*)vq, p->rec_cap,
+                                                         nq, p->d_status)));
     return PF_OK;
 }
 
@@ -946,6 +980,7 @@ BinWork noalloc_binwork(unsigned char* base, int ntiles) {
     b.bin_off = (int*)(base + NOALLOC_HEADER + NOALLOC_TILE_BYTES);
     b.pos = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES;
     b.recs = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES;
+    b.rec_cap = 4 * NOALLOC_MAX_VORTICES;
     return b;
 }
 

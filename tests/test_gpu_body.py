@@ -150,3 +150,33 @@ def test_out_of_grid_body_is_rejected():
     with pytest.raises(pf.GridPfError) as e:
         pf.pf_schur_factor(plan, b.x, b.y, b.ds)
     assert e.value.name == "PF_ERR_OUT_OF_DOMAIN"
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_fft_route_of_the_surface_rhs_matches_the_direct_sum(prec):
+    """E_s L^-1 w from an FP64 FFT solve (the route large grids take) against the
+    direct FP64 LGF sum (the route pinned to the oracle above): same vorticity,
+    same factor; they differ by FP64 rounding amplified by cond(S)."""
+    n, dx = 256, 2.0 / 255
+    g = inputs.centred_grid(n, n, dx)
+    b = inputs.plate(96, 1.0, 0.35)                   # dS/dx = 1.33
+    rng = np.random.default_rng(5)
+    X, Y, G = inputs.uniform_vortices(rng, 3000, -0.9, 0.9, 1e-3)
+    keep = np.hypot(X, Y) > 0.6
+    X, Y, G = X[keep], Y[keep], G[keep]
+    out = {}
+    for route in (pf.PF_RHS_DIRECT, pf.PF_RHS_FFT):
+        plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec)
+        pf.pf_plan_set_rhs_route(plan, route)
+        schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)
+        w = pf.pf_regularize(plan, *(torch.from_numpy(a).cuda() for a in (X, Y, G)))
+        Gw = float(G.sum())
+        f, gn, s0 = pf.pf_sheet_solve(plan, schur, w, (0.0, 0.0, 0.0, 1.0, 0.0), pf.PF_SHEET_KUTTA_SHED, Gw,
+                                      list(b.edges), np.array([b.x[0] - 0.02, b.x[-1] + 0.02]),
+                                      np.array([b.y[0] + 0.01, b.y[-1] - 0.01]))
+        _, _, S = pf.pf_schur_info(schur)
+        out[route] = (f.cpu().numpy(), np.array(gn), np.linalg.cond(S))
+    fd, gd, cond = out[pf.PF_RHS_DIRECT]
+    ff, gf, _ = out[pf.PF_RHS_FFT]
+    tol = cond * 1e-14
+    assert rel(ff, fd) < tol and rel(gf, gd) < tol

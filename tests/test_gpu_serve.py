@@ -139,3 +139,27 @@ def test_submit_checks_capacity():
                             capacity=len(a["X"]))
     assert e.value.name == "PF_ERR_CAPACITY"
     server.close()
+
+
+def test_a_request_that_can_never_fit_fails_instead_of_waiting():
+    """With nothing else resident, a request whose grid tables and instance
+    exceed the budget can never be admitted: it finishes with PF_ERR_OOM (and
+    the requests behind it still run once it is out of the way)."""
+    a = _request_a()
+    big = dict(a, grid=_grid(512))
+    probe = pf.Server(max_slots=1, hbm_budget_bytes=1 << 30)
+    t = _submit(probe, a)
+    one = pf.pf_server_stats(probe)[2]            # 128^2 tables + one instance
+    _drain(probe, [t])
+    probe.close()
+    server = pf.Server(max_slots=4, hbm_budget_bytes=int(one * 1.5), precision=pf.PF_MIXED)
+    tb = _submit(server, big)                      # 512^2 needs ~16x the 128^2 footprint
+    ta = _submit(server, a)
+    done = _drain(server, [tb, ta], timeout=60.0)
+    assert set(done) == {tb, ta}
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_server_result(server, tb, _cap(big))
+    assert e.value.name == "PF_ERR_OOM"
+    X, Y, G, _ = pf.pf_server_result(server, ta, _cap(a))
+    assert len(X) == len(a["X"]) + 2 * a["nsteps"] and np.all(np.isfinite(X))
+    server.close()
