@@ -14,6 +14,7 @@
 //                   (Eq. kuttasystem2) or two edges (Eq. twovortex)
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -173,6 +174,211 @@ __global__ void k_extract_inverse(const double* __restrict__ A, double* __restri
     Sinv[(size_t)i * ns + j] = A[(size_t)i * 2 * ns + ns + j];
 }
 
+// ------------------------------------------------ blocked Gauss-Jordan inverse
+//
+// S^-1 by Gauss-Jordan elimination with row interchanges, 32 columns (a panel
+// K) at a time, out of place between two ns x ns buffers.  Per panel:
+//   P  one block picks the panel's pivot rows by partial pivoting on an FP32
+//      copy of the panel (magnitudes only decide the order) and factors the
+//      row-permuted pivot block X_KK = L U in FP64 (no further pivoting: the
+//      pivots are the elimination's own);
+//   V  per column j: y = L^-1 x_j, z = U^-1 y, with x_j = X_Kj outside the
+//      panel and the unit vector e_j inside it; per row r outside the
+//      panel: the multipliers l_r = X_rK U^-1;
+//   U  the sweep of the permuted X:
+//        X'_rj = X_rj - l_r . y_j (r, j outside K),  X'_rj = -l_r . y_j (j in K),
+//        X'_Kj = z_j.
+// The trailing update goes through the LU factors (as a blocked LU does), not
+// through (X_KK)^-1, whose rounding would be amplified by cond(X_KK).  After
+// the last panel, undoing the accumulated row permutation on the columns
+// gives S^-1.  Three launches per 32 columns instead of two per column; the
+// FP64 work stays ~ns^3 multiply-adds, spread over full warps on every SM.
+constexpr int BGJ_B = 32;              // panel width
+constexpr int BGJ_MAX = 1024;          // ns handled by one panel block (panel rows in shared memory)
+constexpr int BGJ_PANEL_THREADS = 1024;
+
+__global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* __restrict__ X, int n, int k0, int kb,
+                                                                  int* __restrict__ perm, int* __restrict__ gperm,
+                                                                  double* __restrict__ LU, double tiny,
+                                                                  int* __restrict__ status) {
+    extern __shared__ float sp[];                  // (n - k0) x 33 FP32 copy of the panel
+    __shared__ int rowid[BGJ_MAX];                 // local row i of the permuted panel = local row rowid[i]
+    __shared__ int gp[BGJ_MAX];
+    __shared__ float wv[32];
+    __shared__ int wi[32];
+    __shared__ int piv_s;
+    __shared__ double A[BGJ_B][BGJ_B + 1];
+    const int m = n - k0, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    pdl_wait();
+    for (int idx = tid; idx < m * kb; idx += blockDim.x) {
+        const int i = idx / kb, j = idx - (idx / kb) * kb;
+        sp[i * 33 + j] = (float)X[(size_t)(k0 + i) * n + k0 + j];
+    }
+    for (int i = tid; i < m; i += blockDim.x) rowid[i] = i;
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+        // the largest |panel[i][c]| over i >= c, lowest i on ties
+        float best = -1.f;
+        int bi = m;
+        for (int i = c + tid; i < m; i += blockDim.x) {
+            const float v = fabsf(sp[i * 33 + c]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v2 = __shfl_down_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        }
+        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+        __syncthreads();
+        if (wid == 0) {
+            best = lane < (int)(blockDim.x >> 5) ? wv[lane] : -1.f;
+            bi = lane < (int)(blockDim.x >> 5) ? wi[lane] : m;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_down_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+            }
+            if (lane == 0) piv_s = bi < m ? bi : c;
+        }
+        __syncthreads();
+        const int pr = piv_s;
+        if (pr != c) {
+            if (tid < kb) {
+                const float t = sp[c * 33 + tid];
+                sp[c * 33 + tid] = sp[pr * 33 + tid];
+                sp[pr * 33 + tid] = t;
+            }
+            if (tid == BGJ_B) {
+                const int t = rowid[c];
+                rowid[c] = rowid[pr];
+                rowid[pr] = t;
+            }
+        }
+        __syncthreads();
+        // eliminate column c from the rows below it (only they are pivot candidates)
+        const float pv = sp[c * 33 + c];
+        const int w = kb - c - 1;
+        if (pv != 0.f && w > 0) {
+            for (int idx = tid; idx < (m - c - 1) * w; idx += blockDim.x) {
+                const int i = c + 1 + idx / w, j = c + 1 + idx - (idx / w) * w;
+                sp[i * 33 + j] -= sp[i * 33 + c] / pv * sp[c * 33 + j];
+            }
+        }
+        __syncthreads();
+    }
+    // this panel's permutation (rows < k0 stay) and the accumulated one
+    for (int i = tid; i < m; i += blockDim.x) {
+        perm[k0 + i] = k0 + rowid[i];
+        gp[i] = gperm[k0 + rowid[i]];
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) gperm[k0 + i] = gp[i];
+    // FP64 LU of the permuted pivot block, one entry per thread
+    const int i = tid >> 5, j = tid & 31;
+    const bool mine = i < kb && j < kb;
+    if (mine) A[i][j] = X[(size_t)(k0 + rowid[i]) * n + k0 + j];
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+        const double pv = A[c][c];
+        if (tid == 0 && !(fabs(pv) > tiny)) atomicOr(status, ST_SINGULAR);
+        const double d = pv == 0.0 ? 1.0 : pv;
+        if (mine && i > c && j == c) A[i][c] /= d;
+        __syncthreads();
+        if (mine && i > c && j > c) A[i][j] -= A[i][c] * A[c][j];
+        __syncthreads();
+    }
+    if (mine) LU[i * BGJ_B + j] = A[i][j];
+}
+
+// One warp per column j < n (y_j, z_j) and per row r < n outside the panel
+// (l_r); lanes over the panel's kb entries.  Blocks of 8 warps.
+__global__ void __launch_bounds__(256) k_bgj_subst(const double* __restrict__ X, int n, int k0, int kb,
+                                                    const int* __restrict__ perm, const double* __restrict__ LU,
+                                                    double* __restrict__ Y, double* __restrict__ Z,
+                                                    double* __restrict__ Lr) {
+    __shared__ double F[BGJ_B][BGJ_B + 1];
+    const int lane = threadIdx.x & 31;
+    const int wg = blockIdx.x * 8 + (threadIdx.x >> 5);
+    pdl_wait();
+    for (int t = threadIdx.x; t < BGJ_B * BGJ_B; t += blockDim.x) {
+        const int a = t >> 5, b = t & 31;
+        F[a][b] = (a < kb && b < kb) ? LU[a * BGJ_B + b] : (a == b ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    const bool act = lane < kb;
+    if (wg < n) {
+        const int j = wg;
+        double v;
+        if (j >= k0 && j < k0 + kb) v = lane == j - k0 ? 1.0 : 0.0;
+        else v = act ? X[(size_t)perm[k0 + lane] * n + j] : 0.0;
+        for (int l = 0; l < kb; ++l) {            // y = L^-1 x (unit lower)
+            const double yl = __shfl_sync(0xffffffffu, v, l);
+            if (lane > l) v -= F[lane][l] * yl;
+        }
+        if (act) Y[(size_t)lane * n + j] = v;
+        for (int l = kb - 1; l >= 0; --l) {       // z = U^-1 y
+            if (lane == l) v /= F[l][l];
+            const double zl = __shfl_sync(0xffffffffu, v, l);
+            if (lane < l) v -= F[lane][l] * zl;
+        }
+        if (act) Z[(size_t)lane * n + j] = v;
+    } else if (wg < 2 * n) {
+        const int r = wg - n;
+        if (r >= k0 && r < k0 + kb) return;
+        const int src = r < k0 ? r : perm[r];
+        double v = act ? X[(size_t)src * n + k0 + lane] : 0.0;
+        for (int l = 0; l < kb; ++l) {            // l_r U = x_r
+            if (lane == l) v /= F[l][l];
+            const double al = __shfl_sync(0xffffffffu, v, l);
+            if (lane > l) v -= al * F[l][lane];
+        }
+        if (act) Lr[(size_t)r * BGJ_B + lane] = v;
+    }
+}
+
+// The sweep into Y: tile of 8 rows x 32 columns, one entry per thread
+__global__ void __launch_bounds__(256) k_bgj_sweep(const double* __restrict__ X, int n, int k0, int kb,
+                                                    const int* __restrict__ perm, const double* __restrict__ Yk,
+                                                    const double* __restrict__ Zk, const double* __restrict__ Lr,
+                                                    double* __restrict__ Out) {
+    __shared__ double Ls[8][BGJ_B];
+    __shared__ double Ys[BGJ_B][32];
+    const int j = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
+    pdl_wait();
+    const bool rk = r >= k0 && r < k0 + kb;
+    Ls[threadIdx.y][threadIdx.x] = (r < n && !rk && (int)threadIdx.x < kb) ? Lr[(size_t)r * BGJ_B + threadIdx.x] : 0.0;
+    for (int l = threadIdx.y; l < BGJ_B; l += 8)
+        Ys[l][threadIdx.x] = (l < kb && j < n) ? Yk[(size_t)l * n + j] : 0.0;
+    __syncthreads();
+    if (r >= n || j >= n) return;
+    double out;
+    if (rk) {
+        out = Zk[(size_t)(r - k0) * n + j];
+    } else {
+        double acc = 0.0;
+        for (int l = 0; l < kb; ++l) acc += Ls[threadIdx.y][l] * Ys[l][threadIdx.x];
+        const bool jk = j >= k0 && j < k0 + kb;
+        const int src = r < k0 ? r : perm[r];
+        out = (jk ? 0.0 : X[(size_t)src * n + j]) - acc;
+    }
+    Out[(size_t)r * n + j] = out;
+}
+
+// S^-1[i][gperm[r]] = X[i][r]
+__global__ void k_bgj_unpermute(const double* __restrict__ X, int n, const int* __restrict__ gperm,
+                                double* __restrict__ Sinv) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    pdl_wait();
+    if (r >= n) return;
+    Sinv[(size_t)i * n + gperm[r]] = X[(size_t)i * n + r];
+}
+
+__global__ void k_iota(int* __restrict__ v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
 // deterministic block reduction of a double (fixed tree)
 __device__ double block_sum(double v, double* sh) {
     const int tid = threadIdx.x;
@@ -187,20 +393,118 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// f0 = S^-1 1, f0hat = dS f0, Gamma0 = sum f0hat (one block of 256)
-__global__ void k_f0(const double* __restrict__ Sinv, const double* __restrict__ ds, int ns, double* __restrict__ f0,
-                     double* __restrict__ f0hat, double* __restrict__ gamma0) {
+// f0 = S^-1 1 (row sums of S^-1): one warp per row, lanes over strided
+// columns, then a fixed shuffle tree (deterministic)
+__global__ void k_f0_rows(const double* __restrict__ Sinv, int ns, double* __restrict__ f0) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= ns) return;
+    double s = 0.0;
+    for (int q = lane; q < ns; q += 32) s += Sinv[(size_t)row * ns + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) f0[row] = s;
+}
+
+// f0hat = dS f0 and Gamma0 = sum f0hat (one block of 256, fixed order)
+__global__ void k_f0_final(const double* __restrict__ f0, const double* __restrict__ ds, int ns,
+                           double* __restrict__ f0hat, double* __restrict__ gamma0) {
     __shared__ double sh[256];
     double part = 0.0;
     for (int p = threadIdx.x; p < ns; p += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < ns; ++q) s += Sinv[(size_t)p * ns + q];
-        f0[p] = s;
-        f0hat[p] = ds[p] * s;
-        part += ds[p] * s;
+        const double h = ds[p] * f0[p];
+        f0hat[p] = h;
+        part += h;
     }
     const double g = block_sum(part, sh);
     if (threadIdx.x == 0) *gamma0 = g;
+}
+
+// One step of iterative refinement of y_c ~ S^-1 v_c (c < nc <= 3), in two
+// passes, one warp per row and a fixed shuffle tree:
+//   k_residual   r_c = v_c - S y_c   (v_c = 1 when v is null)
+//   k_gemv_add   y_c += S^-1 r_c
+// The residual uses S itself, so the refined y is as accurate as FP64 and
+// cond(S) allow, whatever rounding the inverse carries.
+__global__ void k_residual(const double* __restrict__ S, int ns, const double* __restrict__ v, int nc,
+                           const double* __restrict__ y, double* __restrict__ r) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= ns) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int q = lane; q < ns; q += 32) {
+        const double a = S[(size_t)row * ns + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) acc[c] += a * y[(size_t)c * ns + q];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) r[(size_t)c * ns + row] = (v ? v[(size_t)c * ns + row] : 1.0) - acc[c];
+}
+
+__global__ void k_gemv_add(const double* __restrict__ Sinv, int ns, const double* __restrict__ r, int nc,
+                           double* __restrict__ y) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= ns) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int q = lane; q < ns; q += 32) {
+        const double a = Sinv[(size_t)row * ns + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) acc[c] += a * r[(size_t)c * ns + q];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) y[(size_t)c * ns + row] += acc[c];
+}
+
+// Order of the sheet deposit: the 16 ns stencil entries e = 16 p + 4 b + a
+// sorted by (grid node, e), so that each node's entries are contiguous and in
+// index order.  One block; bitonic sort of the 64-bit keys node 2^16 + e
+// (e < 2^14, node < 2^22) in shared memory, padded to n2 = 2^k >= 16 ns.
+constexpr int SHEET_SORT_MAX = 1024;
+constexpr int SHEET_SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(SHEET_SORT_THREADS) k_sheet_order(const int* __restrict__ six,
+                                                                     const int* __restrict__ siy, int ns, int nx,
+                                                                     int n2, int* __restrict__ sorder,
+                                                                     int* __restrict__ snode) {
+    extern __shared__ unsigned long long key[];
+    const int ne = 16 * ns;
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+        if (e < ne) {
+            const int p = e >> 4, a = e & 3, b = (e >> 2) & 3;
+            const unsigned long long node = (unsigned long long)siy[4 * p + b] * nx + six[4 * p + a];
+            key[e] = (node << 16) | (unsigned long long)e;
+        } else {
+            key[e] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long x = key[i], y = key[l];
+                    if ((x > y) == ((i & k) == 0)) {
+                        key[i] = y;
+                        key[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+        sorder[i] = (int)(key[i] & 0xFFFFull);
+        snode[i] = (int)(key[i] >> 16);
+    }
 }
 
 // E_s L^-1 w at surface point p = dx^2 sum_nodes w_m sum_{16 stencil nodes s} d_p(s) G(s - m),
@@ -490,9 +794,39 @@ __global__ void k_sheet_deposit(const int* __restrict__ six, const int* __restri
     w[n] = (T)((double)w[n] + acc * inv_dx2);
 }
 
+// The same sum from the sorted entries: the first entry of each node sums the
+// node's run in index order (the order of k_sheet_deposit), in O(16 ns).
+template <typename T>
+__global__ void k_sheet_deposit_sorted(const int* __restrict__ sorder, const int* __restrict__ snode,
+                                       const double* __restrict__ swx, const double* __restrict__ swy,
+                                       const double* __restrict__ ds, const double* __restrict__ f, int ne,
+                                       double inv_dx2, T* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int node = snode[i];
+    if (i > 0 && snode[i - 1] == node) return;    // not the node's first entry
+    double acc = 0.0;
+    for (int j = i; j < ne && snode[j] == node; ++j) {
+        const int e2 = sorder[j];
+        const int p2 = e2 >> 4, a2 = e2 & 3, b2 = (e2 >> 2) & 3;
+        acc += ds[p2] * f[p2] * swx[4 * p2 + a2] * swy[4 * p2 + b2];
+    }
+    w[node] = (T)((double)w[node] + acc * inv_dx2);
+}
+
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
     const int n = 16 * s->ns;
     const double inv_dx2 = 1.0 / (p->dx * p->dx);
+    if (s->snode) {
+        if (p->prec == PF_FP64)
+            k_sheet_deposit_sorted<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(s->sorder, s->snode, s->swx, s->swy,
+                                                                                      s->ds, f, n, inv_dx2, (double*)w);
+        else
+            k_sheet_deposit_sorted<float><<<ceil_div(n, 256), 256, 0, p->stream>>>(s->sorder, s->snode, s->swx, s->swy,
+                                                                                     s->ds, f, n, inv_dx2, (float*)w);
+        PF_LAUNCH_CHECK(p);
+        return PF_OK;
+    }
     if (p->prec == PF_FP64)
         k_sheet_deposit<double><<<ceil_div(n, 128), 128, 0, p->stream>>>(s->six, s->siy, s->swx, s->swy, s->ds, f, s->ns,
                                                                           inv_dx2, p->nx, (double*)w);
@@ -507,7 +841,7 @@ pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
 
 static void free_schur(pf_schur s) {
     void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
-                    s->dgamma0, s->work, s->scal};
+                    s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->scal};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -518,20 +852,62 @@ pf_status schur_factor_device(pf_plan p, pf_schur s) {
     k_surface_stencil<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
                                                           s->siy, s->swx, s->swy, p->d_status);
     PF_LAUNCH_CHECK(p);
+    if (s->snode) {
+        int n2 = 1;
+        while (n2 < 16 * ns) n2 <<= 1;
+        const size_t sh = (size_t)n2 * sizeof(unsigned long long);
+        PF_CUDA(p, set_smem(k_sheet_order, sh));
+        k_sheet_order<<<1, SHEET_SORT_THREADS, sh, st>>>(s->six, s->siy, ns, p->nx, n2, s->sorder, s->snode);
+        PF_LAUNCH_CHECK(p);
+    }
     k_schur_build<<<dim3(ceil_div(ns, 128), ns), 128, 0, st>>>(s->six, s->siy, s->swx, s->swy, s->ds, ns, p->G, p->nx,
                                                                 s->S, ns);
     PF_LAUNCH_CHECK(p);
-    k_augment<<<dim3(ceil_div(2 * ns, 256), ns), 256, 0, st>>>(s->S, s->A, ns);
-    PF_LAUNCH_CHECK(p);
-    // pivots smaller than 1e-300 relative scale are reported as singular
-    for (int k = 0; k < ns; ++k) {
-        k_gj_pivot<<<1, 256, 0, st>>>(s->A, ns, k, 1e-300, p->d_status);
-        k_gj_eliminate<<<ns, 256, 0, st>>>(s->A, ns, k);
+    // pivots of magnitude 1e-300 or less are reported as singular
+    if (ns <= BGJ_MAX) {
+        double* LU = s->gj;
+        double* Yk = LU + BGJ_B * BGJ_B;
+        double* Zk = Yk + (size_t)BGJ_B * ns;
+        double* Lr = Zk + (size_t)BGJ_B * ns;
+        int* perm = (int*)(Lr + (size_t)BGJ_B * ns);
+        int* gperm = perm + ns;
+        double* buf[2] = {s->A, s->A + (size_t)ns * ns};
+        k_iota<<<ceil_div(ns, 256), 256, 0, st>>>(gperm, ns);
+        PF_LAUNCH_CHECK(p);
+        const double* X = s->S;
+        int cur = 0;
+        for (int k0 = 0; k0 < ns; k0 += BGJ_B) {
+            const int kb = std::min(BGJ_B, ns - k0);
+            const size_t sh = (size_t)(ns - k0) * 33 * sizeof(float);
+            PF_CUDA(p, set_smem(k_bgj_panel, sh));
+            PF_CUDA(p, pf_launch(k_bgj_panel, 1, BGJ_PANEL_THREADS, sh, st, X, ns, k0, kb, perm, gperm, LU, 1e-300,
+                                 p->d_status));
+            PF_CUDA(p, pf_launch(k_bgj_subst, ceil_div(2 * ns, 8), 256, 0, st, X, ns, k0, kb, (const int*)perm,
+                                 (const double*)LU, Yk, Zk, Lr));
+            PF_CUDA(p, pf_launch(k_bgj_sweep, dim3(ceil_div(ns, 32), ceil_div(ns, 8)), dim3(32, 8), 0, st, X, ns, k0,
+                                 kb, (const int*)perm, (const double*)Yk, (const double*)Zk, (const double*)Lr,
+                                 buf[cur]));
+            X = buf[cur];
+            cur ^= 1;
+        }
+        PF_CUDA(p, pf_launch(k_bgj_unpermute, dim3(ceil_div(ns, 256), ns), dim3(256), 0, st, X, ns,
+                             (const int*)gperm, s->Sinv));
+    } else {
+        k_augment<<<dim3(ceil_div(2 * ns, 256), ns), 256, 0, st>>>(s->S, s->A, ns);
+        PF_LAUNCH_CHECK(p);
+        for (int k = 0; k < ns; ++k) {
+            k_gj_pivot<<<1, 256, 0, st>>>(s->A, ns, k, 1e-300, p->d_status);
+            k_gj_eliminate<<<ns, 256, 0, st>>>(s->A, ns, k);
+        }
+        PF_LAUNCH_CHECK(p);
+        k_extract_inverse<<<dim3(ceil_div(ns, 256), ns), 256, 0, st>>>(s->A, s->Sinv, ns);
+        PF_LAUNCH_CHECK(p);
     }
-    PF_LAUNCH_CHECK(p);
-    k_extract_inverse<<<dim3(ceil_div(ns, 256), ns), 256, 0, st>>>(s->A, s->Sinv, ns);
-    PF_LAUNCH_CHECK(p);
-    k_f0<<<1, 256, 0, st>>>(s->Sinv, s->ds, ns, s->f0, s->f0hat, s->dgamma0);
+    // f0 = S^-1 1 with one refinement step (scratch: the solve workspace)
+    k_f0_rows<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, s->f0);
+    k_residual<<<ceil_div(ns, 8), 256, 0, st>>>(s->S, ns, nullptr, 1, s->f0, s->work);
+    k_gemv_add<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, s->work, 1, s->f0);
+    k_f0_final<<<1, 256, 0, st>>>(s->f0, s->ds, ns, s->f0hat, s->dgamma0);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
@@ -564,6 +940,12 @@ pf_status schur_create(pf_plan p, int ns, pf_schur* out) {
     PF_ALLOC(s->f0, v);
     PF_ALLOC(s->f0hat, v);
     PF_ALLOC(s->dgamma0, sizeof(double));
+    if (ns <= BGJ_MAX)
+        PF_ALLOC(s->gj, (BGJ_B * BGJ_B + 3 * (size_t)BGJ_B * ns) * sizeof(double) + 2 * (size_t)ns * sizeof(int));
+    if (ns <= SHEET_SORT_MAX) {
+        PF_ALLOC(s->sorder, 16 * (size_t)ns * sizeof(int));
+        PF_ALLOC(s->snode, 16 * (size_t)ns * sizeof(int));
+    }
     PF_ALLOC(s->work, 12 * v);
     PF_ALLOC(s->scal, 8 * sizeof(double));
 #undef PF_ALLOC
@@ -639,6 +1021,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     double* ew = sb + ns;
     double* rhs = ew + ns;          // rhs0 | e_1 | e_2 contiguous
     double* y = rhs + 3 * ns;       // S^-1 [rhs0 | e_1 | e_2]
+    double* res = y + 3 * ns;       // refinement residuals
     k_sbprime<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, m, sb);
     PF_LAUNCH_CHECK(p);
     PF_TRY(surface_rhs(p, s, w, ew));
@@ -653,6 +1036,8 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
         PF_LAUNCH_CHECK(p);
     }
     k_gemv<<<ns, 128, 0, st>>>(s->Sinv, ns, rhs, nc, y);
+    k_residual<<<ceil_div(ns, 8), 256, 0, st>>>(s->S, ns, rhs, nc, y, res);
+    k_gemv_add<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, res, nc, y);
     PF_LAUNCH_CHECK(p);
     k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, eb,
                                      param, param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);

@@ -19,6 +19,9 @@ struct pf_schur_s {
     double* f0hat = nullptr;  // dS o f0
     double* dgamma0 = nullptr;
     double gamma0 = 0.0;      // host copy of Gamma0
+    int* sorder = nullptr;    // the 16 ns stencil entries e = 16 p + 4 b + a sorted by (grid node, e)
+    int* snode = nullptr;     // their grid nodes in that order (both null when ns > SHEET_SORT_MAX)
+    double* gj = nullptr;     // blocked Gauss-Jordan scratch: LU (32 x 32), Y, Z (32 x ns), L_R (ns x 32), perm, gperm
     double* work = nullptr;   // 12 ns doubles of solve scratch
     double* scal = nullptr;   // device scalars: s0, Gamma1, Gamma2, -, new-vortex x[2], y[2]
 };

@@ -74,7 +74,9 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
     const int64_t ntiles = (int64_t)((s.nx + 31) / 32) * ((s.ny + 31) / 32);
     const int64_t bins = c * 32 + 4 * c * 32 + (4 + 2 * TILE_REP) * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
     const int64_t state = 5 * cap * 8 + 4 * cap * esz + 4096 * 8;
-    const int64_t schur = (int64_t)ns * ns * 8 * 4 + (int64_t)ns * 200;
+    // two Schur factors (a moving body keeps the last two poses), each S, the
+    // ns x 2 ns Gauss-Jordan workspace, S^-1, and O(ns) vectors and orderings
+    const int64_t schur = 2 * ((int64_t)ns * ns * 8 * 4 + (int64_t)ns * 328);
     // FP64 buffers of the FFT route of the surface right-hand side (mixed plans)
     const int64_t M = (int64_t)s.nx * s.ny;
     const int Q = 1 << (32 - __builtin_clz(2 * s.ny - 1));

@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "body.cuh"
@@ -35,10 +36,15 @@ struct pf_state_s {
     double* f = nullptr;            // sheet strength
     double* red = nullptr;          // reduction scratch: [0] sum Gamma, [1] -sum Gamma, [2..] partials
     double* newpos = nullptr;       // device x[2], y[2] of the vortices being released
-    pf_schur schur = nullptr;       // factor at the last pose
-    double schur_alpha = NAN;
-    int schur_ns = 0;
-    const double* schur_xb = nullptr;   // body the factor belongs to
+    // Schur factors of the two most recent poses, the current one first: an
+    // RK2 step's second stage (t + dt) is the next step's first, so a moving
+    // body is factored once per step
+    struct Factor {
+        pf_schur f = nullptr;
+        double alpha = NAN;
+        int ns = 0;
+        const double* xb = nullptr;   // body the factor belongs to
+    } fac[2];
 };
 
 
@@ -134,7 +140,8 @@ void free_state(pf_state s) {
     void* ptrs[] = {s->X, s->Y, s->G, s->Xs, s->Ys, s->u1, s->v1, s->u2, s->v2, s->f, s->red, s->newpos};
     for (void* q : ptrs)
         if (q) cudaFree(q);
-    if (s->schur) schur_free(s->schur);
+    for (auto& c : s->fac)
+        if (c.f) schur_free(c.f);
 }
 
 int nblocks(int64_t n) { return (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), 152 * 8); }
@@ -162,24 +169,31 @@ Pose body_pose(const pf_body_kinematics& k, double t) {
 // factor S at the pose, asynchronously (errors surface at pf_sync); the
 // previous factor is kept while body and angle are unchanged
 pf_status ensure_schur(pf_plan p, pf_state s, const pf_body_kinematics& k, const Pose& P) {
-    if (s->schur && s->schur_ns == k.ns && s->schur_alpha == P.alpha && s->schur_xb == k.xb) return PF_OK;
-    if (!s->schur || s->schur_ns != k.ns) {
-        if (s->schur) {
+    auto fits = [&](const pf_state_s::Factor& c) { return c.f && c.ns == k.ns && c.alpha == P.alpha && c.xb == k.xb; };
+    if (fits(s->fac[0])) return PF_OK;
+    std::swap(s->fac[0], s->fac[1]);
+    if (fits(s->fac[0])) return PF_OK;
+    // refactor the older entry, now in front, at this pose
+    pf_state_s::Factor& c = s->fac[0];
+    if (!c.f || c.ns != k.ns) {
+        if (c.f) {
             PF_CUDA(p, cudaStreamSynchronize(p->stream));
-            schur_free(s->schur);
-            s->schur = nullptr;
+            schur_free(c.f);
+            c.f = nullptr;
         }
-        PF_TRY(schur_create(p, k.ns, &s->schur));
+        PF_TRY(schur_create(p, k.ns, &c.f));
     }
+    c.ns = 0;                     // invalid until factored
+    c.xb = nullptr;
     const size_t v = (size_t)k.ns * sizeof(double);
     // pageable host sources: the copies complete before the calls return
-    PF_CUDA(p, cudaMemcpyAsync(s->schur->x, P.x.data(), v, cudaMemcpyHostToDevice, p->stream));
-    PF_CUDA(p, cudaMemcpyAsync(s->schur->y, P.y.data(), v, cudaMemcpyHostToDevice, p->stream));
-    PF_CUDA(p, cudaMemcpyAsync(s->schur->ds, k.ds, v, cudaMemcpyHostToDevice, p->stream));
-    PF_TRY(schur_factor_device(p, s->schur));
-    s->schur_ns = k.ns;
-    s->schur_alpha = P.alpha;
-    s->schur_xb = k.xb;
+    PF_CUDA(p, cudaMemcpyAsync(c.f->x, P.x.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(c.f->y, P.y.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(c.f->ds, k.ds, v, cudaMemcpyHostToDevice, p->stream));
+    PF_TRY(schur_factor_device(p, c.f));
+    c.ns = k.ns;
+    c.alpha = P.alpha;
+    c.xb = k.xb;
     return PF_OK;
 }
 
@@ -205,7 +219,7 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
                      const double* Y, bool shed, void* u, void* v) {
     const Pose P = body_pose(k, t);
     PF_TRY(ensure_schur(p, s, k, P));
-    pf_schur sch = s->schur;
+    pf_schur sch = s->fac[0].f;
     const pf_motion m{0.0, 0.0, P.Omega, k.Uinf, k.Vinf};
     const int ns = k.ns;
     int64_t n = s->nv;
@@ -268,7 +282,7 @@ pf_status state_load_async(pf_state s, const double* X, const double* Y, const d
     s->nv = nv;
     s->t = t;
     s->last[0] = s->last[1] = -1;
-    s->schur_xb = nullptr;
+    s->fac[0].xb = s->fac[1].xb = nullptr;
     return PF_OK;
 }
 
@@ -337,7 +351,7 @@ pf_status pf_state_set(pf_state s, const double* X, const double* Y, const doubl
     s->nv = nv;
     s->t = t;
     s->last[0] = s->last[1] = -1;
-    s->schur_xb = nullptr;          // a new history may come with a new body
+    s->fac[0].xb = s->fac[1].xb = nullptr;   // a new history may come with a new body
     return PF_OK;
 }
 
