@@ -248,6 +248,39 @@ pf_status pf_sheet_solve_edges(pf_plan plan, pf_schur schur, const void* w, cons
                                int32_t n_edges, const int32_t* edges, const double* bounds, const double* Xnew,
                                const double* Ynew, double* f, double* gamma_new, double* s0);
 
+/* Several bodies sharing one factor (Sec. 2.7, Eq. kuttasystem4).  The factor
+ * is built (pf_schur_factor) over the surface points of all bodies, body after
+ * body; body b owns the points start[b] .. start[b+1]-1.  Each body has its own
+ * uniform streamfunction value s0_b, a Kutta condition at each of its edges
+ * (0, 1 or 2; one new vortex released per edge) and Kelvin's condition over
+ * itself and the vorticity released from it:
+ *   <1_b, f> + (strengths of its new vortices) = -gamma_w[b].
+ * A body without edges is thereby circulation-constrained: gamma_w[b] is minus
+ * its prescribed bound circulation. */
+#define PF_MAX_BODIES 4
+typedef struct {
+    int32_t n_bodies;                    /* 1 .. PF_MAX_BODIES */
+    int32_t start[PF_MAX_BODIES + 1];    /* start[0] = 0 < start[1] < ... < start[n_bodies] = ns */
+    int32_t n_edges[PF_MAX_BODIES];      /* 0, 1 or 2 per body */
+    int32_t edge[PF_MAX_BODIES][2];      /* edge surface indices, inside the body's range */
+    pf_motion motion[PF_MAX_BODIES];     /* rigid motion of each body; the free stream (Uinf, Vinf)
+                                            is motion[0]'s */
+    double gamma_w[PF_MAX_BODIES];       /* circulation released earlier from body b (see above) */
+} pf_multibody;
+
+/* The several-body shedding solve: s'_b from each body's motion, the free
+ * vorticity w (device, plan precision), new vortices at (Xnew[i], Ynew[i])
+ * (HOST, one per edge, edges in body order).  Results: f (device, ns doubles),
+ * gamma_new (HOST, one per edge, same order), s0 (HOST, n_bodies).  With one
+ * body it is pf_sheet_solve's PF_SHEET_KUTTA_SHED (two or one edge) or
+ * PF_SHEET_CIRCULATION (no edge, param = -gamma_w[0]).  FP64 for both
+ * precisions; the (edges + bodies)-square constraint system is solved by
+ * Gaussian elimination with partial pivoting.  PF_ERR_ARG for an invalid
+ * partition or edge, PF_ERR_SINGULAR (at the return) if the constraint system
+ * has a vanishing pivot.  Synchronises. */
+pf_status pf_sheet_solve_multi(pf_plan plan, pf_schur schur, const void* w, const pf_multibody* mb,
+                               const double* Xnew, const double* Ynew, double* f, double* gamma_new, double* s0);
+
 /* ------------------------------------------------------- time stepping */
 
 /* Device-resident vortex set (positions and strengths, FP64) with a fixed

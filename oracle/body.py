@@ -293,3 +293,100 @@ def sheet_kutta_shed2_monolithic(S, f0, f0hat, PGsb, EinvLw, k1, k2, EinvLd1, Ei
     x = np.linalg.solve(A, rhs)
     ft = x[:ns]
     return f0 * ft, ft, x[ns], x[ns + 1], x[ns + 2]
+
+
+# ----------------------------------------------------------------- several bodies
+def body_indicators(starts, ns):
+    """Columns 1_b (Sec. 2.7): one where a surface point belongs to body b.
+    Body b holds the points starts[b] .. starts[b+1]-1 of the concatenated set."""
+    nb = len(starts) - 1
+    ind = np.zeros((ns, nb))
+    for b in range(nb):
+        ind[starts[b]:starts[b + 1], b] = 1.0
+    return ind
+
+
+def _edge_list(edges):
+    """Edges in body order, with the body each belongs to."""
+    kk, owner = [], []
+    for b, eb in enumerate(edges):
+        for k in eb:
+            kk.append(int(k))
+            owner.append(b)
+    return kk, owner
+
+
+def sheet_multibody_shed(sch, sbp, EinvLw, starts, edges, EinvLds, Gamma_ws):
+    """Several bodies sharing one Schur complement (Sec. 2.7, Eq. kuttasystem4).
+
+    The surface points of all bodies are concatenated; body b has its own
+    uniform value s0_b (the term sum_b 1_b s0_b), a Kutta condition at each of
+    its edges (edges[b]: 0, 1 or 2 surface indices) with one new vortex per
+    edge, and Kelvin's condition over itself and the vorticity it released:
+    <1_b, f> + (its new strengths) = -Gamma_ws[b].  A body without edges is
+    circulation-constrained (its Gamma_ws is minus the prescribed circulation).
+    EinvLds[:, i] = E L^{-1} d_i for the new vortex of the i-th edge (edges in
+    body order).
+
+    Split form, as Eq. twovortex generalised: ftilde* and ftilde_i as for one
+    body, g_b = Stilde^{-1} 1_b, ftilde = ftilde* + sum_i Gamma_i ftilde_i -
+    sum_b s0_b g_b; the E Kutta rows e_k^T ftilde = 0 and the B Kelvin rows
+    f0hat_b^T ftilde + sum_{i of b} Gamma_i = -Gamma_w,b (f0hat_b = f0hat o 1_b)
+    are a dense (E + B) system in (Gamma, s0).  Returns (f, ftilde, s0, Gammas).
+    """
+    ns = len(sbp)
+    ind = body_indicators(starts, ns)
+    nb = ind.shape[1]
+    kk, owner = _edge_list(edges)
+    ne = len(kk)
+    fts = intermediate_sheet(sch, sbp, EinvLw)
+    ftj = [sch.solve_tilde(EinvLds[:, i]) for i in range(ne)]
+    gb = [sch.solve_tilde(ind[:, b]) for b in range(nb)]
+    M = np.zeros((ne + nb, ne + nb))
+    rhs = np.zeros(ne + nb)
+    for r, k in enumerate(kk):                        # Kutta rows
+        for i in range(ne):
+            M[r, i] = ftj[i][k]
+        for b in range(nb):
+            M[r, ne + b] = -gb[b][k]
+        rhs[r] = -fts[k]
+    for c in range(nb):                               # Kelvin rows
+        f0h = sch.f0hat * ind[:, c]
+        for i in range(ne):
+            M[ne + c, i] = float(np.dot(f0h, ftj[i])) + (1.0 if owner[i] == c else 0.0)
+        for b in range(nb):
+            M[ne + c, ne + b] = -float(np.dot(f0h, gb[b]))
+        rhs[ne + c] = -Gamma_ws[c] - float(np.dot(f0h, fts))
+    x = np.linalg.solve(M, rhs)
+    G, s0 = x[:ne], x[ne:]
+    ft = fts + sum(G[i] * ftj[i] for i in range(ne)) - sum(s0[b] * gb[b] for b in range(nb))
+    return sch.f0 * ft, ft, s0, G
+
+
+def sheet_multibody_monolithic(S, f0, f0hat, PGsb, EinvLw, starts, edges, EinvLds, Gamma_ws):
+    """Dense solve of Eq. kuttasystem4 with psi eliminated, unknowns
+    (ftilde, s0_1..s0_B, Gamma_1..Gamma_E):
+      Stilde ftilde + sum_b s0_b 1_b - sum_i Gamma_i E L^{-1} d_i = P^Gamma s'_b + E L^{-1} w
+      e_k^T ftilde = 0 at every edge
+      f0hat_b^T ftilde + sum_{i of b} Gamma_i = -Gamma_w,b for every body."""
+    ns = S.shape[0]
+    ind = body_indicators(starts, ns)
+    nb = ind.shape[1]
+    kk, owner = _edge_list(edges)
+    ne = len(kk)
+    n = ns + nb + ne
+    A = np.zeros((n, n))
+    A[:ns, :ns] = S * f0[None, :]
+    A[:ns, ns:ns + nb] = ind
+    for i in range(ne):
+        A[:ns, ns + nb + i] = -EinvLds[:, i]
+        A[ns + i, kk[i]] = 1.0
+    for b in range(nb):
+        A[ns + ne + b, :ns] = f0hat * ind[:, b]
+        for i in range(ne):
+            if owner[i] == b:
+                A[ns + ne + b, ns + nb + i] = 1.0
+    rhs = np.concatenate([PGsb + EinvLw, np.zeros(ne), -np.asarray(Gamma_ws, dtype=np.float64)])
+    x = np.linalg.solve(A, rhs)
+    ft = x[:ns]
+    return f0 * ft, ft, x[ns:ns + nb], x[ns + nb:]

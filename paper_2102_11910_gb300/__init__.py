@@ -271,6 +271,50 @@ def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None,
     return f, list(gn[:ne]), s0.value
 
 
+PF_MAX_BODIES = _native.MAX_BODIES
+
+
+def pf_sheet_solve_multi(plan, schur, w, starts, edges, motions, gamma_w, Xnew=None, Ynew=None, f=None):
+    """Several bodies sharing one factor (pf_sheet_solve_multi).  starts: the
+    B + 1 point offsets of the bodies in the factor; edges: per body a tuple of
+    0-2 surface indices; motions: per body (U, V, Omega, Uinf, Vinf) (the free
+    stream is the first body's), or one tuple for all; gamma_w: per body.
+    Xnew, Ynew: one new vortex per edge, edges in body order.
+    Returns (f device float64 tensor, gamma_new array, s0 array)."""
+    import numpy as np
+    nb = len(starts) - 1
+    if nb < 1 or nb > PF_MAX_BODIES or len(edges) != nb or len(gamma_w) != nb:
+        raise ValueError("between 1 and %d bodies, with edges and gamma_w per body" % PF_MAX_BODIES)
+    if len(motions) == 5 and not hasattr(motions[0], "__len__"):
+        motions = [motions] * nb
+    mb = _native.PfMultibody()
+    mb.n_bodies = nb
+    for b in range(nb + 1):
+        mb.start[b] = int(starts[b])
+    for b in range(nb):
+        if len(edges[b]) > 2:
+            raise ValueError("at most two edges per body")
+        mb.n_edges[b] = len(edges[b])
+        for j, k in enumerate(edges[b]):
+            mb.edge[b][j] = int(k)
+        mb.motion[b] = _native.PfMotion(*[float(v) for v in motions[b]])
+        mb.gamma_w[b] = float(gamma_w[b])
+    ne = sum(len(e) for e in edges)
+    f = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if f is None else f
+    xn = _host_f64(Xnew if Xnew is not None else np.zeros(max(ne, 1)))
+    yn = _host_f64(Ynew if Ynew is not None else np.zeros(max(ne, 1)))
+    if len(xn) < ne or len(yn) < ne:
+        raise ValueError("one new vortex per edge")
+    gn = np.zeros(max(ne, 1))
+    s0 = np.zeros(nb)
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_sheet_solve_multi(plan.handle, schur.handle, _ptr(w, plan.dtype, "w"),
+                                                     ctypes.byref(mb), c(xn.ctypes.data), c(yn.ctypes.data),
+                                                     _ptr(f, torch.float64, "f"), c(gn.ctypes.data),
+                                                     c(s0.ctypes.data)), "pf_sheet_solve_multi", plan.handle)
+    return f, gn[:ne].copy(), s0
+
+
 PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT = 0, 1, 2
 
 

@@ -40,6 +40,7 @@ SIGNATURES = {
     "pf_impulse": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pf_plan_set_rhs_route": (_c.c_int, [_P, _I32]),
     "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "pf_sheet_solve_multi": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),
@@ -77,6 +78,14 @@ class PfBodyDesc(ctypes.Structure):
 
 class PfMotion(ctypes.Structure):
     _fields_ = [("U", _D), ("V", _D), ("Omega", _D), ("Uinf", _D), ("Vinf", _D)]
+
+
+MAX_BODIES = 4
+
+
+class PfMultibody(ctypes.Structure):
+    _fields_ = [("n_bodies", _I32), ("start", _I32 * (MAX_BODIES + 1)), ("n_edges", _I32 * MAX_BODIES),
+                ("edge", (_I32 * 2) * MAX_BODIES), ("motion", PfMotion * MAX_BODIES), ("gamma_w", _D * MAX_BODIES)]
 
 
 class PfBodyKinematics(ctypes.Structure):

@@ -418,51 +418,42 @@ __global__ void k_f0_final(const double* __restrict__ f0, const double* __restri
     if (threadIdx.x == 0) *gamma0 = g;
 }
 
-// One step of iterative refinement of y_c ~ S^-1 v_c (c < nc <= 3), in two
-// passes, one warp per row and a fixed shuffle tree:
-//   k_residual   r_c = v_c - S y_c   (v_c = 1 when v is null)
-//   k_gemv_add   y_c += S^-1 r_c
-// The residual uses S itself, so the refined y is as accurate as FP64 and
-// cond(S) allow, whatever rounding the inverse carries.
-__global__ void k_residual(const double* __restrict__ S, int ns, const double* __restrict__ v, int nc,
-                           const double* __restrict__ y, double* __restrict__ r) {
+// Rows of a dense ns x ns matrix A against nc vectors x_c (stride ns), one
+// warp per row, three vectors per blockIdx.y, a fixed shuffle tree:
+//   MODE 0  out_c  = A x_c
+//   MODE 1  out_c  = v_c - A x_c     (v_c = 1 when v is null)
+//   MODE 2  out_c += A x_c
+// One step of iterative refinement of y ~ S^-1 v is MODE 1 with A = S (the
+// residual against S itself) and then MODE 2 with A = S^-1: the refined y is
+// as accurate as FP64 and cond(S) allow, whatever rounding the inverse carries.
+template <int MODE>
+__global__ void k_rows(const double* __restrict__ A, int ns, const double* __restrict__ x, int nc,
+                       const double* __restrict__ v, double* __restrict__ out) {
     const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int c0 = 3 * blockIdx.y;
     if (row >= ns) return;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int q = lane; q < ns; q += 32) {
-        const double a = S[(size_t)row * ns + q];
+        const double a = A[(size_t)row * ns + q];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (c < nc) acc[c] += a * y[(size_t)c * ns + q];
+            if (c0 + c < nc) acc[c] += a * x[(size_t)(c0 + c) * ns + q];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
     if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (c < nc) r[(size_t)c * ns + row] = (v ? v[(size_t)c * ns + row] : 1.0) - acc[c];
+        for (int c = 0; c < 3; ++c) {
+            if (c0 + c >= nc) continue;
+            const size_t i = (size_t)(c0 + c) * ns + row;
+            if (MODE == 0) out[i] = acc[c];
+            else if (MODE == 1) out[i] = (v ? v[i] : 1.0) - acc[c];
+            else out[i] += acc[c];
+        }
 }
 
-__global__ void k_gemv_add(const double* __restrict__ Sinv, int ns, const double* __restrict__ r, int nc,
-                           double* __restrict__ y) {
-    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-    if (row >= ns) return;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int q = lane; q < ns; q += 32) {
-        const double a = Sinv[(size_t)row * ns + q];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (c < nc) acc[c] += a * r[(size_t)c * ns + q];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (c < nc) y[(size_t)c * ns + row] += acc[c];
-}
+inline dim3 rows_grid(int ns, int nc) { return dim3((unsigned)ceil_div(ns, 8), (unsigned)ceil_div(nc, 3)); }
 
 // Order of the sheet deposit: the 16 ns stencil entries e = 16 p + 4 b + a
 // sorted by (grid node, e), so that each node's entries are contiguous and in
@@ -577,6 +568,26 @@ __global__ void k_sbprime(const double* __restrict__ x, const double* __restrict
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ns) return;
     sb[p] = (m.U - m.Uinf) * y[p] - (m.V - m.Vinf) * x[p] - 0.5 * m.Omega * (x[p] * x[p] + y[p] * y[p]);
+}
+
+// s'_b of several bodies: each point with its own body's motion, the free
+// stream of motion[0]
+__global__ void k_sbprime_multi(const double* __restrict__ x, const double* __restrict__ y, int ns, pf_multibody mb,
+                                double* __restrict__ sb) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    int b = 0;
+    while (b + 1 < mb.n_bodies && p >= mb.start[b + 1]) ++b;
+    const pf_motion m = mb.motion[b];
+    sb[p] = (m.U - mb.motion[0].Uinf) * y[p] - (m.V - mb.motion[0].Vinf) * x[p] -
+            0.5 * m.Omega * (x[p] * x[p] + y[p] * y[p]);
+}
+
+// the body indicators 1_b as columns out[b*ns + p]
+__global__ void k_indicators(int ns, pf_multibody mb, double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (p >= ns || b >= mb.n_bodies) return;
+    out[(size_t)b * ns + p] = (p >= mb.start[b] && p < mb.start[b + 1]) ? 1.0 : 0.0;
 }
 
 // E_s L^-1 d_j for unit point vortices at (vx[j], vy[j]), j < nj: out[j*ns + p]
@@ -841,7 +852,7 @@ pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
 
 static void free_schur(pf_schur s) {
     void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
-                    s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->scal};
+                    s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->mwork, s->scal};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -905,8 +916,8 @@ pf_status schur_factor_device(pf_plan p, pf_schur s) {
     }
     // f0 = S^-1 1 with one refinement step (scratch: the solve workspace)
     k_f0_rows<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, s->f0);
-    k_residual<<<ceil_div(ns, 8), 256, 0, st>>>(s->S, ns, nullptr, 1, s->f0, s->work);
-    k_gemv_add<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, s->work, 1, s->f0);
+    k_rows<1><<<rows_grid(ns, 1), 256, 0, st>>>(s->S, ns, s->f0, 1, nullptr, s->work);
+    k_rows<2><<<rows_grid(ns, 1), 256, 0, st>>>(s->Sinv, ns, s->work, 1, nullptr, s->f0);
     k_f0_final<<<1, 256, 0, st>>>(s->f0, s->ds, ns, s->f0hat, s->dgamma0);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
@@ -1012,6 +1023,91 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew) {
     return PF_OK;
 }
 
+// Several bodies (Sec. 2.7, Eq. kuttasystem4), one block of 256.  y holds
+// S^-1 of [rhs0 | E L^-1 d_1 .. d_E | 1_1 .. 1_B] (refined).  With ftilde_c =
+// y_c / f0, the Kutta rows e_k^T ftilde = 0 and the Kelvin rows
+//   f0hat_b^T ftilde + sum_{i of b} Gamma_i = -gamma_w[b],
+// where f0hat_b^T ftilde_c = sum_{p in b} dS_p y_c[p], form the (E + B) system
+// in (Gamma, s0), solved by thread 0 with partial pivoting; then
+// f = f0 o ftilde = y_0 + sum_i Gamma_i y_i - sum_b s0_b y_(E+b).
+// out: s0 (B) then Gamma (E).
+constexpr int MB_COLS = 1 + 3 * PF_MAX_BODIES;    // right-hand sides: rhs0, one per edge, one per body
+constexpr int MB_N = 3 * PF_MAX_BODIES;           // unknowns: edges + bodies
+
+__global__ void __launch_bounds__(256) k_constraints_multi(int ns, pf_multibody mb, int ne, const double* __restrict__ y,
+                                                           const double* __restrict__ f0, const double* __restrict__ ds,
+                                                           double* __restrict__ f, double* __restrict__ out,
+                                                           int* __restrict__ status) {
+    __shared__ double circ[MB_COLS * PF_MAX_BODIES];
+    __shared__ double sol[MB_N];
+    const int nb = mb.n_bodies, nc = 1 + ne + nb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = wid; t < nc * nb; t += blockDim.x >> 5) {
+        const int c = t / nb, b = t - (t / nb) * nb;
+        double a = 0.0;
+        for (int p = mb.start[b] + lane; p < mb.start[b + 1]; p += 32) a += ds[p] * y[(size_t)c * ns + p];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) circ[t] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int n = ne + nb;
+        double M[MB_N][MB_N + 1];
+        int kk[2 * PF_MAX_BODIES], own[2 * PF_MAX_BODIES];
+        int e = 0;
+        for (int b = 0; b < nb; ++b)
+            for (int j = 0; j < mb.n_edges[b]; ++j) {
+                kk[e] = mb.edge[b][j];
+                own[e++] = b;
+            }
+        for (int r = 0; r < ne; ++r) {                 // Kutta rows
+            const int k = kk[r];
+            const double inv = 1.0 / f0[k];
+            for (int i = 0; i < ne; ++i) M[r][i] = y[(size_t)(1 + i) * ns + k] * inv;
+            for (int b = 0; b < nb; ++b) M[r][ne + b] = -y[(size_t)(1 + ne + b) * ns + k] * inv;
+            M[r][n] = -y[k] * inv;
+        }
+        for (int c = 0; c < nb; ++c) {                 // Kelvin rows
+            for (int i = 0; i < ne; ++i) M[ne + c][i] = circ[(1 + i) * nb + c] + (own[i] == c ? 1.0 : 0.0);
+            for (int b = 0; b < nb; ++b) M[ne + c][ne + b] = -circ[(1 + ne + b) * nb + c];
+            M[ne + c][n] = -mb.gamma_w[c] - circ[c];
+        }
+        for (int col = 0; col < n; ++col) {            // Gaussian elimination, partial pivoting
+            int pr = col;
+            for (int r = col + 1; r < n; ++r)
+                if (fabs(M[r][col]) > fabs(M[pr][col])) pr = r;
+            if (pr != col)
+                for (int j = 0; j <= n; ++j) {
+                    const double t = M[col][j];
+                    M[col][j] = M[pr][j];
+                    M[pr][j] = t;
+                }
+            if (!(fabs(M[col][col]) > 1e-300)) {
+                atomicOr(status, ST_SINGULAR);
+                M[col][col] = 1.0;
+            }
+            for (int r = col + 1; r < n; ++r) {
+                const double l = M[r][col] / M[col][col];
+                for (int j = col; j <= n; ++j) M[r][j] -= l * M[col][j];
+            }
+        }
+        for (int r = n - 1; r >= 0; --r) {
+            double a = M[r][n];
+            for (int j = r + 1; j < n; ++j) a -= M[r][j] * sol[j];
+            sol[r] = a / M[r][r];
+        }
+        for (int b = 0; b < nb; ++b) out[b] = sol[ne + b];
+        for (int i = 0; i < ne; ++i) out[nb + i] = sol[i];
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < ns; p += blockDim.x) {
+        double v = y[p];
+        for (int i = 0; i < ne; ++i) v += sol[i] * y[(size_t)(1 + i) * ns + p];
+        for (int b = 0; b < nb; ++b) v -= sol[ne + b] * y[(size_t)(1 + ne + b) * ns + p];
+        f[p] = v;
+    }
+}
+
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
                              const double* vy, double* f, const EdgeBounds& eb) {
@@ -1036,8 +1132,8 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
         PF_LAUNCH_CHECK(p);
     }
     k_gemv<<<ns, 128, 0, st>>>(s->Sinv, ns, rhs, nc, y);
-    k_residual<<<ceil_div(ns, 8), 256, 0, st>>>(s->S, ns, rhs, nc, y, res);
-    k_gemv_add<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, res, nc, y);
+    k_rows<1><<<rows_grid(ns, nc), 256, 0, st>>>(s->S, ns, y, nc, rhs, res);
+    k_rows<2><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, res, nc, nullptr, y);
     PF_LAUNCH_CHECK(p);
     k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, eb,
                                      param, param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
@@ -1125,6 +1221,70 @@ pf_status pf_sheet_solve(pf_plan p, pf_schur s, const void* w, const pf_motion* 
     if (s0) *s0 = sc[0];
     if (gamma_new)
         for (int e = 0; e < (mode == PF_SHEET_KUTTA_SHED ? n_edges : 0); ++e) gamma_new[e] = sc[1 + e];
+    return PF_OK;
+}
+
+pf_status pf_sheet_solve_multi(pf_plan p, pf_schur s, const void* w, const pf_multibody* mb, const double* Xnew,
+                               const double* Ynew, double* f, double* gamma_new, double* s0) {
+    if (!p || !w || !mb || !f) return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    const int nb = mb->n_bodies, ns = s->ns;
+    if (nb < 1 || nb > PF_MAX_BODIES || mb->start[0] != 0 || mb->start[nb] != ns) return PF_ERR_ARG;
+    int ne = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (mb->start[b + 1] <= mb->start[b] || mb->n_edges[b] < 0 || mb->n_edges[b] > 2) return PF_ERR_ARG;
+        for (int j = 0; j < mb->n_edges[b]; ++j)
+            if (mb->edge[b][j] < mb->start[b] || mb->edge[b][j] >= mb->start[b + 1]) return PF_ERR_ARG;
+        ne += mb->n_edges[b];
+    }
+    if (ne > 0 && (!Xnew || !Ynew)) return PF_ERR_ARG;
+    const int nc = 1 + ne + nb;
+    cudaStream_t st = p->stream;
+    if (!s->mwork) {
+        PF_CUDA(p, cudaStreamSynchronize(st));
+        PF_CUDA(p, cudaMalloc(&s->mwork, ((2 + 3 * (size_t)MB_COLS) * ns + 8 * PF_MAX_BODIES) * sizeof(double)));
+    }
+    double* sb = s->mwork;
+    double* ew = sb + ns;
+    double* rhs = ew + ns;                       // rhs0 | E L^-1 d_i | 1_b
+    double* y = rhs + (size_t)MB_COLS * ns;
+    double* res = y + (size_t)MB_COLS * ns;
+    double* vx = res + (size_t)MB_COLS * ns;     // new vortices: x (up to 2 B), y (up to 2 B)
+    double* vy = vx + 2 * PF_MAX_BODIES;
+    double* out = vy + 2 * PF_MAX_BODIES;        // s0 (B), Gamma (E)
+    if (ne > 0) {
+        PF_CUDA(p, cudaMemcpyAsync(vx, Xnew, ne * sizeof(double), cudaMemcpyHostToDevice, st));
+        PF_CUDA(p, cudaMemcpyAsync(vy, Ynew, ne * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    k_sbprime_multi<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, *mb, sb);
+    PF_LAUNCH_CHECK(p);
+    PF_TRY(surface_rhs(p, s, w, ew));
+    k_rhs0<<<1, 256, 0, st>>>(PF_SHEET_KUTTA_SHED, ns, 0.0, nullptr, sb, ew, s->f0hat, s->dgamma0, rhs);
+    if (ne > 0)
+        k_unit_vortex<<<dim3(ceil_div(ns, 128), ne), 128, 0, st>>>(vx, vy, ne, s->six, s->siy, s->swx, s->swy, ns,
+                                                                    p->G, p->nx, p->ny, p->x0, p->y0, p->dx, rhs + ns,
+                                                                    p->d_status);
+    k_indicators<<<dim3(ceil_div(ns, 256), nb), 256, 0, st>>>(ns, *mb, rhs + (size_t)(1 + ne) * ns);
+    k_rows<0><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, rhs, nc, nullptr, y);
+    k_rows<1><<<rows_grid(ns, nc), 256, 0, st>>>(s->S, ns, y, nc, rhs, res);
+    k_rows<2><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, res, nc, nullptr, y);
+    k_constraints_multi<<<1, 256, 0, st>>>(ns, *mb, ne, y, s->f0, s->ds, f, out, p->d_status);
+    PF_LAUNCH_CHECK(p);
+    double h[3 * PF_MAX_BODIES];
+    int status = 0;
+    PF_CUDA(p, cudaMemcpyAsync(h, out, (nb + ne) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA(p, cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PF_CUDA(p, cudaStreamSynchronize(st));
+    if (status & ST_SINGULAR) {
+        const int keep = status & ~ST_SINGULAR;
+        PF_CUDA(p, cudaMemcpyAsync(p->d_status, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
+        PF_CUDA(p, cudaStreamSynchronize(st));
+        return PF_ERR_SINGULAR;
+    }
+    if (s0)
+        for (int b = 0; b < nb; ++b) s0[b] = h[b];
+    if (gamma_new)
+        for (int i = 0; i < ne; ++i) gamma_new[i] = h[nb + i];
     return PF_OK;
 }
 

@@ -23,6 +23,7 @@ struct pf_schur_s {
     int* snode = nullptr;     // their grid nodes in that order (both null when ns > SHEET_SORT_MAX)
     double* gj = nullptr;     // blocked Gauss-Jordan scratch: LU (32 x 32), Y, Z (32 x ns), L_R (ns x 32), perm, gperm
     double* work = nullptr;   // 12 ns doubles of solve scratch
+    double* mwork = nullptr;  // several-body solve scratch (allocated by the first such solve)
     double* scal = nullptr;   // device scalars: s0, Gamma1, Gamma2, -, new-vortex x[2], y[2]
 };
 

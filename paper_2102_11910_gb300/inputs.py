@@ -112,6 +112,76 @@ def plate_vortices_128(seed=1000, nv=256, ns=64):
                 Uinf=1.0, Vinf=0.0, dt=0.01, alpha=alpha)
 
 
+def _away(X, Y, bodies, d):
+    """Mask of points farther than d from every surface point of the bodies."""
+    keep = np.ones(len(X), dtype=bool)
+    for b in bodies:
+        dist = np.min(np.hypot(X[:, None] - b.x[None, :], Y[:, None] - b.y[None, :]), axis=1)
+        keep &= dist > d
+    return keep
+
+
+def three_bodies_128(seed=1006, nv=200):
+    """Several bodies in one grid (128^2 nodes, dx 0.02, centred): plate A
+    (24 points, chord 0.6, 20 deg, both edges), plate B (24 points, chord 0.6,
+    -15 deg, trailing edge only) and an ellipse C (40 points, semi-axes 0.25 and
+    0.1, no edge), dS/dx 1.25-1.4; nv vortices N(0, 0.01) away from the bodies;
+    one new-vortex position near each edge; per-body circulations Gamma_w of
+    earlier released vorticity (minus the prescribed circulation for C)."""
+    rng = np.random.default_rng(seed)
+    grid = centred_grid(128, 128, 0.02)
+    A = plate(24, 0.6, math.radians(20.0), -0.5, 0.45)
+    B = plate(24, 0.6, math.radians(-15.0), -0.45, -0.5)
+    C = ellipse(40, 0.25, 0.1, 0.5, 0.05, 0.3)
+    bodies = [A, B, C]
+    X, Y, G = [], [], []
+    while len(X) < nv:
+        x, y, g = uniform_vortices(rng, nv, -1.1, 1.1, 0.01)
+        keep = _away(x, y, bodies, 4 * grid.dx)
+        X += list(x[keep]); Y += list(y[keep]); G += list(g[keep])
+    x = np.concatenate([b.x for b in bodies])
+    y = np.concatenate([b.y for b in bodies])
+    ds = np.concatenate([b.ds for b in bodies])
+    starts = np.array([0, 24, 48, 88])
+    edges = [(0, 23), (47,), ()]
+    # new vortices: 3 dx off each edge, away from its body's centre
+    cen = [(-0.5, 0.45), (-0.45, -0.5), (0.5, 0.05)]
+    VX, VY = [], []
+    for b, eb in enumerate(edges):
+        for k in eb:
+            vx, vy = x[k] - cen[b][0], y[k] - cen[b][1]
+            r = math.hypot(vx, vy)
+            VX.append(x[k] + 3 * grid.dx * vx / r)
+            VY.append(y[k] + 3 * grid.dx * vy / r)
+    return dict(grid=grid, x=x, y=y, ds=ds, starts=starts, edges=edges, X=np.array(X[:nv]), Y=np.array(Y[:nv]),
+                G=np.array(G[:nv]), VX=np.array(VX), VY=np.array(VY), Gamma_w=np.array([0.08, -0.05, 0.03]),
+                Uinf=1.0, Vinf=0.0)
+
+
+def mirrored_plates_128(seed=1007, nv=100):
+    """Two plates mirrored in the x axis (24 points each, chord 0.6, +-20 deg,
+    centres (-0.3, +-0.35)), 128^2 nodes centred on the origin, and a vortex
+    set closed under the mirror (x, y, G) -> (x, -y, -G); uniform flow along x.
+    Mirror images: point p of plate B is point p of plate A reflected."""
+    rng = np.random.default_rng(seed)
+    grid = centred_grid(128, 128, 0.02)
+    A = plate(24, 0.6, math.radians(20.0), -0.3, 0.35)
+    B = plate(24, 0.6, math.radians(-20.0), -0.3, -0.35)
+    X, Y, G = [], [], []
+    while len(X) < nv:
+        x, y, g = uniform_vortices(rng, nv, -1.1, 1.1, 0.01, 0.05, 1.1)
+        keep = _away(x, y, [A, B], 4 * grid.dx)
+        X += list(x[keep]); Y += list(y[keep]); G += list(g[keep])
+    X, Y, G = np.array(X[:nv]), np.array(Y[:nv]), np.array(G[:nv])
+    VX = np.array([A.x[0] - 0.06, A.x[-1] + 0.06])
+    VY = np.array([A.y[0] + 0.03, A.y[-1] - 0.03])
+    return dict(grid=grid, x=np.concatenate([A.x, B.x]), y=np.concatenate([A.y, B.y]),
+                ds=np.concatenate([A.ds, B.ds]), starts=np.array([0, 24, 48]), edges=[(0, 23), (24, 47)],
+                X=np.concatenate([X, X]), Y=np.concatenate([Y, -Y]), G=np.concatenate([G, -G]),
+                VX=np.concatenate([VX, VX]), VY=np.concatenate([VY, -VY]), Gamma_w=np.array([0.04, -0.04]),
+                Uinf=1.0, Vinf=0.0)
+
+
 def vic_1024(seed=1001, nv=1_000_000, n=1024):
     """The body-free VIC workload: n^2 nodes on [-1,1]^2, nv vortices in the central 80 %."""
     rng = np.random.default_rng(seed)
