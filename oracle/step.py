@@ -145,3 +145,103 @@ def body_step(grid, table, kin, state, dt, scheme="euler"):
         state.last = [n_old, n_old + 1]
     state.t = t + dt
     return info
+
+
+# ----------------------------------------------------------------- several bodies
+class MultiBodyState:
+    """Vortices, the index of the last vortex released at every edge (edges in
+    body order) and the circulation released so far by each body."""
+
+    def __init__(self, n_bodies, n_edges):
+        self.X = np.zeros(0)
+        self.Y = np.zeros(0)
+        self.G = np.zeros(0)
+        self.last = [None] * n_edges
+        self.released = np.zeros(n_bodies)
+        self.t = 0.0
+
+
+def _multi_surface(kins, t):
+    """Concatenated surface of the bodies at time t: points, segment lengths,
+    body offsets, edges (global indices, per body) and s'_b of each body's
+    rotation in the free stream of the first body."""
+    xs, ys, ds, starts, edges, sbp = [], [], [], [0], [], []
+    for kin in kins:
+        x, y, d, e = kin.surface(t)
+        off = starts[-1]
+        xs.append(x); ys.append(y); ds.append(d)
+        edges.append(tuple(off + k for k in e))
+        sbp.append(B.sb_prime(x, y, 0.0, 0.0, kin.Omega(t), kins[0].Uinf, kins[0].Vinf))
+        starts.append(off + len(x))
+    return (np.concatenate(xs), np.concatenate(ys), np.concatenate(ds), np.array(starts), edges,
+            np.concatenate(sbp))
+
+
+def _multi_stage(grid, table, kins, t, X, Y, G, shed, dt, last_pos, released):
+    """One stage with several bodies: the sheet of Eq. kuttasystem4 (Kutta at
+    every edge when shedding, otherwise every body circulation-constrained)
+    and the velocities at all vortices.  Gamma_w of body b >= 1 is the
+    circulation it released; body 0 takes the rest of the flow's circulation
+    (so one body is the single-body step)."""
+    xs, ys, ds, starts, edges, sbp = _multi_surface(kins, t)
+    st = B.SurfaceStencil(grid, xs, ys)
+    sch = B.Schur(B.schur_matrix(grid, st, ds, table), ds)
+    w = regularize(grid, X, Y, G)
+    Gtot = circulation(grid, w)
+    Gws = np.concatenate([[Gtot - np.sum(released[1:])], released[1:]])
+    EinvLw = -B.interp_surface(st, streamfunction(grid, w, table))
+    U, V = kins[0].Uinf, kins[0].Vinf
+    if shed:
+        pos = []
+        e = 0
+        for b, eb in enumerate(edges):
+            lo, hi = starts[b], starts[b + 1]      # the edge's neighbour is on its own body
+            for k in eb:
+                pos.append(new_vortex_position(xs[lo:hi], ys[lo:hi], k - lo, last_pos[e], dt, U, V))
+                e += 1
+        nX, nY = np.array([p[0] for p in pos]), np.array([p[1] for p in pos])
+        E = B.EinvL_unit_vortex(grid, st, nX, nY, table)
+        f, ft, s0, nG = B.sheet_multibody_shed(sch, sbp, EinvLw, starts, edges, E, Gws)
+    else:
+        f, ft, s0, _ = B.sheet_multibody_shed(sch, sbp, EinvLw, starts, [()] * len(kins),
+                                              np.zeros((len(xs), 0)), Gws)
+        nX, nY, nG = np.zeros(0), np.zeros(0), np.zeros(0)
+    AX, AY, AG = np.concatenate([X, nX]), np.concatenate([Y, nY]), np.concatenate([G, nG])
+    wt = regularize(grid, AX, AY, AG) + B.regularize_surface(grid, st, f, ds)
+    psi1 = streamfunction(grid, wt, table, pad=1)
+    u, v = node_velocity(grid, psi1, U, V)
+    info = dict(f=f, s0=s0, Gws=Gws, starts=starts, edges=edges, ds=ds,
+                circ_b=[float(np.dot(ds[a:b], f[a:b])) for a, b in zip(starts[:-1], starts[1:])])
+    return interpolate(grid, u, AX, AY), interpolate(grid, v, AX, AY), nX, nY, nG, info
+
+
+def multibody_step(grid, table, kins, state, dt, scheme="euler"):
+    """Advance the vortex set one step with several bodies (Sec. 2.7): one new
+    vortex per edge (Kutta), Kelvin per body; the rules of body_step otherwise."""
+    t = state.t
+    edges_per = [len(k.edges) for k in kins]
+    release = sum(edges_per) > 0
+    last_pos = [None if i is None else (state.X[i], state.Y[i]) for i in state.last]
+    u1, v1, nX, nY, nG, info = _multi_stage(grid, table, kins, t, state.X, state.Y, state.G, release, dt, last_pos,
+                                            state.released)
+    e = 0
+    for b, n in enumerate(edges_per):
+        state.released[b] += float(np.sum(nG[e:e + n]))
+        e += n
+    X = np.concatenate([state.X, nX])
+    Y = np.concatenate([state.Y, nY])
+    G = np.concatenate([state.G, nG])
+    if scheme == "euler":
+        X, Y = X + dt * u1, Y + dt * v1
+    elif scheme == "rk2":
+        Xs, Ys = X + dt * u1, Y + dt * v1
+        u2, v2, _, _, _, _ = _multi_stage(grid, table, kins, t + dt, Xs, Ys, G, False, dt, None, state.released)
+        X, Y = X + 0.5 * dt * (u1 + u2), Y + 0.5 * dt * (v1 + v2)
+    else:
+        raise ValueError(scheme)
+    n_old = len(state.X)
+    state.X, state.Y, state.G = X, Y, G
+    if release:
+        state.last = [n_old + i for i in range(len(nG))]
+    state.t = t + dt
+    return info
