@@ -331,6 +331,22 @@ typedef struct {
 pf_status pf_step(pf_plan plan, pf_state state, const pf_body_kinematics* body, double dt,
                   int32_t scheme);
 
+/* Advance the vortex set by dt around n_bodies bodies (1 .. PF_MAX_BODIES)
+ * sharing one factor (Sec. 2.7, Eq. kuttasystem4): every edge of every body
+ * (n_edges 0, 1 or 2; edge_bounded must be 0) releases one vortex per step
+ * under the Kutta condition, placed by pf_step's rule from its own body's
+ * surface; Kelvin's condition holds per body, body b >= 1 balancing the
+ * vorticity it released and body 0 the rest of the flow's circulation (with
+ * one body this is pf_step); a body without edges is circulation-constrained.
+ * The free stream is bodies[0]'s.  scheme as pf_step, whose second stage
+ * constrains every body's circulation.  The factor of the concatenated
+ * surface is rebuilt when any body's pose changes (the last two poses are
+ * kept).  The state's release history is per edge, edges in body order.
+ * PF_ERR_ARG for an invalid body, PF_ERR_CAPACITY if the new vortices do
+ * not fit. */
+pf_status pf_step_multi(pf_plan plan, pf_state state, int32_t n_bodies, const pf_body_kinematics* bodies,
+                        double dt, int32_t scheme);
+
 /* Independent instances, one step each: pf_step for plans[i], states[i],
  * bodies[i] (i < n), each enqueued on its own plan's stream so instances on
  * distinct streams overlap on the device.  Stops at the first error. */

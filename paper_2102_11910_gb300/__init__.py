@@ -315,6 +315,16 @@ def pf_sheet_solve_multi(plan, schur, w, starts, edges, motions, gamma_w, Xnew=N
     return f, gn[:ne].copy(), s0
 
 
+def pf_step_multi(plan, state, dt, bodies, scheme=0):
+    """One step around several bodies (a list of BodyKinematics, at most
+    PF_MAX_BODIES; the free stream is the first one's)."""
+    if not 1 <= len(bodies) <= PF_MAX_BODIES:
+        raise ValueError("between 1 and %d bodies" % PF_MAX_BODIES)
+    arr = (_native.PfBodyKinematics * len(bodies))(*[b.struct for b in bodies])
+    _native.check(_native.lib().pf_step_multi(plan.handle, state.handle, len(bodies), arr, float(dt), int(scheme)),
+                  "pf_step_multi", plan.handle)
+
+
 PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT = 0, 1, 2
 
 

@@ -41,6 +41,7 @@ SIGNATURES = {
     "pf_plan_set_rhs_route": (_c.c_int, [_P, _I32]),
     "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "pf_sheet_solve_multi": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "pf_step_multi": (_c.c_int, [_P, _P, _I32, _P, _D, _I32]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),

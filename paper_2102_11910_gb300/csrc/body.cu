@@ -1030,14 +1030,16 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew) {
 // where f0hat_b^T ftilde_c = sum_{p in b} dS_p y_c[p], form the (E + B) system
 // in (Gamma, s0), solved by thread 0 with partial pivoting; then
 // f = f0 o ftilde = y_0 + sum_i Gamma_i y_i - sum_b s0_b y_(E+b).
+// gamma_w comes from gw_dev (device, B values) when it is not null.
 // out: s0 (B) then Gamma (E).
 constexpr int MB_COLS = 1 + 3 * PF_MAX_BODIES;    // right-hand sides: rhs0, one per edge, one per body
 constexpr int MB_N = 3 * PF_MAX_BODIES;           // unknowns: edges + bodies
+constexpr int MB_EDGES = 2 * PF_MAX_BODIES;
 
 __global__ void __launch_bounds__(256) k_constraints_multi(int ns, pf_multibody mb, int ne, const double* __restrict__ y,
                                                            const double* __restrict__ f0, const double* __restrict__ ds,
-                                                           double* __restrict__ f, double* __restrict__ out,
-                                                           int* __restrict__ status) {
+                                                           const double* __restrict__ gw_dev, double* __restrict__ f,
+                                                           double* __restrict__ out, int* __restrict__ status) {
     __shared__ double circ[MB_COLS * PF_MAX_BODIES];
     __shared__ double sol[MB_N];
     const int nb = mb.n_bodies, nc = 1 + ne + nb;
@@ -1070,7 +1072,7 @@ __global__ void __launch_bounds__(256) k_constraints_multi(int ns, pf_multibody 
         for (int c = 0; c < nb; ++c) {                 // Kelvin rows
             for (int i = 0; i < ne; ++i) M[ne + c][i] = circ[(1 + i) * nb + c] + (own[i] == c ? 1.0 : 0.0);
             for (int b = 0; b < nb; ++b) M[ne + c][ne + b] = -circ[(1 + ne + b) * nb + c];
-            M[ne + c][n] = -mb.gamma_w[c] - circ[c];
+            M[ne + c][n] = -(gw_dev ? gw_dev[c] : mb.gamma_w[c]) - circ[c];
         }
         for (int col = 0; col < n; ++col) {            // Gaussian elimination, partial pivoting
             int pr = col;
@@ -1138,6 +1140,61 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     k_constraints<<<1, 256, 0, st>>>(mode, ns, n_edges, n_edges > 0 ? edges[0] : 0, n_edges > 1 ? edges[1] : 0, eb,
                                      param, param_dev, s->ds, s->f0, s->f0hat, s->dgamma0, y, f, s->scal);
     PF_LAUNCH_CHECK(p);
+    return PF_OK;
+}
+
+pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total) {
+    const int nb = mb.n_bodies;
+    if (nb < 1 || nb > PF_MAX_BODIES || mb.start[0] != 0 || mb.start[nb] != ns) return PF_ERR_ARG;
+    int ne = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (mb.start[b + 1] <= mb.start[b] || mb.n_edges[b] < 0 || mb.n_edges[b] > 2) return PF_ERR_ARG;
+        for (int j = 0; j < mb.n_edges[b]; ++j)
+            if (mb.edge[b][j] < mb.start[b] || mb.edge[b][j] >= mb.start[b + 1]) return PF_ERR_ARG;
+        ne += mb.n_edges[b];
+    }
+    *n_edges_total = ne;
+    return PF_OK;
+}
+
+// the several-body scratch of a factor: sb, ew, then MB_COLS columns each of
+// rhs, y, res, then new vortices (x, y: MB_EDGES each) and the outputs
+pf_status multibody_scratch(pf_plan p, pf_schur s) {
+    if (s->mwork) return PF_OK;
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    PF_CUDA(p, cudaMalloc(&s->mwork, ((2 + 3 * (size_t)MB_COLS) * s->ns + 2 * MB_EDGES + MB_N) * sizeof(double)));
+    return PF_OK;
+}
+
+double* multibody_newpos(pf_schur s) { return s->mwork + (2 + 3 * (size_t)MB_COLS) * s->ns; }
+
+pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
+                                   const double* vx, const double* vy, double* f, const double* gw_dev,
+                                   double** out_dev) {
+    const int nb = mb.n_bodies, ns = s->ns, nc = 1 + ne + nb;
+    cudaStream_t st = p->stream;
+    PF_TRY(multibody_scratch(p, s));
+    double* sb = s->mwork;
+    double* ew = sb + ns;
+    double* rhs = ew + ns;                       // rhs0 | E L^-1 d_i | 1_b
+    double* y = rhs + (size_t)MB_COLS * ns;
+    double* res = y + (size_t)MB_COLS * ns;
+    double* out = multibody_newpos(s) + 2 * MB_EDGES;   // s0 (B), Gamma (E)
+    k_sbprime_multi<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, mb, sb);
+    PF_LAUNCH_CHECK(p);
+    PF_TRY(surface_rhs(p, s, w, ew));
+    k_rhs0<<<1, 256, 0, st>>>(PF_SHEET_KUTTA_SHED, ns, 0.0, nullptr, sb, ew, s->f0hat, s->dgamma0, rhs);
+    if (ne > 0)
+        k_unit_vortex<<<dim3(ceil_div(ns, 128), ne), 128, 0, st>>>(vx, vy, ne, s->six, s->siy, s->swx, s->swy, ns,
+                                                                    p->G, p->nx, p->ny, p->x0, p->y0, p->dx, rhs + ns,
+                                                                    p->d_status);
+    k_indicators<<<dim3(ceil_div(ns, 256), nb), 256, 0, st>>>(ns, mb, rhs + (size_t)(1 + ne) * ns);
+    k_rows<0><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, rhs, nc, nullptr, y);
+    k_rows<1><<<rows_grid(ns, nc), 256, 0, st>>>(s->S, ns, y, nc, rhs, res);
+    k_rows<2><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, res, nc, nullptr, y);
+    k_constraints_multi<<<1, 256, 0, st>>>(ns, mb, ne, y, s->f0, s->ds, gw_dev, f, out, p->d_status);
+    PF_LAUNCH_CHECK(p);
+    *out_dev = out;
     return PF_OK;
 }
 
@@ -1228,49 +1285,20 @@ pf_status pf_sheet_solve_multi(pf_plan p, pf_schur s, const void* w, const pf_mu
                                const double* Ynew, double* f, double* gamma_new, double* s0) {
     if (!p || !w || !mb || !f) return PF_ERR_ARG;
     if (!s) return PF_ERR_NOT_FACTORED;
-    const int nb = mb->n_bodies, ns = s->ns;
-    if (nb < 1 || nb > PF_MAX_BODIES || mb->start[0] != 0 || mb->start[nb] != ns) return PF_ERR_ARG;
+    const int nb = mb->n_bodies;
     int ne = 0;
-    for (int b = 0; b < nb; ++b) {
-        if (mb->start[b + 1] <= mb->start[b] || mb->n_edges[b] < 0 || mb->n_edges[b] > 2) return PF_ERR_ARG;
-        for (int j = 0; j < mb->n_edges[b]; ++j)
-            if (mb->edge[b][j] < mb->start[b] || mb->edge[b][j] >= mb->start[b + 1]) return PF_ERR_ARG;
-        ne += mb->n_edges[b];
-    }
+    PF_TRY(multibody_check(*mb, s->ns, &ne));
     if (ne > 0 && (!Xnew || !Ynew)) return PF_ERR_ARG;
-    const int nc = 1 + ne + nb;
     cudaStream_t st = p->stream;
-    if (!s->mwork) {
-        PF_CUDA(p, cudaStreamSynchronize(st));
-        PF_CUDA(p, cudaMalloc(&s->mwork, ((2 + 3 * (size_t)MB_COLS) * ns + 8 * PF_MAX_BODIES) * sizeof(double)));
-    }
-    double* sb = s->mwork;
-    double* ew = sb + ns;
-    double* rhs = ew + ns;                       // rhs0 | E L^-1 d_i | 1_b
-    double* y = rhs + (size_t)MB_COLS * ns;
-    double* res = y + (size_t)MB_COLS * ns;
-    double* vx = res + (size_t)MB_COLS * ns;     // new vortices: x (up to 2 B), y (up to 2 B)
-    double* vy = vx + 2 * PF_MAX_BODIES;
-    double* out = vy + 2 * PF_MAX_BODIES;        // s0 (B), Gamma (E)
+    PF_TRY(multibody_scratch(p, s));
+    double* vx = multibody_newpos(s);
     if (ne > 0) {
         PF_CUDA(p, cudaMemcpyAsync(vx, Xnew, ne * sizeof(double), cudaMemcpyHostToDevice, st));
-        PF_CUDA(p, cudaMemcpyAsync(vy, Ynew, ne * sizeof(double), cudaMemcpyHostToDevice, st));
+        PF_CUDA(p, cudaMemcpyAsync(vx + MB_EDGES, Ynew, ne * sizeof(double), cudaMemcpyHostToDevice, st));
     }
-    k_sbprime_multi<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, *mb, sb);
-    PF_LAUNCH_CHECK(p);
-    PF_TRY(surface_rhs(p, s, w, ew));
-    k_rhs0<<<1, 256, 0, st>>>(PF_SHEET_KUTTA_SHED, ns, 0.0, nullptr, sb, ew, s->f0hat, s->dgamma0, rhs);
-    if (ne > 0)
-        k_unit_vortex<<<dim3(ceil_div(ns, 128), ne), 128, 0, st>>>(vx, vy, ne, s->six, s->siy, s->swx, s->swy, ns,
-                                                                    p->G, p->nx, p->ny, p->x0, p->y0, p->dx, rhs + ns,
-                                                                    p->d_status);
-    k_indicators<<<dim3(ceil_div(ns, 256), nb), 256, 0, st>>>(ns, *mb, rhs + (size_t)(1 + ne) * ns);
-    k_rows<0><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, rhs, nc, nullptr, y);
-    k_rows<1><<<rows_grid(ns, nc), 256, 0, st>>>(s->S, ns, y, nc, rhs, res);
-    k_rows<2><<<rows_grid(ns, nc), 256, 0, st>>>(s->Sinv, ns, res, nc, nullptr, y);
-    k_constraints_multi<<<1, 256, 0, st>>>(ns, *mb, ne, y, s->f0, s->ds, f, out, p->d_status);
-    PF_LAUNCH_CHECK(p);
-    double h[3 * PF_MAX_BODIES];
+    double* out = nullptr;
+    PF_TRY(sheet_solve_multi_device(p, s, w, *mb, ne, vx, vx + MB_EDGES, f, nullptr, &out));
+    double h[MB_N];
     int status = 0;
     PF_CUDA(p, cudaMemcpyAsync(h, out, (nb + ne) * sizeof(double), cudaMemcpyDeviceToHost, st));
     PF_CUDA(p, cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));

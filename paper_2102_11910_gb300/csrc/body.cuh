@@ -30,6 +30,15 @@ struct pf_schur_s {
 pf_status schur_create(pf_plan p, int ns, pf_schur* out);
 void schur_free(pf_schur s);
 pf_status schur_factor_device(pf_plan p, pf_schur s);
+// Several bodies (Sec. 2.7): validate a partition (and count its edges); the
+// device-level solve of pf_sheet_solve_multi with new vortices at device
+// (vx, vy) and, when gw_dev is not null, the bodies' gamma_w read from the
+// device; *out_dev receives the device address of s0 (B values) then the new
+// strengths (one per edge).
+pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total);
+pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
+                                   const double* vx, const double* vy, double* f, const double* gw_dev,
+                                   double** out_dev);
 // Generalized edge condition (Sec. 2.5) for the shedding mode: with on = 0 every
 // edge sheds under the Kutta condition; otherwise edge e sheds only when its
 // intermediate value lies outside [lo[e], hi[e]], and ends at the bound crossed.

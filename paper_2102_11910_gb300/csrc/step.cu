@@ -29,22 +29,26 @@ struct pf_state_s {
     pf_plan plan = nullptr;
     int64_t cap = 0, nv = 0;
     double t = 0.0;
-    int64_t last[2] = {-1, -1};     // index of the last vortex released at each edge
+    int64_t last[2 * PF_MAX_BODIES];   // index of the last vortex released at each edge (-1: none yet)
     double *X = nullptr, *Y = nullptr, *G = nullptr;
     double *Xs = nullptr, *Ys = nullptr;            // RK2 predictor positions
     void *u1 = nullptr, *v1 = nullptr, *u2 = nullptr, *v2 = nullptr;   // velocities (plan precision)
     double* f = nullptr;            // sheet strength
     double* red = nullptr;          // reduction scratch: [0] sum Gamma, [1] -sum Gamma, [2..] partials
-    double* newpos = nullptr;       // device x[2], y[2] of the vortices being released
+    double* newpos = nullptr;       // device x[MAX_EDGES], y[MAX_EDGES] of the vortices being released,
+                                    // then per body the released circulation and gamma_w
     // Schur factors of the two most recent poses, the current one first: an
     // RK2 step's second stage (t + dt) is the next step's first, so a moving
     // body is factored once per step
     struct Factor {
         pf_schur f = nullptr;
-        double alpha = NAN;
-        int ns = 0;
-        const double* xb = nullptr;   // body the factor belongs to
+        std::vector<double> alpha;              // pose of each body
+        std::vector<int> ns;
+        std::vector<const double*> xb;          // bodies the factor belongs to
     } fac[2];
+    pf_state_s() {
+        for (auto& l : last) l = -1;
+    }
 };
 
 
@@ -76,16 +80,20 @@ __global__ void k_sum_final(const double* __restrict__ part, int n, double* __re
     }
 }
 
+constexpr int MAX_EDGES = 2 * PF_MAX_BODIES;
+
 struct EdgeGeo {
-    double ex[2], ey[2];     // geometric edge points
-    double nx[2], ny[2];     // unit normal facing the free stream
-    double first_dist;       // 10 dt |U_inf|
-    long long last[2];
+    int n;                            // edges releasing a vortex
+    double ex[MAX_EDGES], ey[MAX_EDGES];   // geometric edge points
+    double nx[MAX_EDGES], ny[MAX_EDGES];   // unit normal facing the free stream
+    double first_dist;                // 10 dt |U_inf|
+    long long last[MAX_EDGES];
 };
 
+// release positions: out[k] = x, out[MAX_EDGES + k] = y of edge k's new vortex
 __global__ void k_place(const double* __restrict__ X, const double* __restrict__ Y, EdgeGeo e, double* __restrict__ out) {
     const int k = threadIdx.x;
-    if (k >= 2) return;
+    if (k >= e.n) return;
     double x, y;
     if (e.last[k] < 0) {
         x = e.ex[k] + e.first_dist * e.nx[k];
@@ -95,17 +103,38 @@ __global__ void k_place(const double* __restrict__ X, const double* __restrict__
         y = e.ey[k] + (Y[e.last[k]] - e.ey[k]) / 3.0;
     }
     out[k] = x;
-    out[2 + k] = y;
+    out[MAX_EDGES + k] = y;
 }
 
-// append the released vortices: positions from pos (x[2], y[2]), strengths scal[1..2]
+// append the n released vortices: positions from pos (as k_place), strengths gam[0..n)
 __global__ void k_append(double* __restrict__ X, double* __restrict__ Y, double* __restrict__ G, int64_t nv,
-                         const double* __restrict__ pos, const double* __restrict__ scal) {
+                         const double* __restrict__ pos, const double* __restrict__ gam, int n) {
     const int k = threadIdx.x;
-    if (k >= 2) return;
+    if (k >= n) return;
     X[nv + k] = pos[k];
-    Y[nv + k] = pos[2 + k];
-    G[nv + k] = scal[1 + k];
+    Y[nv + k] = pos[MAX_EDGES + k];
+    G[nv + k] = gam[k];
+}
+
+// several bodies: gamma_w of body b >= 1 is the circulation it released, body 0
+// takes the rest of the flow's (red[0] = sum Gamma)
+__global__ void k_gamma_w(const double* __restrict__ red, const double* __restrict__ rel, int nb,
+                          double* __restrict__ gw) {
+    if (threadIdx.x != 0) return;
+    double other = 0.0;
+    for (int b = 1; b < nb; ++b) {
+        other += rel[b];
+        gw[b] = rel[b];
+    }
+    gw[0] = red[0] - other;
+}
+
+// add each body's new strengths (gam, edges in body order) to its released circulation
+__global__ void k_released(const double* __restrict__ gam, pf_multibody mb, double* __restrict__ rel) {
+    if (threadIdx.x != 0) return;
+    int e = 0;
+    for (int b = 0; b < mb.n_bodies; ++b)
+        for (int j = 0; j < mb.n_edges[b]; ++j) rel[b] += gam[e++];
 }
 
 template <typename T>
@@ -166,35 +195,75 @@ Pose body_pose(const pf_body_kinematics& k, double t) {
     return P;
 }
 
+// the concatenated surface of one or several bodies at their poses
+struct Surface {
+    std::vector<double> x, y, ds;
+    std::vector<double> alpha;
+    std::vector<int> ns;
+    std::vector<const double*> xb;
+};
+
+Surface surface_of(const pf_body_kinematics* k, int nb, const std::vector<Pose>& P) {
+    Surface S;
+    for (int b = 0; b < nb; ++b) {
+        S.x.insert(S.x.end(), P[b].x.begin(), P[b].x.end());
+        S.y.insert(S.y.end(), P[b].y.begin(), P[b].y.end());
+        S.ds.insert(S.ds.end(), k[b].ds, k[b].ds + k[b].ns);
+        S.alpha.push_back(P[b].alpha);
+        S.ns.push_back(k[b].ns);
+        S.xb.push_back(k[b].xb);
+    }
+    return S;
+}
+
 // factor S at the pose, asynchronously (errors surface at pf_sync); the
-// previous factor is kept while body and angle are unchanged
-pf_status ensure_schur(pf_plan p, pf_state s, const pf_body_kinematics& k, const Pose& P) {
-    auto fits = [&](const pf_state_s::Factor& c) { return c.f && c.ns == k.ns && c.alpha == P.alpha && c.xb == k.xb; };
+// factors of the two latest poses are kept while the bodies are unchanged
+pf_status ensure_schur(pf_plan p, pf_state s, const Surface& B) {
+    auto fits = [&](const pf_state_s::Factor& c) { return c.f && c.alpha == B.alpha && c.ns == B.ns && c.xb == B.xb; };
     if (fits(s->fac[0])) return PF_OK;
     std::swap(s->fac[0], s->fac[1]);
     if (fits(s->fac[0])) return PF_OK;
     // refactor the older entry, now in front, at this pose
     pf_state_s::Factor& c = s->fac[0];
-    if (!c.f || c.ns != k.ns) {
+    const int ns = (int)B.x.size();
+    if (!c.f || c.f->ns != ns) {
         if (c.f) {
             PF_CUDA(p, cudaStreamSynchronize(p->stream));
             schur_free(c.f);
             c.f = nullptr;
         }
-        PF_TRY(schur_create(p, k.ns, &c.f));
+        PF_TRY(schur_create(p, ns, &c.f));
     }
-    c.ns = 0;                     // invalid until factored
-    c.xb = nullptr;
-    const size_t v = (size_t)k.ns * sizeof(double);
+    c.ns.clear();                 // invalid until factored
+    c.xb.clear();
+    const size_t v = (size_t)ns * sizeof(double);
     // pageable host sources: the copies complete before the calls return
-    PF_CUDA(p, cudaMemcpyAsync(c.f->x, P.x.data(), v, cudaMemcpyHostToDevice, p->stream));
-    PF_CUDA(p, cudaMemcpyAsync(c.f->y, P.y.data(), v, cudaMemcpyHostToDevice, p->stream));
-    PF_CUDA(p, cudaMemcpyAsync(c.f->ds, k.ds, v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(c.f->x, B.x.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(c.f->y, B.y.data(), v, cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(c.f->ds, B.ds.data(), v, cudaMemcpyHostToDevice, p->stream));
     PF_TRY(schur_factor_device(p, c.f));
-    c.ns = k.ns;
-    c.alpha = P.alpha;
-    c.xb = k.xb;
+    c.alpha = B.alpha;
+    c.ns = B.ns;
+    c.xb = B.xb;
     return PF_OK;
+}
+
+// geometric edge, unit normal facing the stream, and history of edge point kp
+// of a body whose world points are (x, y), n of them
+void edge_geometry(const std::vector<double>& x, const std::vector<double>& y, int off, int n, int kp, double Uinf,
+                   double Vinf, EdgeGeo& e, int j) {
+    // the neighbour along the surface away from the edge, on the same body
+    const int nb = kp == 0 ? 1 : (kp == n - 1 ? n - 2 : kp + 1);
+    const double tx = x[off + kp] - x[off + nb], ty = y[off + kp] - y[off + nb];
+    e.ex[j] = x[off + kp] + 0.5 * tx;
+    e.ey[j] = y[off + kp] + 0.5 * ty;
+    double nxv = -ty, nyv = tx;
+    const double nn = hypot(nxv, nyv);
+    nxv /= nn;
+    nyv /= nn;
+    if (nxv * Uinf + nyv * Vinf < 0.0) { nxv = -nxv; nyv = -nyv; }
+    e.nx[j] = nxv;
+    e.ny[j] = nyv;
 }
 
 pf_status sum_gamma(pf_plan p, pf_state s, int64_t n) {
@@ -217,34 +286,22 @@ pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, in
 // one stage with the body: shed (two-edge Kutta) or Kelvin-constrained
 pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double t, double dt, const double* X,
                      const double* Y, bool shed, void* u, void* v) {
-    const Pose P = body_pose(k, t);
-    PF_TRY(ensure_schur(p, s, k, P));
+    const std::vector<Pose> P{body_pose(k, t)};
+    PF_TRY(ensure_schur(p, s, surface_of(&k, 1, P)));
     pf_schur sch = s->fac[0].f;
-    const pf_motion m{0.0, 0.0, P.Omega, k.Uinf, k.Vinf};
-    const int ns = k.ns;
+    const pf_motion m{0.0, 0.0, P[0].Omega, k.Uinf, k.Vinf};
     int64_t n = s->nv;
     PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
     PF_TRY(sum_gamma(p, s, n));
     if (shed) {
         EdgeGeo e;
+        e.n = 2;
         const int kk[2] = {k.edge[0], k.edge[1]};
-        const double U = hypot(k.Uinf, k.Vinf);
         for (int j = 0; j < 2; ++j) {
-            // the neighbour along the surface away from the edge
-            const int kp = kk[j], nb = kp == 0 ? 1 : (kp == ns - 1 ? ns - 2 : kp + 1);
-            const double tx = P.x[kp] - P.x[nb], ty = P.y[kp] - P.y[nb];
-            e.ex[j] = P.x[kp] + 0.5 * tx;
-            e.ey[j] = P.y[kp] + 0.5 * ty;
-            double nxv = -ty, nyv = tx;
-            const double nn = hypot(nxv, nyv);
-            nxv /= nn;
-            nyv /= nn;
-            if (nxv * k.Uinf + nyv * k.Vinf < 0.0) { nxv = -nxv; nyv = -nyv; }
-            e.nx[j] = nxv;
-            e.ny[j] = nyv;
+            edge_geometry(P[0].x, P[0].y, 0, k.ns, kk[j], k.Uinf, k.Vinf, e, j);
             e.last[j] = s->last[j];
         }
-        e.first_dist = 10.0 * dt * U;
+        e.first_dist = 10.0 * dt * hypot(k.Uinf, k.Vinf);
         k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
         PF_LAUNCH_CHECK(p);
         EdgeBounds eb;
@@ -253,11 +310,12 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
             eb.lo[j] = k.edge_bounds[2 * j];
             eb.hi[j] = k.edge_bounds[2 * j + 1];
         }
-        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos, s->newpos + 2,
-                                  s->f, eb));
+        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos,
+                                  s->newpos + MAX_EDGES, s->f, eb));
         // release: the new vortices join the arrays X, Y (the caller's position
         // arrays) and G
-        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, sch->scal);
+        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos,
+                                          sch->scal + 1, 2);
         PF_LAUNCH_CHECK(p);
         n += 2;
     } else {
@@ -265,6 +323,52 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
                                   s->f));
     }
     return velocities(p, s, X, Y, n, sch, s->f, k.Uinf, k.Vinf, u, v);
+}
+
+// one stage with several bodies (Sec. 2.7): each edge releases a vortex under
+// the Kutta condition (shed), Kelvin per body; without shedding every body is
+// circulation-constrained
+pf_status bodies_stage(pf_plan p, pf_state s, const pf_body_kinematics* k, int nb, double t, double dt,
+                       const double* X, const double* Y, bool shed, void* u, void* v) {
+    std::vector<Pose> P;
+    for (int b = 0; b < nb; ++b) P.push_back(body_pose(k[b], t));
+    PF_TRY(ensure_schur(p, s, surface_of(k, nb, P)));
+    pf_schur sch = s->fac[0].f;
+    pf_multibody mb{};
+    mb.n_bodies = nb;
+    int ne = 0;
+    EdgeGeo e;
+    for (int b = 0; b < nb; ++b) {
+        mb.start[b + 1] = mb.start[b] + k[b].ns;
+        mb.n_edges[b] = shed ? k[b].n_edges : 0;
+        for (int j = 0; j < mb.n_edges[b]; ++j) {
+            mb.edge[b][j] = mb.start[b] + k[b].edge[j];
+            edge_geometry(P[b].x, P[b].y, 0, k[b].ns, k[b].edge[j], k[0].Uinf, k[0].Vinf, e, ne);
+            e.last[ne] = s->last[ne];
+            ++ne;
+        }
+        mb.motion[b] = pf_motion{0.0, 0.0, P[b].Omega, k[0].Uinf, k[0].Vinf};
+    }
+    e.n = ne;
+    e.first_dist = 10.0 * dt * hypot(k[0].Uinf, k[0].Vinf);
+    double* rel = s->newpos + 2 * MAX_EDGES;
+    double* gw = rel + PF_MAX_BODIES;
+    int64_t n = s->nv;
+    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
+    PF_TRY(sum_gamma(p, s, n));
+    k_gamma_w<<<1, 32, 0, p->stream>>>(s->red, rel, nb, gw);
+    if (ne > 0) k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
+    PF_LAUNCH_CHECK(p);
+    double* out = nullptr;
+    PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out));
+    if (ne > 0) {
+        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, out + nb,
+                                          ne);
+        k_released<<<1, 32, 0, p->stream>>>(out + nb, mb, rel);
+        PF_LAUNCH_CHECK(p);
+        n += ne;
+    }
+    return velocities(p, s, X, Y, n, sch, s->f, k[0].Uinf, k[0].Vinf, u, v);
 }
 
 }  // namespace
@@ -281,8 +385,10 @@ pf_status state_load_async(pf_state s, const double* X, const double* Y, const d
     }
     s->nv = nv;
     s->t = t;
-    s->last[0] = s->last[1] = -1;
-    s->fac[0].xb = s->fac[1].xb = nullptr;
+    for (auto& l : s->last) l = -1;
+    PF_CUDA(s->plan, cudaMemsetAsync(s->newpos + 2 * MAX_EDGES, 0, PF_MAX_BODIES * sizeof(double), s->plan->stream));
+    s->fac[0].xb.clear();
+    s->fac[1].xb.clear();
     return PF_OK;
 }
 
@@ -318,7 +424,9 @@ pf_status pf_state_create(pf_plan p, int64_t cap, pf_state* out) {
         if (err == cudaSuccess) err = cudaMalloc(q, e);
     if (err == cudaSuccess) err = cudaMalloc(&s->f, PF_MAX_SURFACE_POINTS * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&s->red, (2 + RED_BLOCKS) * sizeof(double));
-    if (err == cudaSuccess) err = cudaMalloc(&s->newpos, 4 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&s->newpos, (2 * MAX_EDGES + 2 * PF_MAX_BODIES) * sizeof(double));
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(s->newpos, 0, (2 * MAX_EDGES + 2 * PF_MAX_BODIES) * sizeof(double), p->stream);
     if (err != cudaSuccess) {
         snprintf(p->err, sizeof(p->err), "pf_state_create: %s", cudaGetErrorString(err));
         free_state(s);
@@ -350,8 +458,10 @@ pf_status pf_state_set(pf_state s, const double* X, const double* Y, const doubl
     PF_CUDA(p, cudaStreamSynchronize(p->stream));
     s->nv = nv;
     s->t = t;
-    s->last[0] = s->last[1] = -1;
-    s->fac[0].xb = s->fac[1].xb = nullptr;   // a new history may come with a new body
+    for (auto& l : s->last) l = -1;
+    PF_CUDA(s->plan, cudaMemsetAsync(s->newpos + 2 * MAX_EDGES, 0, PF_MAX_BODIES * sizeof(double), s->plan->stream));
+    s->fac[0].xb.clear();
+    s->fac[1].xb.clear();   // a new history may come with a new body
     return PF_OK;
 }
 
@@ -422,6 +532,45 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_body_kinematics* k, double dt,
         s->last[0] = n0;
         s->last[1] = n0 + 1;
     }
+    s->t += dt;
+    return PF_OK;
+}
+
+pf_status pf_step_multi(pf_plan p, pf_state s, int32_t n_bodies, const pf_body_kinematics* bodies, double dt,
+                        int32_t scheme) {
+    if (!p || !s || !bodies || n_bodies < 1 || n_bodies > PF_MAX_BODIES || !(dt > 0) || (scheme != 0 && scheme != 1))
+        return PF_ERR_ARG;
+    int ns = 0, ne = 0;
+    for (int b = 0; b < n_bodies; ++b) {
+        const pf_body_kinematics& k = bodies[b];
+        if (k.ns < 4 || !k.xb || !k.yb || !k.ds || k.n_edges < 0 || k.n_edges > 2 || k.edge_bounded) return PF_ERR_ARG;
+        for (int j = 0; j < k.n_edges; ++j)
+            if (k.edge[j] < 0 || k.edge[j] >= k.ns) return PF_ERR_ARG;
+        ns += k.ns;
+        ne += k.n_edges;
+    }
+    if (ns > PF_MAX_SURFACE_POINTS) return PF_ERR_ARG;
+    if (s->nv + ne > s->cap) return PF_ERR_CAPACITY;
+    const int64_t n0 = s->nv, n1 = n0 + ne;
+    const int nbk = nblocks(n1);
+    // stage 1 at t: one new vortex per edge (appended to X, Y, G), u1 at all n0 + ne
+    PF_TRY(bodies_stage(p, s, bodies, n_bodies, s->t, dt, s->X, s->Y, ne > 0, s->u1, s->v1));
+    s->nv = n1;
+    if (scheme == 0) {
+        if (p->prec == PF_FP64) k_euler<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt);
+        else k_euler<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt);
+        PF_LAUNCH_CHECK(p);
+    } else {
+        if (p->prec == PF_FP64) k_predict<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt, s->Xs, s->Ys);
+        else k_predict<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt, s->Xs, s->Ys);
+        PF_LAUNCH_CHECK(p);
+        // stage 2 at t + dt: strengths kept, every body circulation-constrained
+        PF_TRY(bodies_stage(p, s, bodies, n_bodies, s->t + dt, dt, s->Xs, s->Ys, false, s->u2, s->v2));
+        if (p->prec == PF_FP64) k_heun<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n1, dt);
+        else k_heun<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n1, dt);
+        PF_LAUNCH_CHECK(p);
+    }
+    for (int e = 0; e < ne; ++e) s->last[e] = n0 + e;
     s->t += dt;
     return PF_OK;
 }
