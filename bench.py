@@ -407,6 +407,22 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                          "mixed": _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, pw["dt"],
                                                                                             body, scheme=1), 8)}
         print("workload done: %s" % 'pitching_plate_768x512', file=sys.stderr, flush=True)
+        # two plates (Sec. 2.7, as the paper's two-plate example): chord 1 at 60 deg, c/2 apart
+        # vertically, dx = c/100, dS/dx = 2 (50 points each), dt U/c = 0.01, four releases per step
+        gtp = inputs.GridSpec(384, 256, 0.01, -1.0, -0.5 * 255 * 0.01)
+        plan = pf.Plan(gtp.nx, gtp.ny, gtp.dx, gtp.x0, gtp.y0, pf.PF_MIXED, stream=stream)
+        state = pf.State(plan, 4 * 40)
+        pf.pf_state_set(state, np.zeros(0), np.zeros(0), np.zeros(0))
+        tp = [inputs.plate(50, 1.0, math.radians(60.0), 0.0, yc) for yc in (0.25, -0.25)]
+        tpk = [pf.BodyKinematics(b.x, b.y, b.ds, b.edges, 0.0, Uinf=1.0) for b in tp]
+        for _ in range(5):
+            pf.pf_step_multi(plan, state, 0.01, tpk)
+        out["two_plates_384x256"] = {"unit": "steps/s", "desc": "two plates, chord 1 at 60 deg, c/2 apart, 384x256, "
+                                     "dx 0.01, Ns 2x50, Euler, dt 0.01, four vortices released per step "
+                                     "(Kutta at every edge, Kelvin per body; factor reused)",
+                                     "mixed": _steps_per_s(pf, plan, lambda: pf.pf_step_multi(plan, state, 0.01, tpk),
+                                                           20)}
+        print("workload done: %s" % 'two_plates_384x256', file=sys.stderr, flush=True)
         # uneven batch: independent instances, one step each per call
         inst = inputs.batched_instances(n=n_batch)
         res = {}

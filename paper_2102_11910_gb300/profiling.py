@@ -4,10 +4,11 @@ Usage:
   python -m paper_2102_11910_gb300.profiling launches launches.csv
       per kernel: launches, total device time and share, from an ncu CSV of
       gpu__time_duration.sum (one pass; cold-cache, serialised launches);
-  python -m paper_2102_11910_gb300.profiling traffic raw.csv
+  python -m paper_2102_11910_gb300.profiling traffic traffic.csv
       per step kernel: DRAM bytes read + written per launch, from
-      `ncu -i report --page raw --csv`, as the JSON that bench.py reads
-      (keyed by the source hash of csrc/, so a stale capture is ignored).
+      `ncu -i report --page raw --csv` or `ncu --metrics ... --csv`, as the
+      JSON that bench.py reads (keyed by the source hash of csrc/, so a stale
+      capture is ignored).
 """
 import collections
 import csv
@@ -77,20 +78,33 @@ def launches(path):
 
 
 def traffic(path):
-    rows = list(csv.reader(open(path)))
-    h, units, body = rows[0], rows[1], rows[2:]
-    ki = h.index("Kernel Name")
-    cols = {m: h.index(m) for m in ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum")}
+    """DRAM bytes per launch of each step kernel, from either CSV layout of
+    ncu: one column per metric (`ncu -i report --page raw --csv`) or one row
+    per metric (`ncu --metrics ... --csv`)."""
     unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    want = ("dram__bytes_read.sum", "dram__bytes_write.sum")
+    h, body = _rows(path)
+    ki = h.index("Kernel Name")
+    per_launch = collections.OrderedDict()         # (launch id, kernel) -> bytes
+    if "Metric Name" in h:
+        ii, ni, ui, vi = h.index("ID"), h.index("Metric Name"), h.index("Metric Unit"), h.index("Metric Value")
+        for r in body:
+            if len(r) <= vi or r[ni] not in want:
+                continue
+            name = STEP_KERNELS.get(kernel_name(r[ki]))
+            if name:
+                key = (r[ii], name)
+                per_launch[key] = per_launch.get(key, 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1.0)
+    else:
+        units, body = body[0], body[1:]
+        cols = {m: h.index(m) for m in want}
+        for n, r in enumerate(body):
+            name = STEP_KERNELS.get(kernel_name(r[ki]))
+            if name:
+                per_launch[(n, name)] = sum(float(r[cols[m]].replace(",", "")) * unit.get(units[cols[m]], 1.0)
+                                            for m in want)
     acc = collections.defaultdict(lambda: [0.0, 0])
-    for r in body:
-        name = STEP_KERNELS.get(kernel_name(r[ki]))
-        if not name:
-            continue
-        b = 0.0
-        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            i = cols[m]
-            b += float(r[i].replace(",", "")) * unit.get(units[i], 1.0)
+    for (_, name), b in per_launch.items():
         acc[name][0] += b
         acc[name][1] += 1
     out = {"csrc_sha": csrc_sha(), "source": os.path.basename(path),
