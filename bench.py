@@ -322,6 +322,39 @@ def bench_ours(args):
             extras["fp64_path"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64}
             extras["mixed_rel_err_vs_fp64_gpu"] = float(num / den)
             p64.close()
+        # the FFT convolution next to cuFFT (torch.fft; a timed comparison, not a product path):
+        # the same zero-padded P x Q real-to-complex transform of w, products with two spectra
+        # (u and v) and two complex-to-real inverses, FP32, L2 flushed between repetitions
+        with torch.cuda.stream(stream):
+            Pp, Qp = plan.P, plan.Q
+            gen = torch.Generator(device="cuda").manual_seed(5)
+            wpad = torch.zeros((Qp, Pp), dtype=torch.float32, device="cuda")
+            wpad[:g.ny, :g.nx] = torch.randn(g.ny, g.nx, device="cuda", generator=gen)
+            H1 = torch.randn(Qp, Pp // 2 + 1, dtype=torch.complex64, device="cuda", generator=gen)
+            H2 = torch.randn(Qp, Pp // 2 + 1, dtype=torch.complex64, device="cuda", generator=gen)
+
+            def cufft_conv():
+                Wh = torch.fft.rfft2(wpad)
+                return (torch.fft.irfft2(Wh * H1, s=(Qp, Pp))[:g.ny, :g.nx],
+                        torch.fft.irfft2(Wh * H2, s=(Qp, Pp))[:g.ny, :g.nx])
+            for _ in range(3):
+                cufft_conv()
+            tot = 0.0
+            for k in range(20):
+                flush.fill_(k & 255)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cufft_conv()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ours = sum(1e3 * kern[k]["avg_ms"] for k in ("fft_rows_fwd", "fft_cols_conv", "fft_rows_inv") if k in kern)
+            extras["fft_vs_cufft"] = {"ours_us": ours, "cufft_us": 1e3 * tot / 20, "grid": [Pp, Qp],
+                                      "desc": "u and v of the padded convolution: our three fused passes (sum of "
+                                              "their per-kernel event averages) against torch.fft rfft2, two "
+                                              "spectral products and two irfft2 (cuFFT)"}
+            del wpad, H1, H2
         if world == 1:
             try:
                 extras["workloads"] = bench_workloads(pf, inputs, torch, stream)

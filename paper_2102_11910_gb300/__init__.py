@@ -325,11 +325,11 @@ def pf_step_multi(plan, state, dt, bodies, scheme=0):
                   "pf_step_multi", plan.handle)
 
 
-PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT = 0, 1, 2
+PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT, PF_RHS_SPARSE = 0, 1, 2, 3
 
 
 def pf_plan_set_rhs_route(plan, route):
-    """Route of E_s L^-1 w in the sheet solves: PF_RHS_AUTO, PF_RHS_DIRECT or PF_RHS_FFT."""
+    """Route of E_s L^-1 w in the sheet solves: PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT or PF_RHS_SPARSE."""
     _native.check(_native.lib().pf_plan_set_rhs_route(plan.handle, int(route)), "pf_plan_set_rhs_route", plan.handle)
 
 

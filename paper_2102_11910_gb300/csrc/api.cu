@@ -22,7 +22,8 @@ void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
     void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->bin_off,
-                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->d_status, p->d_oob};
+                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->nz_idx, p->nz_val,
+                   p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);
     if (p->shared && --p->shared->refs == 0) {
@@ -209,7 +210,7 @@ pf_status pf_plan_destroy(pf_plan p) {
 }
 
 pf_status pf_plan_set_rhs_route(pf_plan p, int32_t route) {
-    if (!p || route < PF_RHS_AUTO || route > PF_RHS_FFT) return PF_ERR_ARG;
+    if (!p || route < PF_RHS_AUTO || route > PF_RHS_SPARSE) return PF_ERR_ARG;
     if (route == PF_RHS_FFT && (p->P < 256 || p->Q < 256)) return PF_ERR_ARG;
     p->rhs_route = route;
     return PF_OK;

@@ -64,23 +64,30 @@ __device__ __forceinline__ bool stencil(double x, double x0, double dx, int n, i
     return true;
 }
 
+// one thread per (point p, axis, node a): the FP64 smoothed-three-point weights
+// (square root and arcsine) run at the GPU's low FP64 rate, so they are spread
+// over many blocks; a point whose stencil leaves the grid on either axis gets
+// index 1 and weight 0 on both axes and raises the out-of-domain status
 __global__ void k_surface_stencil(const double* __restrict__ x, const double* __restrict__ y, int ns, double x0,
                                   double y0, double dx, int nx, int ny, int* __restrict__ six, int* __restrict__ siy,
                                   double* __restrict__ swx, double* __restrict__ swy, int* __restrict__ status) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= ns) return;
-    int ix[4], iy[4];
-    double wx[4], wy[4];
-    const bool ok = stencil(x[p], x0, dx, nx, ix, wx, true) && stencil(y[p], y0, dx, ny, iy, wy, true);
-    if (!ok) {
-        atomicOr(status, ST_OUT_OF_DOMAIN);
-        for (int a = 0; a < 4; ++a) { ix[a] = 1; iy[a] = 1; wx[a] = 0.0; wy[a] = 0.0; }
-    }
-    for (int a = 0; a < 4; ++a) {
-        six[4 * p + a] = ix[a];
-        siy[4 * p + a] = iy[a];
-        swx[4 * p + a] = wx[a];
-        swy[4 * p + a] = wy[a];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * ns) return;
+    const int p = t >> 3, axis = (t >> 2) & 1, a = t & 3;
+    const double gx = (x[p] - x0) / dx, gy = (y[p] - y0) / dx;
+    const double cx = floor(gx), cy = floor(gy);
+    const bool ok = cx >= 1.0 && cx <= nx - 3.0 && cy >= 1.0 && cy <= ny - 3.0;
+    if (!ok && t == 8 * p) atomicOr(status, ST_OUT_OF_DOMAIN);
+    const double g = axis ? gy : gx;
+    const int c = ok ? (int)(axis ? cy : cx) : 0;
+    const int idx = ok ? c - 1 + a : 1;
+    const double wt = ok ? yang3((double)(c - 1 + a) - g) : 0.0;
+    if (axis) {
+        siy[4 * p + a] = idx;
+        swy[4 * p + a] = wt;
+    } else {
+        six[4 * p + a] = idx;
+        swx[4 * p + a] = wt;
     }
 }
 
@@ -256,14 +263,12 @@ __global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* _
             }
         }
         __syncthreads();
-        // eliminate column c from the rows below it (only they are pivot candidates)
+        // eliminate column c from the rows below it (only they are pivot candidates):
+        // lane = column, warps over rows, one reciprocal of the pivot
         const float pv = sp[c * 33 + c];
-        const int w = kb - c - 1;
-        if (pv != 0.f && w > 0) {
-            for (int idx = tid; idx < (m - c - 1) * w; idx += blockDim.x) {
-                const int i = c + 1 + idx / w, j = c + 1 + idx - (idx / w) * w;
-                sp[i * 33 + j] -= sp[i * 33 + c] / pv * sp[c * 33 + j];
-            }
+        if (pv != 0.f && lane > c && lane < kb) {
+            const float q = sp[c * 33 + lane] / pv;
+            for (int i = c + 1 + wid; i < m; i += (int)(blockDim.x >> 5)) sp[i * 33 + lane] -= sp[i * 33 + c] * q;
         }
         __syncthreads();
     }
@@ -289,6 +294,7 @@ __global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* _
         __syncthreads();
     }
     if (mine) LU[i * BGJ_B + j] = A[i][j];
+    if (tid < kb) LU[BGJ_B * BGJ_B + tid] = 1.0 / (A[tid][tid] == 0.0 ? 1.0 : A[tid][tid]);
 }
 
 // One warp per column j < n (y_j, z_j) and per row r < n outside the panel
@@ -298,6 +304,7 @@ __global__ void __launch_bounds__(256) k_bgj_subst(const double* __restrict__ X,
                                                     double* __restrict__ Y, double* __restrict__ Z,
                                                     double* __restrict__ Lr) {
     __shared__ double F[BGJ_B][BGJ_B + 1];
+    __shared__ double rd[BGJ_B];                   // 1 / U_ll
     const int lane = threadIdx.x & 31;
     const int wg = blockIdx.x * 8 + (threadIdx.x >> 5);
     pdl_wait();
@@ -305,6 +312,7 @@ __global__ void __launch_bounds__(256) k_bgj_subst(const double* __restrict__ X,
         const int a = t >> 5, b = t & 31;
         F[a][b] = (a < kb && b < kb) ? LU[a * BGJ_B + b] : (a == b ? 1.0 : 0.0);
     }
+    if (threadIdx.x < BGJ_B) rd[threadIdx.x] = (int)threadIdx.x < kb ? LU[BGJ_B * BGJ_B + threadIdx.x] : 1.0;
     __syncthreads();
     const bool act = lane < kb;
     if (wg < n) {
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(256) k_bgj_subst(const double* __restrict__ X,
         }
         if (act) Y[(size_t)lane * n + j] = v;
         for (int l = kb - 1; l >= 0; --l) {       // z = U^-1 y
-            if (lane == l) v /= F[l][l];
+            if (lane == l) v *= rd[l];
             const double zl = __shfl_sync(0xffffffffu, v, l);
             if (lane < l) v -= F[lane][l] * zl;
         }
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(256) k_bgj_subst(const double* __restrict__ X,
         const int src = r < k0 ? r : perm[r];
         double v = act ? X[(size_t)src * n + k0 + lane] : 0.0;
         for (int l = 0; l < kb; ++l) {            // l_r U = x_r
-            if (lane == l) v /= F[l][l];
+            if (lane == l) v *= rd[l];
             const double al = __shfl_sync(0xffffffffu, v, l);
             if (lane > l) v -= al * F[l][lane];
         }
@@ -535,6 +543,102 @@ __global__ void __launch_bounds__(256) k_surface_einvlw(const T* __restrict__ w,
             s += wy[b] * r;
         }
         acc += wm * s;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[p] = dx2 * tot;
+}
+
+// Sparse route of the same sum for a field with few nonzero nodes: the
+// nonzero nodes are listed once, in node order (deterministic compaction in
+// two passes over fixed chunks), and every surface point sums over the list
+// only, 16 ns nnz multiply-adds instead of a scan of all nx ny nodes per point.
+constexpr int NZ_BLOCKS = 304;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_nz_count(const T* __restrict__ w, int M, int chunk, int* __restrict__ counts) {
+    __shared__ int sh[8];
+    const int lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
+    int c = 0;
+    for (int m = lo + threadIdx.x; m < hi; m += blockDim.x) c += w[m] != (T)0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        counts[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_nz_write(const T* __restrict__ w, int M, int chunk,
+                                                  const int* __restrict__ counts, int* __restrict__ idx,
+                                                  double* __restrict__ val, int* __restrict__ total) {
+    __shared__ int wsum[8];
+    __shared__ int base_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int i = 0; i < (int)blockIdx.x; ++i) b += counts[i];
+        base_s = b;
+        if (blockIdx.x == gridDim.x - 1) *total = b + counts[blockIdx.x];
+    }
+    __syncthreads();
+    int base = base_s;
+    const int lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
+    for (int m0 = lo; m0 < hi; m0 += blockDim.x) {
+        const int m = m0 + threadIdx.x;
+        const bool nz = m < hi && w[m] != (T)0;
+        const unsigned bal = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            before += i < wid ? wsum[i] : 0;
+            all += wsum[i];
+        }
+        if (nz) {
+            const int r = base + before + __popc(bal & ((1u << lane) - 1u));
+            idx[r] = m;
+            val[r] = (double)w[m];
+        }
+        base += all;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_surface_einvlw_sparse(const int* __restrict__ idx, const double* __restrict__ val,
+                                                               const int* __restrict__ total, int nx,
+                                                               const int* __restrict__ six, const int* __restrict__ siy,
+                                                               const double* __restrict__ swx,
+                                                               const double* __restrict__ swy,
+                                                               const double* __restrict__ G, double dx2,
+                                                               double* __restrict__ out) {
+    __shared__ double sh[256];
+    const int p = blockIdx.x;
+    int ix[4], iy[4];
+    double wx[4], wy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ix[a] = six[4 * p + a];
+        iy[a] = siy[4 * p + a];
+        wx[a] = swx[4 * p + a];
+        wy[a] = swy[4 * p + a];
+    }
+    const int n = *total;
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int m = idx[q];
+        const int i = m % nx, j = m / nx;
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            double r = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) r += wx[a] * lgf(G, nx, ix[a] - i, iy[b] - j);
+            s += wy[b] * r;
+        }
+        acc += val[q] * s;
     }
     const double tot = block_sum(acc, sh);
     if (threadIdx.x == 0) out[p] = dx2 * tot;
@@ -860,8 +964,8 @@ static void free_schur(pf_schur s) {
 pf_status schur_factor_device(pf_plan p, pf_schur s) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
-    k_surface_stencil<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
-                                                          s->siy, s->swx, s->swy, p->d_status);
+    k_surface_stencil<<<ceil_div(8 * ns, 32), 32, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
+                                                            s->siy, s->swx, s->swy, p->d_status);
     PF_LAUNCH_CHECK(p);
     if (s->snode) {
         int n2 = 1;
@@ -876,8 +980,8 @@ pf_status schur_factor_device(pf_plan p, pf_schur s) {
     PF_LAUNCH_CHECK(p);
     // pivots of magnitude 1e-300 or less are reported as singular
     if (ns <= BGJ_MAX) {
-        double* LU = s->gj;
-        double* Yk = LU + BGJ_B * BGJ_B;
+        double* LU = s->gj;                       // 32 x 32 factors, then 1 / U_ll
+        double* Yk = LU + BGJ_B * BGJ_B + BGJ_B;
         double* Zk = Yk + (size_t)BGJ_B * ns;
         double* Lr = Zk + (size_t)BGJ_B * ns;
         int* perm = (int*)(Lr + (size_t)BGJ_B * ns);
@@ -952,7 +1056,7 @@ pf_status schur_create(pf_plan p, int ns, pf_schur* out) {
     PF_ALLOC(s->f0hat, v);
     PF_ALLOC(s->dgamma0, sizeof(double));
     if (ns <= BGJ_MAX)
-        PF_ALLOC(s->gj, (BGJ_B * BGJ_B + 3 * (size_t)BGJ_B * ns) * sizeof(double) + 2 * (size_t)ns * sizeof(int));
+        PF_ALLOC(s->gj, (BGJ_B * BGJ_B + BGJ_B + 3 * (size_t)BGJ_B * ns) * sizeof(double) + 2 * (size_t)ns * sizeof(int));
     if (ns <= SHEET_SORT_MAX) {
         PF_ALLOC(s->sorder, 16 * (size_t)ns * sizeof(int));
         PF_ALLOC(s->snode, 16 * (size_t)ns * sizeof(int));
@@ -976,11 +1080,37 @@ void schur_free(pf_schur s) {
 // multiply-adds at the GPU's low FP64 rate; on larger grids the same quantity
 // comes from an FP64 FFT solve psi = -L^-1 w (FP64 rounding, far below what
 // the ill-conditioned S amplifies into the sheet) read at the stencils.
-pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew) {
+pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t nnz_bound) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     const int64_t M = (int64_t)p->nx * p->ny;
     const bool fft_ok = p->P >= 256 && p->Q >= 256;
+    // the sparse route when the caller bounds the nonzero nodes and the sum is small
+    const bool sparse = p->rhs_route == PF_RHS_SPARSE ||
+                        (p->rhs_route == PF_RHS_AUTO && nnz_bound >= 0 && 16 * (int64_t)ns * nnz_bound < ((int64_t)1 << 24));
+    if (sparse) {
+        if (!p->nz_idx) {
+            PF_CUDA(p, cudaStreamSynchronize(st));
+            PF_CUDA(p, cudaMalloc(&p->nz_idx, (size_t)M * sizeof(int) + (NZ_BLOCKS + 1) * sizeof(int)));
+            PF_CUDA(p, cudaMalloc(&p->nz_val, (size_t)M * sizeof(double)));
+        }
+        int* counts = p->nz_idx + M;
+        int* total = counts + NZ_BLOCKS;
+        const int chunk = ceil_div(M, NZ_BLOCKS);
+        if (p->prec == PF_FP64) {
+            k_nz_count<double><<<NZ_BLOCKS, 256, 0, st>>>((const double*)w, (int)M, chunk, counts);
+            k_nz_write<double><<<NZ_BLOCKS, 256, 0, st>>>((const double*)w, (int)M, chunk, counts, p->nz_idx, p->nz_val,
+                                                          total);
+        } else {
+            k_nz_count<float><<<NZ_BLOCKS, 256, 0, st>>>((const float*)w, (int)M, chunk, counts);
+            k_nz_write<float><<<NZ_BLOCKS, 256, 0, st>>>((const float*)w, (int)M, chunk, counts, p->nz_idx, p->nz_val,
+                                                         total);
+        }
+        k_surface_einvlw_sparse<<<ns, 256, 0, st>>>(p->nz_idx, p->nz_val, total, p->nx, s->six, s->siy, s->swx, s->swy,
+                                                    p->G, p->dx * p->dx, ew);
+        PF_LAUNCH_CHECK(p);
+        return PF_OK;
+    }
     const bool fft = fft_ok && (p->rhs_route == PF_RHS_FFT ||
                                 (p->rhs_route == PF_RHS_AUTO && (int64_t)ns * M > ((int64_t)1 << 22)));
     if (!fft) {
@@ -1112,7 +1242,7 @@ __global__ void __launch_bounds__(256) k_constraints_multi(int ns, pf_multibody 
 
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
-                             const double* vy, double* f, const EdgeBounds& eb) {
+                             const double* vy, double* f, const EdgeBounds& eb, int64_t nnz_bound) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     double* sb = s->work;
@@ -1122,7 +1252,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     double* res = y + 3 * ns;       // refinement residuals
     k_sbprime<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, m, sb);
     PF_LAUNCH_CHECK(p);
-    PF_TRY(surface_rhs(p, s, w, ew));
+    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound));
     k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, param_dev, sb, ew, s->f0hat, s->dgamma0, rhs);
     PF_LAUNCH_CHECK(p);
     int nc = 1;
@@ -1170,7 +1300,7 @@ double* multibody_newpos(pf_schur s) { return s->mwork + (2 + 3 * (size_t)MB_COL
 
 pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
                                    const double* vx, const double* vy, double* f, const double* gw_dev,
-                                   double** out_dev) {
+                                   double** out_dev, int64_t nnz_bound) {
     const int nb = mb.n_bodies, ns = s->ns, nc = 1 + ne + nb;
     cudaStream_t st = p->stream;
     PF_TRY(multibody_scratch(p, s));
@@ -1182,7 +1312,7 @@ pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const p
     double* out = multibody_newpos(s) + 2 * MB_EDGES;   // s0 (B), Gamma (E)
     k_sbprime_multi<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, mb, sb);
     PF_LAUNCH_CHECK(p);
-    PF_TRY(surface_rhs(p, s, w, ew));
+    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound));
     k_rhs0<<<1, 256, 0, st>>>(PF_SHEET_KUTTA_SHED, ns, 0.0, nullptr, sb, ew, s->f0hat, s->dgamma0, rhs);
     if (ne > 0)
         k_unit_vortex<<<dim3(ceil_div(ns, 128), ne), 128, 0, st>>>(vx, vy, ne, s->six, s->siy, s->swx, s->swy, ns,

@@ -38,7 +38,7 @@ pf_status schur_factor_device(pf_plan p, pf_schur s);
 pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total);
 pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
                                    const double* vx, const double* vy, double* f, const double* gw_dev,
-                                   double** out_dev);
+                                   double** out_dev, int64_t nnz_bound = -1);
 // Generalized edge condition (Sec. 2.5) for the shedding mode: with on = 0 every
 // edge sheds under the Kutta condition; otherwise edge e sheds only when its
 // intermediate value lies outside [lo[e], hi[e]], and ends at the bound crossed.
@@ -47,10 +47,13 @@ struct EdgeBounds {
     double lo[2] = {0.0, 0.0};
     double hi[2] = {0.0, 0.0};
 };
-// param_dev (nullable): device copy of `param` read by the kernels instead
+// param_dev (nullable): device copy of `param` read by the kernels instead;
+// nnz_bound >= 0: at most that many nodes of w are nonzero (lets the surface
+// right-hand side take the sparse route), -1: unknown
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
-                             const double* vy, double* f, const EdgeBounds& eb = EdgeBounds());
+                             const double* vy, double* f, const EdgeBounds& eb = EdgeBounds(),
+                             int64_t nnz_bound = -1);
 // w += R_s f  (device f of ns doubles, w real[nx*ny])
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);
 

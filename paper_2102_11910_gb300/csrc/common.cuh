@@ -123,6 +123,10 @@ struct pf_plan_s {
     // lazily allocated FP64 buffers: w, psi (nx*ny each), two spectra
     int rhs_route = 0;
     void* rhs64 = nullptr;
+    // sparse route: the nonzero nodes of w (index, FP64 value; nx*ny each), then
+    // the per-chunk counts and the total (allocated by the first sparse solve)
+    int* nz_idx = nullptr;
+    double* nz_val = nullptr;
     // diagnostics scratch (per-block partial sums and results)
     double* diag = nullptr;            // PF_DIAG_DOUBLES
     // status

@@ -81,7 +81,8 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
     const int64_t M = (int64_t)s.nx * s.ny;
     const int Q = 1 << (32 - __builtin_clz(2 * s.ny - 1));
     const bool fft = P >= 256 && Q >= 256 && (int64_t)ns * M > ((int64_t)1 << 22);
-    const int64_t rhs = (fft && prec != PF_FP64) ? 2 * M * 8 + 2 * (int64_t)ldK * ldT * 16 : 0;
+    const int64_t rhs = ((fft && prec != PF_FP64) ? 2 * M * 8 + 2 * (int64_t)ldK * ldT * 16 : 0) +
+                        M * 12;    // node list of the sparse route
     return grid + bins + state + schur + rhs;
 }
 

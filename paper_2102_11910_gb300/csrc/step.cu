@@ -311,7 +311,7 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
             eb.hi[j] = k.edge_bounds[2 * j + 1];
         }
         PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos,
-                                  s->newpos + MAX_EDGES, s->f, eb));
+                                  s->newpos + MAX_EDGES, s->f, eb, 16 * n));
         // release: the new vortices join the arrays X, Y (the caller's position
         // arrays) and G
         k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos,
@@ -320,7 +320,7 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
         n += 2;
     } else {
         PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_CIRCULATION, 0.0, s->red + 1, 0, nullptr, nullptr, nullptr,
-                                  s->f));
+                                  s->f, EdgeBounds(), 16 * n));
     }
     return velocities(p, s, X, Y, n, sch, s->f, k.Uinf, k.Vinf, u, v);
 }
@@ -360,7 +360,7 @@ pf_status bodies_stage(pf_plan p, pf_state s, const pf_body_kinematics* k, int n
     if (ne > 0) k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
     PF_LAUNCH_CHECK(p);
     double* out = nullptr;
-    PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out));
+    PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out, 16 * n));
     if (ne > 0) {
         k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, out + nb,
                                           ne);

@@ -152,11 +152,14 @@ def test_out_of_grid_body_is_rejected():
     assert e.value.name == "PF_ERR_OUT_OF_DOMAIN"
 
 
+@pytest.mark.parametrize("route", [pf.PF_RHS_FFT, pf.PF_RHS_SPARSE])
 @pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
-def test_fft_route_of_the_surface_rhs_matches_the_direct_sum(prec):
-    """E_s L^-1 w from an FP64 FFT solve (the route large grids take) against the
-    direct FP64 LGF sum (the route pinned to the oracle above): same vorticity,
-    same factor; they differ by FP64 rounding amplified by cond(S)."""
+def test_fft_and_sparse_routes_of_the_surface_rhs_match_the_direct_sum(prec, route):
+    """E_s L^-1 w from an FP64 FFT solve (the route large grids take) or from the
+    list of nonzero nodes (the route time stepping takes with few vortices)
+    against the direct FP64 LGF sum over all nodes (the route pinned to the
+    oracle above): same vorticity, same factor; they differ by FP64 rounding
+    amplified by cond(S)."""
     n, dx = 256, 2.0 / 255
     g = inputs.centred_grid(n, n, dx)
     b = inputs.plate(96, 1.0, 0.35)                   # dS/dx = 1.33
@@ -165,9 +168,9 @@ def test_fft_route_of_the_surface_rhs_matches_the_direct_sum(prec):
     keep = np.hypot(X, Y) > 0.6
     X, Y, G = X[keep], Y[keep], G[keep]
     out = {}
-    for route in (pf.PF_RHS_DIRECT, pf.PF_RHS_FFT):
+    for r in (pf.PF_RHS_DIRECT, route):
         plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec)
-        pf.pf_plan_set_rhs_route(plan, route)
+        pf.pf_plan_set_rhs_route(plan, r)
         schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)
         w = pf.pf_regularize(plan, *(torch.from_numpy(a).cuda() for a in (X, Y, G)))
         Gw = float(G.sum())
@@ -175,8 +178,8 @@ def test_fft_route_of_the_surface_rhs_matches_the_direct_sum(prec):
                                       list(b.edges), np.array([b.x[0] - 0.02, b.x[-1] + 0.02]),
                                       np.array([b.y[0] + 0.01, b.y[-1] - 0.01]))
         _, _, S = pf.pf_schur_info(schur)
-        out[route] = (f.cpu().numpy(), np.array(gn), np.linalg.cond(S))
+        out[r] = (f.cpu().numpy(), np.array(gn), np.linalg.cond(S))
     fd, gd, cond = out[pf.PF_RHS_DIRECT]
-    ff, gf, _ = out[pf.PF_RHS_FFT]
+    ff, gf, _ = out[route]
     tol = cond * 1e-14
     assert rel(ff, fd) < tol and rel(gf, gd) < tol
