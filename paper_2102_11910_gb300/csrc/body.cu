@@ -92,24 +92,56 @@ __global__ void k_surface_stencil(const double* __restrict__ x, const double* __
 }
 
 // S[p, q] = -dS_q sum_{a,b,a',b'} wx_p[a] wy_p[b] G(ix_p[a]-ix_q[a'], iy_p[b]-iy_q[b']) wx_q[a'] wy_q[b']
+// A stencil's nodes are consecutive (ix_p[a] = ix_p[0] + a), so the node
+// offsets are ix_p[0] - ix_q[0] + d, d = a - a' in -3..3, and the sum is
+// sum_{d,e} cx[d] cy[e] G(...) with cx[d] = sum_{a-a'=d} wx_p[a] wx_q[a'] (and
+// cy alike): 49 table reads instead of 256.  (A point outside the grid has
+// zero weights, so its placeholder indices contribute nothing.)  The kernel
+// K = S / dS_q is symmetric: the thread of (p, q >= p) writes both entries.
+__device__ __forceinline__ double stencil_pair_lgf(const int* __restrict__ six, const int* __restrict__ siy,
+                                                   const double* __restrict__ swx, const double* __restrict__ swy,
+                                                   int p, const int* ixq, const int* iyq, const double* wxq,
+                                                   const double* wyq, const double* __restrict__ G, int nx) {
+    double cx[7], cy[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) cx[d] = cy[d] = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) {
+            cx[a - a2 + 3] += swx[4 * p + a] * wxq[a2];
+            cy[a - a2 + 3] += swy[4 * p + a] * wyq[a2];
+        }
+    const int bi = six[4 * p] - ixq[0] - 3, bj = siy[4 * p] - iyq[0] - 3;
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < 7; ++e) {
+        double r = 0.0;
+#pragma unroll
+        for (int d = 0; d < 7; ++d) r += cx[d] * lgf(G, nx, bi + d, bj + e);
+        acc += cy[e] * r;
+    }
+    return acc;
+}
+
 __global__ void k_schur_build(const int* __restrict__ six, const int* __restrict__ siy, const double* __restrict__ swx,
                               const double* __restrict__ swy, const double* __restrict__ ds, int ns,
                               const double* __restrict__ G, int nx, double* __restrict__ A, int lda) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = blockIdx.y;
-    if (q >= ns) return;
-    double acc = 0.0;
-    for (int b = 0; b < 4; ++b)
-        for (int a = 0; a < 4; ++a) {
-            const double wp = swx[4 * p + a] * swy[4 * p + b];
-            const int ip = six[4 * p + a], jp = siy[4 * p + b];
-            double s = 0.0;
-            for (int b2 = 0; b2 < 4; ++b2)
-                for (int a2 = 0; a2 < 4; ++a2)
-                    s += lgf(G, nx, ip - six[4 * q + a2], jp - siy[4 * q + b2]) * swx[4 * q + a2] * swy[4 * q + b2];
-            acc += wp * s;
-        }
-    A[(size_t)p * lda + q] = -ds[q] * acc;
+    if (q >= ns || q < p) return;
+    int ixq[4], iyq[4];
+    double wxq[4], wyq[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ixq[a] = six[4 * q + a];
+        iyq[a] = siy[4 * q + a];
+        wxq[a] = swx[4 * q + a];
+        wyq[a] = swy[4 * q + a];
+    }
+    const double k = stencil_pair_lgf(six, siy, swx, swy, p, ixq, iyq, wxq, wyq, G, nx);
+    A[(size_t)p * lda + q] = -ds[q] * k;
+    if (q != p) A[(size_t)q * lda + p] = -ds[p] * k;
 }
 
 // augmented [S | I] for Gauss-Jordan
@@ -279,22 +311,28 @@ __global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* _
     }
     __syncthreads();
     for (int i = tid; i < m; i += blockDim.x) gperm[k0 + i] = gp[i];
-    // FP64 LU of the permuted pivot block, one entry per thread
-    const int i = tid >> 5, j = tid & 31;
+    // FP64 LU of the permuted pivot block, one entry per thread; lanes run down a
+    // column (warp j holds column j), and one thread forms each pivot's
+    // reciprocal: FP64 division is a long sequence at this GPU's FP64 rate
+    __shared__ double rpiv[BGJ_B];
+    const int i = tid & 31, j = tid >> 5;
     const bool mine = i < kb && j < kb;
     if (mine) A[i][j] = X[(size_t)(k0 + rowid[i]) * n + k0 + j];
     __syncthreads();
     for (int c = 0; c < kb; ++c) {
-        const double pv = A[c][c];
-        if (tid == 0 && !(fabs(pv) > tiny)) atomicOr(status, ST_SINGULAR);
-        const double d = pv == 0.0 ? 1.0 : pv;
-        if (mine && i > c && j == c) A[i][c] /= d;
+        if (tid == 0) {
+            const double pv = A[c][c];
+            if (!(fabs(pv) > tiny)) atomicOr(status, ST_SINGULAR);
+            rpiv[c] = 1.0 / (pv == 0.0 ? 1.0 : pv);
+        }
+        __syncthreads();
+        if (mine && i > c && j == c) A[i][c] *= rpiv[c];
         __syncthreads();
         if (mine && i > c && j > c) A[i][j] -= A[i][c] * A[c][j];
         __syncthreads();
     }
     if (mine) LU[i * BGJ_B + j] = A[i][j];
-    if (tid < kb) LU[BGJ_B * BGJ_B + tid] = 1.0 / (A[tid][tid] == 0.0 ? 1.0 : A[tid][tid]);
+    if (tid < kb) LU[BGJ_B * BGJ_B + tid] = rpiv[tid];
 }
 
 // One warp per column j < n (y_j, z_j) and per row r < n outside the panel
@@ -709,17 +747,8 @@ __global__ void k_unit_vortex(const double* __restrict__ vx, const double* __res
         out[(size_t)j * ns + p] = 0.0;
         return;
     }
-    // L^-1 d_j = dx^2 G * (dx^-2 M4' M4'): the dx factors cancel
-    double acc = 0.0;
-    for (int b = 0; b < 4; ++b)
-        for (int a = 0; a < 4; ++a) {
-            const double wp = swx[4 * p + a] * swy[4 * p + b];
-            double s = 0.0;
-            for (int b2 = 0; b2 < 4; ++b2)
-                for (int a2 = 0; a2 < 4; ++a2)
-                    s += lgf(G, nx, six[4 * p + a] - vix[a2], siy[4 * p + b] - viy[b2]) * vwx[a2] * vwy[b2];
-            acc += wp * s;
-        }
+    // L^-1 d_j = dx^2 G * (dx^-2 M4' M4'): the dx factors cancel; separable sum as k_schur_build
+    const double acc = stencil_pair_lgf(six, siy, swx, swy, p, vix, viy, vwx, vwy, G, nx);
     out[(size_t)j * ns + p] = acc;
 }
 
