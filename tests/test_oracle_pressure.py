@@ -1,0 +1,91 @@
+"""Pins of the oracle's surface pressure (Sec. 2.6.1) against closed-form
+potential flows about a circular cylinder, at the first-order accuracy of the
+immersed-boundary discretisation, and against the operator properties the
+paper states."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import body as B
+from oracle import pressure as P
+from oracle import vic
+from oracle.lgf import lgf_table
+from paper_2102_11910_gb300 import inputs
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def cyl():
+    R, dx = 1.0, 0.05
+    ns = int(round(2 * math.pi * R / dx))                # dS/dx = 1 (a denser surface keeps the double layer from leaking)
+    n = int(3.4 * R / dx) + 8
+    gs = inputs.centred_grid(n, n, dx)
+    g = vic.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    b = inputs.circle(ns, R)
+    tab = lgf_table(n + 1, n + 1)
+    st = B.SurfaceStencil(g, b.x, b.y)
+    sch = B.Schur(B.schur_matrix(g, st, b.ds, tab), b.ds)
+    th = 2 * math.pi * np.arange(ns) / ns
+    nxs, nys = np.cos(th), np.sin(th)                    # outward normals
+    cw = P.curl_weights(g, b.x, b.y, nxs, nys)
+    return dict(R=R, g=g, b=b, tab=tab, st=st, sch=sch, th=th, nxs=nxs, nys=nys, cw=cw)
+
+
+def test_jump_operator_is_symmetric_semidefinite(cyl):
+    """-C_s L^-1 C_s^T is symmetric (in the dS inner product) and positive
+    semi-definite, with the uniform vector (nearly) its null space."""
+    c = cyl
+    K = P.jump_matrix(c["g"], c["cw"], c["b"].ds, c["tab"])
+    M = K / c["b"].ds[None, :]
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(M).max()
+    ev, vec = np.linalg.eigh(-0.5 * (M + M.T))
+    assert ev[0] > -1e-10 * ev[-1]
+    # the null direction the paper names: uniform values (here to the first-order
+    # accuracy of the regularised surface), well separated from the rest
+    assert ev[0] < 0.1 * ev[1]
+    v0 = vec[:, 0]
+    assert abs(v0.sum()) / (math.sqrt(len(v0)) * np.linalg.norm(v0)) > 0.999
+    assert np.abs(K @ np.ones(len(K))).max() < 2e-2 * np.abs(K).max()
+
+
+def test_potential_jump_of_a_cylinder_in_uniform_flow(cyl):
+    """gamma = -2 U sin(theta) outside a cylinder at rest; the potential jumps by
+    phi+ - phi- = 2 U R cos(theta) (+ a constant) across the surface."""
+    c = cyl
+    b = c["b"]
+    f, _ = B.sheet_circulation(c["sch"], B.sb_prime(b.x, b.y, 0, 0, 0, 1.0, 0), np.zeros(len(b.x)), 0.0)
+    dphi = P.potential_jump(c["g"], c["st"], c["cw"], b.ds, f, c["tab"])
+    assert abs(np.dot(b.ds, dphi)) < 1e-10
+    assert _rel(dphi, 2 * c["R"] * np.cos(c["th"])) < 0.05
+
+
+def test_steady_pressure_jump_of_a_cylinder(cyl):
+    """Steady Bernoulli across the sheet: p+ - p- = -2 rho U^2 sin^2(theta)
+    (exterior speed 2 U sin(theta), fluid at rest inside)."""
+    c = cyl
+    g, b = c["g"], c["b"]
+    f, _ = B.sheet_circulation(c["sch"], B.sb_prime(b.x, b.y, 0, 0, 0, 1.0, 0), np.zeros(len(b.x)), 0.0)
+    psi = vic.streamfunction(g, B.regularize_surface(g, c["st"], f, b.ds), c["tab"], pad=1)
+    us, vs = P.face_velocity_at_surface(g, b.x, b.y, psi, 1.0, 0.0)
+    dp = P.pressure_jump(us, vs, b.x, b.y, c["nxs"], c["nys"], f, 0, 0, 0, np.zeros(len(b.x)), rho=1.3)
+    assert _rel(dp, -2 * 1.3 * np.sin(c["th"]) ** 2) < 0.06
+
+
+def test_accelerating_cylinder_pressure_jump(cyl):
+    """A cylinder starting from rest with acceleration a: gamma = 2 U sin(theta)
+    at speed U, Delta phi = -2 U R cos(theta), so at t = 0 (U = 0)
+    Delta p = -rho d(Delta phi)/dt = 2 rho a R cos(theta); the sheet and the
+    jump are linear in U, so a one-sided difference over dt is exact."""
+    c = cyl
+    b = c["b"]
+    a, dt = 0.7, 1e-3
+    f1, _ = B.sheet_circulation(c["sch"], B.sb_prime(b.x, b.y, a * dt, 0, 0, 0, 0), np.zeros(len(b.x)), 0.0)
+    d1 = P.potential_jump(c["g"], c["st"], c["cw"], b.ds, f1, c["tab"])
+    dp = P.pressure_jump(np.zeros(len(b.x)), np.zeros(len(b.x)), b.x, b.y, c["nxs"], c["nys"], np.zeros(len(b.x)),
+                         0, 0, 0, d1 / dt, rho=1.0)
+    assert _rel(d1 / dt, -2 * a * c["R"] * np.cos(c["th"])) < 0.05
+    assert _rel(dp, 2 * a * c["R"] * np.cos(c["th"])) < 0.05
