@@ -287,6 +287,45 @@ typedef struct {
 pf_status pf_sheet_solve_multi(pf_plan plan, pf_schur schur, const void* w, const pf_multibody* mb,
                                const double* Xnew, const double* Ynew, double* f, double* gamma_new, double* s0);
 
+/* w += R_s f (device f of ns doubles, w real[nx*ny] of the plan's precision):
+ * the bound sheet regularized onto the nodes (Sec. 2.2.1), as the steps add it
+ * before the corrected solve; deterministic. */
+pf_status pf_sheet_regularize(pf_plan plan, pf_schur schur, const double* f, void* w);
+
+/* ------------------------------------------------------- surface pressure */
+
+/* Surface pressure (Sec. 2.6.1).  The grid is staggered: u = d psi/dy on the
+ * x-faces (x_i, y_j + dx/2), v = -d psi/dx on the y-faces (x_i + dx/2, y_j); E_f
+ * interpolates each component from its own faces with the smoothed
+ * three-point function, and C_s psi = n . E_f C psi is the normal velocity at
+ * the surface points.
+ *
+ * pf_pressure_setup: unit normals of the factor's surface points (HOST, ns
+ * each; + side of the jumps) and the factor of the jump operator
+ * C_s L^-1 C_s^T, augmented with the gauge sum_p dS_p Delta phi_p = 0 (its
+ * null space is the uniform values); once per geometry.  The regularized
+ * double layer needs dS/dx ~ 1: at dS/dx = 2 it leaks and the jump of a
+ * cylinder in a uniform stream comes out a third too small.  Synchronises.
+ *
+ * pf_potential_jump: Delta phi = -(C_s L^-1 C_s^T)^-1 C_s L^-1 R_s f (the jump
+ * in scalar potential of the sheet, Eq. gamphi and below), f and dphi device,
+ * ns doubles; FP64, with one refinement step.
+ *
+ * pf_pressure_jump: Eq. surfbernoulli,
+ *   Delta p = -rho (E_f u - v_s) . (f z x n) - rho d(Delta phi)/dt,
+ * with u from psi (device, real[nx*ny] in the plan's precision: the
+ * streamfunction of the whole flow without the free stream, e.g.
+ * pf_poisson_solve of w + R_s f + new vortices) plus (m->Uinf, m->Vinf), the
+ * rigid surface velocity v_s = (U - Omega y, V + Omega x) of *m, f (device),
+ * dphi_dt (device, ns, e.g. the difference of two pf_potential_jump results
+ * over a step; NULL: steady) and the density rho; dp: device, ns doubles.
+ * The surface pressures are p+/- = E_c p +/- Delta p / 2.
+ * PF_ERR_NOT_FACTORED before pf_pressure_setup. */
+pf_status pf_pressure_setup(pf_plan plan, pf_schur schur, const double* nxs, const double* nys);
+pf_status pf_potential_jump(pf_plan plan, pf_schur schur, const double* f, double* dphi);
+pf_status pf_pressure_jump(pf_plan plan, pf_schur schur, const void* psi, const pf_motion* m, const double* f,
+                           const double* dphi_dt, double rho, double* dp);
+
 /* ------------------------------------------------------- time stepping */
 
 /* Device-resident vortex set (positions and strengths, FP64) with a fixed

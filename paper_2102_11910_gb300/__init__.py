@@ -325,6 +325,41 @@ def pf_step_multi(plan, state, dt, bodies, scheme=0):
                   "pf_step_multi", plan.handle)
 
 
+def pf_sheet_regularize(plan, schur, f, w):
+    """w += R_s f in place (device tensors: f float64 of ns, w of the plan's precision)."""
+    _native.check(_native.lib().pf_sheet_regularize(plan.handle, schur.handle, _ptr(f, torch.float64, "f"),
+                                                    _ptr(w, plan.dtype, "w")), "pf_sheet_regularize", plan.handle)
+    return w
+
+
+def pf_pressure_setup(plan, schur, nx, ny):
+    """Unit surface normals (host arrays) and the factor of the jump operator (Sec. 2.6.1)."""
+    nx, ny = _host_f64(nx), _host_f64(ny)
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_pressure_setup(plan.handle, schur.handle, c(nx.ctypes.data), c(ny.ctypes.data)),
+                  "pf_pressure_setup", plan.handle)
+
+
+def pf_potential_jump(plan, schur, f, dphi=None):
+    """Delta phi of the sheet f (device float64 tensors)."""
+    dphi = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if dphi is None else dphi
+    _native.check(_native.lib().pf_potential_jump(plan.handle, schur.handle, _ptr(f, torch.float64, "f"),
+                                                  _ptr(dphi, torch.float64, "dphi")), "pf_potential_jump", plan.handle)
+    return dphi
+
+
+def pf_pressure_jump(plan, schur, psi, motion, f, dphi_dt=None, rho=1.0, dp=None):
+    """Delta p across the surface (Eq. surfbernoulli); motion = (U, V, Omega, Uinf, Vinf)."""
+    dp = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if dp is None else dp
+    m = _native.PfMotion(*[float(v) for v in motion])
+    _native.check(_native.lib().pf_pressure_jump(plan.handle, schur.handle, _ptr(psi, plan.dtype, "psi"),
+                                                 ctypes.byref(m), _ptr(f, torch.float64, "f"),
+                                                 _ptr(dphi_dt, torch.float64, "dphi_dt") if dphi_dt is not None else None,
+                                                 float(rho), _ptr(dp, torch.float64, "dp")), "pf_pressure_jump",
+                  plan.handle)
+    return dp
+
+
 PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT, PF_RHS_SPARSE = 0, 1, 2, 3
 
 

@@ -42,6 +42,10 @@ SIGNATURES = {
     "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "pf_sheet_solve_multi": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pf_step_multi": (_c.c_int, [_P, _P, _I32, _P, _D, _I32]),
+    "pf_sheet_regularize": (_c.c_int, [_P, _P, _P, _P]),
+    "pf_pressure_setup": (_c.c_int, [_P, _P, _P, _P]),
+    "pf_potential_jump": (_c.c_int, [_P, _P, _P, _P]),
+    "pf_pressure_jump": (_c.c_int, [_P, _P, _P, _P, _P, _P, _D, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),

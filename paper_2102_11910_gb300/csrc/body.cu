@@ -985,28 +985,21 @@ pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
 
 static void free_schur(pf_schur s) {
     void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
-                    s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->mwork, s->scal};
+                    s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->mwork, s->scal, s->pnx, s->pny,
+                    s->fidx, s->fwt, s->ci, s->cj, s->cw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (s->jump) {
+        free_schur(s->jump);
+        delete s->jump;
+    }
 }
 
-pf_status schur_factor_device(pf_plan p, pf_schur s) {
+// S^-1 of s->S into s->Sinv: blocked Gauss-Jordan with row interchanges for
+// ns <= BGJ_MAX, the column-at-a-time form beyond
+pf_status invert_schur_matrix(pf_plan p, pf_schur s) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
-    k_surface_stencil<<<ceil_div(8 * ns, 32), 32, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
-                                                            s->siy, s->swx, s->swy, p->d_status);
-    PF_LAUNCH_CHECK(p);
-    if (s->snode) {
-        int n2 = 1;
-        while (n2 < 16 * ns) n2 <<= 1;
-        const size_t sh = (size_t)n2 * sizeof(unsigned long long);
-        PF_CUDA(p, set_smem(k_sheet_order, sh));
-        k_sheet_order<<<1, SHEET_SORT_THREADS, sh, st>>>(s->six, s->siy, ns, p->nx, n2, s->sorder, s->snode);
-        PF_LAUNCH_CHECK(p);
-    }
-    k_schur_build<<<dim3(ceil_div(ns, 128), ns), 128, 0, st>>>(s->six, s->siy, s->swx, s->swy, s->ds, ns, p->G, p->nx,
-                                                                s->S, ns);
-    PF_LAUNCH_CHECK(p);
     // pivots of magnitude 1e-300 or less are reported as singular
     if (ns <= BGJ_MAX) {
         double* LU = s->gj;                       // 32 x 32 factors, then 1 / U_ll
@@ -1047,6 +1040,27 @@ pf_status schur_factor_device(pf_plan p, pf_schur s) {
         k_extract_inverse<<<dim3(ceil_div(ns, 256), ns), 256, 0, st>>>(s->A, s->Sinv, ns);
         PF_LAUNCH_CHECK(p);
     }
+    return PF_OK;
+}
+
+pf_status schur_factor_device(pf_plan p, pf_schur s) {
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    k_surface_stencil<<<ceil_div(8 * ns, 32), 32, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
+                                                            s->siy, s->swx, s->swy, p->d_status);
+    PF_LAUNCH_CHECK(p);
+    if (s->snode) {
+        int n2 = 1;
+        while (n2 < 16 * ns) n2 <<= 1;
+        const size_t sh = (size_t)n2 * sizeof(unsigned long long);
+        PF_CUDA(p, set_smem(k_sheet_order, sh));
+        k_sheet_order<<<1, SHEET_SORT_THREADS, sh, st>>>(s->six, s->siy, ns, p->nx, n2, s->sorder, s->snode);
+        PF_LAUNCH_CHECK(p);
+    }
+    k_schur_build<<<dim3(ceil_div(ns, 128), ns), 128, 0, st>>>(s->six, s->siy, s->swx, s->swy, s->ds, ns, p->G, p->nx,
+                                                                s->S, ns);
+    PF_LAUNCH_CHECK(p);
+    PF_TRY(invert_schur_matrix(p, s));
     // f0 = S^-1 1 with one refinement step (scratch: the solve workspace)
     k_f0_rows<<<ceil_div(ns, 8), 256, 0, st>>>(s->Sinv, ns, s->f0);
     k_rows<1><<<rows_grid(ns, 1), 256, 0, st>>>(s->S, ns, s->f0, 1, nullptr, s->work);
@@ -1302,6 +1316,157 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     return PF_OK;
 }
 
+// ------------------------------------------------ surface pressure (Sec. 2.6.1)
+//
+// Staggered grid: u = d psi/dy on the x-faces (x_i, y_j + dx/2) as
+// (psi[j+1][i] - psi[j][i]) / dx, v = -d psi/dx on the y-faces (x_i + dx/2, y_j)
+// as -(psi[j][i+1] - psi[j][i]) / dx (the discrete curl C).  E_f interpolates
+// each component from its own face lattice with the smoothed three-point
+// function; C_s = n . E_f C is then a 64-node stencil per surface point, and
+// the jump operator C_s L^-1 C_s^T = A G A^T D_dS (L^-1 = dx^2 G *, C_s^T =
+// C^T R_f (n o .) with R_f carrying dS / dx^2).
+
+// face stencils: thread per (point, lattice l, node a); lattice l = 0: u's x
+// (nodes), 1: u's y (half-shifted, ny - 1 rows), 2: v's x (half-shifted,
+// nx - 1 columns), 3: v's y (nodes)
+__global__ void k_face_stencil(const double* __restrict__ x, const double* __restrict__ y, int ns, double x0,
+                               double y0, double dx, int nx, int ny, int* __restrict__ fidx, double* __restrict__ fwt,
+                               int* __restrict__ status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 16 * ns) return;
+    const int p = t >> 4, l = (t >> 2) & 3, a = t & 3;
+    const double pos = (l == 0 || l == 2) ? x[p] : y[p];
+    const double org = l == 0 ? x0 : (l == 1 ? y0 + 0.5 * dx : (l == 2 ? x0 + 0.5 * dx : y0));
+    const int n = l == 0 ? nx : (l == 1 ? ny - 1 : (l == 2 ? nx - 1 : ny));
+    const double g = (pos - org) / dx;
+    const double c = floor(g);
+    const bool ok = c >= 1.0 && c <= n - 3.0;
+    if (!ok && a == 0) atomicOr(status, ST_OUT_OF_DOMAIN);
+    const int ci = ok ? (int)c : 0;
+    fidx[t] = ok ? ci - 1 + a : 1;
+    fwt[t] = ok ? yang3((double)(ci - 1 + a) - g) : 0.0;
+}
+
+// C_s node stencils: thread per (point, entry k < 64), entries in the order
+// (b, a) of the two face stencils, four per pair: u's upper and lower node,
+// v's right and left node
+__global__ void k_curl_stencil(const int* __restrict__ fidx, const double* __restrict__ fwt,
+                               const double* __restrict__ nxs, const double* __restrict__ nys, int ns, double dx,
+                               int* __restrict__ ci, int* __restrict__ cj, double* __restrict__ cw) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 64 * ns) return;
+    const int p = t >> 6, k = t & 63, pair = k >> 2, r = k & 3, b = pair >> 2, a = pair & 3;
+    const int* fi = fidx + 16 * p;
+    const double* fw = fwt + 16 * p;
+    int i, j;
+    double w;
+    if (r < 2) {                      // u = (psi[j+1] - psi[j]) / dx on lattice (0, 1)
+        const double wu = nxs[p] * fw[a] * fw[4 + b] / dx;
+        i = fi[a];
+        j = fi[4 + b] + (r == 0 ? 1 : 0);
+        w = r == 0 ? wu : -wu;
+    } else {                          // v = -(psi[i+1] - psi[i]) / dx on lattice (2, 3)
+        const double wv = nys[p] * fw[8 + a] * fw[12 + b] / dx;
+        i = fi[8 + a] + (r == 2 ? 1 : 0);
+        j = fi[12 + b];
+        w = r == 2 ? -wv : wv;
+    }
+    ci[t] = i;
+    cj[t] = j;
+    cw[t] = w;
+}
+
+// the augmented jump matrix, leading dimension ns + 1:
+//   A[p][q] = dS_q sum_k sum_l cw[p][k] G(node_pk - node_ql) cw[q][l],
+//   A[p][ns] = 1 (multiplier of the uniform null space), A[ns][q] = dS_q, A[ns][ns] = 0
+__global__ void __launch_bounds__(256) k_jump_build(const int* __restrict__ ci, const int* __restrict__ cj,
+                                                    const double* __restrict__ cw, const double* __restrict__ ds, int ns,
+                                                    const double* __restrict__ G, int nx, double* __restrict__ A) {
+    __shared__ int pi[64], pj[64];
+    __shared__ double pw[64];
+    __shared__ double sh[256];
+    const int p = blockIdx.y, q = blockIdx.x, n1 = ns + 1;
+    if (p == ns || q == ns) {
+        if (threadIdx.x == 0) A[(size_t)p * n1 + q] = p == ns ? (q == ns ? 0.0 : ds[q]) : 1.0;
+        return;
+    }
+    if (threadIdx.x < 64) {
+        pi[threadIdx.x] = ci[64 * p + threadIdx.x];
+        pj[threadIdx.x] = cj[64 * p + threadIdx.x];
+        pw[threadIdx.x] = cw[64 * p + threadIdx.x];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int k = e >> 6, l = e & 63;
+        acc += pw[k] * lgf(G, nx, pi[k] - ci[64 * q + l], pj[k] - cj[64 * q + l]) * cw[64 * q + l];
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) A[(size_t)p * n1 + q] = ds[q] * tot;
+}
+
+// right-hand side of the jump: r_p = -C_s L^-1 R_s f
+//   = -sum_k cw[p][k] sum_q dS_q f_q sum_(a,b) G(node_pk - (ix_qa, iy_qb)) wx_qa wy_qb ; r_ns = 0
+__global__ void __launch_bounds__(256) k_jump_rhs(const int* __restrict__ ci, const int* __restrict__ cj,
+                                                  const double* __restrict__ cw, const int* __restrict__ six,
+                                                  const int* __restrict__ siy, const double* __restrict__ swx,
+                                                  const double* __restrict__ swy, const double* __restrict__ ds,
+                                                  const double* __restrict__ f, int ns, const double* __restrict__ G,
+                                                  int nx, double* __restrict__ r) {
+    __shared__ int pi[64], pj[64];
+    __shared__ double pw[64];
+    __shared__ double sh[256];
+    const int p = blockIdx.x;
+    if (p == ns) {
+        if (threadIdx.x == 0) r[ns] = 0.0;
+        return;
+    }
+    if (threadIdx.x < 64) {
+        pi[threadIdx.x] = ci[64 * p + threadIdx.x];
+        pj[threadIdx.x] = cj[64 * p + threadIdx.x];
+        pw[threadIdx.x] = cw[64 * p + threadIdx.x];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < 16 * ns; e += blockDim.x) {
+        const int q = e >> 4, a = e & 3, b = (e >> 2) & 3;
+        const int mi = six[4 * q + a], mj = siy[4 * q + b];
+        const double src = ds[q] * f[q] * swx[4 * q + a] * swy[4 * q + b];
+        double g = 0.0;
+        for (int k = 0; k < 64; ++k) g += pw[k] * lgf(G, nx, pi[k] - mi, pj[k] - mj);
+        acc += g * src;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) r[p] = -tot;
+}
+
+// Delta p = -rho (E_f u - v_s) . (f z x n) - rho d(Delta phi)/dt, u from psi on the faces
+template <typename T>
+__global__ void k_pressure_jump(const T* __restrict__ psi, int nx, double dx, const int* __restrict__ fidx,
+                                const double* __restrict__ fwt, const double* __restrict__ x,
+                                const double* __restrict__ y, const double* __restrict__ nxs,
+                                const double* __restrict__ nys, const double* __restrict__ f,
+                                const double* __restrict__ dphi_dt, pf_motion m, double rho, int ns,
+                                double* __restrict__ dp) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    const int* fi = fidx + 16 * p;
+    const double* fw = fwt + 16 * p;
+    double us = 0.0, vs = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            const size_t ju = (size_t)fi[4 + b] * nx + fi[a];
+            us += fw[a] * fw[4 + b] * ((double)psi[ju + nx] - (double)psi[ju]) / dx;
+            const size_t jv = (size_t)fi[12 + b] * nx + fi[8 + a];
+            vs += fw[8 + a] * fw[12 + b] * -((double)psi[jv + 1] - (double)psi[jv]) / dx;
+        }
+    us += m.Uinf;
+    vs += m.Vinf;
+    const double vsx = m.U - m.Omega * y[p], vsy = m.V + m.Omega * x[p];
+    const double tx = -nys[p], ty = nxs[p];
+    dp[p] = -rho * ((us - vsx) * f[p] * tx + (vs - vsy) * f[p] * ty) - rho * (dphi_dt ? dphi_dt[p] : 0.0);
+}
+
 pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total) {
     const int nb = mb.n_bodies;
     if (nb < 1 || nb > PF_MAX_BODIES || mb.start[0] != 0 || mb.start[nb] != ns) return PF_ERR_ARG;
@@ -1472,6 +1637,76 @@ pf_status pf_sheet_solve_multi(pf_plan p, pf_schur s, const void* w, const pf_mu
         for (int b = 0; b < nb; ++b) s0[b] = h[b];
     if (gamma_new)
         for (int i = 0; i < ne; ++i) gamma_new[i] = h[nb + i];
+    return PF_OK;
+}
+
+pf_status pf_sheet_regularize(pf_plan p, pf_schur s, const double* f, void* w) {
+    if (!p || !f || !w) return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    return sheet_deposit(p, s, f, w);
+}
+
+pf_status pf_pressure_setup(pf_plan p, pf_schur s, const double* nxs, const double* nys) {
+    if (!p || !nxs || !nys) return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    PF_CUDA(p, cudaStreamSynchronize(st));
+    if (!s->pnx) {
+        PF_CUDA(p, cudaMalloc(&s->pnx, ns * sizeof(double)));
+        PF_CUDA(p, cudaMalloc(&s->pny, ns * sizeof(double)));
+        PF_CUDA(p, cudaMalloc(&s->fidx, 16 * (size_t)ns * sizeof(int)));
+        PF_CUDA(p, cudaMalloc(&s->fwt, 16 * (size_t)ns * sizeof(double)));
+        PF_CUDA(p, cudaMalloc(&s->ci, 64 * (size_t)ns * sizeof(int)));
+        PF_CUDA(p, cudaMalloc(&s->cj, 64 * (size_t)ns * sizeof(int)));
+        PF_CUDA(p, cudaMalloc(&s->cw, 64 * (size_t)ns * sizeof(double)));
+    }
+    if (!s->jump) PF_TRY(schur_create(p, ns + 1, &s->jump));
+    PF_CUDA(p, cudaMemcpyAsync(s->pnx, nxs, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(p, cudaMemcpyAsync(s->pny, nys, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_face_stencil<<<ceil_div(16 * ns, 64), 64, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->fidx,
+                                                          s->fwt, p->d_status);
+    k_curl_stencil<<<ceil_div(64 * ns, 256), 256, 0, st>>>(s->fidx, s->fwt, s->pnx, s->pny, ns, p->dx, s->ci, s->cj,
+                                                            s->cw);
+    k_jump_build<<<dim3(ns + 1, ns + 1), 256, 0, st>>>(s->ci, s->cj, s->cw, s->ds, ns, p->G, p->nx, s->jump->S);
+    PF_LAUNCH_CHECK(p);
+    PF_TRY(invert_schur_matrix(p, s->jump));
+    PF_CUDA(p, cudaStreamSynchronize(st));
+    return PF_OK;
+}
+
+pf_status pf_potential_jump(pf_plan p, pf_schur s, const double* f, double* dphi) {
+    if (!p || !f || !dphi) return PF_ERR_ARG;
+    if (!s || !s->jump) return PF_ERR_NOT_FACTORED;
+    const int ns = s->ns, n1 = ns + 1;
+    cudaStream_t st = p->stream;
+    double* r = s->jump->work;          // right-hand side (n1), then the solution (n1), then the residual
+    double* y = r + n1;
+    double* res = y + n1;
+    k_jump_rhs<<<n1, 256, 0, st>>>(s->ci, s->cj, s->cw, s->six, s->siy, s->swx, s->swy, s->ds, f, ns, p->G, p->nx, r);
+    k_rows<0><<<rows_grid(n1, 1), 256, 0, st>>>(s->jump->Sinv, n1, r, 1, nullptr, y);
+    k_rows<1><<<rows_grid(n1, 1), 256, 0, st>>>(s->jump->S, n1, y, 1, r, res);
+    k_rows<2><<<rows_grid(n1, 1), 256, 0, st>>>(s->jump->Sinv, n1, res, 1, nullptr, y);
+    PF_LAUNCH_CHECK(p);
+    PF_CUDA(p, cudaMemcpyAsync(dphi, y, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return PF_OK;
+}
+
+pf_status pf_pressure_jump(pf_plan p, pf_schur s, const void* psi, const pf_motion* m, const double* f,
+                           const double* dphi_dt, double rho, double* dp) {
+    if (!p || !psi || !m || !f || !dp) return PF_ERR_ARG;
+    if (!s || !s->jump) return PF_ERR_NOT_FACTORED;
+    const int ns = s->ns;
+    cudaStream_t st = p->stream;
+    if (p->prec == PF_FP64)
+        k_pressure_jump<double><<<ceil_div(ns, 128), 128, 0, st>>>((const double*)psi, p->nx, p->dx, s->fidx, s->fwt,
+                                                                   s->x, s->y, s->pnx, s->pny, f, dphi_dt, *m, rho, ns,
+                                                                   dp);
+    else
+        k_pressure_jump<float><<<ceil_div(ns, 128), 128, 0, st>>>((const float*)psi, p->nx, p->dx, s->fidx, s->fwt,
+                                                                  s->x, s->y, s->pnx, s->pny, f, dphi_dt, *m, rho, ns,
+                                                                  dp);
+    PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
 

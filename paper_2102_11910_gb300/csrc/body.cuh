@@ -24,12 +24,25 @@ struct pf_schur_s {
     double* gj = nullptr;     // blocked Gauss-Jordan scratch: LU (32 x 32), Y, Z (32 x ns), L_R (ns x 32), perm, gperm
     double* work = nullptr;   // 12 ns doubles of solve scratch
     double* mwork = nullptr;  // several-body solve scratch (allocated by the first such solve)
+    // surface pressure (pf_pressure_setup): unit normals (ns each), the face
+    // stencils (per point 16 indices and weights: u lattice x, y then v lattice
+    // x, y, 4 nodes each), the node stencils of C_s (ns x 64), and the factor of
+    // the jump operator augmented with the gauge row (an (ns + 1) system)
+    double* pnx = nullptr;
+    double* pny = nullptr;
+    int* fidx = nullptr;
+    double* fwt = nullptr;
+    int* ci = nullptr;
+    int* cj = nullptr;
+    double* cw = nullptr;
+    struct pf_schur_s* jump = nullptr;
     double* scal = nullptr;   // device scalars: s0, Gamma1, Gamma2, -, new-vortex x[2], y[2]
 };
 
 pf_status schur_create(pf_plan p, int ns, pf_schur* out);
 void schur_free(pf_schur s);
 pf_status schur_factor_device(pf_plan p, pf_schur s);
+pf_status invert_schur_matrix(pf_plan p, pf_schur s);
 // Several bodies (Sec. 2.7): validate a partition (and count its edges); the
 // device-level solve of pf_sheet_solve_multi with new vortices at device
 // (vx, vy) and, when gw_dev is not null, the bodies' gamma_w read from the
