@@ -456,6 +456,35 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                      "mixed": _steps_per_s(pf, plan, lambda: pf.pf_step_multi(plan, state, 0.01, tpk),
                                                            20)}
         print("workload done: %s" % 'two_plates_384x256', file=sys.stderr, flush=True)
+        # surface pressure (Sec. 2.6.1) of the 128^2 plate at dS/dx = 1: the jump operator's setup
+        # once, then per step the potential jump of the sheet and the pressure jump
+        gsp = inputs.centred_grid(128, 128, 0.02)
+        plan = pf.Plan(gsp.nx, gsp.ny, gsp.dx, gsp.x0, gsp.y0, pf.PF_MIXED, stream=stream)
+        pb = inputs.plate(50, 1.0, math.radians(20.0))
+        schur = pf.pf_schur_factor(plan, pb.x, pb.y, pb.ds)
+        t0 = time.perf_counter()
+        pf.pf_pressure_setup(plan, schur, np.full(50, math.sin(math.radians(20.0))),
+                             np.full(50, math.cos(math.radians(20.0))))
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        wsp = plan.field()
+        wsp.zero_()
+        fsp, _, _ = pf.pf_sheet_solve(plan, schur, wsp, (0.0, 0.0, 0.0, 1.0, 0.0), pf.PF_SHEET_KUTTA_STEADY, 0.0,
+                                      [pb.edges[1]])
+        pf.pf_sheet_regularize(plan, schur, fsp, wsp)
+        psi_sp = pf.pf_poisson_solve(plan, wsp)
+        prev = pf.pf_potential_jump(plan, schur, fsp)
+
+        def pressure_step():
+            d = pf.pf_potential_jump(plan, schur, fsp)
+            return pf.pf_pressure_jump(plan, schur, psi_sp, (0.0, 0.0, 0.0, 1.0, 0.0), fsp, (d - prev) / 0.01)
+        for _ in range(3):
+            pressure_step()
+        out["surface_pressure_plate_128"] = {"unit": "calls/s", "setup_ms": setup_ms,
+                                             "desc": "plate 128^2, Ns 50 (dS/dx 1): potential jump + pressure jump "
+                                                     "per call (steady Kutta sheet, psi of the sheet); setup = "
+                                                     "jump operator build and inverse, once per geometry",
+                                             "mixed": _steps_per_s(pf, plan, pressure_step, 50)}
+        print("workload done: %s" % 'surface_pressure_plate_128', file=sys.stderr, flush=True)
         # uneven batch: independent instances, one step each per call
         inst = inputs.batched_instances(n=n_batch)
         res = {}

@@ -20,8 +20,12 @@ vic      regularization R_v (Eq. vortexregularization), the unbounded inverse
 body     surface operators R_s/E_s, Schur complement S (Eq. vsheet), f0, Gamma0,
          circulation removal, Kutta projection and the constrained sheet solves
          of Sec. 2.3-2.4 (Eqs. circsystem, kuttasystem, kuttasystem2,
-         kuttasystem3/twovortex).
-step     vortex shedding placement and the Euler / RK2 time step (Sec. 2.4.2).
+         kuttasystem3/twovortex), the generalized edge condition (Sec. 2.5)
+         and several bodies sharing one S (Sec. 2.7, Eq. kuttasystem4).
+step     vortex shedding placement and the Euler / RK2 time step (Sec. 2.4.2),
+         with one body or several.
 diagnostics  linear and angular impulse of the fluid (Sec. 2.6.2, Eqs.
          linimpxd, linimpyd, angimpd).
+pressure the jump in scalar potential of the sheet and the surface pressure
+         jump of the immersed-boundary Bernoulli equation (Sec. 2.6.1).
 """
