@@ -126,3 +126,72 @@ def pressure_jump(us, vs, xs, ys, nxs, nys, f, U, V, Omega, dphi_dt, rho=1.0):
     vsy = V + Omega * xs
     tx, ty = -nys, nxs                       # z x n
     return -rho * ((us - vsx) * f * tx + (vs - vsy) * f * ty) - rho * dphi_dt
+
+
+# ----------------------------------------------------------------- pressure field
+# Eq. pgrid at the cell centres (x_i + dx/2, y_j + dx/2), i < nx - 1, j < ny - 1,
+# read with the surface term inside the divergence (L^-1 acts on centre data):
+#   p = -rho/2 |u|^2 - rho L^-1 D [ w x u + R_f(n o d(Delta phi)/dt - v_s x f) ],
+# w the free vorticity on the nodes, u the face velocity of the whole flow,
+# D the divergence from the faces to the centres, L^-1 = dx^2 G * on the centre
+# lattice (the same five-point Laplacian).  Face arrays: u[j, i] on the x-face
+# (x_i, y_j + dx/2), shape (ny - 1, nx); v[j, i] on the y-face (x_i + dx/2, y_j),
+# shape (ny, nx - 1).
+
+def face_velocities(grid, psi, Uinf, Vinf):
+    """u = (psi[j+1, i] - psi[j, i]) / dx + Uinf, v = -(psi[j, i+1] - psi[j, i]) / dx + Vinf."""
+    dx = grid.dx
+    return (psi[1:, :] - psi[:-1, :]) / dx + Uinf, -(psi[:, 1:] - psi[:, :-1]) / dx + Vinf
+
+
+def lamb_faces(w, u, v):
+    """w x u = (-w v, w u) on the faces: the x-component on the x-faces with w
+    averaged over the face's two nodes and v over the four y-faces around it,
+    the y-component on the y-faces alike; faces on the grid's edge take the
+    missing neighbours as zero."""
+    ny, nx = w.shape
+    vpad = np.zeros((ny, nx + 1))
+    vpad[:, 1:-1] = v                          # y-face (i - 1/2, j) at vpad[j, i]
+    v_at_x = 0.25 * (vpad[:-1, :-1] + vpad[:-1, 1:] + vpad[1:, :-1] + vpad[1:, 1:])   # (ny - 1, nx)
+    lx = -0.5 * (w[:-1, :] + w[1:, :]) * v_at_x
+    upad = np.zeros((ny + 1, nx))
+    upad[1:-1, :] = u                          # x-face (i, j - 1/2) at upad[j, i]
+    u_at_y = 0.25 * (upad[:-1, :-1] + upad[1:, :-1] + upad[:-1, 1:] + upad[1:, 1:])   # (ny, nx - 1)
+    ly = 0.5 * (w[:, :-1] + w[:, 1:]) * u_at_y
+    return lx, ly
+
+
+def surface_faces(grid, xs, ys, nxs, nys, ds, dphi_dt, f, U, V, Omega):
+    """R_f(n o d(Delta phi)/dt - v_s x f) on the faces: the x-component on the
+    u lattice, the y-component on the v lattice, each with dS/dx^2 and the
+    smoothed three-point weights; v_s x (f z) = (v_sy f, -v_sx f)."""
+    dx = grid.dx
+    vsx, vsy = U - Omega * ys, V + Omega * xs
+    ax = nxs * dphi_dt - vsy * f
+    ay = nys * dphi_dt + vsx * f
+    qx = np.zeros((grid.ny - 1, grid.nx))
+    qy = np.zeros((grid.ny, grid.nx - 1))
+    ixu, wxu = stencil_1d(xs, grid.x0, dx, grid.nx, yang3)
+    iyu, wyu = stencil_1d(ys, grid.y0 + 0.5 * dx, dx, grid.ny - 1, yang3)
+    ixv, wxv = stencil_1d(xs, grid.x0 + 0.5 * dx, dx, grid.nx - 1, yang3)
+    iyv, wyv = stencil_1d(ys, grid.y0, dx, grid.ny, yang3)
+    for b in range(4):
+        for a in range(4):
+            np.add.at(qx, (iyu[:, b], ixu[:, a]), ds * ax * wxu[:, a] * wyu[:, b])
+            np.add.at(qy, (iyv[:, b], ixv[:, a]), ds * ay * wxv[:, a] * wyv[:, b])
+    return qx / dx ** 2, qy / dx ** 2
+
+
+def divergence(grid, qx, qy):
+    """D q at the centres: (qx[j, i+1] - qx[j, i] + qy[j+1, i] - qy[j, i]) / dx."""
+    return (qx[:, 1:] - qx[:, :-1] + qy[1:, :] - qy[:-1, :]) / grid.dx
+
+
+def pressure_field(grid, table, u, v, w, qx_s, qy_s, rho=1.0):
+    """Eq. pgrid at the cell centres (the surface faces qx_s, qy_s may be zero)."""
+    from .vic import Grid, inv_laplacian
+    lx, ly = lamb_faces(w, u, v)
+    src = divergence(grid, lx + qx_s, ly + qy_s)
+    gc = Grid(grid.nx - 1, grid.ny - 1, grid.dx, grid.x0 + 0.5 * grid.dx, grid.y0 + 0.5 * grid.dx)
+    ke = 0.5 * (u[:, :-1] ** 2 + u[:, 1:] ** 2) + 0.5 * (v[:-1, :] ** 2 + v[1:, :] ** 2)
+    return -0.5 * rho * ke - rho * inv_laplacian(gc, src, table)

@@ -89,3 +89,59 @@ def test_accelerating_cylinder_pressure_jump(cyl):
                          0, 0, 0, d1 / dt, rho=1.0)
     assert _rel(d1 / dt, -2 * a * c["R"] * np.cos(c["th"])) < 0.05
     assert _rel(dp, 2 * a * c["R"] * np.cos(c["th"])) < 0.05
+
+
+def _centres(g):
+    xc = g.x0 + g.dx * (np.arange(g.nx - 1) + 0.5)
+    yc = g.y0 + g.dx * (np.arange(g.ny - 1) + 0.5)
+    return np.meshgrid(xc, yc)
+
+
+def test_pressure_field_of_an_accelerating_cylinder(cyl):
+    """A cylinder starting from rest with acceleration a (u = 0 at t = 0): the
+    pressure is -rho dphi/dt, rho a R^2 cos(theta) / r outside and
+    -rho a r cos(theta) inside (the fluid inside moves with the body), up to a
+    constant; Eq. pgrid reduces to -rho L^-1 D R_f(n o d(Delta phi)/dt)."""
+    c = cyl
+    g, b, R = c["g"], c["b"], c["R"]
+    a, dt = 0.7, 1e-3
+    f1, _ = B.sheet_circulation(c["sch"], B.sb_prime(b.x, b.y, a * dt, 0, 0, 0, 0), np.zeros(len(b.x)), 0.0)
+    dphidt = P.potential_jump(g, c["st"], c["cw"], b.ds, f1, c["tab"]) / dt
+    qx, qy = P.surface_faces(g, b.x, b.y, c["nxs"], c["nys"], b.ds, dphidt, np.zeros(len(b.x)), 0, 0, 0)
+    zu, zv = np.zeros((g.ny - 1, g.nx)), np.zeros((g.ny, g.nx - 1))
+    p = P.pressure_field(g, c["tab"], zu, zv, np.zeros((g.ny, g.nx)), qx, qy, rho=1.2)
+    X, Y = _centres(g)
+    r = np.hypot(X, Y)
+    ex = np.where(r > R, 1.2 * a * R * R * X / np.maximum(r, 1e-12) ** 2, -1.2 * a * X)
+    sel = (r < 0.8 * R) | ((r > 1.25 * R) & (r < 1.6 * R))      # away from the regularized layer
+    d = p[sel] - ex[sel]
+    assert np.linalg.norm(d - d.mean()) / np.linalg.norm(ex[sel]) < 0.05
+
+
+def test_pressure_field_of_a_lamb_oseen_vortex():
+    """A steady Lamb-Oseen vortex, vorticity Gamma/(pi s^2) exp(-r^2/s^2) on the
+    nodes, u_theta = Gamma/(2 pi r)(1 - exp(-r^2/s^2)): the radial balance
+    dp/dr = rho u_theta^2 / r gives p(r) = -rho int_r^inf u_theta^2/s ds
+    (one-dimensional quadrature of the closed form).  Eq. pgrid (kinetic term
+    plus the Lamb-vector term) must reproduce it up to a constant."""
+    from scipy.integrate import quad
+    gs = inputs.centred_grid(97, 97, 0.05)
+    g = vic.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    tab = lgf_table(98, 98)
+    sig, Gam, rho = 0.3, 1.0, 1.1
+    Xn, Yn = np.meshgrid(g.node_x(), g.node_y())
+    w = Gam / (math.pi * sig ** 2) * np.exp(-(Xn ** 2 + Yn ** 2) / sig ** 2)
+    psi = vic.streamfunction(g, w, tab)
+    u, v = P.face_velocities(g, psi, 0.0, 0.0)
+    p = P.pressure_field(g, tab, u, v, w, np.zeros_like(u), np.zeros_like(v), rho=rho)
+    X, Y = _centres(g)
+    r = np.hypot(X, Y)
+    ut = lambda s: Gam / (2 * math.pi * s) * (1 - math.exp(-s * s / sig ** 2)) if s > 0 else 0.0
+    sel = r < 1.2
+    ex = np.array([-rho * quad(lambda s: ut(s) ** 2 / s, rv, np.inf, limit=200)[0] for rv in r[sel]])
+    d = p[sel] - ex
+    assert np.linalg.norm(d - d.mean()) < 0.02 * np.linalg.norm(ex - ex.mean())
+    # and the Lamb-vector term carries the core: without it the profile is far off
+    ke = 0.5 * (u[:, :-1] ** 2 + u[:, 1:] ** 2) + 0.5 * (v[:-1, :] ** 2 + v[1:, :] ** 2)
+    d0 = -0.5 * rho * ke[sel] - ex
+    assert np.linalg.norm(d0 - d0.mean()) > 0.3 * np.linalg.norm(ex - ex.mean())
