@@ -326,6 +326,25 @@ pf_status pf_potential_jump(pf_plan plan, pf_schur schur, const double* f, doubl
 pf_status pf_pressure_jump(pf_plan plan, pf_schur schur, const void* psi, const pf_motion* m, const double* f,
                            const double* dphi_dt, double rho, double* dp);
 
+/* Pressure field at the cell centres (x0 + (i + 1/2) dx, y0 + (j + 1/2) dx),
+ * i < nx - 1, j < ny - 1 (Eq. pgrid, the surface term read inside the
+ * divergence since L^-1 acts on centre data):
+ *   p = -rho/2 |u|^2 - rho L^-1 D [ w x u + R_f(n o d(Delta phi)/dt - v_s x f) ]
+ * with u on the faces from psi (as pf_pressure_jump) plus (m->Uinf, m->Vinf),
+ * w the free vorticity on the nodes (device, plan precision), the Lamb vector
+ * w x u on the faces from two-node averages of w and four-face averages of the
+ * other component (faces outside the grid count as zero), D the divergence
+ * to the centres and L^-1 = dx^2 G * on the centre lattice.  schur (after
+ * pf_pressure_setup) with f and dphi_dt (device, ns each, either may be NULL)
+ * adds the surface terms; schur = NULL: a flow without body.  p: device,
+ * (nx-1)(ny-1) doubles, row-major; defined up to nothing (no free constant:
+ * the LGF solve is unique).  The first call builds and keeps a plan of the
+ * centre lattice (its LGF table and spectra, same stream and precision);
+ * FP64 arithmetic except that Poisson solve, in the plan's precision; the
+ * surface terms are gathered per centre in a fixed order (deterministic). */
+pf_status pf_pressure_field(pf_plan plan, pf_schur schur, const void* psi, const void* w, const pf_motion* m,
+                            const double* f, const double* dphi_dt, double rho, double* p);
+
 /* ------------------------------------------------------- time stepping */
 
 /* Device-resident vortex set (positions and strengths, FP64) with a fixed

@@ -360,6 +360,19 @@ def pf_pressure_jump(plan, schur, psi, motion, f, dphi_dt=None, rho=1.0, dp=None
     return dp
 
 
+def pf_pressure_field(plan, psi, w, motion, schur=None, f=None, dphi_dt=None, rho=1.0, p=None):
+    """Pressure at the cell centres (Eq. pgrid), a (ny-1, nx-1) float64 device tensor.
+    motion = (U, V, Omega, Uinf, Vinf); schur, f, dphi_dt: the surface terms (optional)."""
+    p = torch.empty((plan.ny - 1, plan.nx - 1), dtype=torch.float64, device="cuda") if p is None else p
+    m = _native.PfMotion(*[float(v) for v in motion])
+    _native.check(_native.lib().pf_pressure_field(plan.handle, schur.handle if schur is not None else None,
+                                                  _ptr(psi, plan.dtype, "psi"), _ptr(w, plan.dtype, "w"),
+                                                  ctypes.byref(m), _ptr(f, torch.float64, "f"),
+                                                  _ptr(dphi_dt, torch.float64, "dphi_dt"), float(rho),
+                                                  _ptr(p, torch.float64, "p")), "pf_pressure_field", plan.handle)
+    return p
+
+
 PF_RHS_AUTO, PF_RHS_DIRECT, PF_RHS_FFT, PF_RHS_SPARSE = 0, 1, 2, 3
 
 

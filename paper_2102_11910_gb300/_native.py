@@ -46,6 +46,7 @@ SIGNATURES = {
     "pf_pressure_setup": (_c.c_int, [_P, _P, _P, _P]),
     "pf_potential_jump": (_c.c_int, [_P, _P, _P, _P]),
     "pf_pressure_jump": (_c.c_int, [_P, _P, _P, _P, _P, _P, _D, _P]),
+    "pf_pressure_field": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _D, _P]),
     "pf_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
     "pf_state_destroy": (_c.c_int, [_P]),
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),

@@ -26,6 +26,11 @@ void free_plan(pf_plan p) {
                    p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);
+    if (p->pscr) cudaFree(p->pscr);
+    if (p->centres) {
+        free_plan(p->centres);
+        delete p->centres;
+    }
     if (p->shared && --p->shared->refs == 0) {
         void* tables[] = {p->G, p->H64, p->H32, p->Hu64, p->Hv64, p->Hu32, p->Hv32, p->twP64, p->twQ64, p->twP32,
                           p->twQ32, p->tw256_64, p->tw256_32};

@@ -1467,6 +1467,91 @@ __global__ void k_pressure_jump(const T* __restrict__ psi, int nx, double dx, co
     dp[p] = -rho * ((us - vsx) * f[p] * tx + (vs - vsy) * f[p] * ty) - rho * (dphi_dt ? dphi_dt[p] : 0.0);
 }
 
+// Pressure field at the cell centres (Eq. pgrid, the surface term inside the
+// divergence):  p = -rho/2 |u|^2 - rho L^-1 D [w x u + R_f(n o dDphi/dt - v_s x f)].
+// Faces outside the grid count as zero, as in the oracle.
+template <typename T>
+struct FaceField {
+    const T* psi;
+    const T* w;
+    int nx, ny;
+    double dx, Uinf, Vinf;
+    __device__ double u(int i, int j) const {            // x-face (i, j + 1/2)
+        if (i < 0 || i >= nx || j < 0 || j >= ny - 1) return 0.0;
+        return ((double)psi[(size_t)(j + 1) * nx + i] - (double)psi[(size_t)j * nx + i]) / dx + Uinf;
+    }
+    __device__ double v(int i, int j) const {            // y-face (i + 1/2, j)
+        if (i < 0 || i >= nx - 1 || j < 0 || j >= ny) return 0.0;
+        return -((double)psi[(size_t)j * nx + i + 1] - (double)psi[(size_t)j * nx + i]) / dx + Vinf;
+    }
+    __device__ double lx(int i, int j) const {           // -w v on the x-face (i, j + 1/2)
+        const double wf = 0.5 * ((double)w[(size_t)j * nx + i] + (double)w[(size_t)(j + 1) * nx + i]);
+        return -wf * 0.25 * (v(i - 1, j) + v(i, j) + v(i - 1, j + 1) + v(i, j + 1));
+    }
+    __device__ double ly(int i, int j) const {           // w u on the y-face (i + 1/2, j)
+        const double wf = 0.5 * ((double)w[(size_t)j * nx + i] + (double)w[(size_t)j * nx + i + 1]);
+        return wf * 0.25 * (u(i, j - 1) + u(i, j) + u(i + 1, j - 1) + u(i + 1, j));
+    }
+};
+
+// one thread per centre: the Lamb-vector divergence and the kinetic energy
+template <typename T>
+__global__ void k_pressure_src(FaceField<T> F, double* __restrict__ src, double* __restrict__ ke) {
+    const int nc = F.nx - 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc * (F.ny - 1)) return;
+    const int i = t % nc, j = t / nc;
+    src[t] = (F.lx(i + 1, j) - F.lx(i, j) + F.ly(i, j + 1) - F.ly(i, j)) / F.dx;
+    const double u0 = F.u(i, j), u1 = F.u(i + 1, j), v0 = F.v(i, j), v1 = F.v(i, j + 1);
+    ke[t] = 0.5 * (u0 * u0 + u1 * u1) + 0.5 * (v0 * v0 + v1 * v1);
+}
+
+// surface faces R_f(n o dDphi/dt - v_s x f) gathered by each centre of the box
+// from every surface point in index order (deterministic), their divergence
+// added to src
+__device__ __forceinline__ double face_weight(const int* fi, const double* fw, int lx, int ly, int ii, int jj) {
+    const int a = ii - fi[lx], b = jj - fi[ly];
+    return (a >= 0 && a < 4 && b >= 0 && b < 4) ? fw[lx + a] * fw[ly + b] : 0.0;
+}
+
+__global__ void k_surface_src(const int* __restrict__ fidx, const double* __restrict__ fwt,
+                              const double* __restrict__ x, const double* __restrict__ y,
+                              const double* __restrict__ nxs, const double* __restrict__ nys,
+                              const double* __restrict__ ds, const double* __restrict__ dphi_dt,
+                              const double* __restrict__ f, pf_motion m, int ns, int nx, double dx, int i0, int j0,
+                              int bw, int bh, double* __restrict__ src) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= bw * bh) return;
+    const int i = i0 + t % bw, j = j0 + t / bw;
+    double qx0 = 0.0, qx1 = 0.0, qy0 = 0.0, qy1 = 0.0;
+    for (int p = 0; p < ns; ++p) {
+        const double dd = dphi_dt ? dphi_dt[p] : 0.0, ff = f ? f[p] : 0.0;
+        const double vsx = m.U - m.Omega * y[p], vsy = m.V + m.Omega * x[p];
+        const double ax = ds[p] * (nxs[p] * dd - vsy * ff), ay = ds[p] * (nys[p] * dd + vsx * ff);
+        const int* fi = fidx + 16 * p;
+        const double* fw = fwt + 16 * p;
+        qx0 += ax * face_weight(fi, fw, 0, 4, i, j);
+        qx1 += ax * face_weight(fi, fw, 0, 4, i + 1, j);
+        qy0 += ay * face_weight(fi, fw, 8, 12, i, j);
+        qy1 += ay * face_weight(fi, fw, 8, 12, i, j + 1);
+    }
+    src[(size_t)j * (nx - 1) + i] += (qx1 - qx0 + qy1 - qy0) / (dx * dx * dx);
+}
+
+template <typename T>
+__global__ void k_to_plan(const double* __restrict__ a, int64_t n, T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)a[i];
+}
+
+// p = -rho/2 ke - rho L^-1 src = -rho/2 ke + rho psi_c with psi_c = -L^-1 src
+template <typename T>
+__global__ void k_pressure_final(const double* __restrict__ ke, const T* __restrict__ psic, int64_t n, double rho,
+                                 double* __restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = -0.5 * rho * ke[i] + rho * (double)psic[i];
+}
+
 pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total) {
     const int nb = mb.n_bodies;
     if (nb < 1 || nb > PF_MAX_BODIES || mb.start[0] != 0 || mb.start[nb] != ns) return PF_ERR_ARG;
@@ -1671,7 +1756,59 @@ pf_status pf_pressure_setup(pf_plan p, pf_schur s, const double* nxs, const doub
     k_jump_build<<<dim3(ns + 1, ns + 1), 256, 0, st>>>(s->ci, s->cj, s->cw, s->ds, ns, p->G, p->nx, s->jump->S);
     PF_LAUNCH_CHECK(p);
     PF_TRY(invert_schur_matrix(p, s->jump));
+    // the cell-centre box the surface faces can reach (stencils of 4 faces from floor - 1)
+    std::vector<double> hx(ns), hy(ns);
+    PF_CUDA(p, cudaMemcpyAsync(hx.data(), s->x, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA(p, cudaMemcpyAsync(hy.data(), s->y, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
     PF_CUDA(p, cudaStreamSynchronize(st));
+    const double xlo = *std::min_element(hx.begin(), hx.end()), xhi = *std::max_element(hx.begin(), hx.end());
+    const double ylo = *std::min_element(hy.begin(), hy.end()), yhi = *std::max_element(hy.begin(), hy.end());
+    s->pbox[0] = std::max(0, (int)floor((xlo - p->x0) / p->dx) - 4);
+    s->pbox[1] = std::min(p->nx - 2, (int)floor((xhi - p->x0) / p->dx) + 4);
+    s->pbox[2] = std::max(0, (int)floor((ylo - p->y0) / p->dx) - 4);
+    s->pbox[3] = std::min(p->ny - 2, (int)floor((yhi - p->y0) / p->dx) + 4);
+    return PF_OK;
+}
+
+pf_status pf_pressure_field(pf_plan p, pf_schur s, const void* psi, const void* w, const pf_motion* m, const double* f,
+                            const double* dphi_dt, double rho, double* pout) {
+    if (!p || !psi || !w || !m || !pout) return PF_ERR_ARG;
+    if (s && !s->jump) return PF_ERR_NOT_FACTORED;
+    cudaStream_t st = p->stream;
+    const int64_t nc = (int64_t)(p->nx - 1) * (p->ny - 1);
+    if (!p->centres) {
+        pf_grid_desc d{p->nx - 1, p->ny - 1, p->dx, p->x0 + 0.5 * p->dx, p->y0 + 0.5 * p->dx, p->prec};
+        PF_TRY(pf_plan_create(&d, st, &p->centres));
+        PF_CUDA(p, cudaMalloc(&p->pscr, 2 * (size_t)nc * sizeof(double)));
+    }
+    double* src = p->pscr;
+    double* ke = src + nc;
+    const int nb = (int)std::min<int64_t>(ceil_div(nc, 256), 152 * 8);
+    if (p->prec == PF_FP64)
+        k_pressure_src<double><<<ceil_div(nc, 256), 256, 0, st>>>(
+            FaceField<double>{(const double*)psi, (const double*)w, p->nx, p->ny, p->dx, m->Uinf, m->Vinf}, src, ke);
+    else
+        k_pressure_src<float><<<ceil_div(nc, 256), 256, 0, st>>>(
+            FaceField<float>{(const float*)psi, (const float*)w, p->nx, p->ny, p->dx, m->Uinf, m->Vinf}, src, ke);
+    PF_LAUNCH_CHECK(p);
+    if (s && (f || dphi_dt) && s->pbox[1] >= s->pbox[0] && s->pbox[3] >= s->pbox[2]) {
+        const int bw = s->pbox[1] - s->pbox[0] + 1, bh = s->pbox[3] - s->pbox[2] + 1;
+        k_surface_src<<<ceil_div(bw * bh, 128), 128, 0, st>>>(s->fidx, s->fwt, s->x, s->y, s->pnx, s->pny, s->ds,
+                                                               dphi_dt, f, *m, s->ns, p->nx, p->dx, s->pbox[0],
+                                                               s->pbox[2], bw, bh, src);
+        PF_LAUNCH_CHECK(p);
+    }
+    pf_plan c = p->centres;
+    if (p->prec == PF_FP64) {
+        k_to_plan<double><<<nb, 256, 0, st>>>(src, nc, (double*)c->w);
+        PF_TRY(conv_solve(c, c->w, c->uv, CONV_PSI, 0.0, 0.0));
+        k_pressure_final<double><<<nb, 256, 0, st>>>(ke, (const double*)c->uv, nc, rho, pout);
+    } else {
+        k_to_plan<float><<<nb, 256, 0, st>>>(src, nc, (float*)c->w);
+        PF_TRY(conv_solve(c, c->w, c->uv, CONV_PSI, 0.0, 0.0));
+        k_pressure_final<float><<<nb, 256, 0, st>>>(ke, (const float*)c->uv, nc, rho, pout);
+    }
+    PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
 

@@ -127,6 +127,11 @@ struct pf_plan_s {
     // the per-chunk counts and the total (allocated by the first sparse solve)
     int* nz_idx = nullptr;
     double* nz_val = nullptr;
+    // pressure field: the plan of the cell-centre lattice ((nx-1) x (ny-1),
+    // origin shifted by dx/2, same stream and precision) and its FP64 source
+    // and kinetic-energy scratch, built by the first pf_pressure_field call
+    struct pf_plan_s* centres = nullptr;
+    double* pscr = nullptr;
     // diagnostics scratch (per-block partial sums and results)
     double* diag = nullptr;            // PF_DIAG_DOUBLES
     // status

@@ -90,3 +90,35 @@ def test_sheet_regularize_matches_oracle(case, prec):
     pf.pf_sheet_regularize(plan, schur, torch.from_numpy(c["f"]).cuda(), w)
     ref = OB.regularize_surface(c["g"], c["st"], c["f"], b.ds).ravel()
     assert rel(w.double().cpu().numpy(), ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_pressure_field_matches_oracle(case, prec):
+    """Eq. pgrid at the cell centres, with the surface terms of a body in motion
+    (a given sheet, a given dDelta phi/dt) and free vorticity around it."""
+    c = case
+    gs, b, g = c["gs"], c["b"], c["g"]
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, prec)
+    schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)
+    pf.pf_pressure_setup(plan, schur, c["nxs"], c["nys"])
+    rng = np.random.default_rng(9)
+    X, Y, G = rng.uniform(g.x0 + 0.25 * (g.nx - 1) * g.dx, g.x0 + 0.4 * (g.nx - 1) * g.dx, 30), \
+        rng.uniform(g.y0 + 0.3 * (g.ny - 1) * g.dx, g.y0 + 0.7 * (g.ny - 1) * g.dx, 30), rng.normal(0, 0.05, 30)
+    w = OV.regularize(g, X, Y, G)
+    psi = OV.streamfunction(g, w + OB.regularize_surface(g, c["st"], c["f"], b.ds), c["tab"])
+    to_dev = lambda a: torch.from_numpy(a.ravel()).to(device="cuda", dtype=plan.dtype).contiguous()
+    psi_d, w_d = to_dev(psi), to_dev(w)
+    psi_u, w_u = psi_d.double().cpu().numpy().reshape(psi.shape), w_d.double().cpu().numpy().reshape(w.shape)
+    dphidt = rng.normal(0.0, 0.2, len(b.x))
+    m = (0.2, -0.1, 0.3, 1.0, 0.0)
+    p = pf.pf_pressure_field(plan, psi_d, w_d, m, schur, torch.from_numpy(c["f"]).cuda(),
+                             torch.from_numpy(dphidt).cuda(), 1.2).cpu().numpy()
+    u, v = OP.face_velocities(g, psi_u, m[3], m[4])
+    qx, qy = OP.surface_faces(g, b.x, b.y, c["nxs"], c["nys"], b.ds, dphidt, c["f"], m[0], m[1], m[2])
+    ref = OP.pressure_field(g, c["tab"], u, v, w_u, qx, qy, rho=1.2)
+    tol = 1e-11 if prec == pf.PF_FP64 else 1e-5
+    assert np.abs(p - ref).max() < tol * np.abs(ref).max()
+    # without a body: the free-vortex terms alone
+    p0 = pf.pf_pressure_field(plan, psi_d, w_d, m).cpu().numpy()
+    ref0 = OP.pressure_field(g, c["tab"], u, v, w_u, np.zeros_like(u), np.zeros_like(v), rho=1.0)
+    assert np.abs(p0 - ref0).max() < tol * np.abs(ref0).max()
