@@ -26,6 +26,7 @@ step     vortex shedding placement and the Euler / RK2 time step (Sec. 2.4.2),
          with one body or several.
 diagnostics  linear and angular impulse of the fluid (Sec. 2.6.2, Eqs.
          linimpxd, linimpyd, angimpd).
-pressure the jump in scalar potential of the sheet and the surface pressure
-         jump of the immersed-boundary Bernoulli equation (Sec. 2.6.1).
+pressure the jump in scalar potential of the sheet, the surface pressure
+         jump of the immersed-boundary Bernoulli equation and the cell-centre
+         pressure field (Sec. 2.6.1).
 """

@@ -1,6 +1,7 @@
-"""Surface pressure (Sec. 2.6.1): the jump in scalar potential carried by the
-bound vortex sheet and the pressure jump across the surface from the
-immersed-boundary Bernoulli equation.
+"""Pressure (Sec. 2.6.1): the jump in scalar potential carried by the bound
+vortex sheet, the pressure jump across the surface from the immersed-boundary
+Bernoulli equation, and the pressure field at the cell centres (Eq. pgrid,
+second half of this module).
 
 Test infrastructure only (see the package docstring).
 
