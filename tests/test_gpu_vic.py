@@ -69,6 +69,35 @@ def test_regularize(prec, nx, ny, nv):
 
 
 @pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("nblob,nspread", [(6000, 2000), (70000, 500)])
+def test_regularize_dense_and_sparse_tiles(prec, nblob, nspread):
+    """One grid holding tiles of a few records and one tile of thousands or of
+    more than 65536 (where the FP32 deposit leaves its split 32-bit sums for
+    64-bit ones): a Gaussian blob of vortices on a uniform spread."""
+    g = inputs.centred_grid(96, 96, 2.0 / 95)
+    rng = np.random.default_rng(17)
+    cx, cy = g.x0 + 48.3 * g.dx, g.y0 + 47.6 * g.dx          # inside node tile (1, 1)
+    Xb = cx + 4.0 * g.dx * rng.standard_normal(nblob)
+    Yb = cy + 4.0 * g.dx * rng.standard_normal(nblob)
+    Gb = rng.normal(0.0, 0.1, nblob)
+    Xs, Ys, Gs = inputs.uniform_vortices(rng, nspread, g.x0 + 2 * g.dx, g.x0 + 92 * g.dx, 1e-2,
+                                         g.y0 + 2 * g.dx, g.y0 + 92 * g.dx)
+    X, Y, G = (np.concatenate(p) for p in ((Xb, Xs), (Yb, Ys), (Gb, Gs)))
+    keep = (X > g.x0 + 1.5 * g.dx) & (X < g.x0 + 92.5 * g.dx) & (Y > g.y0 + 1.5 * g.dx) & (Y < g.y0 + 92.5 * g.dx)
+    X, Y, G = X[keep], Y[keep], G[keep]
+    plan = _plan(g, prec)
+    w = pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    pf.pf_sync(plan)
+    ref = OV.regularize(_og(g), X, Y, G)
+    # the fixed-point step of a tile grows with its record count x max|Gamma|
+    # (each term is rounded to 2^-sh with 2^(61-sh) > count max|Gamma|): a
+    # 70000-record tile leaves ~2e-13 in FP64, within the FP64 path's 1e-12
+    assert rel(w.cpu().numpy(), ref) < TOL[prec] / (1.0 if prec == pf.PF_FP64 else 10.0)
+    w2 = pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    assert torch.equal(w, w2)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
 @pytest.mark.parametrize("nx,ny", [(64, 64), (100, 77), (37, 45), (128, 48), (300, 200), (600, 100)])
 def test_poisson_solve(prec, nx, ny):
     g, X, Y, G = _case(nx, ny, 200, 12)
