@@ -154,6 +154,17 @@ pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const 
 pf_status pf_vic_velocity_host(pf_plan plan, const double* X, const double* Y, const double* Gam,
                                int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 
+/* Same step with HOST buffers, asynchronous: the inputs are copied by the
+ * copy engine into the plan's device staging buffer, the step runs, and uq,
+ * vq are copied back, all queued on the plan's stream; the call returns
+ * without waiting.  X, Y, Gam must stay unchanged and uq, vq unread until
+ * pf_sync(plan) returns.  With page-locked buffers the copies of one plan
+ * overlap the kernels of another, so a caller alternating two plans keeps
+ * the host link and the GPU busy together.  Errors of the queued work are
+ * reported by pf_sync. */
+pf_status pf_vic_velocity_host_async(pf_plan plan, const double* X, const double* Y, const double* Gam,
+                                     int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
+
 /* ------------------------------------------------------- immersed body */
 
 #define PF_MAX_SURFACE_POINTS 4096

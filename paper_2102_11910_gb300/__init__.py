@@ -168,6 +168,25 @@ def pf_vic_velocity_host(plan, X, Y, G, Uinf=0.0, Vinf=0.0, uq=None, vq=None):
     return uq, vq
 
 
+def pf_vic_velocity_host_async(plan, X, Y, G, Uinf, Vinf, uq, vq):
+    """Asynchronous host-buffer step: queues the copies in, the step and the
+    copies out on the plan's stream and returns.  X, Y, G, uq, vq are CPU
+    tensors (page-locked for the copies to overlap other work); they are in use
+    until pf_sync(plan) returns."""
+    n = X.numel()
+    for t, nm in ((X, "X"), (Y, "Y"), (G, "G")):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("%s must be a contiguous CPU float64 tensor of %d elements" % (nm, n))
+    for t, nm in ((uq, "uq"), (vq, "vq")):
+        if t.is_cuda or t.dtype != plan.dtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("%s must be a contiguous CPU %s tensor of %d elements" % (nm, plan.dtype, n))
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_vic_velocity_host_async(plan.handle, c(X.data_ptr()), c(Y.data_ptr()),
+                                                           c(G.data_ptr()), n, float(Uinf), float(Vinf),
+                                                           c(uq.data_ptr()), c(vq.data_ptr())),
+                  "pf_vic_velocity_host_async", plan.handle)
+
+
 def pf_timing_enable(plan, on=True):
     _native.check(_native.lib().pf_timing_enable(plan.handle, 1 if on else 0), "pf_timing_enable", plan.handle)
 

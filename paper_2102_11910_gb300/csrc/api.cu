@@ -332,15 +332,8 @@ static const double* pinned_device_ptr(const double* h) {
     return (const double*)at.devicePointer;
 }
 
-pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,
-                               double Vinf, void* uq, void* vq) {
-    if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
-    if (nv == 0) return PF_OK;
-    // page-locked inputs are read by the locate pass directly over the host link
-    // (one transfer, no staging copy); pageable inputs are copied first
-    const double* dXp = pinned_device_ptr(X);
-    const double* dYp = dXp ? pinned_device_ptr(Y) : nullptr;
-    const double* dGp = dYp ? pinned_device_ptr(G) : nullptr;
+// device staging buffers for nv vortices: inputs (3 nv doubles), outputs (2 nv reals)
+static pf_status ensure_stage(pf_plan p, int64_t nv) {
     if (nv > p->stage_cap) {
         PF_CUDA(p, cudaStreamSynchronize(p->stream));
         if (p->stage) cudaFree(p->stage);
@@ -352,6 +345,19 @@ pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, cons
         PF_CUDA(p, cudaMalloc(&p->stage_out, (size_t)2 * nv * p->esz));
         p->stage_cap = nv;
     }
+    return PF_OK;
+}
+
+pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,
+                               double Vinf, void* uq, void* vq) {
+    if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
+    if (nv == 0) return PF_OK;
+    // page-locked inputs are read by the locate pass directly over the host link
+    // (one transfer, no staging copy); pageable inputs are copied first
+    const double* dXp = pinned_device_ptr(X);
+    const double* dYp = dXp ? pinned_device_ptr(Y) : nullptr;
+    const double* dGp = dYp ? pinned_device_ptr(G) : nullptr;
+    PF_TRY(ensure_stage(p, nv));
     char* du = (char*)p->stage_out;
     char* dv = du + (size_t)nv * p->esz;
     if (dGp) {
@@ -368,6 +374,26 @@ pf_status pf_vic_velocity_host(pf_plan p, const double* X, const double* Y, cons
     PF_CUDA(p, cudaMemcpyAsync(uq, du, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
     PF_CUDA(p, cudaMemcpyAsync(vq, dv, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
     PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    return PF_OK;
+}
+
+pf_status pf_vic_velocity_host_async(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv,
+                                     double Uinf, double Vinf, void* uq, void* vq) {
+    if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
+    if (nv == 0) return PF_OK;
+    PF_TRY(ensure_stage(p, nv));
+    double* dX = p->stage;
+    double* dY = dX + nv;
+    double* dG = dY + nv;
+    char* du = (char*)p->stage_out;
+    char* dv = du + (size_t)nv * p->esz;
+    // copy-engine transfers: the SMs stay free for another plan's kernels
+    PF_CUDA(p, cudaMemcpyAsync(dX, X, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(dY, Y, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(dG, G, nv * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PF_TRY(pf_vic_velocity(p, dX, dY, dG, nv, Uinf, Vinf, du, dv));
+    PF_CUDA(p, cudaMemcpyAsync(uq, du, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaMemcpyAsync(vq, dv, nv * p->esz, cudaMemcpyDeviceToHost, p->stream));
     return PF_OK;
 }
 

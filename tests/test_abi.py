@@ -22,6 +22,8 @@ def test_null_arguments_are_rejected_without_touching_the_gpu():
     assert L.pf_plan_create(None, None, None) == 1          # PF_ERR_ARG
     assert L.pf_sync(None, None) == 1
     assert L.pf_regularize(None, None, None, None, 0, None) == 1
+    assert L.pf_vic_velocity_host(None, None, None, None, 1, 0.0, 0.0, None, None) == 1
+    assert L.pf_vic_velocity_host_async(None, None, None, None, 1, 0.0, 0.0, None, None) == 1
     desc = _native.PfGridDesc(4, 4, 0.1, 0.0, 0.0, 0)      # nx < 8
     h = ctypes.c_void_p()
     assert L.pf_plan_create(ctypes.byref(desc), None, ctypes.byref(h)) == 1

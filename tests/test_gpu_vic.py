@@ -162,6 +162,39 @@ def test_vic_velocity_end_to_end(prec, n, nv):
     assert torch.equal(hu, uq.cpu()) and torch.equal(hv, vq.cpu())
 
 
+def test_async_host_steps_on_two_plans_in_turn_match_the_device_step():
+    """pf_vic_velocity_host_async on two plans in turn (each synchronised
+    before its next step, the other's step in flight meanwhile) gives, step
+    after step, bitwise the velocities of the device-buffer step."""
+    g, X, Y, G = _case(128, 128, 3000, 18, variance=1e-4)
+    plans = [_plan(g, pf.PF_MIXED) for _ in range(2)]
+    ru, rv = pf.pf_vic_velocity(plans[0], _dev(X), _dev(Y), _dev(G), 0.25, -0.1)
+    pf.pf_sync(plans[0])
+    ru, rv = ru.cpu(), rv.cpu()
+    hX, hY, hG = (torch.from_numpy(a).pin_memory() for a in (X, Y, G))
+    outs = [(torch.full((len(X),), float("nan")).pin_memory(), torch.full((len(X),), float("nan")).pin_memory())
+            for _ in range(2)]
+    for k in range(6):
+        pl, (hu, hv) = plans[k % 2], outs[k % 2]
+        if k >= 2:
+            pf.pf_sync(pl)
+            assert torch.equal(hu, ru) and torch.equal(hv, rv)
+            hu.fill_(float("nan"))
+            hv.fill_(float("nan"))
+        pf.pf_vic_velocity_host_async(pl, hX, hY, hG, 0.25, -0.1, hu, hv)
+    for pl, (hu, hv) in zip(plans, outs):
+        pf.pf_sync(pl)
+        assert torch.equal(hu, ru) and torch.equal(hv, rv)
+    # pageable host buffers take the same path (their copies do not overlap)
+    pu, pv = torch.empty(len(X)), torch.empty(len(X))
+    pf.pf_vic_velocity_host_async(plans[1], torch.from_numpy(X), torch.from_numpy(Y), torch.from_numpy(G),
+                                  0.25, -0.1, pu, pv)
+    pf.pf_sync(plans[1])
+    assert torch.equal(pu, ru) and torch.equal(pv, rv)
+    with pytest.raises(ValueError):
+        pf.pf_vic_velocity_host_async(plans[1], hX, hY, hG, 0.25, -0.1, pu, pv[:-1])
+
+
 def test_out_of_domain_is_reported_not_dropped_silently():
     g, X, Y, G = _case(64, 64, 100, 16)
     X = X.copy()
