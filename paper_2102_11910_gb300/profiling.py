@@ -1,9 +1,11 @@
 """Summaries of ncu output for the step kernels.
 
 Usage:
-  python -m paper_2102_11910_gb300.profiling launches launches.csv
+  python -m paper_2102_11910_gb300.profiling launches launches.csv [N]
       per kernel: launches, total device time and share, from an ncu CSV of
       gpu__time_duration.sum (one pass; cold-cache, serialised launches);
+      with N, the step-kernel table counts only the first N launches of each
+      step kernel (the device-resident steps a bench run starts with);
   python -m paper_2102_11910_gb300.profiling traffic traffic.csv
       per step kernel: DRAM bytes read + written per launch, from
       `ncu -i report --page raw --csv` or `ncu --metrics ... --csv`, as the
@@ -49,10 +51,12 @@ def _rows(path):
     return rows[hi], rows[hi + 1:]
 
 
-def launches(path):
+def launches(path, first=None):
     h, body = _rows(path)
     ki, mi, ui = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Unit")
     tot, cnt = collections.OrderedDict(), collections.Counter()
+    ftot, fcnt = collections.OrderedDict(), collections.Counter()
+    first = int(first) if first is not None else None
     scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3, "s": 1e6,
              "second": 1e6}
     for r in body:
@@ -62,19 +66,24 @@ def launches(path):
         name = kernel_name(r[ki])
         tot[name] = tot.get(name, 0.0) + us
         cnt[name] += 1
+        if name in STEP_KERNELS and (first is None or fcnt[name] < first):
+            ftot[name] = ftot.get(name, 0.0) + us
+            fcnt[name] += 1
 
-    def table(names, title):
+    def table(tot, cnt, names, title):
         T = sum(tot[k] for k in names)
         print(title)
-        print("%-34s %8s %12s %7s" % ("kernel", "launches", "total_us", "share"))
+        print("%-34s %8s %12s %7s %9s" % ("kernel", "launches", "total_us", "share", "avg_us"))
         for k in sorted(names, key=lambda x: -tot[x]):
-            print("%-34s %8d %12.1f %6.1f%%" % (k, cnt[k], tot[k], 100 * tot[k] / T))
+            print("%-34s %8d %12.1f %6.1f%% %9.2f" % (k, cnt[k], tot[k], 100 * tot[k] / T, tot[k] / cnt[k]))
         print()
 
-    table(list(tot), "all launches")
-    step = [k for k in tot if k in STEP_KERNELS]
-    if step:
-        table(step, "kernels of the VIC step only (plan set-up and torch fills excluded)")
+    table(tot, cnt, list(tot), "all launches")
+    if ftot:
+        title = "kernels of the VIC step only (plan set-up and torch fills excluded)"
+        if first is not None:
+            title += ", first %d launches of each" % first
+        table(ftot, fcnt, list(ftot), title)
 
 
 def traffic(path):
@@ -113,4 +122,4 @@ def traffic(path):
 
 
 if __name__ == "__main__":
-    {"launches": launches, "traffic": traffic}[sys.argv[1]](sys.argv[2])
+    {"launches": launches, "traffic": traffic}[sys.argv[1]](*sys.argv[2:])
