@@ -26,6 +26,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# 32 hardware work queues (read when CUDA starts, so before torch is imported):
+# the batched and served workloads run one stream per instance
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "VIC steps/s (R+L^-1+Schur+E) at <=1e-5 rel err vs FP64; p50/p99 latency"
 UNIT = "steps/s"

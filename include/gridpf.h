@@ -424,7 +424,14 @@ pf_status pf_step_multi(pf_plan plan, pf_state state, int32_t n_bodies, const pf
 
 /* Independent instances, one step each: pf_step for plans[i], states[i],
  * bodies[i] (i < n), each enqueued on its own plan's stream so instances on
- * distinct streams overlap on the device.  Stops at the first error. */
+ * distinct streams overlap on the device.  When the process runs with
+ * CUDA_DEVICE_MAX_CONNECTIONS >= 32 (set before CUDA starts), a batch of more
+ * than 8 distinct plans and states is enqueued from several host threads (up
+ * to 16, on the caller's device), taking the instances in turn; otherwise,
+ * and when a plan or a state appears twice, the calling thread enqueues the
+ * instances in order.
+ * Returns the first error met; after an error the instances not yet taken
+ * are not stepped. */
 pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
                         double dt, int32_t scheme);
 

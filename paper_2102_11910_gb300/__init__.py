@@ -535,7 +535,9 @@ def pf_step(plan, state, dt, body=None, scheme=0):
 
 
 def pf_step_batch(plans, states, bodies, dt, scheme=0):
-    """One step of many independent instances (each on its own plan's stream)."""
+    """One step of many independent instances (each on its own plan's stream;
+    a large batch of distinct plans and states is enqueued from several host
+    threads)."""
     n = len(plans)
     P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     S = (ctypes.c_void_p * n)(*[s.handle.value for s in states])

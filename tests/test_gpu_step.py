@@ -104,3 +104,57 @@ def test_step_capacity_is_enforced():
     with pytest.raises(pf.GridPfError) as e:
         pf.pf_step(plan, state, 0.01, pf.plate_kinematics(16, 1.0, 0.3, Uinf=1.0))
     assert e.value.name == "PF_ERR_CAPACITY"
+
+
+def test_step_batch_from_host_threads_matches_single_steps(monkeypatch):
+    """pf_step_batch on 20 independent 128^2 instances (enqueued from several
+    host threads: the library reads CUDA_DEVICE_MAX_CONNECTIONS at each call)
+    gives, instance by instance and bitwise, the states of pf_step called on
+    each one alone; a batch naming one plan twice is stepped in order and
+    matches too."""
+    monkeypatch.setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    rng = np.random.default_rng(1003)
+    inst = [inputs.batched_instance(rng, shape=(128, 128)) for _ in range(20)]
+    g = inst[0]["grid"]
+    base = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED)
+
+    def make():
+        plans, states, bodies = [], [], []
+        for r in inst:
+            p = pf.pf_plan_clone(base, pf.PF_MIXED, torch.cuda.Stream())
+            st = pf.State(p, len(r["X"]) + 16)
+            pf.pf_state_set(st, r["X"], r["Y"], r["G"])
+            b = r["body"]
+            plans.append(p)
+            states.append(st)
+            bodies.append(pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"]))
+        return plans, states, bodies
+
+    pa, sa, ba = make()
+    pb, sb, bb = make()
+    for _ in range(2):
+        pf.pf_step_batch(pa, sa, ba, 0.002)
+        for p, st, b in zip(pb, sb, bb):
+            pf.pf_step(p, st, 0.002, b)
+    for p in pa + pb:
+        pf.pf_sync(p)
+    for s1, s2 in zip(sa, sb):
+        a, b = pf.pf_state_get(s1), pf.pf_state_get(s2)
+        assert len(a[0]) == len(b[0]) > 0
+        for u, v in zip(a[:3], b[:3]):
+            assert np.array_equal(u, v)
+    # one plan named twice: two states stepped in order on it
+    shared = pf.pf_plan_clone(base, pf.PF_MIXED, torch.cuda.Stream())
+    sc = [pf.State(shared, len(inst[k]["X"]) + 16) for k in (0, 1)]
+    for st, k in zip(sc, (0, 1)):
+        pf.pf_state_set(st, inst[k]["X"], inst[k]["Y"], inst[k]["G"])
+    pd, sd, bd = make()
+    plans = [shared, shared] + pd[2:]
+    states = sc + sd[2:]
+    pf.pf_step_batch(plans, states, bd, 0.002)
+    pf.pf_step_batch(plans, states, bd, 0.002)
+    pf.pf_sync(shared)
+    for k in (0, 1):
+        a, b = pf.pf_state_get(sc[k]), pf.pf_state_get(sb[k])
+        for u, v in zip(a[:3], b[:3]):
+            assert np.array_equal(u, v)
