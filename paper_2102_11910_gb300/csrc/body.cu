@@ -240,70 +240,95 @@ __global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* _
                                                                   int* __restrict__ perm, int* __restrict__ gperm,
                                                                   double* __restrict__ LU, double tiny,
                                                                   int* __restrict__ status) {
+    static_assert(BGJ_PANEL_THREADS == 32 * 32 && BGJ_MAX <= 32 * 32,
+                  "32 warps; a lane's rows lane + 32 k (k < 32) fit one bit mask");
     extern __shared__ float sp[];                  // (n - k0) x 33 FP32 copy of the panel
+    __shared__ int used[BGJ_MAX];
     __shared__ int rowid[BGJ_MAX];                 // local row i of the permuted panel = local row rowid[i]
     __shared__ int gp[BGJ_MAX];
-    __shared__ float wv[32];
-    __shared__ int wi[32];
-    __shared__ int piv_s;
+    __shared__ int wsum[32];
     __shared__ double A[BGJ_B][BGJ_B + 1];
+    __shared__ double rpiv[BGJ_B];
     const int m = n - k0, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     pdl_wait();
     for (int idx = tid; idx < m * kb; idx += blockDim.x) {
         const int i = idx / kb, j = idx - (idx / kb) * kb;
         sp[i * 33 + j] = (float)X[(size_t)(k0 + i) * n + k0 + j];
     }
-    for (int i = tid; i < m; i += blockDim.x) rowid[i] = i;
     __syncthreads();
+    // Pivot rows by partial pivoting on the FP32 copy.  Rows are not moved:
+    // warp 0 keeps, lane by lane, a bit mask of the rows lane + 32 k already
+    // taken as pivots, finds each pivot and publishes it with the masks; the
+    // block then eliminates the pivot's column from the rows not taken.  (The
+    // kernel runs on one SM and is bound by instruction issue, so the search
+    // is done once, not by every warp.)
+    __shared__ unsigned tk[32];
+    __shared__ int piv_s;
+    unsigned taken = 0u;
+    if (tid < 32) tk[tid] = 0u;
     for (int c = 0; c < kb; ++c) {
-        // the largest |panel[i][c]| over i >= c, lowest i on ties
-        float best = -1.f;
-        int bi = m;
-        for (int i = c + tid; i < m; i += blockDim.x) {
-            const float v = fabsf(sp[i * 33 + c]);
-            if (v > best) { best = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float v2 = __shfl_down_sync(0xffffffffu, best, o);
-            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
-        }
-        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
-        __syncthreads();
         if (wid == 0) {
-            best = lane < (int)(blockDim.x >> 5) ? wv[lane] : -1.f;
-            bi = lane < (int)(blockDim.x >> 5) ? wi[lane] : m;
+            // the largest |panel[i][c]| over rows i not yet taken, lowest i on
+            // ties; all NaN: the lowest row not taken
+            float best = -1.f;
+            int bi = m, first = m;
+            for (int k = 0, i = lane; i < m; ++k, i += 32) {
+                if ((taken >> k) & 1u) continue;
+                first = min(first, i);
+                const float v = fabsf(sp[i * 33 + c]);
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
+            }
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_down_sync(0xffffffffu, best, o);
-                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+                const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+                if (v2 > best || (v2 == best && i2 < bi)) {
+                    best = v2;
+                    bi = i2;
+                }
             }
-            if (lane == 0) piv_s = bi < m ? bi : c;
+            const int pr = bi < m ? bi : (first < m ? first : 0);   // a row not taken exists: c < kb <= m
+            if (lane == (pr & 31)) {
+                taken |= 1u << (pr >> 5);
+                tk[lane] = taken;
+            }
+            if (lane == 0) {
+                piv_s = pr;
+                rowid[c] = pr;
+            }
         }
         __syncthreads();
+        // lane = column, warp w takes the rows w + 32 k not taken
         const int pr = piv_s;
-        if (pr != c) {
-            if (tid < kb) {
-                const float t = sp[c * 33 + tid];
-                sp[c * 33 + tid] = sp[pr * 33 + tid];
-                sp[pr * 33 + tid] = t;
-            }
-            if (tid == BGJ_B) {
-                const int t = rowid[c];
-                rowid[c] = rowid[pr];
-                rowid[pr] = t;
-            }
-        }
-        __syncthreads();
-        // eliminate column c from the rows below it (only they are pivot candidates):
-        // lane = column, warps over rows, one reciprocal of the pivot
-        const float pv = sp[c * 33 + c];
+        const unsigned rows_taken = tk[wid];
+        const float pv = sp[pr * 33 + c];
         if (pv != 0.f && lane > c && lane < kb) {
-            const float q = sp[c * 33 + lane] / pv;
-            for (int i = c + 1 + wid; i < m; i += (int)(blockDim.x >> 5)) sp[i * 33 + lane] -= sp[i * 33 + c] * q;
+            const float q = sp[pr * 33 + lane] / pv;
+            for (int k = 0, i = wid; i < m; ++k, i += 32)
+                if (!((rows_taken >> k) & 1u)) sp[i * 33 + lane] -= sp[i * 33 + c] * q;
         }
         __syncthreads();
     }
+    // the rows not taken follow the pivots, in ascending order
+    for (int i = tid; i < m; i += blockDim.x) used[i] = (int)((tk[i & 31] >> (i >> 5)) & 1u);
+    __syncthreads();
+    const int free_i = tid < m && !used[tid] ? 1 : 0;
+    int incl = free_i;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int before = incl - free_i;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    if (free_i) rowid[kb + before] = tid;
+    __syncthreads();
     // this panel's permutation (rows < k0 stay) and the accumulated one
     for (int i = tid; i < m; i += blockDim.x) {
         perm[k0 + i] = k0 + rowid[i];
@@ -311,27 +336,35 @@ __global__ void __launch_bounds__(BGJ_PANEL_THREADS) k_bgj_panel(const double* _
     }
     __syncthreads();
     for (int i = tid; i < m; i += blockDim.x) gperm[k0 + i] = gp[i];
-    // FP64 LU of the permuted pivot block, one entry per thread; lanes run down a
-    // column (warp j holds column j), and one thread forms each pivot's
-    // reciprocal: FP64 division is a long sequence at this GPU's FP64 rate
-    __shared__ double rpiv[BGJ_B];
-    const int i = tid & 31, j = tid >> 5;
+    // FP64 LU of the permuted pivot block, thread (i, j) = (warp, lane) owning
+    // entry (i, j), one block barrier per column: at step c, rows i > c take
+    // l_i = A[i][c] / U_cc (kept apart in Lf, so A[i][c] is never written while
+    // it is read) and update A[i][j], j > c, from row c, which no thread writes
+    // in this step.  The thread of entry (c + 1, c + 1) forms the next pivot's
+    // reciprocal as soon as its last update is done (FP64 division is a long
+    // sequence at this GPU's FP64 rate: one thread per pivot).
+    __shared__ double Lf[BGJ_B][BGJ_B + 1];
+    const int i = tid >> 5, j = lane;
     const bool mine = i < kb && j < kb;
     if (mine) A[i][j] = X[(size_t)(k0 + rowid[i]) * n + k0 + j];
     __syncthreads();
+    auto pivot = [&](int c) {
+        const double pv = A[c][c];
+        if (!(fabs(pv) > tiny)) atomicOr(status, ST_SINGULAR);
+        rpiv[c] = 1.0 / (pv == 0.0 ? 1.0 : pv);
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
     for (int c = 0; c < kb; ++c) {
-        if (tid == 0) {
-            const double pv = A[c][c];
-            if (!(fabs(pv) > tiny)) atomicOr(status, ST_SINGULAR);
-            rpiv[c] = 1.0 / (pv == 0.0 ? 1.0 : pv);
+        if (mine && i > c && j >= c) {
+            const double l = A[i][c] * rpiv[c];
+            if (j == c) Lf[i][c] = l;
+            else A[i][j] -= l * A[c][j];
+            if (i == c + 1 && j == c + 1) pivot(c + 1);
         }
         __syncthreads();
-        if (mine && i > c && j == c) A[i][c] *= rpiv[c];
-        __syncthreads();
-        if (mine && i > c && j > c) A[i][j] -= A[i][c] * A[c][j];
-        __syncthreads();
     }
-    if (mine) LU[i * BGJ_B + j] = A[i][j];
+    if (mine) LU[i * BGJ_B + j] = j < i ? Lf[i][j] : A[i][j];
     if (tid < kb) LU[BGJ_B * BGJ_B + tid] = rpiv[tid];
 }
 
