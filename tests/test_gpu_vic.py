@@ -245,3 +245,45 @@ def test_full_size_vic_sampled_against_oracle():
             v_s.append(OV.interpolate(big, V, X[q:q + 1], Y[q:q + 1])[0])
         got = np.concatenate([uq.cpu().numpy()[qs], vq.cpu().numpy()[qs]])
         assert rel(got, np.concatenate([u_s, v_s])) < TOL[prec]
+
+
+def test_largest_grid_sampled_against_oracle():
+    """The largest grid a plan takes along x, 2048 x 1800 nodes (4096-point
+    padded transforms on both axes; 1800 rows leave a ragged last row of
+    tiles), 2e5 vortices: w on every node, psi and vortex velocities at
+    sampled points by the oracle's direct sums."""
+    nx, ny, nv = 2048, 1800, 200_000
+    g = inputs.centred_grid(nx, ny, 2.0 / (nx - 1))
+    rng = np.random.default_rng(23)
+    hx, hy = 0.5 * (nx - 1) * g.dx, 0.5 * (ny - 1) * g.dx
+    X, Y, G = inputs.uniform_vortices(rng, nv, -0.8 * hx, 0.8 * hx, 1e-4, -0.8 * hy, 0.8 * hy)
+    og = _og(g)
+    w_ref = OV.regularize(og, X, Y, G)
+    tab = lgf_table(nx + 1, ny + 1)
+    ti = np.concatenate([[0, nx - 1, 0, nx - 1], rng.integers(0, nx, 8)])
+    tj = np.concatenate([[0, 0, ny - 1, ny - 1], rng.integers(0, ny, 8)])
+    psi_ref = -OV.inv_laplacian_at(og, w_ref, ti, tj, tab)
+    qs = rng.integers(0, nv, 4)
+    u_s, v_s = [], []
+    for q in qs:
+        ci = int(math.floor((X[q] - g.x0) / g.dx)); cj = int(math.floor((Y[q] - g.y0) / g.dx))
+        bi, bj = np.meshgrid(np.arange(ci - 1, ci + 3), np.arange(cj - 1, cj + 3))
+        un, vn = OV.node_velocity_at(og, w_ref, bi.ravel(), bj.ravel(), tab)
+        box = OV.Grid(8, 8, g.dx, g.x0 + (ci - 3) * g.dx, g.y0 + (cj - 3) * g.dx)
+        U = np.zeros((8, 8)); V = np.zeros((8, 8))
+        U[2:6, 2:6] = un.reshape(4, 4); V[2:6, 2:6] = vn.reshape(4, 4)
+        u_s.append(OV.interpolate(box, U, X[q:q + 1], Y[q:q + 1])[0])
+        v_s.append(OV.interpolate(box, V, X[q:q + 1], Y[q:q + 1])[0])
+    for prec in (pf.PF_FP64, pf.PF_MIXED):
+        plan = _plan(g, prec)
+        assert plan.P == 4096 and plan.Q == 4096
+        dX, dY, dG = _dev(X), _dev(Y), _dev(G)
+        w = pf.pf_regularize(plan, dX, dY, dG)
+        psi = pf.pf_poisson_solve(plan, w).cpu().numpy()
+        uq, vq = pf.pf_vic_velocity(plan, dX, dY, dG)
+        pf.pf_sync(plan)
+        assert rel(w.cpu().numpy(), w_ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+        assert rel(psi[tj, ti], psi_ref) < TOL[prec]
+        got = np.concatenate([uq.cpu().numpy()[qs], vq.cpu().numpy()[qs]])
+        assert rel(got, np.concatenate([u_s, v_s])) < TOL[prec]
+        del plan
