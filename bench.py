@@ -41,6 +41,18 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over the ranks of the process group (x itself on one rank):
+    every timing of a multi-GPU run is the slowest rank's."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ oracle timing
 ORACLE_SAMPLE = r"""
 import json, sys, time
@@ -220,11 +232,7 @@ def bench_ours(args):
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
         pf.pf_sync(plan)
         per = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        total_ms = sum(per)
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(per), world)
         value = world * K / (total_ms / 1e3)
         ms_per_step = total_ms / K
         srt = sorted(per)
@@ -307,6 +315,7 @@ def bench_ours(args):
     for pl in plans:
         pf.pf_sync(pl)
     tp = time.perf_counter() - t0
+    te, tp = max_over_ranks(te, world), max_over_ranks(tp, world)
     e2e = {"value": world * KP / tp, "unit": UNIT, "h2d_bytes_per_step": 24 * nv, "d2h_bytes_per_step": 8 * nv,
            "mode": "pf_vic_velocity_host_async on a ring of %d plans (pipelined), %d steps" % (NPIPE, KP),
            "sync_value": world * KE / te, "sync_mode": "pf_vic_velocity_host, one synchronous call per step"}
