@@ -283,12 +283,6 @@ constexpr int OFF_TILES = 8, OFF_SEGS = 128, OFF_RUN = 5;
 static_assert(OFF_SEGS * OFF_RUN >= BIN_MAX_BLOCKS, "k_offsets covers every block");
 static_assert(OFF_TILES * OFF_SEGS == 1024, "k_offsets runs 1024 threads");
 
-__device__ __forceinline__ int warp_sum(int v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {

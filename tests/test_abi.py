@@ -31,3 +31,19 @@ def test_null_arguments_are_rejected_without_touching_the_gpu():
     assert L.pf_plan_create(ctypes.byref(desc), None, ctypes.byref(h)) == 1
     desc = _native.PfGridDesc(64, 64, 0.1, 0.0, 0.0, 7)    # bad precision
     assert L.pf_plan_create(ctypes.byref(desc), None, ctypes.byref(h)) == 1
+
+
+def test_header_is_plain_c_and_cpp():
+    """include/gridpf.h compiles as C99 and as C++ with warnings as errors:
+    the boundary carries no C++ or torch types."""
+    import os
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = os.path.join(root, "include", "gridpf.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip("%s not installed" % cc)
+        r = subprocess.run([cc, "-fsyntax-only", std, "-Wall", "-Wextra", "-Werror", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
