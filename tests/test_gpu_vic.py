@@ -208,6 +208,27 @@ def test_out_of_domain_is_reported_not_dropped_silently():
     assert pf.pf_sync(plan) == 0       # the status is cleared once reported
 
 
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_odd_count_across_blocks_and_out_of_domain(prec):
+    """5001 vortices over several binning blocks, the last one odd-sized, 7
+    of them off the grid (first and last vortices among them): w matches the
+    oracle on the others, and the 7 are reported."""
+    g, X, Y, G = _case(96, 80, 5001, 19)
+    X, Y = X.copy(), Y.copy()
+    off = [0, 1, 777, 2048, 4095, 4999, 5000]
+    X[off[:4]] = g.x0 - 3.0 * g.dx
+    Y[off[4:]] = g.y0 + (g.ny + 2) * g.dx
+    keep = np.ones(len(X), bool)
+    keep[off] = False
+    plan = _plan(g, prec)
+    w = pf.pf_regularize(plan, _dev(X), _dev(Y), _dev(G))
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_sync(plan)
+    assert e.value.name == "PF_ERR_OUT_OF_DOMAIN" and "7 points" in str(e.value)
+    ref = OV.regularize(_og(g), X[keep], Y[keep], G[keep])
+    assert rel(w.cpu().numpy(), ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
+
+
 def test_full_size_vic_sampled_against_oracle():
     """1024^2 nodes, 1e6 vortices: w on every node, and psi / velocity at sampled
     nodes and vortices computed one by one by the oracle's direct sums."""
