@@ -183,3 +183,49 @@ def test_fft_and_sparse_routes_of_the_surface_rhs_match_the_direct_sum(prec, rou
     ff, gf, _ = out[route]
     tol = cond * 1e-14
     assert rel(ff, fd) < tol and rel(gf, gd) < tol
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_pitching_plate_size_sheet_matches_oracle(prec):
+    """The pitching-plate configuration at full size: 768 x 512 nodes, dx 0.01,
+    plate of 256 points at 30 deg (dS/dx = 0.39, cond(S) ~ 2e9), 2000 vortices
+    in its wake, body rotating in the stream.  Factor (f0, Gamma0) and a
+    two-edge shedding sheet against the oracle, whose E L^-1 w comes from
+    direct sums at the surface stencil nodes; tolerances scale with cond(S)."""
+    pw = inputs.pitching_plate_512x768()
+    gs = pw["grid"]
+    g = OV.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    b = inputs.plate(pw["ns"], pw["chord"], pw["alpha0"])
+    tab = lgf_table(gs.nx + 1, gs.ny + 1)
+    st = OB.SurfaceStencil(g, b.x, b.y)
+    S = OB.schur_matrix(g, st, b.ds, tab)
+    sch = OB.Schur(S, b.ds)
+    tol = np.linalg.cond(S) * 1e-15
+    rng = np.random.default_rng(31)
+    X, Y, G = inputs.uniform_vortices(rng, 2000, 0.7, 3.0, 1e-3, -1.2, 1.2)
+    w = OV.regularize(g, X, Y, G)
+    k1, k2 = b.edges
+    X1 = np.array([b.x[k1] - 3 * gs.dx, b.x[k2] + 3 * gs.dx])
+    Y1 = np.array([b.y[k1] + 2 * gs.dx, b.y[k2] - 2 * gs.dx])
+    E = OB.EinvL_unit_vortex(g, st, X1, Y1, tab)
+    motion = (0.05, -0.1, 0.4, 1.0, 0.0)
+    sbp = OB.sb_prime(b.x, b.y, *motion)
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, prec)
+    schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)
+    gamma0, f0, _ = pf.pf_schur_info(schur)
+    assert rel(f0, sch.f0) < tol
+    assert abs(gamma0 - sch.Gamma0) < tol * abs(sch.Gamma0)
+    w_dev = torch.from_numpy(w).to(device="cuda", dtype=plan.dtype).contiguous()
+    w_used = w_dev.double().cpu().numpy()
+    # E L^-1 w = -E psi, psi = -L^-1 w summed directly at the stencil nodes
+    nodes, inv = np.unique(np.stack([st.NI.ravel(), st.NJ.ravel()], 1), axis=0, return_inverse=True)
+    psi_nodes = -OV.inv_laplacian_at(g, w_used, nodes[:, 0], nodes[:, 1], tab)
+    EinvLw = -np.sum(st.W * psi_nodes[inv.reshape(st.W.shape)], axis=1)
+    Gw = OV.circulation(g, w_used)
+    f_ref, _, s0_ref, G1, G2 = OB.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+    f, gam, s0 = pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2], X1, Y1)
+    pf.pf_sync(plan)
+    assert rel(f.cpu().numpy(), f_ref) < tol
+    assert abs(s0 - s0_ref) < tol * max(1.0, abs(s0_ref))
+    for a, r in zip(gam, (G1, G2)):
+        assert abs(a - r) < tol * abs(r)
