@@ -557,19 +557,33 @@ __global__ void __launch_bounds__(SHEET_SORT_THREADS) k_sheet_order(const int* _
         }
     }
     __syncthreads();
+    // Stages whose partner distance j is below SEG stay inside SEG-key
+    // segments; warp w owns segments w, w + 32, ... and runs them with warp
+    // barriers only, so block barriers remain for the j >= SEG stages.
+    // Pair p of a stage (p < n2 / 2) is the key index with a zero bit
+    // inserted at bit log2(j), and its partner has that bit set.
+    constexpr int SEG = 64;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto cmpx = [&](int p, int j, int k) {
+        const int lo = p & (j - 1);
+        const int i = ((p - lo) << 1) | lo, l = i | j;
+        const unsigned long long x = key[i], y = key[l];
+        if ((x > y) == ((i & k) == 0)) {
+            key[i] = y;
+            key[l] = x;
+        }
+    };
     for (int k = 2; k <= n2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long x = key[i], y = key[l];
-                    if ((x > y) == ((i & k) == 0)) {
-                        key[i] = y;
-                        key[l] = x;
-                    }
-                }
+            if (j >= SEG) {
+                for (int p = threadIdx.x; p < (n2 >> 1); p += blockDim.x) cmpx(p, j, k);
+                __syncthreads();
+            } else {
+                // this warp's segments: SEG / 2 pairs each, one per lane
+                for (int sgm = wid; sgm * SEG < n2; sgm += nw) cmpx(sgm * (SEG / 2) + lane, j, k);
+                __syncwarp();
+                if (j == 1) __syncthreads();   // the next k begins with a block-wide distance
             }
-            __syncthreads();
         }
     for (int i = threadIdx.x; i < ne; i += blockDim.x) {
         sorder[i] = (int)(key[i] & 0xFFFFull);
