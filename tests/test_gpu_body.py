@@ -229,3 +229,49 @@ def test_pitching_plate_size_sheet_matches_oracle(prec):
     assert abs(s0 - s0_ref) < tol * max(1.0, abs(s0_ref))
     for a, r in zip(gam, (G1, G2)):
         assert abs(a - r) < tol * abs(r)
+
+
+@pytest.mark.parametrize("seed,prec", [(5, pf.PF_FP64), (8, pf.PF_MIXED)])
+def test_largest_served_instance_sheet_matches_oracle(seed, prec):
+    """A body at the served path's largest size: 1024^2 nodes, 1e5 vortices,
+    Ns ~ 160-270 (seed 5: an ellipse under Kelvin's condition; seed 8: a plate
+    shedding at both edges).  The GPU forms E L^-1 w by its FP64 FFT route at
+    this size, whose rounding (~1e-15 relative) cond(S) amplifies: the
+    tolerance is cond(S) 1e-14, at least 1e-11."""
+    r = inputs.batched_instance(np.random.default_rng(seed), big=True)
+    gs, b = r["grid"], r["body"]
+    g = OV.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    xb, yb, ds = b["xb"], b["yb"], b["ds"]
+    tab = lgf_table(gs.nx + 1, gs.ny + 1)
+    st = OB.SurfaceStencil(g, xb, yb)
+    S = OB.schur_matrix(g, st, ds, tab)
+    sch = OB.Schur(S, ds)
+    tol = max(np.linalg.cond(S) * 1e-14, 1e-11)
+    w = OV.regularize(g, r["X"], r["Y"], r["G"])
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, prec)
+    schur = pf.pf_schur_factor(plan, xb, yb, ds)
+    w_dev = torch.from_numpy(w).to(device="cuda", dtype=plan.dtype).contiguous()
+    w_used = w_dev.double().cpu().numpy()
+    nodes, inv = np.unique(np.stack([st.NI.ravel(), st.NJ.ravel()], 1), axis=0, return_inverse=True)
+    psi_nodes = -OV.inv_laplacian_at(g, w_used, nodes[:, 0], nodes[:, 1], tab)
+    EinvLw = -np.sum(st.W * psi_nodes[inv.reshape(st.W.shape)], axis=1)
+    Gw = OV.circulation(g, w_used)
+    motion = (0.0, 0.0, 0.2, r["Uinf"], 0.0)
+    sbp = OB.sb_prime(xb, yb, *motion)
+    if b["edges"]:
+        k1, k2 = b["edges"]
+        X1 = np.array([xb[k1] - 3 * gs.dx, xb[k2] + 3 * gs.dx])
+        Y1 = np.array([yb[k1], yb[k2]])
+        E = OB.EinvL_unit_vortex(g, st, X1, Y1, tab)
+        f_ref, _, s0_ref, G1, G2 = OB.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+        g_ref = (G1, G2)
+        f, gam, s0 = pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2], X1, Y1)
+    else:
+        f_ref, s0_ref = OB.sheet_circulation(sch, sbp, EinvLw, -Gw)
+        g_ref = ()
+        f, gam, s0 = pf.pf_sheet_solve(plan, schur, w_dev, motion, pf.PF_SHEET_CIRCULATION, -Gw)
+    pf.pf_sync(plan)
+    assert rel(f.cpu().numpy(), f_ref) < tol
+    assert abs(s0 - s0_ref) < tol * max(1.0, abs(s0_ref))
+    for a, ref in zip(gam, g_ref):
+        assert abs(a - ref) < tol * abs(ref)
