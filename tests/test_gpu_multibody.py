@@ -98,3 +98,56 @@ def test_invalid_partitions_are_rejected(case):
             pf.pf_sheet_solve_multi(plan, schur, w, b["starts"], b["edges"], MOTIONS, wl["Gamma_w"],
                                     wl["VX"], wl["VY"])
         assert e.value.name == "PF_ERR_ARG"
+
+
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+def test_two_plates_at_the_benchmark_size(prec):
+    """The two-plate configuration of the benchmark: 384 x 256 nodes, dx 0.01,
+    two plates of chord 1 at 60 deg a half chord apart (50 points each), 1500
+    vortices downstream; Kutta at all four edges with one new vortex each,
+    Kelvin per body, each body in its own motion.  E L^-1 w of the oracle
+    comes from direct sums at the surface stencil nodes; the GPU's FP64 FFT
+    route leaves ~1e-15 relative on it, which cond(S) amplifies: tolerance
+    cond(S) 1e-14, at least 1e-11."""
+    gs = inputs.GridSpec(384, 256, 0.01, -1.0, -0.5 * 255 * 0.01)
+    g = OV.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    plates = [inputs.plate(50, 1.0, np.radians(60.0), 0.0, yc) for yc in (0.25, -0.25)]
+    x = np.concatenate([p.x for p in plates])
+    y = np.concatenate([p.y for p in plates])
+    ds = np.concatenate([p.ds for p in plates])
+    starts = [0, 50, 100]
+    edges = [(0, 49), (50, 99)]
+    # one new vortex 3 dx beyond each edge along the chord
+    VX, VY = [], []
+    for k0, k1 in edges:
+        tx, ty = x[k1] - x[k0], y[k1] - y[k0]
+        n = np.hypot(tx, ty)
+        VX += [x[k0] - 3 * gs.dx * tx / n, x[k1] + 3 * gs.dx * tx / n]
+        VY += [y[k0] - 3 * gs.dx * ty / n, y[k1] + 3 * gs.dx * ty / n]
+    VX, VY = np.array(VX), np.array(VY)
+    motions = [(0.0, 0.0, 0.0, 1.0, 0.0), (0.05, -0.02, 0.3, 1.0, 0.0)]
+    Gamma_w = np.array([0.03, -0.02])
+    rng = np.random.default_rng(41)
+    X, Y, G = inputs.uniform_vortices(rng, 1500, 0.8, 2.3, 1e-4, -0.9, 0.9)
+    tab = lgf_table(g.nx + 1, g.ny + 1)
+    st = OB.SurfaceStencil(g, x, y)
+    S = OB.schur_matrix(g, st, ds, tab)
+    sch = OB.Schur(S, ds)
+    tol = max(np.linalg.cond(S) * 1e-14, 1e-11)
+    sbp = np.concatenate([OB.sb_prime(x[lo:hi], y[lo:hi], *motions[b])
+                          for b, (lo, hi) in enumerate(zip(starts[:-1], starts[1:]))])
+    E = OB.EinvL_unit_vortex(g, st, VX, VY, tab)
+    w = OV.regularize(g, X, Y, G)
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, prec)
+    schur = pf.pf_schur_factor(plan, x, y, ds)
+    w_dev = torch.from_numpy(w).to(device="cuda", dtype=plan.dtype).contiguous()
+    w_used = w_dev.double().cpu().numpy()
+    nodes, inv = np.unique(np.stack([st.NI.ravel(), st.NJ.ravel()], 1), axis=0, return_inverse=True)
+    psi_nodes = -OV.inv_laplacian_at(g, w_used, nodes[:, 0], nodes[:, 1], tab)
+    EinvLw = -np.sum(st.W * psi_nodes[inv.reshape(st.W.shape)], axis=1)
+    f_ref, _, s0_ref, G_ref = OB.sheet_multibody_shed(sch, sbp, EinvLw, starts, edges, E, Gamma_w)
+    f, Gn, s0 = pf.pf_sheet_solve_multi(plan, schur, w_dev, starts, edges, motions, Gamma_w, VX, VY)
+    pf.pf_sync(plan)
+    assert len(Gn) == 4 and len(s0) == 2
+    assert rel(f.cpu().numpy(), f_ref) < tol
+    assert rel(s0, s0_ref) < tol and rel(Gn, G_ref) < tol
