@@ -276,8 +276,11 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
     }
 }
 
+// FP32 at P = 2048: at most 64 registers, so four blocks fit an SM and the
+// 512 blocks of a 1024-row grid run in one wave (three at 76 registers took
+// 1.12 waves: 18.2 -> 15.3 us)
 template <typename T, int R3>
-__global__ void __launch_bounds__(32 * R3) k_rows_inv_r(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
+__global__ void __launch_bounds__(32 * R3, sizeof(T) == 4 && R3 == 8 ? 4 : 1) k_rows_inv_r(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
                                                         T* __restrict__ out, int nx, int ny, int mode, T Uinf,
                                                         T Vinf, const C_t<T>* __restrict__ tw256,
                                                         const C_t<T>* __restrict__ twP) {
