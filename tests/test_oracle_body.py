@@ -100,6 +100,32 @@ def test_no_penetration_on_final_field(plate_case):
     assert np.abs(lhs - rhs).max() < 1e-15 * np.linalg.cond(sch.S) * 100 * np.abs(rhs).max()
 
 
+def test_given_s0_sheet_satisfies_no_penetration(plate_case):
+    """Basic system with s0 prescribed (Eqs. basicblock, vsheet): the sheet f of
+    sheet_given_s0 makes the total field obey the no-penetration row
+    E psi + s0 1 = s'_b, psi = -L^{-1}(w + R_s f) by direct summation, for
+    several s0 (a wrong sign on E L^{-1} w or on s0 fails here)."""
+    c = plate_case
+    g, sch, st = c["g"], c["sch"], c["st"]
+    for s0 in (0.0, 0.37, -1.2):
+        f = B.sheet_given_s0(sch, c["sbp"], c["EinvLw"], s0)
+        psi = vic.streamfunction(g, c["w"] + B.regularize_surface(g, st, f, c["b"].ds), c["tab"])
+        lhs = B.interp_surface(st, psi) + s0
+        scale = np.abs(c["sbp"]).max() + abs(s0) + np.abs(c["EinvLw"]).max()
+        assert np.abs(lhs - c["sbp"]).max() < 1e-15 * np.linalg.cond(sch.S) * 100 * scale
+
+
+def test_given_s0_reproduces_the_circulation_solve(plate_case):
+    """With s0 set to the multiplier the circulation-constrained solve returns
+    (Eq. circsystem), the basic system gives that solve's sheet."""
+    c = plate_case
+    sch = c["sch"]
+    f_c, s0 = B.sheet_circulation(sch, c["sbp"], c["EinvLw"], 0.25)
+    f = B.sheet_given_s0(sch, c["sbp"], c["EinvLw"], s0)
+    assert abs(sch.circ(f) - 0.25) < 1e-9
+    assert np.abs(f - f_c).max() < 1e-15 * np.linalg.cond(sch.S) * 100 * np.abs(f_c).max()
+
+
 def test_lgf_constant_does_not_change_constrained_solutions(plate_case):
     """Adding a constant to G (the homogeneous part the paper leaves free) leaves
     f, Gamma1, Gamma2 of the Kutta solve unchanged and shifts only s0."""
