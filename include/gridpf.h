@@ -496,27 +496,38 @@ pf_status pf_server_stats(pf_server server, int32_t* queued, int32_t* active, in
  * pf_regularize computes, with the same kernels, but needs no plan and makes
  * no allocation: its scratch (tile counters and offsets, 65536 per-vortex cell
  * records and up to 4 * 65536 binned records) is one static device array of
- * about 11.6 MiB inside this library,
- * which every GPU that loads the library holds until the process exits.  The
- * paper has no counterpart; it is an interface convenience.
+ * about 11.1 MiB inside this library, which every GPU that loads the library
+ * holds until the process exits.  The paper has no counterpart; it is an
+ * interface convenience.
  *
- *   desc          grid and precision, as for pf_plan_create (host pointer)
+ *   desc          grid and precision, as for pf_plan_create (host pointer);
+ *                 grids up to 2048 x 2048 nodes
  *   X, Y, Gam     nv doubles each (device); nv <= 65536, larger nv returns
  *                 PF_ERR_CAPACITY without doing anything
  *   w             real[nx*ny] output (device), fully overwritten
  *   out_of_domain optional device int64: receives the number of vortices whose
  *                 stencil left the grid (they are skipped); may be NULL
+ *   status        optional device int32: receives, in stream order, the status
+ *                 the work ended with: PF_OK, PF_ERR_OUT_OF_DOMAIN (see
+ *                 out_of_domain; w holds the other vortices) or
+ *                 PF_ERR_INTERNAL (a consistency check of the binning failed;
+ *                 the affected tiles were skipped and w is not valid); may be
+ *                 NULL
  *   stream        cudaStream_t to enqueue on (NULL = default stream)
  *
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture on the device.  All calls share the one array and
- * it keeps the previous call's contents, so calls whose work overlaps on the
- * GPU (different streams, or different host threads on one device) race and
- * must be serialised by the caller. */
+ * The return value covers what the host can check (arguments, capacity,
+ * launch errors); the device-side outcome arrives through status.  The first
+ * call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current, and caches it per device
+ * (thread-safe); make that first call before any stream capture on the
+ * device.  Calls after cudaDeviceReset on a device are not supported (the
+ * cached address belongs to the old context).  All calls share the one array
+ * and it keeps the previous call's contents, so calls whose work overlaps on
+ * the GPU (different streams, or different host threads on one device) race
+ * and must be serialised by the caller. */
 pf_status pf_regularize_noalloc(const pf_grid_desc* desc, const double* X, const double* Y,
                                 const double* Gam, int64_t nv, void* w, int64_t* out_of_domain,
-                                void* stream);
+                                int32_t* status, void* stream);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,9 @@ from ._native import GridPfError
 
 PF_FP64 = 0
 PF_MIXED = 1
+# status codes (include/gridpf.h)
+(PF_OK, PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_OUT_OF_DOMAIN, PF_ERR_SINGULAR, PF_ERR_TIMEOUT,
+ PF_ERR_NOT_FACTORED, PF_ERR_CAPACITY, PF_ERR_INTERNAL) = range(10)
 
 
 def _ptr(t, dtype=None, name="tensor"):
@@ -202,19 +205,35 @@ def pf_timing_report(plan):
     return out
 
 
-def pf_regularize_noalloc(nx, ny, dx, x0, y0, precision, X, Y, G, w, out_of_domain=None, stream=None):
+def pf_regularize_noalloc(nx, ny, dx, x0, y0, precision, X, Y, G, w, out_of_domain=None, status=None, stream=None):
     """Allocation-free regularization (no plan; static device scratch, nv <= 65536).
 
     `w` must be a preallocated CUDA tensor of ny*nx elements of the precision's
-    dtype; `out_of_domain` an optional CUDA int64 tensor of one element."""
+    dtype; `out_of_domain` an optional CUDA int64 tensor and `status` an
+    optional CUDA int32 tensor of at least one element, which receive the
+    out-of-domain count and the device-side status code.  Every tensor must be
+    on the current CUDA device (the library resolves its scratch there)."""
     desc = _native.PfGridDesc(int(nx), int(ny), float(dx), float(x0), float(y0), int(precision))
     dtype = torch.float64 if int(precision) == PF_FP64 else torch.float32
+    nv = X.numel()
+    if Y.numel() != nv or G.numel() != nv:
+        raise ValueError("X, Y and G must have the same length")
+    if w.numel() != int(nx) * int(ny):
+        raise ValueError("w must hold nx*ny = %d elements, got %d" % (int(nx) * int(ny), w.numel()))
+    if out_of_domain is not None and out_of_domain.numel() < 1:
+        raise ValueError("out_of_domain must hold at least one element")
+    if status is not None and status.numel() < 1:
+        raise ValueError("status must hold at least one element")
+    dev = torch.cuda.current_device()
+    for name, t in (("X", X), ("Y", Y), ("G", G), ("w", w), ("out_of_domain", out_of_domain), ("status", status)):
+        if t is not None and t.is_cuda and t.device.index != dev:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))
     if stream is None:
         stream = torch.cuda.current_stream()
     st = _native.lib().pf_regularize_noalloc(ctypes.byref(desc), _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
-                                             _ptr(G, torch.float64, "G"), X.numel(), _ptr(w, dtype, "w"),
+                                             _ptr(G, torch.float64, "G"), nv, _ptr(w, dtype, "w"),
                                              _ptr(out_of_domain, torch.int64, "out_of_domain"),
-                                             ctypes.c_void_p(stream.cuda_stream))
+                                             _ptr(status, torch.int32, "status"), ctypes.c_void_p(stream.cuda_stream))
     _native.check(st, "pf_regularize_noalloc")
     return w
 

@@ -21,7 +21,7 @@ int next_pow2(int v) {
 void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
-    void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->tile_start, p->bin_off,
+    void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->gmax, p->tile_start, p->bin_off,
                    p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->nz_idx, p->nz_val,
                    p->d_status, p->d_oob};
     for (void* q : own)
@@ -71,9 +71,16 @@ pf_status plan_init(pf_plan p) {
     p->shared = new (std::nothrow) PlanTables();
     if (!p->shared) return PF_ERR_OOM;
     PF_CUDA(p, cudaMalloc(&p->G, (size_t)(nx + 1) * (ny + 1) * sizeof(double)));
-    const size_t hq = (size_t)(P / 2 + 1) * (Q / 2 + 1);
-    for (double** h : {&p->H64, &p->Hu64, &p->Hv64}) PF_CUDA(p, cudaMalloc(h, hq * sizeof(double)));
-    for (float** h : {&p->H32, &p->Hu32, &p->Hv32}) PF_CUDA(p, cudaMalloc(h, hq * sizeof(float)));
+    p->Hld = (Q / 2 + 1 + 3) / 4 * 4;
+    const size_t hq = (size_t)(P / 2 + 1) * p->Hld;
+    for (double** h : {&p->H64, &p->Hu64, &p->Hv64}) {
+        PF_CUDA(p, cudaMalloc(h, hq * sizeof(double)));
+        PF_CUDA(p, cudaMemsetAsync(*h, 0, hq * sizeof(double), p->stream));
+    }
+    for (float** h : {&p->H32, &p->Hu32, &p->Hv32}) {
+        PF_CUDA(p, cudaMalloc(h, hq * sizeof(float)));
+        PF_CUDA(p, cudaMemsetAsync(*h, 0, hq * sizeof(float), p->stream));
+    }
     std::vector<double2> tpd, tqd;
     std::vector<float2> tpf, tqf;
     twiddles(tpd, P); twiddles(tqd, Q); twiddles(tpf, P); twiddles(tqf, Q);
@@ -106,20 +113,17 @@ pf_status plan_workspaces(pf_plan p) {
     p->ntx = ceil_div(nx, BIN_TILE);
     p->nty = ceil_div(ny, BIN_TILE);
     p->ntiles = p->ntx * p->nty;
-    // count and gmax are contiguous so one memset clears them
-    PF_CUDA(p, cudaMalloc(&p->tile_count, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned)));
-    p->tile_gmax = p->tile_count + p->ntiles;
-    p->tile_rep = p->tile_count + 2 * p->ntiles;
+    PF_CUDA(p, cudaMalloc(&p->tile_count, (size_t)p->ntiles * sizeof(unsigned)));
+    PF_CUDA(p, cudaMalloc(&p->gmax, (BIN_MAX_BLOCKS + 1) * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->diag, PF_DIAG_DOUBLES * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
-    // The first binning pass adds into the tile replicas, so they must be zero
-    // before any kernel of this plan runs.  A plain cudaMemset goes to the
-    // legacy stream, which a non-blocking plan stream does not wait for; zero
-    // on the plan's stream and wait, so that the plan is ready whatever stream
-    // it is later used on.
-    PF_CUDA(p, cudaMemsetAsync(p->tile_count, 0, (2 + 2 * (size_t)TILE_REP) * p->ntiles * sizeof(unsigned), p->stream));
+    // The status words are read before any kernel writes them.  A plain
+    // cudaMemset goes to the legacy stream, which a non-blocking plan stream
+    // does not wait for; zero on the plan's stream and wait, so that the plan
+    // is ready whatever stream it is later used on.
+    PF_CUDA(p, cudaMemsetAsync(p->tile_count, 0, (size_t)p->ntiles * sizeof(unsigned), p->stream));
     PF_CUDA(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
     PF_CUDA(p, cudaMemsetAsync(p->d_oob, 0, sizeof(unsigned long long), p->stream));
     PF_CUDA(p, cudaStreamSynchronize(p->stream));
@@ -182,7 +186,7 @@ pf_status pf_plan_clone(pf_plan src, int32_t precision, void* stream, pf_plan* o
     *out = nullptr;
     pf_plan p = new (std::nothrow) pf_plan_s();
     if (!p) return PF_ERR_OOM;
-    p->nx = src->nx; p->ny = src->ny; p->P = src->P; p->Q = src->Q; p->dx = src->dx; p->x0 = src->x0;
+    p->nx = src->nx; p->ny = src->ny; p->P = src->P; p->Q = src->Q; p->Hld = src->Hld; p->dx = src->dx; p->x0 = src->x0;
     p->y0 = src->y0; p->prec = precision;
     p->stream = (cudaStream_t)stream;
     p->shared = src->shared;

@@ -62,10 +62,6 @@ inline int64_t bin_span(int64_t nv) {
     return s < 1024 ? 1024 : s;
 }
 inline int bin_blocks(int64_t nv) { return nv > 0 ? (int)((nv + bin_span(nv) - 1) / bin_span(nv)) : 0; }
-// The locate pass reduces its per-block tile counts and largest |Gamma| into
-// TILE_REP replicas per tile (block b into replica b % TILE_REP), so that no
-// address takes more than a few tens of the global reductions.
-constexpr int TILE_REP = 16;
 
 // Read-only tables of one grid shape, shared by a plan and its clones.
 struct PlanTables {
@@ -79,8 +75,10 @@ struct pf_plan_s {
     cudaStream_t stream = nullptr;
     // LGF and spectrum
     double* G = nullptr;           // (nx+1)*(ny+1), index n*(nx+1)+m
-    // spectra on the padded torus, quadrant k in [0, P/2], l in [0, Q/2], index k*(Q/2+1)+l,
+    // spectra on the padded torus, quadrant k in [0, P/2], l in [0, Q/2], index k*Hld+l with
+    // Hld = Q/2+1 rounded up to 4 (rows start on 16-byte boundaries; the pad is zero),
     // all divided by P*Q (the inverse FFTs are unnormalised):
+    int Hld = 0;
     double* H64 = nullptr;         // psi:  -dx^2 Ghat (real, even in k and l)
     double* Hu64 = nullptr;        // u:    spectrum = i * Hu, Hu = -dx/2 Im(DyG^), odd in l
     double* Hv64 = nullptr;        // v:    spectrum = i * Hv, Hv = +dx/2 Im(DxG^), odd in k
@@ -104,9 +102,8 @@ struct pf_plan_s {
     void* uv = nullptr;            // 2*nx*ny real
     // binning
     int ntx = 0, nty = 0, ntiles = 0;
-    unsigned* tile_count = nullptr;    // one allocation: count | gmax | replicas (2 TILE_REP per tile)
-    unsigned* tile_gmax = nullptr;     // bits of the largest |Gamma| (FP32, rounded up) per tile
-    unsigned* tile_rep = nullptr;      // [t][r] counts, then [t][r] gmax
+    unsigned* tile_count = nullptr;    // records per tile (written by every binning pass)
+    double* gmax = nullptr;            // largest |Gamma| of the last binning, then per locate block
     int* tile_start = nullptr;
     int* bin_off = nullptr;            // per (block, tile): histogram, then first record slot
     int64_t bin_off_cap = 0;           // entries
@@ -189,14 +186,18 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
     return ensure_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
-// Programmatic dependent launch.  A kernel launched by pf_launch may begin
-// while the kernel before it on the stream is finishing: it runs only
-// shared-memory set-up before pdl_wait(), which returns once that kernel has
-// completed and its writes are visible (immediately for an ordinary launch).
-// pdl_trigger() is called by every block after its main work, so the next
-// kernel is launched only once all blocks of this one are running.
+// Programmatic dependent launch.  A kernel launched by pf_launch is queued
+// behind the kernel before it on the stream without a full stream barrier; it
+// runs only shared-memory set-up before pdl_wait(), which returns once that
+// kernel has completed and its writes are visible.  No kernel here signals
+// griddepcontrol.launch_dependents early: a dependent grid whose blocks are
+// resident while the kernel before it still runs can read lines that the
+// earlier kernel's blocks left in the same SM's L1, and the wait does not
+// drop them.  That happened with the in-place histogram-to-offset pass of the
+// binning (whole tiles of wrong records on the first call after the inputs
+// changed, 2048^2 grids); launching dependents at completion removed it and
+// was also faster (the waiting blocks no longer hold SM resources).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t pf_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

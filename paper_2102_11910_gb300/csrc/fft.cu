@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
         v[r] = cmake<C>(a, b);
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twP);
-    pdl_trigger();
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf[spad(t + TP * r)] = v[r];
     __syncthreads();
@@ -216,6 +215,14 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
     }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Column pass.  The block's rows of the kernel spectra (Hu and Hv, or H) are
+// copied into shared memory by cp.async as the block starts, so their loads
+// overlap the column load and the forward transform.
 template <typename T, int R3>
 __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_r(
     const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a, C_t<T>* __restrict__ T2b, int ny, int nk, int mode,
@@ -223,11 +230,23 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
     const C_t<T>* __restrict__ tw256, const C_t<T>* __restrict__ twQ) {
     using C = C_t<T>;
     constexpr int Q = 256 * R3, TQ = Q / 16, SB = SBuf<Q>::size;
+    constexpr int NH = (Q / 2 + 1 + 3) / 4 * 4, PER = 16 / sizeof(T);   // spectrum row length, elements per copy
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* keep = buf + SB;
+    T* hs0 = reinterpret_cast<T*>(keep + SB);
+    T* hs1 = hs0 + NH;
     const int k = blockIdx.x, t = threadIdx.x;
+    const size_t row = (size_t)k * Hld;
     pdl_wait();
+    {
+        const T* s0 = mode == CONV_UV ? Hu : H;
+        for (int i = PER * t; i < NH; i += PER * TQ) {
+            cp_async16(hs0 + i, s0 + row + i);
+            if (mode == CONV_UV) cp_async16(hs1 + i, Hv + row + i);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     C v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -235,8 +254,8 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
         v[r] = l < ny ? T1[spec_at(l, k, nk)] : cmake<C>(T(0), T(0));
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twQ);
-    pdl_trigger();
-    const size_t row = (size_t)k * Hld;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
     if (mode == CONV_UV) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -244,8 +263,8 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
             const bool lo = l <= Q / 2;
             const int lq = lo ? l : Q - l;
             const C iw = mul_i(v[r]);
-            const T hu = Hu[row + lq];
-            keep[spad(l)] = iw * Hv[row + lq];     // even in l
+            const T hu = hs0[lq];
+            keep[spad(l)] = iw * hs1[lq];          // even in l
             v[r] = iw * (lo ? hu : -hu);            // odd in l
         }
         fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int l = t + TQ * r;
-            v[r] = v[r] * H[row + (l <= Q / 2 ? l : Q - l)];
+            v[r] = v[r] * hs0[l <= Q / 2 ? l : Q - l];
         }
         fft_strided<C, true, R3>(v, buf, t, tw256, twQ);
 #pragma unroll
@@ -318,7 +337,6 @@ __global__ void __launch_bounds__(32 * R3, sizeof(T) == 4 && R3 == 8 ? 4 : 1) k_
     for (int r = 0; r < 16; ++r) v[r] = buf[spad(t + TP * r)];
     __syncthreads();
     fft_strided<C, true, R3>(v, buf, t, tw256, twP);
-    pdl_trigger();
     if (mode == CONV_UV) {
         if (ha) {
             C* o = reinterpret_cast<C*>(out) + (size_t)ja * nx;
@@ -353,7 +371,8 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     using C = C_t<T>;
     constexpr int P = 256 * R3P, Q = 256 * R3Q;
     const int nx = p->nx, ny = p->ny;
-    const size_t sr = 2 * (size_t)SBuf<P>::size * sizeof(C), sc = 2 * (size_t)SBuf<Q>::size * sizeof(C);
+    const size_t sr = 2 * (size_t)SBuf<P>::size * sizeof(C);
+    const size_t sc = 2 * (size_t)SBuf<Q>::size * sizeof(C) + 2 * (size_t)((Q / 2 + 1 + 3) / 4 * 4) * sizeof(T);
     PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sr));
     PF_CUDA(p, set_smem(k_cols_r<T, R3Q>, sc));
     PF_CUDA(p, set_smem(k_rows_inv_r<T, R3P>, sr));
@@ -363,7 +382,7 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     PF_KERNEL(p, "fft_rows_fwd", PF_CUDA(p, pf_launch(k_rows_fwd_r<T, R3P>, (ny + 3) / 4, 32 * R3P, sr, p->stream, w, T1,
                                                       nx, ny, tw256, twP)));
     PF_KERNEL(p, "fft_cols_conv", PF_CUDA(p, pf_launch(k_cols_r<T, R3Q>, P / 2 + 1, 16 * R3Q, sc, p->stream, T1, T2a,
-                                                       T2b, ny, P / 2 + 1, mode, H, Hu, Hv, Q / 2 + 1, tw256, twQ)));
+                                                       T2b, ny, P / 2 + 1, mode, H, Hu, Hv, p->Hld, tw256, twQ)));
     const int nb = mode == CONV_UV ? (ny + 1) / 2 : (ny + 3) / 4;
     PF_KERNEL(p, "fft_rows_inv", PF_CUDA(p, pf_launch(k_rows_inv_r<T, R3P>, nb, 32 * R3P, sr, p->stream, T2a, T2b, out,
                                                       nx, ny, mode, Uinf, Vinf, tw256, twP)));
@@ -409,7 +428,7 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     C* T2a = reinterpret_cast<C*>(p->T2a);
     C* T2b = reinterpret_cast<C*>(p->T2b);
     PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, 256, sr, p->stream>>>(w, T1, nx, ny, P, twP));
-    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, Q / 2 + 1, twQ));
+    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ));
     const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
     PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, 256, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
     return PF_OK;

@@ -152,9 +152,9 @@ __device__ __forceinline__ void fft_strided(C (&v)[16], C* buf, int t, const C* 
     __syncthreads();
     // pass 3: radix R3, Ns = 256, butterflies j = t + m T, m < 16 / R3;
     // outputs j + 256 r = t + T (m + r 16/R3) stay in registers
+    // (v was stored to buf by pass 2, so the outputs go straight into v)
     if (R3 > 1) {
         constexpr int M = 16 / R3;
-        C w[16];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int j = t + m * T;
@@ -165,10 +165,8 @@ __device__ __forceinline__ void fft_strided(C (&v)[16], C* buf, int t, const C* 
             for (int r = 1; r < R3; ++r) u[r] = u[r] * twiddle<C, INV>(twN, r * j);
             dft_r<C, INV, R3>(u);
 #pragma unroll
-            for (int r = 0; r < R3; ++r) w[m + r * M] = u[r];
+            for (int r = 0; r < R3; ++r) v[m + r * M] = u[r];
         }
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = w[r];
         __syncthreads();
     }
 }

@@ -95,15 +95,15 @@ __global__ void k_torus(double2* __restrict__ g, const double* __restrict__ G, i
 
 // quadrant k in [0, P/2], l in [0, Q/2] of scale * (Re or Im) of the spectrum
 __global__ void k_extract(const double2* __restrict__ g, double* __restrict__ H64, float* __restrict__ H32, int P,
-                          int Q, double scale, int imag) {
+                          int Q, int Hld, double scale, int imag) {
     const int hp = P / 2 + 1, hq = Q / 2 + 1;
     const int64_t total = (int64_t)hp * hq;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(e % hq), k = (int)(e / hq);
         const double2 c = g[(size_t)l * P + k];
         const double v = scale * (imag ? c.y : c.x);
-        H64[e] = v;
-        H32[e] = (float)v;
+        H64[(size_t)k * Hld + l] = v;
+        H32[(size_t)k * Hld + l] = (float)v;
     }
 }
 
@@ -147,7 +147,7 @@ pf_status lgf_build(pf_plan p) {
         PF_LAUNCH_CHECK(p);
         pf_status st = fft2d_inplace_f64(p, g);
         if (st != PF_OK) return st;
-        k_extract<<<4 * 152, 256, 0, p->stream>>>(g, H64[which], H32[which], P, Q, scale[which], which != 0);
+        k_extract<<<4 * 152, 256, 0, p->stream>>>(g, H64[which], H32[which], P, Q, p->Hld, scale[which], which != 0);
         PF_LAUNCH_CHECK(p);
     }
     PF_CUDA(p, cudaStreamSynchronize(p->stream));

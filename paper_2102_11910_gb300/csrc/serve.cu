@@ -72,7 +72,7 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
     const int64_t grid = 3 * spec + 3 * (int64_t)s.nx * s.ny * esz;
     const int64_t c = cap > 4096 ? cap : 4096;
     const int64_t ntiles = (int64_t)((s.nx + 31) / 32) * ((s.ny + 31) / 32);
-    const int64_t bins = c * 32 + 4 * c * 32 + (4 + 2 * TILE_REP) * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
+    const int64_t bins = c * 32 + 4 * c * 32 + 2 * ntiles * 4 + (int64_t)bin_blocks(c) * ntiles * 4;
     const int64_t state = 5 * cap * 8 + 4 * cap * esz + 4096 * 8;
     // two Schur factors (a moving body keeps the last two poses), each S, the
     // ns x 2 ns Gauss-Jordan workspace, S^-1, and O(ns) vectors and orderings
@@ -88,7 +88,7 @@ int64_t slot_bytes(const Shape& s, int prec, int64_t cap, int ns) {
 
 int64_t table_bytes(int nx, int ny) {
     const int P = 1 << (32 - __builtin_clz(2 * nx - 1)), Q = 1 << (32 - __builtin_clz(2 * ny - 1));
-    return (int64_t)(nx + 1) * (ny + 1) * 8 + 3 * (int64_t)(P / 2 + 1) * (Q / 2 + 1) * 12;
+    return (int64_t)(nx + 1) * (ny + 1) * 8 + 3 * (int64_t)(P / 2 + 1) * ((Q / 2 + 4) / 4 * 4) * 12;
 }
 
 }  // namespace

@@ -6,8 +6,8 @@
 //   locate   FP64 position -> integer cell + fraction (one pass, FP64 used only
 //            for g = (X - x0)/dx), compact per-vortex record, per-block tile
 //            histogram in shared memory, written out as one row per block;
-//   offsets  column scan of the block histograms: the first record slot of
-//            every (block, tile) pair, and the first slot of every tile;
+//   offsets  column scan of the block histograms: the tile totals and the first
+//            record slot of every (block, tile) pair within its tile;
 //   scatter  per-block ranks in shared memory, records written into their
 //            tiles at the block's offsets (no global atomics); a vortex whose
 //            4x4 stencil straddles tiles is entered in every tile it touches;
@@ -15,9 +15,11 @@
 //            memory as fixed-point integers with a per-tile scale chosen from
 //            the tile's record count and largest |Gamma|.  Integer sums are
 //            exact, so the result does not depend on the order of the adds.
+//
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -193,16 +195,14 @@ template <typename T> using Frac = typename std::conditional<sizeof(T) == 4, uns
 template <typename T>
 __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
                                                        const double* __restrict__ G, int64_t nv, int64_t span, Geo geo,
-                                                       Pos<T>* __restrict__ pos, unsigned* __restrict__ tile_rep,
-                                                       int* __restrict__ hist,
-                                                       int* __restrict__ status, unsigned long long* __restrict__ oob) {
+                                                       Pos<T>* __restrict__ pos, int* __restrict__ hist,
+                                                       double* __restrict__ gmax_blk, int* __restrict__ status,
+                                                       unsigned long long* __restrict__ oob) {
     extern __shared__ unsigned sm[];
+    __shared__ double wmax[BIN_THREADS / 32];
     unsigned* cnt = sm;
-    unsigned* gmx = sm + geo.ntiles;
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) {
-        cnt[i] = 0u;
-        gmx[i] = 0u;
-    }
+    double gm = 0.0;
+    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) cnt[i] = 0u;
     pdl_wait();
     __syncthreads();
     const int64_t lo = (int64_t)blockIdx.x * span;
@@ -236,41 +236,34 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
             }
             make_pos(p, ci, cj, fx, fy, gs[k]);
             pos[q] = p;
-            // |Gamma| rounded to FP32 and widened by two ulps: an upper bound of |Gamma|
-            const unsigned gb = __float_as_uint(fabsf(d2f(gs[k])) * 1.0000003f);
+            gm = fmax(gm, fabs((double)p.g));      // |Gamma| as the record carries it
             const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
             const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    const int t = ty * geo.ntx + tx;
-                    atomicAdd(&cnt[t], 1u);
-                    atomicMax(&gmx[t], gb);
-                }
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&cnt[ty * geo.ntx + tx], 1u);
         }
     }
-    pdl_trigger();
     if (bad) {
         atomicAdd(oob, (unsigned long long)bad);
         atomicOr(status, ST_OUT_OF_DOMAIN);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gm;
     __syncthreads();
-    int* row = hist + (size_t)blockIdx.x * geo.ntiles;
-    unsigned* rc = tile_rep + blockIdx.x % TILE_REP;
-    unsigned* rg = rc + (size_t)geo.ntiles * TILE_REP;
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) {
-        const unsigned c = cnt[i];
-        row[i] = (int)c;
-        if (c) {
-            atomicAdd(&rc[i * TILE_REP], c);
-            atomicMax(&rg[i * TILE_REP], gmx[i]);
-        }
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < BIN_THREADS / 32; ++i) m = fmax(m, wmax[i]);
+        gmax_blk[blockIdx.x] = m;
     }
+    int* row = hist + (size_t)blockIdx.x * geo.ntiles;
+    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) row[i] = (int)cnt[i];
 }
 
 // Fixed-point exponent of a tile: every node sum is bounded by
 // count * max|Gamma| < 2^e and is scaled to stay below 2^61.
-__device__ __forceinline__ int tile_shift_of(unsigned count, unsigned gmax_bits) {
-    const double bound = (double)count * (double)__uint_as_float(gmax_bits);
+__device__ __forceinline__ int tile_shift_of(unsigned count, double gmax) {
+    const double bound = (double)count * gmax;
     int e = 0;
     if (bound > 0.0) frexp(bound, &e);
     const int sh = 61 - e;
@@ -293,12 +286,11 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 }
 
 // Per-tile totals and per-(block, tile) offsets within the tile: tile_count
-// and tile_gmax (reduced over the replicas) and, in place over the block
-// histograms, off[b][t] = sum_{b' < b} hist[b'][t].  Blocks are independent
-// (the tiles' first slots are added by the scatter pass).
-__global__ void __launch_bounds__(1024) k_offsets(unsigned* __restrict__ tile_rep, int ntiles, int nb,
-                                                  int* __restrict__ hist_off, unsigned* __restrict__ tile_count,
-                                                  unsigned* __restrict__ tile_gmax) {
+// and, in place over the block histograms, off[b][t] = sum_{b' < b} hist[b'][t].
+// Blocks are independent (the tiles' first slots are added by the scatter pass).
+__global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __restrict__ hist_off,
+                                                  unsigned* __restrict__ tile_count, const double* __restrict__ gmax_blk,
+                                                  double* __restrict__ gmax_all) {
     __shared__ int part[OFF_SEGS][OFF_TILES + 1];
     const int tx = threadIdx.x % OFF_TILES, ty = threadIdx.x / OFF_TILES;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -314,42 +306,26 @@ __global__ void __launch_bounds__(1024) k_offsets(unsigned* __restrict__ tile_re
         if (k < S && b0 + k < nb && t < ntiles) v[k] = hist_off[(size_t)(b0 + k) * ntiles + t];
         seg += v[k];
     }
-    pdl_trigger();
+    if (blockIdx.x == 0 && wid == OFF_TILES) {       // largest |Gamma| over the locate blocks
+        double m = 0.0;
+        for (int b = lane; b < nb; b += 32) m = fmax(m, gmax_blk[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) *gmax_all = m;
+    }
     part[ty][tx] = seg;
     __syncthreads();
     if (wid < OFF_TILES) {                            // exclusive scan over the runs of tile t0 + wid
         const int a0 = part[4 * lane][wid], a1 = part[4 * lane + 1][wid];
         const int a2 = part[4 * lane + 2][wid], a3 = part[4 * lane + 3][wid];
         const int sum4 = a0 + a1 + a2 + a3;
-        const int ex = warp_incl_scan(sum4, lane) - sum4;
+        const int incl = warp_incl_scan(sum4, lane);
+        const int ex = incl - sum4;
         part[4 * lane][wid] = ex;
         part[4 * lane + 1][wid] = ex + a0;
         part[4 * lane + 2][wid] = ex + a0 + a1;
         part[4 * lane + 3][wid] = ex + a0 + a1 + a2;
-    } else if (wid == OFF_TILES) {                    // totals of the block's tiles
-        static_assert(OFF_TILES * 4 == 32 && TILE_REP % 4 == 0, "four lanes per tile");
-        const int tl = lane / 4, q = lane % 4;          // tile t0 + tl, replicas [q R/4, (q + 1) R/4)
-        unsigned c = 0u, gm = 0u;
-        if (t0 + tl < ntiles) {
-            unsigned* rc = tile_rep + (size_t)(t0 + tl) * TILE_REP + q * (TILE_REP / 4);
-            unsigned* rg = rc + (size_t)ntiles * TILE_REP;
-#pragma unroll
-            for (int r = 0; r < TILE_REP / 4; ++r) {
-                c += rc[r];
-                gm = max(gm, rg[r]);
-                rc[r] = 0u;          // cleared for the next locate pass
-                rg[r] = 0u;
-            }
-        }
-#pragma unroll
-        for (int o = 1; o < 4; o <<= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-        }
-        if (q == 0 && t0 + tl < ntiles) {
-            tile_count[t0 + tl] = c;
-            tile_gmax[t0 + tl] = gm;
-        }
+        if (lane == 31 && t0 + wid < ntiles) tile_count[t0 + wid] = (unsigned)incl;
     }
     __syncthreads();
     if (t < ntiles) {
@@ -419,7 +395,6 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
             run += (int)tile_count[i];
         }
     }
-    pdl_trigger();
     __syncthreads();
     for (int64_t base = lo; base < hi; base += BIN_THREADS * ScatterUnroll<T>::value) {
         if (base != lo) {
@@ -473,7 +448,11 @@ __device__ __forceinline__ void split_hilo(float x, int& hi, int& lo) {
 // hi 2^16 + lo, goes into two native 32-bit shared adds (exact while the tile
 // has fewer than 65536 records and |sum| < 2^38); otherwise, and for FP64, one
 // 64-bit add.  Integer sums are exact, so the result does not depend on the
-// order of the adds.
+// order of the adds.  The scale bounds every node sum by the tile's record
+// count times the largest |Gamma| of the whole regularization (reduced by
+// k_offsets from the locate blocks' maxima).  (A one-add variant with a
+// node-window bound measured no faster and lost seven bits on clustered
+// vortices; shared adds are not what bounds this kernel.)
 //
 // A record's local cell (lx, ly) lies in [-2, 32], so its nodes lie in
 // [-3, 34]: the accumulator covers that range (ACC_W^2 nodes) and the adds
@@ -519,7 +498,7 @@ __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs,
 template <typename T>
 __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs, const int* __restrict__ tile_start,
                                                  const unsigned* __restrict__ tile_count,
-                                                 const unsigned* __restrict__ tile_gmax, Geo geo, T* __restrict__ w,
+                                                 const double* __restrict__ gmax_all, Geo geo, T* __restrict__ w,
                                                  int64_t rec_cap, int* __restrict__ status) {
     __shared__ unsigned long long acc[ACC_W * ACC_W];
     const int t = blockIdx.x;
@@ -533,12 +512,11 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
         start = cnt = 0;
     }
     const bool split32 = sizeof(T) == 4 && cnt < 65536;
-    const int sh = tile_shift_of((unsigned)cnt, tile_gmax[t]) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
+    const int sh = tile_shift_of((unsigned)cnt, *gmax_all) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
     const T scale = pow2<T>(sh);
     if (sizeof(T) == 8) deposit_records<DEP_F64_64>(recs + start, cnt, scale, acc);
     else if (split32) deposit_records<DEP_SPLIT32>(recs + start, cnt, scale, acc);
     else deposit_records<DEP_F32_64>(recs + start, cnt, scale, acc);
-    pdl_trigger();
     __syncthreads();
     const int* acc_hi = reinterpret_cast<const int*>(acc);
     const int* acc_lo = reinterpret_cast<const int*>(acc) + ACC_W * ACC_W;
@@ -613,7 +591,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
         patch[i] = v;
     }
     __syncthreads();
-    pdl_trigger();
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<T> rc[U];
@@ -697,7 +674,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         }
     }
     __syncthreads();
-    pdl_trigger();
     constexpr int U = 4;
     for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
         Rec<float> rc[U];
@@ -763,8 +739,7 @@ struct BinWork {
     int* status;
     unsigned long long* oob;
     unsigned* tile_count;     // written by k_offsets
-    unsigned* tile_gmax;
-    unsigned* tile_rep;       // 2 TILE_REP * ntiles, zero on entry (k_offsets leaves it zero)
+    double* gmax;             // [0]: largest |Gamma| (k_offsets); [1 + b]: that of locate block b
     int* tile_start;
     int* bin_off;             // bin_blocks(nv) * ntiles
     void* pos;
@@ -792,28 +767,30 @@ inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
 template <typename T>
 pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
                             const double* G, int64_t nv, T* w, cudaStream_t s) {
-    // the replicas are zero here: cleared when allocated and by every k_offsets pass
     const int nb = bin_blocks(nv);
     const int64_t span = bin_span(nv);
-    const size_t sh = 2 * (size_t)geo.ntiles * sizeof(unsigned);
-    if (set_smem(k_locate<T>, sh) != cudaSuccess || set_smem(k_scatter<T>, sh) != cudaSuccess) return PF_ERR_CUDA;
+    const size_t sh_loc = (size_t)geo.ntiles * sizeof(unsigned);
+    const size_t sh_sc = 2 * (size_t)geo.ntiles * sizeof(unsigned);
+    if (set_smem(k_locate<T>, sh_loc) != cudaSuccess || set_smem(k_scatter<T>, sh_sc) != cudaSuccess)
+        return PF_ERR_CUDA;
     Pos<T>* pos = (Pos<T>*)bw.pos;
     if (nb > 0) {
-        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T>, nb, BIN_THREADS, sh, s, X, Y, G, nv, span, geo, pos,
-                                                       bw.tile_rep, bw.bin_off, bw.status, bw.oob)));
+        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T>, nb, BIN_THREADS, sh_loc, s, X, Y, G, nv, span, geo,
+                                                       pos, bw.bin_off, bw.gmax + 1, bw.status, bw.oob)));
     }
-    PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s, bw.tile_rep,
-                                                     geo.ntiles, nb, bw.bin_off, bw.tile_count, bw.tile_gmax)));
+    PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s,
+                                                     geo.ntiles, nb, bw.bin_off, bw.tile_count,
+                                                     (const double*)(bw.gmax + 1), bw.gmax)));
     if (nb > 0) {
-        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T>, nb, BIN_THREADS, sh, s, pos, nv, span, geo,
+        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T>, nb, BIN_THREADS, sh_sc, s, pos, nv, span, geo,
                                                          bw.bin_off, bw.tile_count, bw.tile_start, (Rec<T>*)bw.recs,
                                                          bw.rec_cap, bw.status)));
     } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
         return PF_ERR_CUDA;
     }
     PF_KERNEL(p, "regularize", PF_CUDA(p, pf_launch(k_deposit<T>, geo.ntiles, 256, 0, s, (const Rec<T>*)bw.recs,
-                                                    bw.tile_start, bw.tile_count, bw.tile_gmax, geo, w, bw.rec_cap,
-                                                    bw.status)));
+                                                    bw.tile_start, bw.tile_count, (const double*)bw.gmax, geo, w,
+                                                    bw.rec_cap, bw.status)));
     return PF_OK;
 }
 
@@ -862,8 +839,7 @@ BinWork plan_binwork(pf_plan p) {
     b.status = p->d_status;
     b.oob = p->d_oob;
     b.tile_count = p->tile_count;
-    b.tile_gmax = p->tile_gmax;
-    b.tile_rep = p->tile_rep;
+    b.gmax = p->gmax;
     b.tile_start = p->tile_start;
     b.bin_off = p->bin_off;
     b.pos = p->pos;
@@ -895,11 +871,12 @@ pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void
                                                          (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
                                                          (const double2*)uv, geo, (double*)uq, (double*)vq, p->rec_cap,
                                                          nq, p->d_status)));
-    else
+    else {
         PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32, geo.ntiles, 256, 0, p->stream,
                                                          (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
                                                          (const float2*)uv, geo, (float*)uq, (float*)vq, p->rec_cap,
                                                          nq, p->d_status)));
+    }
     return PF_OK;
 }
 
@@ -922,35 +899,43 @@ pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const d
 // Allocation-free regularization.
 //
 // Same kernels as pf_regularize, but every piece of scratch (tile counters,
-// fixed-point exponents, status words, the per-vortex cell records and the
-// binned records) lives in one file-scope device array, so the entry point
-// needs no plan and makes no allocation.  The array is part of the library
-// image: each GPU that loads the library holds NOALLOC_SCRATCH_BYTES of it
-// until the process exits.
+// status words, the per-vortex cell records and the binned records) lives in
+// one file-scope device array, so the entry point needs no plan and makes no
+// allocation.  The array is part of the library image: each GPU that loads the
+// library holds NOALLOC_SCRATCH_BYTES of it until the process exits.
 namespace {
 
 constexpr int64_t NOALLOC_MAX_VORTICES = 65536;
 constexpr int NOALLOC_MAX_TILES = (2048 / BIN_TILE) * (2048 / BIN_TILE);
 constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_VORTICES / 1024);   // bin_blocks() at the maximum
+// every region starts on a 256-byte boundary (the records are stored 16 bytes at a time)
+constexpr size_t noalloc_round(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t NOALLOC_HEADER = 256;   // status int + out-of-domain counter, padded
-constexpr size_t NOALLOC_TILE_BYTES = (size_t)NOALLOC_MAX_TILES * (4 + 2 * TILE_REP) * sizeof(int);
-constexpr size_t NOALLOC_OFF_BYTES = (size_t)NOALLOC_MAX_BLOCKS * NOALLOC_MAX_TILES * sizeof(int);
-constexpr size_t NOALLOC_POS_BYTES = (size_t)NOALLOC_MAX_VORTICES * sizeof(Pos<double>);
+constexpr size_t NOALLOC_TILE_BYTES = noalloc_round((size_t)NOALLOC_MAX_TILES * 2 * sizeof(int) + (NOALLOC_MAX_BLOCKS + 1) * 8);
+constexpr size_t NOALLOC_OFF_BYTES = noalloc_round((size_t)NOALLOC_MAX_BLOCKS * NOALLOC_MAX_TILES * sizeof(int));
+constexpr size_t NOALLOC_POS_BYTES = noalloc_round((size_t)NOALLOC_MAX_VORTICES * sizeof(Pos<double>));
+static_assert((size_t)NOALLOC_MAX_TILES * 2 * sizeof(int) % 8 == 0, "the |Gamma| maxima are 8-byte aligned");
+static_assert(NOALLOC_HEADER % 256 == 0 && NOALLOC_TILE_BYTES % 256 == 0 && NOALLOC_OFF_BYTES % 256 == 0 &&
+                  NOALLOC_POS_BYTES % 256 == 0,
+              "scratch regions stay 256-byte aligned");
 constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES +
                                          (size_t)4 * NOALLOC_MAX_VORTICES * sizeof(Rec<double>);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 // Resolve the array's device address for the current device (first call per
-// device only).  The host-side name g_noalloc_scratch is not a device address.
+// device only; later calls read the cached address under the same lock).  The
+// host-side name g_noalloc_scratch is not a device address.
 cudaError_t noalloc_scratch(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -961,16 +946,14 @@ cudaError_t noalloc_scratch(unsigned char** out) {
     return cudaSuccess;
 }
 
-BinWork noalloc_binwork(unsigned char* base, int ntiles) {
+BinWork noalloc_binwork(unsigned char* base) {
     BinWork b;
     b.status = (int*)base;
     b.oob = (unsigned long long*)(base + 8);
     unsigned* t = (unsigned*)(base + NOALLOC_HEADER);
-    const int nt = ntiles;         // <= NOALLOC_MAX_TILES
     b.tile_count = t;
-    b.tile_gmax = t + nt;
-    b.tile_start = (int*)(t + 2 * nt);
-    b.tile_rep = t + 3 * nt;       // 2 TILE_REP * nt
+    b.tile_start = (int*)(t + NOALLOC_MAX_TILES);
+    b.gmax = (double*)(t + 2 * NOALLOC_MAX_TILES);
     b.bin_off = (int*)(base + NOALLOC_HEADER + NOALLOC_TILE_BYTES);
     b.pos = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES;
     b.recs = base + NOALLOC_HEADER + NOALLOC_TILE_BYTES + NOALLOC_OFF_BYTES + NOALLOC_POS_BYTES;
@@ -978,10 +961,17 @@ BinWork noalloc_binwork(unsigned char* base, int ntiles) {
     return b;
 }
 
+// status word bits -> the pf_status the call reports (the same order as pf_sync)
+__global__ void k_noalloc_status(const int* __restrict__ bits, int32_t* __restrict__ out) {
+    const int st = *bits;
+    *out = (st & ST_INTERNAL) ? PF_ERR_INTERNAL : (st & ST_OUT_OF_DOMAIN) ? PF_ERR_OUT_OF_DOMAIN : PF_OK;
+}
+
 }  // namespace
 
 extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* X, const double* Y, const double* G,
-                                           int64_t nv, void* w, int64_t* out_of_domain, void* stream) {
+                                           int64_t nv, void* w, int64_t* out_of_domain, int32_t* status,
+                                           void* stream) {
     if (!d || !w || nv < 0 || (nv > 0 && (!X || !Y || !G))) return PF_ERR_ARG;
     if (d->nx < 8 || d->ny < 8 || d->nx > 2048 || d->ny > 2048 || !(d->dx > 0) || !isfinite(d->x0) ||
         !isfinite(d->y0) || (d->precision != PF_FP64 && d->precision != PF_MIXED))
@@ -991,12 +981,10 @@ extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* 
     if (noalloc_scratch(&base) != cudaSuccess) return PF_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const Geo geo = make_geo(d->nx, d->ny, d->dx, d->x0, d->y0);
-    const BinWork bw = noalloc_binwork(base, geo.ntiles);
-    // the array keeps the previous call's contents: clear the status words and
-    // the tile replicas (a call that stopped early may have left them dirty)
+    const BinWork bw = noalloc_binwork(base);
+    // the array keeps the previous call's contents: clear the status words
+    // (every other piece of scratch is written before it is read)
     if (cudaMemsetAsync(base, 0, NOALLOC_HEADER, s) != cudaSuccess) return PF_ERR_CUDA;
-    if (cudaMemsetAsync(bw.tile_rep, 0, 2 * (size_t)TILE_REP * geo.ntiles * sizeof(unsigned), s) != cudaSuccess)
-        return PF_ERR_CUDA;
     pf_status st = d->precision == PF_FP64
                        ? regularize_launch<double>(nullptr, geo, bw, X, Y, G, nv, (double*)w, s)
                        : regularize_launch<float>(nullptr, geo, bw, X, Y, G, nv, (float*)w, s);
@@ -1005,5 +993,9 @@ extern "C" pf_status pf_regularize_noalloc(const pf_grid_desc* d, const double* 
     if (out_of_domain &&
         cudaMemcpyAsync(out_of_domain, bw.oob, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return PF_ERR_CUDA;
+    if (status) {
+        k_noalloc_status<<<1, 1, 0, s>>>(bw.status, status);
+        if (cudaGetLastError() != cudaSuccess) return PF_ERR_CUDA;
+    }
     return PF_OK;
 }

@@ -35,15 +35,50 @@ def test_noalloc_matches_plan_path_on_two_calls_in_a_row(prec, tol):
         ref = pf.pf_regularize(plan, X, Y, G)
         w = torch.full((g.ny, g.nx), float("nan"), dtype=dtype, device="cuda")
         oob = torch.full((1,), -1, dtype=torch.int64, device="cuda")
-        pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, prec, X, Y, G, w, oob)
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, prec, X, Y, G, w, oob, st)
         torch.cuda.synchronize()
         pf.pf_sync(plan)
         assert int(oob.item()) == 0
+        assert int(st.item()) == 0          # PF_OK: no binning check failed
         assert torch.isfinite(w).all()
         assert _rel(w, ref) <= tol
         # same kernels on other scratch: the tiles' counts, exponents and
         # integer sums are the same, so w is bitwise the same
         assert torch.equal(w, ref)
+
+
+@pytest.mark.parametrize("prec", [pf.PF_MIXED, pf.PF_FP64])
+def test_noalloc_at_its_largest_grid_and_vortex_count(prec):
+    """The scratch layout at its stated maximum (2048^2 nodes: 4096 tiles, the
+    whole offset table; 65536 vortices: 64 binning blocks), bitwise against
+    the plan path, twice in a row."""
+    g = inputs.centred_grid(2048, 2048, 1.0 / 1024)
+    plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec)
+    dtype = torch.float64 if prec == pf.PF_FP64 else torch.float32
+    for seed in (31, 32):
+        rng = np.random.default_rng(seed)
+        h = 0.49 * (g.nx - 1) * g.dx
+        X, Y, G = (torch.from_numpy(a).cuda() for a in inputs.uniform_vortices(rng, 65536, -h, h, 1e-3))
+        ref = pf.pf_regularize(plan, X, Y, G)
+        w = torch.full((g.ny, g.nx), float("nan"), dtype=dtype, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, prec, X, Y, G, w, None, st)
+        torch.cuda.synchronize()
+        pf.pf_sync(plan)
+        assert int(st.item()) == 0
+        assert torch.equal(w, ref)
+    plan.close()
+
+
+def test_noalloc_wrapper_rejects_mismatched_arguments():
+    g = inputs.centred_grid(64, 64, 0.02)
+    X = torch.zeros(4, dtype=torch.float64, device="cuda")
+    w = torch.empty((g.ny, g.nx), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, X, X[:3], X, w)
+    with pytest.raises(ValueError):
+        pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, X, X, X, w[:10])
 
 
 def test_noalloc_reports_out_of_domain_and_rejects_oversize():
@@ -53,9 +88,11 @@ def test_noalloc_reports_out_of_domain_and_rejects_oversize():
     G = torch.ones(3, dtype=torch.float64, device="cuda")
     w = torch.empty((g.ny, g.nx), dtype=torch.float32, device="cuda")
     oob = torch.zeros(1, dtype=torch.int64, device="cuda")
-    pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, X, Y, G, w, oob)
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    pf.pf_regularize_noalloc(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, X, Y, G, w, oob, st)
     torch.cuda.synchronize()
     assert int(oob.item()) == 1
+    assert int(st.item()) == pf.PF_ERR_OUT_OF_DOMAIN
     assert abs(float(w.double().sum()) * g.dx ** 2 - 2.0) < 1e-5     # the two valid vortices
     big = torch.zeros(65537, dtype=torch.float64, device="cuda")
     with pytest.raises(pf.GridPfError) as e:
