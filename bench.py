@@ -61,62 +61,146 @@ sys.path.insert(0, {root!r})
 from oracle import vic as OV
 from oracle.lgf import lgf_table
 from paper_2102_11910_gb300 import inputs
-nsub, nodes, reps = int(sys.argv[1]), int(sys.argv[2]), int(sys.argv[3])
+nsub, nodes, reps, worker = int(sys.argv[1]), int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4])
 wl = inputs.vic_1024()
 g = wl["grid"]; og = OV.Grid(g.nx, g.ny, g.dx, g.x0, g.y0)
 X, Y, G = wl["X"], wl["Y"], wl["G"]
-nv = len(X); M = (g.nx + 2) * (g.ny + 2)
+nv = len(X)
 t0 = time.perf_counter(); tab = lgf_table(g.nx + 1, g.ny + 1); t_tab = time.perf_counter() - t0
 w_full = OV.regularize(og, X, Y, G)          # source field of the sampled direct sums
 f = np.zeros((g.ny, g.nx))
-rng = np.random.default_rng(0)
+rng = np.random.default_rng(100 + worker)
+sys.stdout.write("ready\n"); sys.stdout.flush()
+sys.stdin.readline()                          # all workers start the timed part together
 out = []
 for r in range(reps):
     sel = rng.integers(0, nv, nsub)
-    t0 = time.perf_counter(); OV.regularize(og, X[sel], Y[sel], G[sel]); t_reg = (time.perf_counter() - t0) * nv / nsub
+    t0 = time.perf_counter(); OV.regularize(og, X[sel], Y[sel], G[sel]); t_reg = (time.perf_counter() - t0) / nsub
     ti = rng.integers(0, g.nx, nodes); tj = rng.integers(0, g.ny, nodes)
     t0 = time.perf_counter(); OV.inv_laplacian_at(og, w_full, ti, tj, tab); t_node = (time.perf_counter() - t0) / nodes
-    t0 = time.perf_counter(); OV.interpolate(og, f, X[sel], Y[sel]); t_int = 2 * (time.perf_counter() - t0) * nv / nsub
-    out.append(dict(step_s=t_reg + t_node * M + t_int, t_reg=t_reg, t_node=t_node, t_int=t_int))
-print(json.dumps(dict(reps=out, t_table=t_tab, nsub=nsub, nodes=nodes)))
+    t0 = time.perf_counter(); OV.interpolate(og, f, X[sel], Y[sel]); t_int = 2 * (time.perf_counter() - t0) / nsub
+    out.append(dict(t_reg=t_reg, t_node=t_node, t_int=t_int))
+print(json.dumps(dict(reps=out, t_table=t_tab)))
 """
 
 
-def run_oracle_sample(nsub, nodes, reps):
-    """Time the oracle (one thread) in a fresh process; returns the parsed JSON."""
+def run_oracle_sample(nsub, nodes, reps, cores=None):
+    """Time the oracle on `cores` host cores (default: all): one worker process
+    per core, each a single thread running its share of the sample, all timed
+    while running together.  Returns per-repetition step times extrapolated to
+    the full step divided over the cores."""
+    cores = cores or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = ORACLE_SAMPLE.format(root=ROOT)
-    r = subprocess.run([sys.executable, "-c", code, str(nsub), str(nodes), str(reps)], capture_output=True, text=True,
-                       env=env, timeout=3600)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ns, nn = max(1000, nsub // cores), max(1, nodes // cores)
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(ns), str(nn), str(reps), str(i)], stdin=subprocess.PIPE,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env) for i in range(cores)]
+    for p in procs:
+        if p.stdout.readline().strip() != "ready":
+            raise RuntimeError("oracle worker failed: " + p.stderr.read()[-2000:])
+    for p in procs:
+        p.stdin.write("go\n")
+        p.stdin.flush()
+    res = []
+    for p in procs:
+        o, e = p.communicate(timeout=3600)
+        if p.returncode != 0:
+            raise RuntimeError("oracle worker failed: " + e[-2000:])
+        res.append(json.loads(o.strip().splitlines()[-1]))
+    nv, M = 1_000_000, 1026 * 1026
+    steps = []
+    for r in range(reps):
+        t_reg = statistics.mean(w["reps"][r]["t_reg"] for w in res)
+        t_node = statistics.mean(w["reps"][r]["t_node"] for w in res)
+        t_int = statistics.mean(w["reps"][r]["t_int"] for w in res)
+        steps.append((t_reg * nv + t_node * M + t_int * nv) / cores)
+    return {"steps": steps, "cores": cores, "nsub": ns, "nodes": nn, "t_table": res[0]["t_table"]}
 
 
 def oracle_line_fields(res):
-    steps = [x["step_s"] for x in res["reps"]]
-    mean = statistics.mean(steps)
-    sample = ("per step: R_v of %d random vortices, direct-sum L^-1 at %d random nodes, E_v (u and v) of the same "
-              "%d vortices, each extrapolated linearly to 1e6 vortices and all 1026^2 nodes the step needs "
-              "(O(M^2) direct sum); one thread; LGF table by quadrature excluded (%.2f s, once per grid)") % (
-                  res["nsub"], res["nodes"], res["nsub"], res["t_table"])
+    mean = statistics.mean(res["steps"])
+    sample = ("per step and core: R_v of %d random vortices, the direct-sum L^-1 at %d random nodes, E_v (u and v) of "
+              "the same vortices, each worker a single thread, %d workers running together; per-unit times "
+              "extrapolated to 1e6 vortices and all 1026^2 nodes the step needs (O(M^2) direct sum) and divided "
+              "over the %d cores; LGF table by quadrature excluded (%.2f s, once per grid)") % (
+                  res["nsub"], res["nodes"], res["cores"], res["cores"], res["t_table"])
     return mean, sample
 
 
 # ------------------------------------------------------------------ clocks
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (ctypes, the driver's
+    libnvidia-ml) every millisecond in a thread, so that even a timed loop of a
+    few milliseconds has its own record.  Reading only; nothing is set."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+        import threading
+        self.ok = False
+        self.samples, self.reasons, self.maxmhz = [], 0, 0
+        self._stop = threading.Event()
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.lib.nvmlDeviceGetMaxClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.maxmhz = mx.value
+            self.reason_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(self.lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(clk)) == 0:
+                self.samples.append(clk.value)
+            if self.reason_fn(self.h, ctypes.byref(rs)) == 0:
+                self.reasons |= rs.value
+            time.sleep(0.001)
+
+    def start(self):
+        import threading
+        if self.ok:
+            self.th = threading.Thread(target=self._run, daemon=True)
+            self.th.start()
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self._stop.set()
+        self.th.join()
+        if not self.samples:
+            return None
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.maxmhz,
+                "reasons": sorted(v for k, v in self.REASONS.items() if self.reasons & k),
+                "samples": len(self.samples), "source": "nvml, 1 ms"}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self):
+    def __init__(self, index=0):
         self.proc = None
         self.path = None
+        self.index = index
+        self.nvml = NvmlSampler(index)
 
     def start(self):
+        self.nvml.start()
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -126,56 +210,125 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self, gpu_index=0):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
+    def stop(self, gpu_index=None):
+        gpu_index = self.index if gpu_index is None else gpu_index
+        nv = self.nvml.stop()
+        smi = None
+        if self.proc is not None:
+            self.proc.terminate()
             try:
-                if int(parts[0]) != gpu_index:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            sm, mx, reasons = [], [], set()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
                     continue
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+                try:
+                    if int(parts[0]) != gpu_index:
+                        continue
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+            if sm:
+                smi = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                       "samples": len(sm), "source": "nvidia-smi, 50 ms"}
+        return nv or smi
 
 
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    return int(vis) if vis.isdigit() else local
 
 
-def kernel_bytes(name, nx, ny, P, Q, nv, nrec, esz):
-    """Bytes a launch must move by its design: each input read once, each
-    output written once (the records and per-block histograms included)."""
+def kernel_bytes(name, nx, ny, nv, esz):
+    """Algorithmic bytes of a launch in the step model (36 B/vortex + 28 B/node
+    for the FP32 path): R_v reads a 16-byte cell record per vortex and writes w;
+    the three FFT passes read w and the kernel spectrum quadrant and write the
+    node velocity; E_v reads 12 bytes of position per vortex and the node
+    velocity and writes (u, v).  Binning, record copies and FFT intermediates
+    are implementation traffic (None here; reported from ncu)."""
     M = nx * ny
-    ntiles = -(-nx // 32) * -(-ny // 32)
-    spec = (P // 2 + 1) * ny * 2 * esz
-    nb = min(608, -(-nv // 1024))
     return {
-        "bin_locate": 24 * nv + 16 * nv + 4 * nb * ntiles,
-        "bin_offsets": 8 * nb * ntiles,
-        "bin_scatter": 16 * nv + 16 * nrec + 4 * nb * ntiles,
-        "regularize": 16 * nrec + esz * M,
-        "fft_rows_fwd": esz * M + spec,
-        "fft_cols_conv": spec + (P // 2 + 1) * (Q // 2 + 1) * esz + 2 * spec,
-        "fft_rows_inv": 2 * spec + 2 * esz * M,
-        "interpolate": 16 * nrec + 2 * esz * M + 2 * esz * nv,
+        "regularize": 16 * nv + esz * M,
+        "fft_rows_fwd": esz * M,
+        "fft_cols_conv": esz * M,
+        "fft_rows_inv": 2 * esz * M,
+        "interpolate": 12 * nv + 2 * esz * nv + 2 * esz * M,
+        "vic_advect": 12 * nv + 2 * esz * nv + 2 * esz * M,
     }.get(name)
+
+
+def step_traffic():
+    """Per-step DRAM bytes of the step kernels from the committed ncu summary,
+    if it was taken from the current sources."""
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    tj = json.load(open(tpath))
+    if tj.get("csrc_sha") != csrc_sha():
+        return None
+    return tj
+
+
+def csrc_sha():
+    """Short hash of the CUDA sources (ties an ncu record to the build it measured)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2102_11910_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def time_events(step, K, stream, flush):
+    """K steps bracketed by CUDA events on `stream`, L2 flushed before each
+    (outside the events); returns the per-step times in ms."""
+    import torch
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 255)
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+def kernel_table(rep, nsteps, g, nv, esz, hbm_peak):
+    """Per-kernel event times of the timing pass with each kernel's algorithmic
+    bytes (scope model) and the bandwidth they represent."""
+    kern = {}
+    total = sum(v[1] for v in rep.values())
+    for name, (n, ms) in rep.items():
+        b = kernel_bytes(name, g.nx, g.ny, nv, esz)
+        avg = ms / n
+        kern[name] = {"launches_per_step": n / nsteps, "avg_ms": avg, "share": ms / total, "alg_bytes": b,
+                      "gbs": (b / (avg / 1e3) / 1e9) if b else None,
+                      "frac": (b / (avg / 1e3) / 1e9 / hbm_peak) if b else None}
+    return kern
+
+
+def roofline_of(kern, hbm_peak, peak_note, traffic_rec):
+    """The dominant kernel (most time among those with algorithmic bytes)."""
+    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
+    traffic = None
+    if traffic_rec and dom in traffic_rec.get("kernels", {}):
+        traffic = traffic_rec["kernels"][dom].get("dram_bytes")
+    return {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / hbm_peak, "traffic": traffic, "peak_source": peak_note,
+            "alg_bytes_per_launch": kern[dom]["alg_bytes"]}
 
 
 # ------------------------------------------------------------------ our arm
@@ -213,7 +366,7 @@ def bench_ours(args):
         K = args.steps
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        clk = ClockSampler()
+        clk = ClockSampler(gpu_index(local))
         clk.start()
         if world > 1:
             dist.barrier()
@@ -228,8 +381,7 @@ def bench_ours(args):
         t_wall = time.perf_counter() - t_wall0
         if world > 1:
             dist.barrier()
-        clocks = clk.stop(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0)
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+        clocks = clk.stop()
         pf.pf_sync(plan)
         per = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         total_ms = max_over_ranks(sum(per), world)
@@ -253,30 +405,50 @@ def bench_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_note = "measured" if peaks else "fallback"
-    # records per vortex for uniform positions: a 4-node stencil straddles a
-    # 32-node tile edge with probability 3/32 per direction
-    dup = (1 + 3 / 32) ** 2
-    nrec_est = int(nv * dup)
-    kern = {}
-    for name, (n, ms) in rep.items():
-        b = kernel_bytes(name, g.nx, g.ny, plan.P, plan.Q, nv, nrec_est, 4)
-        avg = ms / n
-        kern[name] = {"launches_per_step": n / KT, "avg_ms": avg, "share": ms / sum(v[1] for v in rep.values()),
-                      "alg_bytes": b, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
-    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
-        tj = json.load(open(tpath))
-        from paper_2102_11910_gb300.profiling import csrc_sha
-        if tj.get("csrc_sha") == csrc_sha() and dom in tj.get("kernels", {}):
-            traffic = tj["kernels"][dom].get("dram_bytes")
-    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["gbs"], "peak": hbm_peak, "unit": "GB/s",
-            "frac": kern[dom]["gbs"] / hbm_peak, "traffic": traffic, "peak_source": peak_note,
-            "alg_bytes_per_launch": kern[dom]["alg_bytes"]}
+    kern = kernel_table(rep, KT, g, nv, 4, hbm_peak)
+    traffic_rec = step_traffic()
+    roof = roofline_of(kern, hbm_peak, peak_note, traffic_rec)
     step_bytes = 36 * nv + 28 * g.nx * g.ny
-    step_roof = {"alg_bytes": step_bytes, "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
-                 "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak}
+    step_roof = {"alg_bytes": step_bytes, "model": "36 B/vortex + 28 B/node (FP32)",
+                 "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
+                 "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak, "peak": hbm_peak,
+                 "dram_bytes_measured": (traffic_rec or {}).get("step_dram_bytes", {}).get("pf_vic_velocity")}
+
+    # the same workload as a tile-ordered vortex state, stepped in time (forward
+    # Euler): deposit, node velocity, E_v with the move, incremental re-bin
+    with torch.cuda.stream(stream):
+        vstate = pf.VicState(plan, nv)
+        pf.pf_vic_state_set(vstate, X, Y, G)
+        umax = float(torch.sqrt(uq.double() ** 2 + vq.double() ** 2).max())
+        dt = 0.25 * g.dx / max(umax, 1e-30)       # a quarter cell per step at the fastest vortex
+
+        def vstep():
+            pf.pf_vic_step(vstate, dt, 0.0, 0.0)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            vstep()
+        pf.pf_sync(plan)
+        KV = min(K, 400)
+        per_v = time_events(vstep, KV, stream, flush)
+        pf.pf_sync(plan)
+        pf.pf_timing_enable(plan, True)
+        for k in range(min(KV, 100)):
+            flush.fill_(k & 255)
+            vstep()
+        rep_v = pf.pf_timing_report(plan)
+        pf.pf_timing_enable(plan, False)
+        _, _, _, nv_left, _ = pf.pf_vic_state_get(vstate)
+        vstate.close()
+    ms_v = max_over_ranks(sum(per_v), world) / KV
+    kern_v = kernel_table(rep_v, min(KV, 100), g, nv, 4, hbm_peak)
+    vic_state = {"value": world / (ms_v / 1e3), "unit": UNIT, "ms_per_step": ms_v, "steps": KV,
+                 "dt": dt, "vortices_after": nv_left,
+                 "step_roofline": {"alg_bytes": step_bytes, "achieved_gbs": step_bytes / (ms_v / 1e3) / 1e9,
+                                   "frac": step_bytes / (ms_v / 1e3) / 1e9 / hbm_peak},
+                 "roofline": roofline_of(kern_v, hbm_peak, peak_note, traffic_rec), "kernels": kern_v,
+                 "desc": "same 1e6 vortices as a tile-ordered pf_vic_state: one forward-Euler time step per "
+                         "call (R_v from the binned records, spectral node velocity, E_v with the move, "
+                         "incremental re-bin), dt = a quarter cell at the fastest vortex, L2 flushed between steps"}
 
     # end to end through the host-buffer entry points (page-locked host memory),
     # every step copying its inputs in and its velocities out:
@@ -403,9 +575,9 @@ def bench_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
-        res = run_oracle_sample(nsub=200000, nodes=600, reps=1)
+        res = run_oracle_sample(nsub=400000, nodes=1200, reps=1)
         mean, sample = oracle_line_fields(res)
-        cpu = {"value": 1.0 / mean, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": 1.0 / mean, "unit": UNIT, "cores": res["cores"], "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {
@@ -419,6 +591,7 @@ def bench_ours(args):
             "roofline": roof, "step_roofline": step_roof,
             "kernels": kern, "gpu_launches": int(round(launches_per_step * K)),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed_loop": t_wall,
+            "vic_state_step": vic_state,
         }
         line.update(extras)
         print(json.dumps(line))
@@ -622,19 +795,20 @@ def bench_reference(args):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
-    # per-step sample sized so that K + W steps take about two minutes of CPU time
-    per = 120.0 / max(1, K + W)
-    nodes = max(1, int(per / 3 / 0.012))
-    nsub = max(2000, min(200000, int(per / 3 / 1.5e-6)))
-    res = run_oracle_sample(nsub=nsub, nodes=nodes, reps=K + W)
-    res["reps"] = res["reps"][W:]
+    # per-step sample sized so that K + W steps take about two minutes on the host cores
+    cores = os.cpu_count() or 1
+    per = 120.0 / max(1, K + W) * cores
+    nodes = max(cores, int(per / 3 / 0.012))
+    nsub = max(1000 * cores, min(200000 * cores, int(per / 3 / 1.5e-6)))
+    res = run_oracle_sample(nsub=nsub, nodes=nodes, reps=K + W, cores=cores)
+    res["steps"] = res["steps"][W:]
     mean, sample = oracle_line_fields(res)
     value = 1.0 / mean
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

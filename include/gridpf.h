@@ -56,6 +56,7 @@ typedef struct {
 typedef struct pf_plan_s* pf_plan;
 typedef struct pf_schur_s* pf_schur;
 typedef struct pf_state_s* pf_state;
+typedef struct pf_vic_state_s* pf_vic_state;
 
 /* ------------------------------------------------------------------ plan */
 
@@ -369,6 +370,47 @@ pf_status pf_state_set(pf_state state, const double* X, const double* Y, const d
 /* Copy the current vortices to HOST arrays (each at least nv long; any may be
  * NULL) and report nv and t.  Synchronises. */
 pf_status pf_state_get(pf_state state, double* X, double* Y, double* Gam, int64_t* nv, double* t);
+
+/* Body-free vortex-in-cell time stepping on a tile-ordered vortex set
+ * (Sec. 2.1: R_v, L^-1 with the LGF, node velocity, E_v; vortices advected
+ * with the local velocity by forward Euler, Sec. 2.4.2).
+ *
+ * The state keeps its vortices binned by 32 x 32 node tile between steps (a
+ * home record per vortex plus a copy in each other tile its 4 x 4 stencil
+ * reaches), so a step moves the vortices and re-bins them incrementally
+ * instead of binning from positions: pf_vic_step = R_v, the spectral node
+ * velocity, E_v with the Euler move, and the re-bin.  Mixed plans keep each
+ * position as an integer cell and a 24-bit fixed-point fraction (moved in
+ * fixed point, rounded to nearest), FP64 plans as a cell and a double
+ * fraction.  The state uses its plan's stream and work buffers; the plan must
+ * outlive it.
+ *
+ *   capacity     the most vortices the state holds (1 .. 2^27); device memory
+ *                is about 2 x 4 x capacity records (16 bytes mixed, 32 FP64)
+ *                plus per-tile tables
+ */
+pf_status pf_vic_state_create(pf_plan plan, int64_t capacity, pf_vic_state* out);
+pf_status pf_vic_state_destroy(pf_vic_state state);
+/* Bin nv vortices given as DEVICE arrays (nv <= capacity; PF_ERR_ARG beyond).
+ * Vortex k keeps the index k for pf_vic_state_get and pf_vic_step's optional
+ * velocity output.  Vortices whose stencil leaves the grid are skipped and
+ * counted (PF_ERR_OUT_OF_DOMAIN at pf_sync).  Resets the time to 0.
+ * Synchronises the plan's stream. */
+pf_status pf_vic_state_set(pf_vic_state state, const double* X, const double* Y, const double* Gam, int64_t nv);
+/* Positions and strengths in DEVICE arrays of at least the nv of the last
+ * set call, at the vortices' indices (a dropped vortex reads NaN); any of X,
+ * Y, Gam may be NULL only if all are.  nv (host, may be NULL) receives the
+ * number of vortices still held and t (host, may be NULL) the time; asking
+ * for nv synchronises. */
+pf_status pf_vic_state_get(pf_vic_state state, double* X, double* Y, double* Gam, int64_t* nv, double* t);
+/* One forward-Euler step of length dt in the uniform flow (Uinf, Vinf).  uq,
+ * vq: optional DEVICE arrays (real, both or neither) that receive the
+ * velocity each vortex moved with, at its index.  A vortex whose home tile
+ * would move by more than one tile in a step (possible only for moves of 32
+ * cells or more) is dropped (PF_ERR_CAPACITY at pf_sync); one whose stencil
+ * would leave the grid is dropped and counted (PF_ERR_OUT_OF_DOMAIN).
+ * Asynchronous on the plan's stream. */
+pf_status pf_vic_step(pf_vic_state state, double dt, double Uinf, double Vinf, void* uq, void* vq);
 
 /* A rigid body given in its own frame (HOST arrays of ns points: coordinates
  * and segment lengths), turned by the angle -alpha(t) about the origin,

@@ -205,6 +205,65 @@ def pf_timing_report(plan):
     return out
 
 
+class VicState:
+    """Handle of a pf_vic_state: a tile-ordered vortex set stepped on `plan`'s
+    stream (body-free vortex-in-cell, forward Euler)."""
+
+    def __init__(self, plan, capacity):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _native.check(_native.lib().pf_vic_state_create(plan.handle, int(capacity), ctypes.byref(h)),
+                      "pf_vic_state_create", plan.handle)
+        self.handle = h
+        self.nv0 = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_vic_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pf_vic_state_set(state, X, Y, G):
+    n = X.numel()
+    if Y.numel() != n or G.numel() != n:
+        raise ValueError("X, Y and G must have the same length")
+    _native.check(_native.lib().pf_vic_state_set(state.handle, _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
+                                                 _ptr(G, torch.float64, "G"), n),
+                  "pf_vic_state_set", state.plan.handle)
+    state.nv0 = n
+
+
+def pf_vic_state_get(state):
+    """(X, Y, G, nv, t): device FP64 tensors indexed like the set call's input."""
+    n = state.nv0
+    X, Y, G = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    nv = ctypes.c_int64()
+    t = ctypes.c_double()
+    _native.check(_native.lib().pf_vic_state_get(state.handle, _ptr(X), _ptr(Y), _ptr(G), ctypes.byref(nv),
+                                                 ctypes.byref(t)),
+                  "pf_vic_state_get", state.plan.handle)
+    return X, Y, G, nv.value, t.value
+
+
+def pf_vic_step(state, dt, Uinf=0.0, Vinf=0.0, uq=None, vq=None):
+    """One Euler step; with uq, vq (device tensors of the plan's precision) the
+    velocities the vortices moved with are written at their indices."""
+    dtype = state.plan.dtype
+    if (uq is None) != (vq is None):
+        raise ValueError("give both uq and vq or neither")
+    if uq is not None and (uq.numel() < state.nv0 or vq.numel() < state.nv0):
+        raise ValueError("uq and vq must hold the set call's vortex count")
+    _native.check(_native.lib().pf_vic_step(state.handle, float(dt), float(Uinf), float(Vinf),
+                                            _ptr(uq, dtype, "uq"), _ptr(vq, dtype, "vq")),
+                  "pf_vic_step", state.plan.handle)
+
+
 def pf_regularize_noalloc(nx, ny, dx, x0, y0, precision, X, Y, G, w, out_of_domain=None, status=None, stream=None):
     """Allocation-free regularization (no plan; static device scratch, nv <= 65536).
 

@@ -33,6 +33,11 @@ SIGNATURES = {
     "pf_vic_velocity": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
     "pf_vic_velocity_host": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
     "pf_vic_velocity_host_async": (_c.c_int, [_P, _P, _P, _P, _I64, _D, _D, _P, _P]),
+    "pf_vic_state_create": (_c.c_int, [_P, _I64, _c.POINTER(_P)]),
+    "pf_vic_state_destroy": (_c.c_int, [_P]),
+    "pf_vic_state_set": (_c.c_int, [_P, _P, _P, _P, _I64]),
+    "pf_vic_state_get": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
+    "pf_vic_step": (_c.c_int, [_P, _D, _D, _D, _P, _P]),
     "pf_regularize_noalloc": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "pf_schur_factor": (_c.c_int, [_P, _P, _c.POINTER(_P)]),
     "pf_schur_destroy": (_c.c_int, [_P]),

@@ -191,15 +191,13 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
     const bool h0 = j0 < ny, h1 = j0 + 1 < ny;
     pdl_wait();
     C v[16];
+    const int ja = h0 ? j0 : ny - 1, jb = h1 ? j0 + 1 : ny - 1;     // clamped rows: loads never branch
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int n = t + TP * r;
-        T a = 0, b = 0;
-        if (n < nx) {
-            if (h0) a = w[(size_t)j0 * nx + n];
-            if (h1) b = w[(size_t)(j0 + 1) * nx + n];
-        }
-        v[r] = cmake<C>(a, b);
+        const int nc = n < nx ? n : nx - 1;
+        const T a = w[(size_t)ja * nx + nc], b = w[(size_t)jb * nx + nc];
+        v[r] = cmake<C>(n < nx && h0 ? a : T(0), n < nx && h1 ? b : T(0));
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twP);
 #pragma unroll
@@ -249,9 +247,10 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
     }
     C v[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < 16; ++r) {            // clamped row: loads never branch
         const int l = t + TQ * r;
-        v[r] = l < ny ? T1[spec_at(l, k, nk)] : cmake<C>(T(0), T(0));
+        const C x = T1[spec_at(l < ny ? l : ny - 1, k, nk)];
+        v[r] = l < ny ? x : cmake<C>(T(0), T(0));
     }
     fft_strided<C, false, R3>(v, buf, t, tw256, twQ);
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -324,9 +323,12 @@ __global__ void __launch_bounds__(32 * R3, sizeof(T) == 4 && R3 == 8 ? 4 : 1) k_
     }
     const int h = P / 2;
     pdl_wait();
+    const int jla = ha ? ja : ny - 1, jlb = hb ? jb : ny - 1;       // clamped rows: loads never branch
     for (int k = t; k <= h; k += TP) {
-        C a = ha ? T2a[spec_at(ja, k, NK)] : cmake<C>(T(0), T(0));
-        C b = hb ? Sb[spec_at(jb, k, NK)] : cmake<C>(T(0), T(0));
+        C a = T2a[spec_at(jla, k, NK)];
+        C b = Sb[spec_at(jlb, k, NK)];
+        if (!ha) a = cmake<C>(T(0), T(0));
+        if (!hb) b = cmake<C>(T(0), T(0));
         if (k == 0 || k == h) { a.y = 0; b.y = 0; }
         buf[spad(k)] = a + mul_i(b);
         if (k > 0 && k < h) buf[spad(P - k)] = conjc(a) + mul_i(conjc(b));
