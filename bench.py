@@ -719,21 +719,21 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                 plans.append(p)
                 states.append(st)
                 bodies.append(pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"]))
-            dt = 0.002
+            dts = [r["dt"] for r in inst]
             if name.startswith("batched"):
-                pf.pf_step_batch(plans, states, bodies, dt)          # factorisations
+                pf.pf_step_batch(plans, states, bodies, dts)          # factorisations
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 for _ in range(3):
-                    pf.pf_step_batch(plans, states, bodies, dt)
+                    pf.pf_step_batch(plans, states, bodies, dts)
                 torch.cuda.synchronize()
                 res[name] = 3 * len(inst) / (time.perf_counter() - t0)
             else:
-                for p, st, b in zip(plans, states, bodies):
+                for p, st, b, dt in zip(plans, states, bodies, dts):
                     pf.pf_step(p, st, dt, b)
                     pf.pf_sync(p)
                 t0 = time.perf_counter()
-                for p, st, b in zip(plans, states, bodies):
+                for p, st, b, dt in zip(plans, states, bodies, dts):
                     pf.pf_step(p, st, dt, b)
                     pf.pf_sync(p)
                 res[name] = len(inst) / (time.perf_counter() - t0)
@@ -743,8 +743,17 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                        "batched: one stream per instance, shared tables; unbatched FP64: one "
                                        "instance at a time", **res}
         print("workload done: %s" % 'uneven_batch', file=sys.stderr, flush=True)
-    # request server: burst, then Poisson arrivals at 70 % of the burst throughput
+    out["serving"] = bench_serving(pf, inputs, n_requests, (0.3, 0.7, 1.0))
+    return out
+
+
+def bench_serving(pf, inputs, n_requests, fractions):
+    """The request server under load: a burst (every request at time 0) gives the
+    saturation throughput; then Poisson arrivals at the given fractions of it,
+    with p50/p99 latency (submission to completion) at each rate."""
+    import numpy as np
     reqs = inputs.serving_requests(n=n_requests)
+
     def run(rate):
         server = pf.Server(max_slots=32, hbm_budget_bytes=32 << 30, precision=pf.PF_MIXED)
         rng = np.random.default_rng(7)
@@ -764,7 +773,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                 body = pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"])
                 gg = r["grid"]
                 pending.add(pf.pf_server_submit(server, (gg.nx, gg.ny, gg.dx, gg.x0, gg.y0), r["X"], r["Y"], r["G"],
-                                                r["nsteps"], 0.002, body))
+                                                r["nsteps"], r["dt"], body))
                 steps += r["nsteps"]
                 i += 1
             for t in pf.pf_server_progress(server):
@@ -777,15 +786,18 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
         server.close()
-        lats = sorted(lats)
+        lats = sorted(lats) or [float("nan")]
         return {"requests": len(reqs), "failed": failed, "steps": steps, "wall_s": wall, "steps_per_s": steps / wall,
-                "requests_per_s": len(reqs) / wall, "p50_ms": 1e3 * lats[len(lats) // 2],
-                "p99_ms": 1e3 * lats[min(len(lats) - 1, int(0.99 * len(lats)))]}
+                "requests_per_s": len(reqs) / wall, "offered_requests_per_s": rate,
+                "p50_ms": 1e3 * lats[len(lats) // 2], "p99_ms": 1e3 * lats[min(len(lats) - 1, int(0.99 * len(lats)))]}
     burst = run(None)
-    poisson = run(0.7 * burst["requests_per_s"])
-    out["serving"] = {"desc": "requests as the uneven batch plus 10% at 1024^2 with 1e5 vortices, 1-50 steps "
-                              "each, dt 0.002, mixed precision, 32 slots", "burst": burst,
-                      "poisson_at_0.7x": poisson}
+    out = {"desc": "%d requests: instances of the uneven batch (strengths N(0,1e-3), a CFL step each) plus 10%% at "
+                   "1024^2 with 1e5 vortices, 1-50 steps each, mixed precision, 32 slots; burst = all at t=0 "
+                   "(saturation), then Poisson arrivals at fractions of the burst throughput" % len(reqs),
+           "burst": burst}
+    for f in fractions:
+        out["poisson_at_%gx" % f] = run(f * burst["requests_per_s"])
+        print("serving rate %gx done" % f, file=sys.stderr, flush=True)
     return out
 
 
@@ -821,7 +833,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 leg and the CPU baseline")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="only the request server: 4096 requests, Poisson arrivals from 0.1x to 1.2x of saturation")
     args = ap.parse_args()
+    if args.serving_sweep:
+        import torch
+        import paper_2102_11910_gb300 as pf
+        from paper_2102_11910_gb300 import inputs
+        torch.cuda.set_device(dist_env()[2])
+        res = bench_serving(pf, inputs, 4096, (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2))
+        print(json.dumps({"serving_sweep": res}))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

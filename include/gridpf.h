@@ -227,6 +227,20 @@ pf_status pf_sheet_solve(pf_plan plan, pf_schur schur, const void* w, const pf_m
                          const double* Xnew, const double* Ynew, double* f, double* gamma_new,
                          double* s0);
 
+/* The same solve for the free vorticity of point vortices given directly:
+ * X, Y, Gam are DEVICE arrays of nv vortices.  E_s L^-1 R_v Gamma is summed
+ * in FP64 from the vortices themselves (sixteen M4' node entries each, Eq.
+ * vortexregularization, against the FP64 LGF), so no FP32 rounding of a
+ * regularized field enters the sheet, whatever the plan's precision: the sheet
+ * of a mixed plan then carries only FP64 rounding times cond(S) (Sec. 2.2.2,
+ * S ill-conditioned below dS/dx ~ 1).  Cost: 256 ns nv FP64 multiply-adds.
+ * Vortices whose stencil leaves the grid are left out.  Other arguments,
+ * outputs and errors as pf_sheet_solve.  Synchronises. */
+pf_status pf_sheet_solve_vortices(pf_plan plan, pf_schur schur, const double* X, const double* Y,
+                                  const double* Gam, int64_t nv, const pf_motion* m, int32_t mode, double param,
+                                  int32_t n_edges, const int32_t* edges, const double* Xnew, const double* Ynew,
+                                  double* f, double* gamma_new, double* s0);
+
 /* Linear and angular impulse of the fluid about the origin (Sec. 2.6.2,
  * Eqs. linimpxd, linimpyd, angimpd); for a single body the force and moment
  * are F = -rho dP/dt and M_O = -rho dPi_O/dt (Eq. FMimp):
@@ -465,7 +479,8 @@ pf_status pf_step_multi(pf_plan plan, pf_state state, int32_t n_bodies, const pf
                         double dt, int32_t scheme);
 
 /* Independent instances, one step each: pf_step for plans[i], states[i],
- * bodies[i] (i < n), each enqueued on its own plan's stream so instances on
+ * bodies[i] and step length dt[i] (host arrays, i < n), each enqueued on its
+ * own plan's stream so instances on
  * distinct streams overlap on the device.  When the process runs with
  * CUDA_DEVICE_MAX_CONNECTIONS >= 32 (set before CUDA starts), a batch of more
  * than 8 distinct plans and states is enqueued from several host threads (up
@@ -475,7 +490,7 @@ pf_status pf_step_multi(pf_plan plan, pf_state state, int32_t n_bodies, const pf
  * Returns the first error met; after an error the instances not yet taken
  * are not stepped. */
 pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
-                        double dt, int32_t scheme);
+                        const double* dt, int32_t scheme);
 
 /* ------------------------------------------------------- request server */
 

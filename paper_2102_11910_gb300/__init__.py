@@ -368,6 +368,31 @@ def pf_sheet_solve(plan, schur, w, motion, mode, param=0.0, edges=(), Xnew=None,
     return f, list(gn[:ne]), s0.value
 
 
+def pf_sheet_solve_vortices(plan, schur, X, Y, G, motion, mode, param=0.0, edges=(), Xnew=None, Ynew=None, f=None):
+    """Bound sheet for the free vorticity of point vortices (device FP64 X, Y, G),
+    E_s L^-1 R_v Gamma summed in FP64 from the vortices themselves.
+    Returns (f device float64 tensor, gamma_new host list, s0)."""
+    import numpy as np
+    n = X.numel()
+    if Y.numel() != n or G.numel() != n:
+        raise ValueError("X, Y and G must have the same length")
+    f = torch.empty(schur.ns, dtype=torch.float64, device="cuda") if f is None else f
+    ed = np.ascontiguousarray(edges, dtype=np.int32)
+    ne = len(ed)
+    xn = _host_f64(Xnew if Xnew is not None else np.zeros(max(ne, 1)))
+    yn = _host_f64(Ynew if Ynew is not None else np.zeros(max(ne, 1)))
+    gn = np.zeros(max(ne, 1))
+    s0 = ctypes.c_double()
+    m = _native.PfMotion(*[float(v) for v in motion])
+    c = ctypes.c_void_p
+    _native.check(_native.lib().pf_sheet_solve_vortices(
+        plan.handle, schur.handle, _ptr(X, torch.float64, "X"), _ptr(Y, torch.float64, "Y"),
+        _ptr(G, torch.float64, "G"), n, ctypes.byref(m), int(mode), float(param), ne, c(ed.ctypes.data) if ne else None,
+        c(xn.ctypes.data), c(yn.ctypes.data), _ptr(f, torch.float64, "f"), c(gn.ctypes.data), ctypes.byref(s0)),
+        "pf_sheet_solve_vortices", plan.handle)
+    return f, list(gn[:ne]), s0.value
+
+
 PF_MAX_BODIES = _native.MAX_BODIES
 
 
@@ -615,12 +640,16 @@ def pf_step(plan, state, dt, body=None, scheme=0):
 def pf_step_batch(plans, states, bodies, dt, scheme=0):
     """One step of many independent instances (each on its own plan's stream;
     a large batch of distinct plans and states is enqueued from several host
-    threads)."""
+    threads).  dt: one step length for all, or one per instance."""
     n = len(plans)
     P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     S = (ctypes.c_void_p * n)(*[s.handle.value for s in states])
     B = (_native.PfBodyKinematics * n)(*[b.struct for b in bodies])
-    _native.check(_native.lib().pf_step_batch(n, P, S, B, float(dt), int(scheme)), "pf_step_batch")
+    dts = [float(dt)] * n if not hasattr(dt, "__len__") else [float(d) for d in dt]
+    if len(dts) != n:
+        raise ValueError("one step length per instance")
+    D = (ctypes.c_double * n)(*dts)
+    _native.check(_native.lib().pf_step_batch(n, P, S, B, D, int(scheme)), "pf_step_batch")
 
 
 class Server:

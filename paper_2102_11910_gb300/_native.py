@@ -43,6 +43,7 @@ SIGNATURES = {
     "pf_schur_destroy": (_c.c_int, [_P]),
     "pf_schur_info": (_c.c_int, [_P, _P, _P, _P]),
     "pf_sheet_solve": (_c.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
+    "pf_sheet_solve_vortices": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _P, _I32, _D, _I32, _P, _P, _P, _P, _P, _P]),
     "pf_impulse": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pf_plan_set_rhs_route": (_c.c_int, [_P, _I32]),
     "pf_sheet_solve_edges": (_c.c_int, [_P, _P, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _P]),
@@ -58,7 +59,7 @@ SIGNATURES = {
     "pf_state_set": (_c.c_int, [_P, _P, _P, _P, _I64, _D]),
     "pf_state_get": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
     "pf_step": (_c.c_int, [_P, _P, _P, _D, _I32]),
-    "pf_step_batch": (_c.c_int, [_I32, _P, _P, _P, _D, _I32]),
+    "pf_step_batch": (_c.c_int, [_I32, _P, _P, _P, _P, _I32]),
     "pf_plan_clone": (_c.c_int, [_P, _I32, _P, _c.POINTER(_P)]),
     "pf_server_create": (_c.c_int, [_P, _c.POINTER(_P)]),
     "pf_server_destroy": (_c.c_int, [_P]),

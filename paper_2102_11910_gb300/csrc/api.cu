@@ -22,7 +22,7 @@ void free_plan(pf_plan p) {
     for (cudaEvent_t e : p->tm.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->tm.pool) cudaEventDestroy(e);
     void* own[] = {p->T1, p->T2a, p->T2b, p->w, p->uv, p->tile_count, p->gmax, p->tile_start, p->bin_off,
-                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->nz_idx, p->nz_val,
+                   p->pos, p->recs, p->stage, p->stage_out, p->diag, p->rhs64, p->nz_idx, p->nz_val, p->vent_idx, p->vent_val,
                    p->d_status, p->d_oob};
     for (void* q : own)
         if (q) cudaFree(q);

@@ -729,6 +729,31 @@ __global__ void __launch_bounds__(256) k_surface_einvlw_sparse(const int* __rest
     if (threadIdx.x == 0) out[p] = dx2 * tot;
 }
 
+// Vortex route of the same sum: the node entries of R_v Gamma listed straight
+// from the FP64 positions, sixteen per vortex (M4' weights in FP64, Eq.
+// vortexregularization), duplicates and all (the sum is linear), for the
+// sparse kernel.  A vortex whose stencil leaves the grid gives zero entries
+// (regularization skips it as well).
+__global__ void k_vortex_entries(const double* __restrict__ X, const double* __restrict__ Y,
+                                 const double* __restrict__ G, int64_t n, int nx, int ny, double x0, double y0,
+                                 double dx, int* __restrict__ idx, double* __restrict__ val, int* __restrict__ total) {
+    const double inv_dx2 = 1.0 / (dx * dx);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        int ix[4], iy[4];
+        double wx[4], wy[4];
+        const bool in = stencil(X[q], x0, dx, nx, ix, wx, false) && stencil(Y[q], y0, dx, ny, iy, wy, false);
+        const double g = in ? G[q] * inv_dx2 : 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                idx[16 * q + 4 * b + a] = in ? iy[b] * nx + ix[a] : 0;
+                val[16 * q + 4 * b + a] = in ? g * wy[b] * wx[a] : 0.0;
+            }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *total = (int)(16 * n);
+}
+
 // The same quantity from an FP64 psi = -L^-1 w on the grid: E_s L^-1 w = -E_s psi.
 __global__ void k_surface_from_psi(const double* __restrict__ psi, int nx, int ns, const int* __restrict__ six,
                                    const int* __restrict__ siy, const double* __restrict__ swx,
@@ -1170,10 +1195,40 @@ void schur_free(pf_schur s) {
 // multiply-adds at the GPU's low FP64 rate; on larger grids the same quantity
 // comes from an FP64 FFT solve psi = -L^-1 w (FP64 rounding, far below what
 // the ill-conditioned S amplifies into the sheet) read at the stencils.
-pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t nnz_bound) {
+pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t nnz_bound,
+                      const VortexSource* vs = nullptr) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     const int64_t M = (int64_t)p->nx * p->ny;
+    // the vortex route: forced, or for mixed plans while 256 ns nv multiply-adds stay below 2^31
+    if (vs && vs->n > 0 && (vs->force || (p->prec != PF_FP64 && 256 * (int64_t)ns * vs->n < ((int64_t)1 << 31)))) {
+        const int64_t ne = 16 * vs->n;
+        if (ne > ((int64_t)1 << 30)) {
+            snprintf(p->err, sizeof(p->err), "%lld vortices exceed the vortex route's entry list",
+                     (long long)vs->n);
+            return PF_ERR_CAPACITY;
+        }
+        if (ne > p->vent_cap) {
+            PF_CUDA(p, cudaStreamSynchronize(st));
+            if (p->vent_idx) cudaFree(p->vent_idx);
+            if (p->vent_val) cudaFree(p->vent_val);
+            p->vent_idx = nullptr;
+            p->vent_val = nullptr;
+            p->vent_cap = 0;
+            const int64_t cap = std::max<int64_t>(ne, 2 * p->vent_cap);
+            PF_CUDA(p, cudaMalloc(&p->vent_idx, (size_t)cap * sizeof(int) + 16));
+            PF_CUDA(p, cudaMalloc(&p->vent_val, (size_t)cap * sizeof(double)));
+            p->vent_cap = cap;
+        }
+        int* total = p->vent_idx + p->vent_cap;
+        const int nb = (int)std::min<int64_t>(ceil_div(vs->n, 256), 152 * 8);
+        k_vortex_entries<<<nb, 256, 0, st>>>(vs->X, vs->Y, vs->G, vs->n, p->nx, p->ny, p->x0, p->y0, p->dx,
+                                             p->vent_idx, p->vent_val, total);
+        k_surface_einvlw_sparse<<<ns, 256, 0, st>>>(p->vent_idx, p->vent_val, total, p->nx, s->six, s->siy, s->swx,
+                                                    s->swy, p->G, p->dx * p->dx, ew);
+        PF_LAUNCH_CHECK(p);
+        return PF_OK;
+    }
     const bool fft_ok = p->P >= 256 && p->Q >= 256;
     // the sparse route when the caller bounds the nonzero nodes and the sum is small
     const bool sparse = p->rhs_route == PF_RHS_SPARSE ||
@@ -1332,7 +1387,8 @@ __global__ void __launch_bounds__(256) k_constraints_multi(int ns, pf_multibody 
 
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
-                             const double* vy, double* f, const EdgeBounds& eb, int64_t nnz_bound) {
+                             const double* vy, double* f, const EdgeBounds& eb, int64_t nnz_bound,
+                             const VortexSource* vs) {
     const int ns = s->ns;
     cudaStream_t st = p->stream;
     double* sb = s->work;
@@ -1342,7 +1398,7 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
     double* res = y + 3 * ns;       // refinement residuals
     k_sbprime<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, m, sb);
     PF_LAUNCH_CHECK(p);
-    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound));
+    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound, vs));
     k_rhs0<<<1, 256, 0, st>>>(mode, ns, param, param_dev, sb, ew, s->f0hat, s->dgamma0, rhs);
     PF_LAUNCH_CHECK(p);
     int nc = 1;
@@ -1626,7 +1682,7 @@ double* multibody_newpos(pf_schur s) { return s->mwork + (2 + 3 * (size_t)MB_COL
 
 pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
                                    const double* vx, const double* vy, double* f, const double* gw_dev,
-                                   double** out_dev, int64_t nnz_bound) {
+                                   double** out_dev, int64_t nnz_bound, const VortexSource* vs) {
     const int nb = mb.n_bodies, ns = s->ns, nc = 1 + ne + nb;
     cudaStream_t st = p->stream;
     PF_TRY(multibody_scratch(p, s));
@@ -1638,7 +1694,7 @@ pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const p
     double* out = multibody_newpos(s) + 2 * MB_EDGES;   // s0 (B), Gamma (E)
     k_sbprime_multi<<<ceil_div(ns, 128), 128, 0, st>>>(s->x, s->y, ns, mb, sb);
     PF_LAUNCH_CHECK(p);
-    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound));
+    PF_TRY(surface_rhs(p, s, w, ew, nnz_bound, vs));
     k_rhs0<<<1, 256, 0, st>>>(PF_SHEET_KUTTA_SHED, ns, 0.0, nullptr, sb, ew, s->f0hat, s->dgamma0, rhs);
     if (ne > 0)
         k_unit_vortex<<<dim3(ceil_div(ns, 128), ne), 128, 0, st>>>(vx, vy, ne, s->six, s->siy, s->swx, s->swy, ns,
@@ -1727,6 +1783,46 @@ pf_status pf_sheet_solve(pf_plan p, pf_schur s, const void* w, const pf_motion* 
         PF_CUDA(p, cudaMemcpyAsync(vxy + 2, Ynew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     }
     pf_status st = sheet_solve_device(p, s, w, *m, mode, param, nullptr, n_edges, edges, vxy, vxy + 2, f);
+    if (st != PF_OK) return st;
+    double sc[3];
+    PF_CUDA(p, cudaMemcpyAsync(sc, s->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (s0) *s0 = sc[0];
+    if (gamma_new)
+        for (int e = 0; e < (mode == PF_SHEET_KUTTA_SHED ? n_edges : 0); ++e) gamma_new[e] = sc[1 + e];
+    return PF_OK;
+}
+
+pf_status pf_sheet_solve_vortices(pf_plan p, pf_schur s, const double* X, const double* Y, const double* Gam,
+                                  int64_t nv, const pf_motion* m, int32_t mode, double param, int32_t n_edges,
+                                  const int32_t* edges, const double* Xnew, const double* Ynew, double* f,
+                                  double* gamma_new, double* s0) {
+    if (!p || !m || !f || nv < 0 || (nv > 0 && (!X || !Y || !Gam)) || mode < PF_SHEET_GIVEN_S0 ||
+        mode > PF_SHEET_KUTTA_SHED)
+        return PF_ERR_ARG;
+    if (!s) return PF_ERR_NOT_FACTORED;
+    const bool kutta = mode == PF_SHEET_KUTTA_STEADY || mode == PF_SHEET_KUTTA_SHED;
+    if (kutta && (n_edges < 1 || n_edges > 2 || !edges || (mode == PF_SHEET_KUTTA_STEADY && n_edges != 1)))
+        return PF_ERR_ARG;
+    if (!kutta) n_edges = 0;
+    for (int e = 0; e < n_edges; ++e)
+        if (edges[e] < 0 || edges[e] >= s->ns) return PF_ERR_ARG;
+    if (mode == PF_SHEET_KUTTA_SHED && (!Xnew || !Ynew)) return PF_ERR_ARG;
+    double* vxy = s->scal + 4;
+    if (mode == PF_SHEET_KUTTA_SHED) {
+        PF_CUDA(p, cudaMemcpyAsync(vxy, Xnew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        PF_CUDA(p, cudaMemcpyAsync(vxy + 2, Ynew, n_edges * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    }
+    VortexSource vs;
+    vs.X = X;
+    vs.Y = Y;
+    vs.G = Gam;
+    vs.n = nv;
+    vs.force = true;
+    // with no vortices the free vorticity is zero: the plan's zeroed field stands in for w
+    if (nv == 0) PF_CUDA(p, cudaMemsetAsync(p->w, 0, (size_t)p->nx * p->ny * p->esz, p->stream));
+    pf_status st = sheet_solve_device(p, s, p->w, *m, mode, param, nullptr, n_edges, edges, vxy, vxy + 2, f,
+                                      EdgeBounds(), -1, nv > 0 ? &vs : nullptr);
     if (st != PF_OK) return st;
     double sc[3];
     PF_CUDA(p, cudaMemcpyAsync(sc, s->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));

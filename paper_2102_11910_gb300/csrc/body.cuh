@@ -50,9 +50,19 @@ pf_status invert_schur_matrix(pf_plan p, pf_schur s);
 // device; *out_dev receives the device address of s0 (B values) then the new
 // strengths (one per edge).
 pf_status multibody_check(const pf_multibody& mb, int ns, int* n_edges_total);
+// Point vortices (device FP64 arrays of n) whose E_s L^-1 R_v Gamma a sheet
+// solve forms directly (the vortex route of surface_rhs): always when force is
+// set; otherwise only for mixed plans while the direct sum is cheap.
+struct VortexSource {
+    const double* X = nullptr;
+    const double* Y = nullptr;
+    const double* G = nullptr;
+    int64_t n = 0;
+    bool force = false;
+};
 pf_status sheet_solve_multi_device(pf_plan p, pf_schur s, const void* w, const pf_multibody& mb, int ne,
                                    const double* vx, const double* vy, double* f, const double* gw_dev,
-                                   double** out_dev, int64_t nnz_bound = -1);
+                                   double** out_dev, int64_t nnz_bound = -1, const VortexSource* vs = nullptr);
 // Generalized edge condition (Sec. 2.5) for the shedding mode: with on = 0 every
 // edge sheds under the Kutta condition; otherwise edge e sheds only when its
 // intermediate value lies outside [lo[e], hi[e]], and ends at the bound crossed.
@@ -67,7 +77,7 @@ struct EdgeBounds {
 pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_motion& m, int mode, double param,
                              const double* param_dev, int n_edges, const int* edges, const double* vx,
                              const double* vy, double* f, const EdgeBounds& eb = EdgeBounds(),
-                             int64_t nnz_bound = -1);
+                             int64_t nnz_bound = -1, const VortexSource* vs = nullptr);
 // w += R_s f  (device f of ns doubles, w real[nx*ny])
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);
 

@@ -124,6 +124,10 @@ struct pf_plan_s {
     // the per-chunk counts and the total (allocated by the first sparse solve)
     int* nz_idx = nullptr;
     double* nz_val = nullptr;
+    // vortex route: sixteen (node, FP64 value) entries per vortex, then the count
+    int* vent_idx = nullptr;
+    double* vent_val = nullptr;
+    int64_t vent_cap = 0;
     // pressure field: the plan of the cell-centre lattice ((nx-1) x (ny-1),
     // origin shifted by dx/2, same stream and precision) and its FP64 source
     // and kinetic-energy scratch, built by the first pf_pressure_field call

@@ -597,9 +597,9 @@ pf_status pf_step_multi(pf_plan p, pf_state s, int32_t n_bodies, const pf_body_k
     return PF_OK;
 }
 
-pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies, double dt,
-                        int32_t scheme) {
-    if (n < 0 || (n > 0 && (!plans || !states || !bodies))) return PF_ERR_ARG;
+pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
+                        const double* dt, int32_t scheme) {
+    if (n < 0 || (n > 0 && (!plans || !states || !bodies || !dt))) return PF_ERR_ARG;
     // Every instance is enqueued on its own plan's stream, and distinct streams
     // run concurrently on the device.  Enqueueing one step costs tens of
     // microseconds of host time (launches, kinematics, shedding bookkeeping),
@@ -623,7 +623,7 @@ pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_bo
     }
     if (nthreads <= 1) {
         for (int32_t i = 0; i < n; ++i) {
-            const pf_status st = pf_step(plans[i], states[i], &bodies[i], dt, scheme);
+            const pf_status st = pf_step(plans[i], states[i], &bodies[i], dt[i], scheme);
             if (st != PF_OK) return st;
         }
         return PF_OK;
@@ -641,7 +641,7 @@ pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_bo
         for (;;) {
             const int32_t i = next.fetch_add(1);
             if (i >= n || first_err.load() != PF_OK) return;
-            const pf_status st = pf_step(plans[i], states[i], &bodies[i], dt, scheme);
+            const pf_status st = pf_step(plans[i], states[i], &bodies[i], dt[i], scheme);
             if (st != PF_OK) {
                 int expect = PF_OK;
                 first_err.compare_exchange_strong(expect, (int)st);

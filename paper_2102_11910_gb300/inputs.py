@@ -221,9 +221,13 @@ def batched_instance(rng, shape=None, big=False):
     size 1 at the origin: a flat plate at 5-30 deg releasing at both edges, or
     an ellipse of aspect 2-10 (Kelvin-constrained); surface points 32-256 with
     dS/dx in [1, 4] (below 1 the sheet system is so ill-conditioned that the
-    released strengths diverge within a few steps, in FP64 too); 100-20000 vortices (log-uniform) outside radius 0.55, in
-    x from -0.8 to 0.4 of the half-width and at least 0.35 from the top and bottom,
-    strengths normal with variance 0.2 / count (induced speeds of order U_inf).
+    released strengths diverge within a few steps, in FP64 too); 100-20000
+    vortices (log-uniform) outside radius 0.55, in x from -0.8 to 0.4 of the
+    half-width and at least 0.35 from the top and bottom, strengths normal
+    with variance 1e-3.  Those strengths induce speeds that grow like
+    sqrt(count) (median ~0.023 sqrt(count) U_inf, peaks about three times
+    that), so each instance carries its own time step: at most 0.002, and at
+    most half a cell per step at three times that median speed plus U_inf.
     """
     if big:
         nx = ny = 1024
@@ -257,10 +261,10 @@ def batched_instance(rng, shape=None, big=False):
         y = rng.uniform(-hy, hy, 2 * nv)
         keep = np.hypot(x, y) > 0.55
         X, Y = np.concatenate([X, x[keep]]), np.concatenate([Y, y[keep]])
-    # total circulation variance fixed (that of 200 vortices of variance 1e-3), so
-    # that induced speeds stay O(U_inf) whatever the count
-    G = rng.normal(0.0, math.sqrt(1e-3 * 200.0 / nv), nv)
-    return dict(grid=grid, body=body, X=X[:nv], Y=Y[:nv], G=G, Uinf=1.0)
+    G = rng.normal(0.0, math.sqrt(1e-3), nv)
+    speed = 1.0 + 3.0 * 0.023 * math.sqrt(nv)
+    dt = min(0.002, 0.5 * dx / speed)
+    return dict(grid=grid, body=body, X=X[:nv], Y=Y[:nv], G=G, Uinf=1.0, dt=dt)
 
 
 def batched_instances(seed=1003, n=256):

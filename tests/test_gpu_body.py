@@ -6,6 +6,8 @@ points, 256 vortices (the single-step plate case).  cond(S) is ~6e5 here
 the sheet scale with it: FP64 results agree to ~cond * 1e-16; the mixed path,
 whose vorticity field is FP32, must stay within 1e-4 in sheet strength.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -275,3 +277,77 @@ def test_largest_served_instance_sheet_matches_oracle(seed, prec):
     assert abs(s0 - s0_ref) < tol * max(1.0, abs(s0_ref))
     for a, ref in zip(gam, g_ref):
         assert abs(a - ref) < tol * abs(ref)
+
+
+def test_coincident_surface_points_give_a_singular_factor():
+    """Two surface points at the same place give S two identical rows (Eq.
+    vsheet): the factor reports PF_ERR_SINGULAR instead of returning garbage,
+    and the plan stays usable."""
+    g = inputs.centred_grid(96, 96, 0.02)
+    plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_FP64)
+    b = inputs.plate(32, 1.0, math.radians(20.0))
+    x, y, ds = np.insert(b.x, 6, b.x[5]), np.insert(b.y, 6, b.y[5]), np.insert(b.ds, 6, b.ds[5])
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_schur_factor(plan, x, y, ds)
+    assert e.value.name == "PF_ERR_SINGULAR"
+    schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)      # the same points without the copy factor fine
+    gamma0, _, _ = pf.pf_schur_info(schur)
+    assert np.isfinite(gamma0)
+
+
+def test_mixed_sheet_from_positions_at_pitching_plate_size(capsys):
+    """The mixed path end to end at the pitching-plate size (768 x 512, dx 0.01,
+    256 points at 30 deg, dS/dx = 0.39, cond(S) ~ 2e9), from FP64 vortex
+    positions, against the oracle run from the same positions: through the
+    plan's FP32 field (pf_regularize, then pf_sheet_solve, as the mixed time
+    step does) and through pf_sheet_solve_vortices (an FP64 right-hand side
+    from the vortices).  Both meet the mixed path's 1e-4 sheet tolerance; the
+    field's rounding (~1e-7 relative) is white and smoothed by L^-1, so it
+    barely excites the directions S amplifies (measured: 1.3e-8 either way)."""
+    pw = inputs.pitching_plate_512x768()
+    gs = pw["grid"]
+    g = OV.Grid(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0)
+    b = inputs.plate(pw["ns"], pw["chord"], pw["alpha0"])
+    tab = lgf_table(gs.nx + 1, gs.ny + 1)
+    st = OB.SurfaceStencil(g, b.x, b.y)
+    S = OB.schur_matrix(g, st, b.ds, tab)
+    sch = OB.Schur(S, b.ds)
+    cond = np.linalg.cond(S)
+    rng = np.random.default_rng(31)
+    X, Y, G = inputs.uniform_vortices(rng, 2000, 0.7, 3.0, 1e-3, -1.2, 1.2)
+    w = OV.regularize(g, X, Y, G)
+    k1, k2 = b.edges
+    X1 = np.array([b.x[k1] - 3 * gs.dx, b.x[k2] + 3 * gs.dx])
+    Y1 = np.array([b.y[k1] + 2 * gs.dx, b.y[k2] - 2 * gs.dx])
+    E = OB.EinvL_unit_vortex(g, st, X1, Y1, tab)
+    motion = (0.05, -0.1, 0.4, 1.0, 0.0)
+    sbp = OB.sb_prime(b.x, b.y, *motion)
+    nodes, inv = np.unique(np.stack([st.NI.ravel(), st.NJ.ravel()], 1), axis=0, return_inverse=True)
+    EinvLw = OV.inv_laplacian_at(g, w, nodes[:, 0], nodes[:, 1], tab)
+    EinvLw = np.sum(st.W * EinvLw[inv.reshape(st.W.shape)], axis=1)
+    Gw = OV.circulation(g, w)
+    f_ref, _, s0_ref, G1, G2 = OB.sheet_kutta_shed2(sch, sbp, EinvLw, k1, k2, E[:, 0], E[:, 1], Gw)
+    plan = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, pf.PF_MIXED)
+    schur = pf.pf_schur_factor(plan, b.x, b.y, b.ds)
+    d = [torch.from_numpy(a).cuda() for a in (X, Y, G)]
+    w32 = pf.pf_regularize(plan, *d)
+    f_a, gam_a, _ = pf.pf_sheet_solve(plan, schur, w32, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2], X1, Y1)
+    f_b, gam_b, s0_b = pf.pf_sheet_solve_vortices(plan, schur, *d, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2],
+                                                  X1, Y1)
+    pf.pf_sync(plan)
+    err_a = rel(f_a.cpu().numpy(), f_ref)
+    err_b = rel(f_b.cpu().numpy(), f_ref)
+    eg_b = max(abs(a - r) / abs(r) for a, r in zip(gam_b, (G1, G2)))
+    with capsys.disabled():
+        print("\n  cond(S) %.2e; sheet error from the FP32 field %.2e, from the vortices %.2e (Gamma_new %.2e)"
+              % (cond, err_a, err_b, eg_b))
+    eg_a = max(abs(a - r) / abs(r) for a, r in zip(gam_a, (G1, G2)))
+    assert err_a < 1e-4 and eg_a < 1e-4
+    assert err_b < 1e-4 and eg_b < 1e-4
+    assert abs(s0_b - s0_ref) < 1e-4 * max(1.0, abs(s0_ref))
+    # and the same solve in an FP64 plan agrees with the FP64 field's route
+    p64 = pf.Plan(gs.nx, gs.ny, gs.dx, gs.x0, gs.y0, pf.PF_FP64)
+    s64 = pf.pf_schur_factor(p64, b.x, b.y, b.ds)
+    f_c, _, _ = pf.pf_sheet_solve_vortices(p64, s64, *d, motion, pf.PF_SHEET_KUTTA_SHED, Gw, [k1, k2], X1, Y1)
+    pf.pf_sync(p64)
+    assert rel(f_c.cpu().numpy(), f_ref) < cond * 1e-14
