@@ -353,6 +353,11 @@ def bench_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
         plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+        # launch configuration picked by the library's autotuner for this grid
+        # and vortex count (before the warm-up; not part of any timed step)
+        t0 = time.perf_counter()
+        tuned_cfg, tuned_us = pf.pf_autotune(plan, nv, None, reps=5)
+        tune_s = time.perf_counter() - t0
         uq = torch.empty(nv, dtype=torch.float32, device="cuda")
         vq = torch.empty(nv, dtype=torch.float32, device="cuda")
 
@@ -474,6 +479,7 @@ def bench_ours(args):
         sk = torch.cuda.Stream()
         with torch.cuda.stream(sk):
             plans.append(pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=sk))
+            pf.pf_launch_config_set(plans[-1], **tuned_cfg)
     for k in range(NPIPE):
         pf.pf_vic_velocity_host_async(plans[k], hX, hY, hG, 0.0, 0.0, *hout[k])
     for pl in plans:
@@ -586,7 +592,9 @@ def bench_ours(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "mixed (FP32 grid path, FP64 positions and LGF setup)",
                        "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "launch_config": dict(tuned_cfg, source="pf_autotune (%.2f s, best %.1f us on its synthetic "
+                                             "vortices, L2 warm)" % (tune_s, tuned_us))},
             "latency_ms": {"p50": p50, "p99": p99},
             "roofline": roof, "step_roofline": step_roof,
             "kernels": kern, "gpu_launches": int(round(launches_per_step * K)),
@@ -758,6 +766,67 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
     return out
 
 
+def bench_body_profile(pf, inputs, torch, which, K, W):
+    """CUDA-event shares of the body step's phases (Schur factor, R_v with the
+    circulation sum, sheet solve with release, velocity = R_v + sheet
+    deposit + L^-1 + E_v, position update) and of the kernels timed inside
+    them, for the 128^2 plate (Euler, factor reused) and the 768x512 pitching
+    plate (Ns 64, RK2, refactored at every stage).  W steps untimed, then K
+    steps each bracketed by events on the plan stream."""
+    import numpy as np
+    stream = torch.cuda.Stream()
+    out = {}
+    cases = []
+    if which in ("all", "plate"):
+        wl = inputs.plate_vortices_128()
+        g = wl["grid"]
+        # the free stream carries the outer vortices off the 128^2 grid after ~40
+        # steps: the state is reloaded every 20 steps (outside the events)
+        cases.append(("plate_128", g, wl["X"], wl["Y"], wl["G"], pf.plate_kinematics(64, 1.0, wl["alpha"], Uinf=1.0),
+                      0.002, 0, 256 + 2 * 21, 20))
+    if which in ("all", "pitching"):
+        pw = inputs.pitching_plate_512x768()
+        g = pw["grid"]
+        omega = 2.0 * pw["k"] * pw["Uinf"] / pw["chord"]
+        cases.append(("pitching_plate_768x512_ns64", g, np.zeros(0), np.zeros(0), np.zeros(0),
+                      pf.plate_kinematics(64, pw["chord"], pw["alpha0"], pw["amp"], omega, pw["Uinf"]), pw["dt"], 1,
+                      2 * (K + W + 1), None))
+    with torch.cuda.stream(stream):
+        for name, g, X, Y, G, body, dt, scheme, cap, reload in cases:
+            plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+            state = pf.State(plan, cap)
+            pf.pf_state_set(state, X, Y, G)
+            for _ in range(W):
+                pf.pf_step(plan, state, dt, body, scheme=scheme)
+            pf.pf_sync(plan)
+            pf.pf_timing_enable(plan, True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for k, (a, b) in enumerate(ev):
+                if reload and k % reload == 0:
+                    pf.pf_state_set(state, X, Y, G)
+                a.record(stream)
+                pf.pf_step(plan, state, dt, body, scheme=scheme)
+                b.record(stream)
+            pf.pf_sync(plan)
+            rep = pf.pf_timing_report(plan)
+            pf.pf_timing_enable(plan, False)
+            step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+            phases = {k: v for k, v in rep.items() if k.startswith("phase_")}
+            tot = sum(v[1] for v in phases.values())
+            _, _, Gs, _ = pf.pf_state_get(state)
+            out[name] = {
+                "steps": K, "warmup": W, "scheme": "RK2" if scheme else "Euler", "vortices_at_end": len(Gs),
+                "step_ms": step_ms, "phase_ms_per_step": {k: v[1] / K for k, v in phases.items()},
+                "phase_share": {k: v[1] / tot for k, v in phases.items()},
+                "phase_sum_over_step": tot / K / step_ms,
+                "kernels_ms_per_step": {k: v[1] / K for k, v in rep.items() if not k.startswith("phase_")},
+                "kernel_launches_per_step": {k: v[0] / K for k, v in rep.items() if not k.startswith("phase_")},
+            }
+            state.close()
+            plan.close()
+    return out
+
+
 def bench_serving(pf, inputs, n_requests, fractions):
     """The request server under load: a burst (every request at time 0) gives the
     saturation throughput; then Poisson arrivals at the given fractions of it,
@@ -846,7 +915,17 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 leg and the CPU baseline")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the request server: 4096 requests, Poisson arrivals from 0.1x to 1.2x of saturation")
+    ap.add_argument("--body-profile", choices=["all", "plate", "pitching"],
+                    help="only the body steps' phase shares (CUDA events): --warmup steps untimed, --steps timed")
     args = ap.parse_args()
+    if args.body_profile:
+        import torch
+        import paper_2102_11910_gb300 as pf
+        from paper_2102_11910_gb300 import inputs
+        torch.cuda.set_device(dist_env()[2])
+        print(json.dumps({"body_profile": bench_body_profile(pf, inputs, torch, args.body_profile, args.steps,
+                                                             args.warmup)}))
+        return
     if args.serving_sweep:
         import torch
         import paper_2102_11910_gb300 as pf

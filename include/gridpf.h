@@ -118,6 +118,50 @@ const char* pf_last_error(pf_plan plan);
 pf_status pf_timing_enable(pf_plan plan, int32_t on);
 pf_status pf_timing_report(pf_plan plan, char* buf, int64_t buflen);
 
+/* Launch configuration of a plan's transfer passes (R_v binning and deposit,
+ * E_v, Sec. 2.1) and of its Poisson solve L^-1 (Sec. 2.3).  Only how the work
+ * is cut into thread blocks changes:
+ *   tile          node tile edge of the binning, deposit and E_v passes: 32, or
+ *                 16 on grids of at most 4096 such tiles.  The deposit's
+ *                 fixed-point scale is per tile, so w differs between edges by
+ *                 rounding (within the plan precision's tolerance).
+ *   min_span      fewest vortices per binning block: 256, 512, 1024, 2048 or
+ *                 4096.  Results are bitwise the same for every value.
+ *   tile_threads  threads per tile block of the deposit and E_v: 128 or 256.
+ *                 Results are bitwise the same for both.
+ *   fft           0: register-resident radix-16 Stockham passes (grids whose
+ *                 padded torus is at least 256 x 256; smaller ones always take
+ *                 the shared-memory passes); 1: shared-memory passes.  Results
+ *                 differ by rounding.
+ * A new plan has {32, 1024, 256, 0}; clones copy their source's. */
+typedef struct {
+    int32_t tile;
+    int32_t min_span;
+    int32_t tile_threads;
+    int32_t fft;
+} pf_launch_config;
+
+pf_status pf_launch_config_get(pf_plan plan, pf_launch_config* out);
+/* PF_ERR_ARG (plan unchanged) for a value outside the lists above. */
+pf_status pf_launch_config_set(pf_plan plan, const pf_launch_config* cfg);
+
+/* Autotuner: time every valid launch configuration on nv synthetic vortices
+ * (uniform in the grid's interior, strengths uniform in [-1e-3, 1e-3], drawn
+ * on the device by a counter-based hash) through one body-free velocity
+ * evaluation (R_v, L^-1 with the curl, E_v) on the plan's stream: one untimed
+ * call, then `reps` calls timed by CUDA events, each after a write of twice
+ * the L2 size (so that it starts with a cold cache), the median kept; the
+ * fastest is set on the plan.  The plan's grid, precision and the device (name and
+ * compute capability) with floor(log2 nv) form the key of one line of the
+ * text file `cache_path` (may be null: no file).  A key found there is applied
+ * without timing; a new one is appended.  `chosen` and `best_us` (host, may
+ * be null) receive the configuration and its median time in microseconds.
+ * Synchronises; allocates and frees 5 nv values and the flush buffer of
+ * scratch.  PF_ERR_ARG for nv < 1 or reps < 1; PF_ERR_CUDA if the cache file
+ * cannot be appended to. */
+pf_status pf_autotune(pf_plan plan, int64_t nv, const char* cache_path, int32_t reps, pf_launch_config* chosen,
+                      double* best_us);
+
 /* --------------------------------------------------- body-free VIC path */
 
 /* w = R_v Gamma: w_ij = dx^-2 sum_q Gamma_q M4'((x_i-X_q)/dx) M4'((y_j-Y_q)/dx)

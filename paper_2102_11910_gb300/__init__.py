@@ -7,6 +7,7 @@ each function has the C entry point's name and forwards device pointers and
 sizes.  PyTorch provides device memory and the current CUDA stream.
 """
 import ctypes
+import os
 
 import torch
 
@@ -192,6 +193,41 @@ def pf_vic_velocity_host_async(plan, X, Y, G, Uinf, Vinf, uq, vq):
 
 def pf_timing_enable(plan, on=True):
     _native.check(_native.lib().pf_timing_enable(plan.handle, 1 if on else 0), "pf_timing_enable", plan.handle)
+
+
+def _config_dict(c):
+    return {"tile": c.tile, "min_span": c.min_span, "tile_threads": c.tile_threads, "fft": c.fft}
+
+
+def pf_launch_config_get(plan):
+    """The plan's launch configuration: {tile, min_span, tile_threads, fft}."""
+    c = _native.PfLaunchConfig()
+    _native.check(_native.lib().pf_launch_config_get(plan.handle, ctypes.byref(c)), "pf_launch_config_get",
+                  plan.handle)
+    return _config_dict(c)
+
+
+def pf_launch_config_set(plan, tile=None, min_span=None, tile_threads=None, fft=None):
+    """Set some or all of the plan's launch configuration (the others kept)."""
+    cur = pf_launch_config_get(plan)
+    for k, v in (("tile", tile), ("min_span", min_span), ("tile_threads", tile_threads), ("fft", fft)):
+        if v is not None:
+            cur[k] = int(v)
+    c = _native.PfLaunchConfig(cur["tile"], cur["min_span"], cur["tile_threads"], cur["fft"])
+    _native.check(_native.lib().pf_launch_config_set(plan.handle, ctypes.byref(c)), "pf_launch_config_set",
+                  plan.handle)
+
+
+def pf_autotune(plan, nv, cache_path=None, reps=5):
+    """Time every launch configuration on nv synthetic vortices, set the fastest
+    (or the one cached under this device, grid, precision and nv's power of two
+    in the text file cache_path); returns (config dict, median microseconds)."""
+    c = _native.PfLaunchConfig()
+    us = ctypes.c_double()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _native.check(_native.lib().pf_autotune(plan.handle, int(nv), path, int(reps), ctypes.byref(c), ctypes.byref(us)),
+                  "pf_autotune", plan.handle)
+    return _config_dict(c), us.value
 
 
 def pf_timing_report(plan):

@@ -26,6 +26,9 @@ SIGNATURES = {
     "pf_last_error": (_c.c_char_p, [_P]),
     "pf_timing_enable": (_c.c_int, [_P, _I32]),
     "pf_timing_report": (_c.c_int, [_P, _c.c_char_p, _I64]),
+    "pf_launch_config_get": (_c.c_int, [_P, _P]),
+    "pf_launch_config_set": (_c.c_int, [_P, _P]),
+    "pf_autotune": (_c.c_int, [_P, _I64, _c.c_char_p, _I32, _P, _P]),
     "pf_regularize": (_c.c_int, [_P, _P, _P, _P, _I64, _P]),
     "pf_poisson_solve": (_c.c_int, [_P, _P, _P]),
     "pf_velocity_solve": (_c.c_int, [_P, _P, _D, _D, _P]),
@@ -83,6 +86,10 @@ class GridPfError(RuntimeError):
 
 class PfGridDesc(ctypes.Structure):
     _fields_ = [("nx", _I32), ("ny", _I32), ("dx", _D), ("x0", _D), ("y0", _D), ("precision", _I32)]
+
+
+class PfLaunchConfig(ctypes.Structure):
+    _fields_ = [("tile", _I32), ("min_span", _I32), ("tile_threads", _I32), ("fft", _I32)]
 
 
 class PfBodyDesc(ctypes.Structure):

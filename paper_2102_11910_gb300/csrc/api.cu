@@ -113,9 +113,11 @@ pf_status plan_workspaces(pf_plan p) {
     p->ntx = ceil_div(nx, BIN_TILE);
     p->nty = ceil_div(ny, BIN_TILE);
     p->ntiles = p->ntx * p->nty;
-    PF_CUDA(p, cudaMalloc(&p->tile_count, (size_t)p->ntiles * sizeof(unsigned)));
+    const int small = ceil_div(nx, BIN_TILE_SMALL) * ceil_div(ny, BIN_TILE_SMALL);
+    p->tile_slots = small <= BIN_MAX_TILES ? small : p->ntiles;
+    PF_CUDA(p, cudaMalloc(&p->tile_count, (size_t)p->tile_slots * sizeof(unsigned)));
     PF_CUDA(p, cudaMalloc(&p->gmax, (BIN_MAX_BLOCKS + 1) * sizeof(double)));
-    PF_CUDA(p, cudaMalloc(&p->tile_start, p->ntiles * sizeof(int)));
+    PF_CUDA(p, cudaMalloc(&p->tile_start, (size_t)p->tile_slots * sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->diag, PF_DIAG_DOUBLES * sizeof(double)));
     PF_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
     PF_CUDA(p, cudaMalloc(&p->d_oob, sizeof(unsigned long long)));
@@ -123,7 +125,7 @@ pf_status plan_workspaces(pf_plan p) {
     // cudaMemset goes to the legacy stream, which a non-blocking plan stream
     // does not wait for; zero on the plan's stream and wait, so that the plan
     // is ready whatever stream it is later used on.
-    PF_CUDA(p, cudaMemsetAsync(p->tile_count, 0, (size_t)p->ntiles * sizeof(unsigned), p->stream));
+    PF_CUDA(p, cudaMemsetAsync(p->tile_count, 0, (size_t)p->tile_slots * sizeof(unsigned), p->stream));
     PF_CUDA(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
     PF_CUDA(p, cudaMemsetAsync(p->d_oob, 0, sizeof(unsigned long long), p->stream));
     PF_CUDA(p, cudaStreamSynchronize(p->stream));
@@ -188,6 +190,7 @@ pf_status pf_plan_clone(pf_plan src, int32_t precision, void* stream, pf_plan* o
     if (!p) return PF_ERR_OOM;
     p->nx = src->nx; p->ny = src->ny; p->P = src->P; p->Q = src->Q; p->Hld = src->Hld; p->dx = src->dx; p->x0 = src->x0;
     p->y0 = src->y0; p->prec = precision;
+    p->tile = src->tile; p->min_span = src->min_span; p->tile_threads = src->tile_threads; p->fft_impl = src->fft_impl;
     p->stream = (cudaStream_t)stream;
     p->shared = src->shared;
     p->shared->refs++;

@@ -1195,6 +1195,39 @@ void schur_free(pf_schur s) {
 // multiply-adds at the GPU's low FP64 rate; on larger grids the same quantity
 // comes from an FP64 FFT solve psi = -L^-1 w (FP64 rounding, far below what
 // the ill-conditioned S amplifies into the sheet) read at the stencils.
+// Route of E_s L^-1 w from the field w (no vortex source): the sparse sum when
+// the caller bounds the nonzero nodes and the sum is small, else the FP64 FFT
+// solve on larger grids, else the direct sum.
+enum FieldRoute { ROUTE_SPARSE, ROUTE_DIRECT, ROUTE_FFT };
+
+FieldRoute field_route(pf_plan p, int ns, int64_t nnz_bound) {
+    const int64_t M = (int64_t)p->nx * p->ny;
+    const bool fft_ok = p->P >= 256 && p->Q >= 256;
+    if (p->rhs_route == PF_RHS_SPARSE ||
+        (p->rhs_route == PF_RHS_AUTO && nnz_bound >= 0 && 16 * (int64_t)ns * nnz_bound < ((int64_t)1 << 24)))
+        return ROUTE_SPARSE;
+    if (fft_ok && (p->rhs_route == PF_RHS_FFT || (p->rhs_route == PF_RHS_AUTO && (int64_t)ns * M > ((int64_t)1 << 22))))
+        return ROUTE_FFT;
+    return ROUTE_DIRECT;
+}
+
+// the scratch a field route allocates on first use: the sparse route's node
+// list, the mixed plan's FP64 field, streamfunction and spectra for the FFT
+pf_status field_route_buffers(pf_plan p, FieldRoute r) {
+    const int64_t M = (int64_t)p->nx * p->ny;
+    if (r == ROUTE_SPARSE && !p->nz_idx) {
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        PF_CUDA(p, cudaMalloc(&p->nz_idx, (size_t)M * sizeof(int) + (NZ_BLOCKS + 1) * sizeof(int)));
+        PF_CUDA(p, cudaMalloc(&p->nz_val, (size_t)M * sizeof(double)));
+    }
+    if (r == ROUTE_FFT && p->prec != PF_FP64 && !p->rhs64) {
+        const size_t spec = (size_t)p->ldK * p->ldT * 2 * sizeof(double);
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        PF_CUDA(p, cudaMalloc(&p->rhs64, 2 * (size_t)M * sizeof(double) + 2 * spec));
+    }
+    return PF_OK;
+}
+
 pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t nnz_bound,
                       const VortexSource* vs = nullptr) {
     const int ns = s->ns;
@@ -1229,16 +1262,9 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
         PF_LAUNCH_CHECK(p);
         return PF_OK;
     }
-    const bool fft_ok = p->P >= 256 && p->Q >= 256;
-    // the sparse route when the caller bounds the nonzero nodes and the sum is small
-    const bool sparse = p->rhs_route == PF_RHS_SPARSE ||
-                        (p->rhs_route == PF_RHS_AUTO && nnz_bound >= 0 && 16 * (int64_t)ns * nnz_bound < ((int64_t)1 << 24));
-    if (sparse) {
-        if (!p->nz_idx) {
-            PF_CUDA(p, cudaStreamSynchronize(st));
-            PF_CUDA(p, cudaMalloc(&p->nz_idx, (size_t)M * sizeof(int) + (NZ_BLOCKS + 1) * sizeof(int)));
-            PF_CUDA(p, cudaMalloc(&p->nz_val, (size_t)M * sizeof(double)));
-        }
+    const FieldRoute route = field_route(p, ns, nnz_bound);
+    PF_TRY(field_route_buffers(p, route));
+    if (route == ROUTE_SPARSE) {
         int* counts = p->nz_idx + M;
         int* total = counts + NZ_BLOCKS;
         const int chunk = ceil_div(M, NZ_BLOCKS);
@@ -1256,9 +1282,7 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
         PF_LAUNCH_CHECK(p);
         return PF_OK;
     }
-    const bool fft = fft_ok && (p->rhs_route == PF_RHS_FFT ||
-                                (p->rhs_route == PF_RHS_AUTO && (int64_t)ns * M > ((int64_t)1 << 22)));
-    if (!fft) {
+    if (route == ROUTE_DIRECT) {
         const double dx2 = p->dx * p->dx;
         if (p->prec == PF_FP64)
             k_surface_einvlw<double><<<ns, 256, 0, st>>>((const double*)w, p->nx, p->ny, s->six, s->siy, s->swx,
@@ -1279,10 +1303,6 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
         T1 = p->T1;
         T2 = p->T2a;
     } else {
-        if (!p->rhs64) {
-            PF_CUDA(p, cudaStreamSynchronize(st));
-            PF_CUDA(p, cudaMalloc(&p->rhs64, 2 * (size_t)M * sizeof(double) + 2 * spec));
-        }
         double* b = (double*)p->rhs64;
         double* wd = b;
         psi = b + M;
@@ -1296,6 +1316,12 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
     k_surface_from_psi<<<ceil_div(ns, 128), 128, 0, st>>>(psi, p->nx, ns, s->six, s->siy, s->swx, s->swy, ew);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
+}
+
+// allocate ahead of time what a sheet solve with this nonzero bound would
+// allocate on first use (a step captured for replay may not allocate)
+pf_status sheet_solve_reserve(pf_plan p, pf_schur s, int64_t nnz_bound) {
+    return field_route_buffers(p, field_route(p, s->ns, nnz_bound));
 }
 
 // Several bodies (Sec. 2.7, Eq. kuttasystem4), one block of 256.  y holds

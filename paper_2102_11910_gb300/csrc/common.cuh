@@ -49,7 +49,9 @@ struct KTiming {
 };
 
 // ------------------------------------------------------------ plan
-constexpr int BIN_TILE = 32;   // node tile edge used by binning and regularization
+constexpr int BIN_TILE = 32;        // node tile edge used by binning and regularization (default)
+constexpr int BIN_TILE_SMALL = 16;  // the other tile edge a plan may be configured with
+constexpr int BIN_MAX_TILES = 4096; // tiles one binning pass handles (the reach of its block scan)
 constexpr int PF_DIAG_DOUBLES = 4 * 2048 + 3 + 5 * 4096;   // impulse scratch: row partials, results, surface
 
 // Vortex partition of the binning passes: block b owns vortices
@@ -57,11 +59,14 @@ constexpr int PF_DIAG_DOUBLES = 4 * 2048 + 3 + 5 * 4096;   // impulse scratch: r
 // blocks (four per SM, all resident at once, equal work per SM); small sets
 // use fewer blocks of at least 1024 vortices.
 constexpr int BIN_MAX_BLOCKS = 608;
-inline int64_t bin_span(int64_t nv) {
+constexpr int BIN_MIN_SPAN = 1024;   // default fewest vortices per block (a tuned plan may use another)
+inline int64_t bin_span(int64_t nv, int min_span = BIN_MIN_SPAN) {
     const int64_t s = (nv + BIN_MAX_BLOCKS - 1) / BIN_MAX_BLOCKS;
-    return s < 1024 ? 1024 : s;
+    return s < min_span ? min_span : s;
 }
-inline int bin_blocks(int64_t nv) { return nv > 0 ? (int)((nv + bin_span(nv) - 1) / bin_span(nv)) : 0; }
+inline int bin_blocks(int64_t nv, int min_span = BIN_MIN_SPAN) {
+    return nv > 0 ? (int)((nv + bin_span(nv, min_span) - 1) / bin_span(nv, min_span)) : 0;
+}
 
 // Read-only tables of one grid shape, shared by a plan and its clones.
 struct PlanTables {
@@ -100,8 +105,17 @@ struct pf_plan_s {
     void* T2b = nullptr;
     void* w = nullptr;             // nx*ny real
     void* uv = nullptr;            // 2*nx*ny real
+    // launch configuration of the transfer and Poisson passes (pf_launch_config_set,
+    // pf_autotune): tile edge, fewest vortices per binning block, threads per
+    // tile block, FFT kernels (0 register-resident radix-16, 1 shared-memory)
+    int tile = BIN_TILE;
+    int min_span = BIN_MIN_SPAN;
+    int tile_threads = 256;
+    int fft_impl = 0;
+    int bin_tile = BIN_TILE;           // tile edge of the last binning (its records serve E_v)
     // binning
-    int ntx = 0, nty = 0, ntiles = 0;
+    int ntx = 0, nty = 0, ntiles = 0;  // tiles at BIN_TILE
+    int tile_slots = 0;                // entries of tile_count and tile_start (tiles at the smallest offered edge)
     unsigned* tile_count = nullptr;    // records per tile (written by every binning pass)
     double* gmax = nullptr;            // largest |Gamma| of the last binning, then per locate block
     int* tile_start = nullptr;
@@ -182,6 +196,31 @@ cudaEvent_t tm_event(pf_plan p);   // api.cu
         if (s_ != PF_OK) return s_; \
     } while (0)
 
+// A phase of a step (several launches) timed like one kernel: events on the
+// plan stream at construction and destruction, reported under `name` next to
+// the kernel names when timing is on.
+struct PhaseSpan {
+    pf_plan p;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    PhaseSpan(pf_plan p_, const char* name_) : p(p_), name(name_) {
+        if (p && p->tm.on) {
+            a = tm_event(p);
+            cudaEventRecord(a, p->stream);
+        }
+    }
+    ~PhaseSpan() {
+        if (!a) return;
+        cudaEvent_t b = tm_event(p);
+        cudaEventRecord(b, p->stream);
+        p->tm.names.push_back(name);
+        p->tm.ev.push_back(a);
+        p->tm.ev.push_back(b);
+    }
+    PhaseSpan(const PhaseSpan&) = delete;
+    PhaseSpan& operator=(const PhaseSpan&) = delete;
+};
+
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (once per
 // device, kernel and size; safe to call from several host threads).
 cudaError_t ensure_smem(const void* kernel, size_t bytes);   // api.cu
@@ -227,6 +266,7 @@ pf_status lgf_build(pf_plan p);                                  // lgf.cu
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf);  // fft.cu
 pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2);           // fft.cu
 enum { CONV_PSI = 0, CONV_UV = 1 };
-pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w);  // transfer.cu
+pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,
+                            const int64_t* dn = nullptr);  // transfer.cu
 pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq);
 pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void* uq, void* vq);

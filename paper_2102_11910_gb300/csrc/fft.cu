@@ -437,7 +437,9 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
 }
 
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf) {
-    const bool reg = p->P >= 256 && p->Q >= 256;   // register-resident kernels; small grids use the generic ones
+    // register-resident kernels unless the plan is configured for the shared-memory
+    // ones; grids below 256 x 256 padded nodes always take the shared-memory ones
+    const bool reg = p->fft_impl == 0 && p->P >= 256 && p->Q >= 256;
     const ConvWs ws{p->T1, p->T2a, p->T2b};
     if (p->prec == PF_FP64) {
         if (reg)

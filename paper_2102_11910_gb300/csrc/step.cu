@@ -59,6 +59,12 @@ struct pf_state_s {
     double* red = nullptr;          // reduction scratch: [0] sum Gamma, [1] -sum Gamma, [2..] partials
     double* newpos = nullptr;       // device x[MAX_EDGES], y[MAX_EDGES] of the vortices being released,
                                     // then per body the released circulation and gamma_w
+    // device copy of the counts: [0] vortices, [1 + e] the last vortex released at
+    // edge e (-1: none yet); kept by every step.  While a step is captured for
+    // replay (`capture`), the kernels read the counts from here and the
+    // launches are sized by the capacity.
+    int64_t* dn = nullptr;
+    bool capture = false;
     // Schur factors of the two most recent poses, the current one first: an
     // RK2 step's second stage (t + dt) is the next step's first, so a moving
     // body is factored once per step
@@ -79,8 +85,10 @@ namespace {
 constexpr int RED_BLOCKS = 64;
 
 // sum of Gamma over nv vortices: fixed partition, fixed reduction tree
-__global__ void k_sum_partial(const double* __restrict__ G, int64_t nv, double* __restrict__ part) {
+__global__ void k_sum_partial(const double* __restrict__ G, int64_t nv, const int64_t* __restrict__ dn,
+                              double* __restrict__ part) {
     __shared__ double sh[256];
+    if (dn) nv = dn[0];
     double s = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x)
         s += G[q];
@@ -113,29 +121,52 @@ struct EdgeGeo {
 };
 
 // release positions: out[k] = x, out[MAX_EDGES + k] = y of edge k's new vortex
-__global__ void k_place(const double* __restrict__ X, const double* __restrict__ Y, EdgeGeo e, double* __restrict__ out) {
+// (the last released vortex from e.last, or from dn[1 + k] when dn is given)
+__global__ void k_place(const double* __restrict__ X, const double* __restrict__ Y, EdgeGeo e,
+                        const int64_t* __restrict__ dn, double* __restrict__ out) {
     const int k = threadIdx.x;
     if (k >= e.n) return;
+    const long long last = dn ? (long long)dn[1 + k] : e.last[k];
     double x, y;
-    if (e.last[k] < 0) {
+    if (last < 0) {
         x = e.ex[k] + e.first_dist * e.nx[k];
         y = e.ey[k] + e.first_dist * e.ny[k];
     } else {
-        x = e.ex[k] + (X[e.last[k]] - e.ex[k]) / 3.0;
-        y = e.ey[k] + (Y[e.last[k]] - e.ey[k]) / 3.0;
+        x = e.ex[k] + (X[last] - e.ex[k]) / 3.0;
+        y = e.ey[k] + (Y[last] - e.ey[k]) / 3.0;
     }
     out[k] = x;
     out[MAX_EDGES + k] = y;
 }
 
-// append the n released vortices: positions from pos (as k_place), strengths gam[0..n)
+// append the n released vortices at index nv (dn[0] when use_dn): positions
+// from pos (as k_place), strengths gam[0..n); the device counts follow.  One
+// warp.  A release past the capacity is dropped and flagged (the host checks
+// the capacity first, so only a corrupted count gets here).
 __global__ void k_append(double* __restrict__ X, double* __restrict__ Y, double* __restrict__ G, int64_t nv,
-                         const double* __restrict__ pos, const double* __restrict__ gam, int n) {
+                         const double* __restrict__ pos, const double* __restrict__ gam, int n,
+                         int64_t* __restrict__ dn, int use_dn, int64_t cap, int* __restrict__ status) {
     const int k = threadIdx.x;
-    if (k >= n) return;
-    X[nv + k] = pos[k];
-    Y[nv + k] = pos[MAX_EDGES + k];
-    G[nv + k] = gam[k];
+    if (use_dn) nv = dn[0];
+    const bool fits = nv >= 0 && nv + n <= cap;
+    if (k < n && fits) {
+        X[nv + k] = pos[k];
+        Y[nv + k] = pos[MAX_EDGES + k];
+        G[nv + k] = gam[k];
+        dn[1 + k] = nv + k;
+    }
+    __syncwarp();                       // every lane has read dn[0]
+    if (k == 0) {
+        if (fits) dn[0] = nv + n;
+        else atomicOr(status, ST_CAPACITY);
+    }
+}
+
+// the device counts of a loaded state: nv vortices, nothing released yet
+__global__ void k_set_counts(int64_t* __restrict__ dn, int64_t nv) {
+    const int k = threadIdx.x;
+    if (k == 0) dn[0] = nv;
+    if (k < MAX_EDGES) dn[1 + k] = -1;
 }
 
 // several bodies: gamma_w of body b >= 1 is the circulation it released, body 0
@@ -161,7 +192,8 @@ __global__ void k_released(const double* __restrict__ gam, pf_multibody mb, doub
 
 template <typename T>
 __global__ void k_euler(double* __restrict__ X, double* __restrict__ Y, const T* __restrict__ u, const T* __restrict__ v,
-                        int64_t nv, double dt) {
+                        int64_t nv, const int64_t* __restrict__ dn, double dt) {
+    if (dn) nv = dn[0];
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
         X[q] += dt * (double)u[q];
         Y[q] += dt * (double)v[q];
@@ -170,8 +202,9 @@ __global__ void k_euler(double* __restrict__ X, double* __restrict__ Y, const T*
 
 template <typename T>
 __global__ void k_predict(const double* __restrict__ X, const double* __restrict__ Y, const T* __restrict__ u,
-                          const T* __restrict__ v, int64_t nv, double dt, double* __restrict__ Xs,
-                          double* __restrict__ Ys) {
+                          const T* __restrict__ v, int64_t nv, const int64_t* __restrict__ dn, double dt,
+                          double* __restrict__ Xs, double* __restrict__ Ys) {
+    if (dn) nv = dn[0];
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
         Xs[q] = X[q] + dt * (double)u[q];
         Ys[q] = Y[q] + dt * (double)v[q];
@@ -180,7 +213,9 @@ __global__ void k_predict(const double* __restrict__ X, const double* __restrict
 
 template <typename T>
 __global__ void k_heun(double* __restrict__ X, double* __restrict__ Y, const T* __restrict__ u1, const T* __restrict__ v1,
-                       const T* __restrict__ u2, const T* __restrict__ v2, int64_t nv, double dt) {
+                       const T* __restrict__ u2, const T* __restrict__ v2, int64_t nv, const int64_t* __restrict__ dn,
+                       double dt) {
+    if (dn) nv = dn[0];
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
         X[q] += 0.5 * dt * ((double)u1[q] + (double)u2[q]);
         Y[q] += 0.5 * dt * ((double)v1[q] + (double)v2[q]);
@@ -188,7 +223,7 @@ __global__ void k_heun(double* __restrict__ X, double* __restrict__ Y, const T* 
 }
 
 void free_state(pf_state s) {
-    void* ptrs[] = {s->X, s->Y, s->G, s->Xs, s->Ys, s->u1, s->v1, s->u2, s->v2, s->f, s->red, s->newpos};
+    void* ptrs[] = {s->X, s->Y, s->G, s->Xs, s->Ys, s->u1, s->v1, s->u2, s->v2, s->f, s->red, s->newpos, s->dn};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (auto& c : s->fac)
@@ -288,63 +323,104 @@ void edge_geometry(const std::vector<double>& x, const std::vector<double>& y, i
     e.ny[j] = nyv;
 }
 
-pf_status sum_gamma(pf_plan p, pf_state s, int64_t n) {
-    k_sum_partial<<<RED_BLOCKS, 256, 0, p->stream>>>(s->G, n, s->red + 2);
+pf_status sum_gamma(pf_plan p, pf_state s, int64_t n, const int64_t* dn) {
+    k_sum_partial<<<RED_BLOCKS, 256, 0, p->stream>>>(s->G, n, dn, s->red + 2);
     k_sum_final<<<1, 32, 0, p->stream>>>(s->red + 2, RED_BLOCKS, s->red);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
 
+// Launch size and device count of a stage: the host count, or while the step
+// is captured for replay, the capacity with the count read from s->dn.
+struct Count {
+    int64_t n;
+    const int64_t* dn;
+};
+Count count_of(pf_state s) { return s->capture ? Count{s->cap, s->dn} : Count{s->nv, nullptr}; }
+
 // velocity (plan precision) at the n vortices (X, Y, G) of the current arrays,
 // optionally with a body sheet f added to the source
-pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, int64_t n, pf_schur sch,
+pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, Count c, pf_schur sch,
                      const double* f, double Uinf, double Vinf, void* u, void* v) {
-    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
+    PF_TRY(vortex_regularize(p, X, Y, s->G, c.n, p->w, c.dn));
     if (sch) PF_TRY(sheet_deposit(p, sch, f, p->w));
     PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
-    return vortex_interpolate_located(p, p->uv, n, u, v);
+    return vortex_interpolate_located(p, p->uv, c.n, u, v);
+}
+
+enum { ADV_EULER = 0, ADV_PREDICT = 1, ADV_HEUN = 2 };
+
+template <typename T>
+void advance_t(pf_plan p, pf_state s, int kind, Count c, double dt) {
+    const int nb = nblocks(c.n);
+    const T *u1 = (const T*)s->u1, *v1 = (const T*)s->v1;
+    if (kind == ADV_EULER)
+        k_euler<T><<<nb, 256, 0, p->stream>>>(s->X, s->Y, u1, v1, c.n, c.dn, dt);
+    else if (kind == ADV_PREDICT)
+        k_predict<T><<<nb, 256, 0, p->stream>>>(s->X, s->Y, u1, v1, c.n, c.dn, dt, s->Xs, s->Ys);
+    else
+        k_heun<T><<<nb, 256, 0, p->stream>>>(s->X, s->Y, u1, v1, (const T*)s->u2, (const T*)s->v2, c.n, c.dn, dt);
+}
+
+// X += dt u1 (Euler), (Xs, Ys) = X + dt u1 (predictor), X += dt (u1 + u2) / 2 (Heun)
+pf_status advance(pf_plan p, pf_state s, int kind, Count c, double dt) {
+    PhaseSpan ph(p, "phase_update");
+    if (p->prec == PF_FP64) advance_t<double>(p, s, kind, c, dt);
+    else advance_t<float>(p, s, kind, c, dt);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
 }
 
 // one stage with the body: shed (two-edge Kutta) or Kelvin-constrained
 pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double t, double dt, const double* X,
                      const double* Y, bool shed, void* u, void* v) {
     const std::vector<Pose> P{body_pose(k, t)};
-    PF_TRY(ensure_schur(p, s, surface_of(&k, 1, P)));
+    {
+        PhaseSpan ph(p, "phase_schur_factor");
+        PF_TRY(ensure_schur(p, s, surface_of(&k, 1, P)));
+    }
     pf_schur sch = s->fac[0].f;
     const pf_motion m{0.0, 0.0, P[0].Omega, k.Uinf, k.Vinf};
-    int64_t n = s->nv;
-    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
-    PF_TRY(sum_gamma(p, s, n));
-    if (shed) {
-        EdgeGeo e;
-        e.n = 2;
-        const int kk[2] = {k.edge[0], k.edge[1]};
-        for (int j = 0; j < 2; ++j) {
-            edge_geometry(P[0].x, P[0].y, 0, k.ns, kk[j], k.Uinf, k.Vinf, e, j);
-            e.last[j] = s->last[j];
-        }
-        e.first_dist = 10.0 * dt * hypot(k.Uinf, k.Vinf);
-        k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
-        PF_LAUNCH_CHECK(p);
-        EdgeBounds eb;
-        eb.on = k.edge_bounded ? 1 : 0;
-        for (int j = 0; j < 2; ++j) {
-            eb.lo[j] = k.edge_bounds[2 * j];
-            eb.hi[j] = k.edge_bounds[2 * j + 1];
-        }
-        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos,
-                                  s->newpos + MAX_EDGES, s->f, eb, 16 * n));
-        // release: the new vortices join the arrays X, Y (the caller's position
-        // arrays) and G
-        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos,
-                                          sch->scal + 1, 2);
-        PF_LAUNCH_CHECK(p);
-        n += 2;
-    } else {
-        PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_CIRCULATION, 0.0, s->red + 1, 0, nullptr, nullptr, nullptr,
-                                  s->f, EdgeBounds(), 16 * n));
+    Count c = count_of(s);
+    {
+        PhaseSpan ph(p, "phase_regularize");
+        PF_TRY(vortex_regularize(p, X, Y, s->G, c.n, p->w, c.dn));
+        PF_TRY(sum_gamma(p, s, c.n, c.dn));
     }
-    return velocities(p, s, X, Y, n, sch, s->f, k.Uinf, k.Vinf, u, v);
+    {
+        PhaseSpan ph(p, "phase_sheet_solve");
+        if (shed) {
+            EdgeGeo e;
+            e.n = 2;
+            const int kk[2] = {k.edge[0], k.edge[1]};
+            for (int j = 0; j < 2; ++j) {
+                edge_geometry(P[0].x, P[0].y, 0, k.ns, kk[j], k.Uinf, k.Vinf, e, j);
+                e.last[j] = s->last[j];
+            }
+            e.first_dist = 10.0 * dt * hypot(k.Uinf, k.Vinf);
+            k_place<<<1, 32, 0, p->stream>>>(X, Y, e, c.dn, s->newpos);
+            PF_LAUNCH_CHECK(p);
+            EdgeBounds eb;
+            eb.on = k.edge_bounded ? 1 : 0;
+            for (int j = 0; j < 2; ++j) {
+                eb.lo[j] = k.edge_bounds[2 * j];
+                eb.hi[j] = k.edge_bounds[2 * j + 1];
+            }
+            PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos,
+                                      s->newpos + MAX_EDGES, s->f, eb, 16 * c.n));
+            // release: the new vortices join the arrays X, Y (the caller's position
+            // arrays) and G
+            k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, c.n, s->newpos,
+                                              sch->scal + 1, 2, s->dn, c.dn != nullptr, s->cap, p->d_status);
+            PF_LAUNCH_CHECK(p);
+            if (!c.dn) c.n += 2;
+        } else {
+            PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_CIRCULATION, 0.0, s->red + 1, 0, nullptr, nullptr,
+                                      nullptr, s->f, EdgeBounds(), 16 * c.n));
+        }
+    }
+    PhaseSpan ph(p, "phase_velocity");
+    return velocities(p, s, X, Y, c, sch, s->f, k.Uinf, k.Vinf, u, v);
 }
 
 // one stage with several bodies (Sec. 2.7): each edge releases a vortex under
@@ -375,22 +451,23 @@ pf_status bodies_stage(pf_plan p, pf_state s, const pf_body_kinematics* k, int n
     e.first_dist = 10.0 * dt * hypot(k[0].Uinf, k[0].Vinf);
     double* rel = s->newpos + 2 * MAX_EDGES;
     double* gw = rel + PF_MAX_BODIES;
-    int64_t n = s->nv;
-    PF_TRY(vortex_regularize(p, X, Y, s->G, n, p->w));
-    PF_TRY(sum_gamma(p, s, n));
+    Count c = count_of(s);
+    PF_TRY(vortex_regularize(p, X, Y, s->G, c.n, p->w, c.dn));
+    PF_TRY(sum_gamma(p, s, c.n, c.dn));
     k_gamma_w<<<1, 32, 0, p->stream>>>(s->red, rel, nb, gw);
-    if (ne > 0) k_place<<<1, 32, 0, p->stream>>>(X, Y, e, s->newpos);
+    if (ne > 0) k_place<<<1, 32, 0, p->stream>>>(X, Y, e, c.dn, s->newpos);
     PF_LAUNCH_CHECK(p);
     double* out = nullptr;
-    PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out, 16 * n));
+    PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out,
+                                    16 * c.n));
     if (ne > 0) {
-        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, n, s->newpos, out + nb,
-                                          ne);
+        k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, c.n, s->newpos,
+                                          out + nb, ne, s->dn, c.dn != nullptr, s->cap, p->d_status);
         k_released<<<1, 32, 0, p->stream>>>(out + nb, mb, rel);
         PF_LAUNCH_CHECK(p);
-        n += ne;
+        if (!c.dn) c.n += ne;
     }
-    return velocities(p, s, X, Y, n, sch, s->f, k[0].Uinf, k[0].Vinf, u, v);
+    return velocities(p, s, X, Y, c, sch, s->f, k[0].Uinf, k[0].Vinf, u, v);
 }
 
 }  // namespace
@@ -408,6 +485,8 @@ pf_status state_load_async(pf_state s, const double* X, const double* Y, const d
     s->nv = nv;
     s->t = t;
     for (auto& l : s->last) l = -1;
+    k_set_counts<<<1, 32, 0, p->stream>>>(s->dn, nv);
+    PF_LAUNCH_CHECK(p);
     PF_CUDA(s->plan, cudaMemsetAsync(s->newpos + 2 * MAX_EDGES, 0, PF_MAX_BODIES * sizeof(double), s->plan->stream));
     s->fac[0].xb.clear();
     s->fac[1].xb.clear();
@@ -447,8 +526,13 @@ pf_status pf_state_create(pf_plan p, int64_t cap, pf_state* out) {
     if (err == cudaSuccess) err = cudaMalloc(&s->f, PF_MAX_SURFACE_POINTS * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&s->red, (2 + RED_BLOCKS) * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&s->newpos, (2 * MAX_EDGES + 2 * PF_MAX_BODIES) * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&s->dn, (1 + MAX_EDGES) * sizeof(int64_t));
     if (err == cudaSuccess)
         err = cudaMemsetAsync(s->newpos, 0, (2 * MAX_EDGES + 2 * PF_MAX_BODIES) * sizeof(double), p->stream);
+    if (err == cudaSuccess) {
+        k_set_counts<<<1, 32, 0, p->stream>>>(s->dn, 0);
+        err = cudaGetLastError();
+    }
     if (err != cudaSuccess) {
         snprintf(p->err, sizeof(p->err), "pf_state_create: %s", cudaGetErrorString(err));
         free_state(s);
@@ -477,11 +561,13 @@ pf_status pf_state_set(pf_state s, const double* X, const double* Y, const doubl
         PF_CUDA(p, cudaMemcpyAsync(s->Y, Y, b, cudaMemcpyHostToDevice, p->stream));
         PF_CUDA(p, cudaMemcpyAsync(s->G, G, b, cudaMemcpyHostToDevice, p->stream));
     }
-    PF_CUDA(p, cudaStreamSynchronize(p->stream));
     s->nv = nv;
     s->t = t;
     for (auto& l : s->last) l = -1;
+    k_set_counts<<<1, 32, 0, p->stream>>>(s->dn, nv);
+    PF_LAUNCH_CHECK(p);
     PF_CUDA(s->plan, cudaMemsetAsync(s->newpos + 2 * MAX_EDGES, 0, PF_MAX_BODIES * sizeof(double), s->plan->stream));
+    PF_CUDA(p, cudaStreamSynchronize(p->stream));
     s->fac[0].xb.clear();
     s->fac[1].xb.clear();   // a new history may come with a new body
     return PF_OK;
@@ -515,40 +601,28 @@ pf_status pf_step(pf_plan p, pf_state s, const pf_body_kinematics* k, double dt,
     const bool release = body && k->n_edges == 2;
     if (release && s->nv + 2 > s->cap) return PF_ERR_CAPACITY;
     const int64_t n0 = s->nv;
-    const int nb = nblocks(n0 + 2);
     if (!body) {
-        PF_TRY(velocities(p, s, s->X, s->Y, n0, nullptr, nullptr, k->Uinf, k->Vinf, s->u1, s->v1));
+        const Count c = count_of(s);
+        PF_TRY(velocities(p, s, s->X, s->Y, c, nullptr, nullptr, k->Uinf, k->Vinf, s->u1, s->v1));
         if (scheme == 0) {
-            if (p->prec == PF_FP64) k_euler<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n0, dt);
-            else k_euler<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n0, dt);
+            PF_TRY(advance(p, s, ADV_EULER, c, dt));
         } else {
-            if (p->prec == PF_FP64) k_predict<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n0, dt, s->Xs, s->Ys);
-            else k_predict<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n0, dt, s->Xs, s->Ys);
-            PF_LAUNCH_CHECK(p);
-            PF_TRY(velocities(p, s, s->Xs, s->Ys, n0, nullptr, nullptr, k->Uinf, k->Vinf, s->u2, s->v2));
-            if (p->prec == PF_FP64) k_heun<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n0, dt);
-            else k_heun<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n0, dt);
+            PF_TRY(advance(p, s, ADV_PREDICT, c, dt));
+            PF_TRY(velocities(p, s, s->Xs, s->Ys, c, nullptr, nullptr, k->Uinf, k->Vinf, s->u2, s->v2));
+            PF_TRY(advance(p, s, ADV_HEUN, c, dt));
         }
-        PF_LAUNCH_CHECK(p);
         s->t += dt;
         return PF_OK;
     }
     // stage 1 at t: release two vortices (appended to X, Y, G) and get u1 at all n0 + 2
     PF_TRY(body_stage(p, s, *k, s->t, dt, s->X, s->Y, release, s->u1, s->v1));
-    const int64_t n1 = n0 + (release ? 2 : 0);
-    s->nv = n1;
+    s->nv = n0 + (release ? 2 : 0);
     if (scheme == 0) {
-        if (p->prec == PF_FP64) k_euler<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt);
-        else k_euler<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_EULER, count_of(s), dt));
     } else {
-        if (p->prec == PF_FP64) k_predict<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt, s->Xs, s->Ys);
-        else k_predict<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt, s->Xs, s->Ys);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_PREDICT, count_of(s), dt));
         PF_TRY(body_stage(p, s, *k, s->t + dt, dt, s->Xs, s->Ys, false, s->u2, s->v2));
-        if (p->prec == PF_FP64) k_heun<double><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n1, dt);
-        else k_heun<float><<<nb, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n1, dt);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_HEUN, count_of(s), dt));
     }
     if (release) {
         s->last[0] = n0;
@@ -573,24 +647,17 @@ pf_status pf_step_multi(pf_plan p, pf_state s, int32_t n_bodies, const pf_body_k
     }
     if (ns > PF_MAX_SURFACE_POINTS) return PF_ERR_ARG;
     if (s->nv + ne > s->cap) return PF_ERR_CAPACITY;
-    const int64_t n0 = s->nv, n1 = n0 + ne;
-    const int nbk = nblocks(n1);
+    const int64_t n0 = s->nv;
     // stage 1 at t: one new vortex per edge (appended to X, Y, G), u1 at all n0 + ne
     PF_TRY(bodies_stage(p, s, bodies, n_bodies, s->t, dt, s->X, s->Y, ne > 0, s->u1, s->v1));
-    s->nv = n1;
+    s->nv = n0 + ne;
     if (scheme == 0) {
-        if (p->prec == PF_FP64) k_euler<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt);
-        else k_euler<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_EULER, count_of(s), dt));
     } else {
-        if (p->prec == PF_FP64) k_predict<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, n1, dt, s->Xs, s->Ys);
-        else k_predict<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, n1, dt, s->Xs, s->Ys);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_PREDICT, count_of(s), dt));
         // stage 2 at t + dt: strengths kept, every body circulation-constrained
         PF_TRY(bodies_stage(p, s, bodies, n_bodies, s->t + dt, dt, s->Xs, s->Ys, false, s->u2, s->v2));
-        if (p->prec == PF_FP64) k_heun<double><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (double*)s->u1, (double*)s->v1, (double*)s->u2, (double*)s->v2, n1, dt);
-        else k_heun<float><<<nbk, 256, 0, p->stream>>>(s->X, s->Y, (float*)s->u1, (float*)s->v1, (float*)s->u2, (float*)s->v2, n1, dt);
-        PF_LAUNCH_CHECK(p);
+        PF_TRY(advance(p, s, ADV_HEUN, count_of(s), dt));
     }
     for (int e = 0; e < ne; ++e) s->last[e] = n0 + e;
     s->t += dt;

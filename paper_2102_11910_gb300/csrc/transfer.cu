@@ -53,9 +53,10 @@ pf_status plan_bin_reserve(pf_plan p, int64_t nv) {
         PF_CUDA(p, cudaMalloc(&p->recs, (size_t)cap * rsz));
         p->rec_cap = cap;
     }
-    const int64_t need = (int64_t)bin_blocks(nv) * p->ntiles;
+    const int64_t ntiles = (int64_t)ceil_div(p->nx, p->tile) * ceil_div(p->ny, p->tile);
+    const int64_t need = (int64_t)bin_blocks(nv, p->min_span) * ntiles;
     if (need > p->bin_off_cap) {
-        const int64_t cap = std::max<int64_t>(need, (int64_t)bin_blocks(p->pos_cap) * p->ntiles);
+        const int64_t cap = std::max<int64_t>(need, (int64_t)bin_blocks(p->pos_cap, p->min_span) * ntiles);
         PF_CUDA(p, cudaStreamSynchronize(p->stream));
         if (p->bin_off) cudaFree(p->bin_off);
         p->bin_off = nullptr;
@@ -80,6 +81,32 @@ BinWork plan_binwork(pf_plan p) {
     return b;
 }
 
+template <typename T>
+pf_status regularize_configured(pf_plan p, const BinWork& bw, const double* X, const double* Y, const double* G,
+                                int64_t nv, T* w, const int64_t* dn) {
+    const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0, p->tile);
+    p->bin_tile = p->tile;
+    if (p->tile == BIN_TILE_SMALL)
+        return regularize_launch<T, BIN_TILE_SMALL>(p, geo, bw, X, Y, G, nv, w, p->stream, p->min_span,
+                                                    p->tile_threads, dn);
+    return regularize_launch<T, BIN_TILE>(p, geo, bw, X, Y, G, nv, w, p->stream, p->min_span, p->tile_threads, dn);
+}
+
+template <int TILE>
+pf_status interpolate_tiles(pf_plan p, const Geo& geo, const void* uv, int64_t nq, void* uq, void* vq) {
+    if (p->prec == PF_FP64)
+        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles<double, TILE>, geo.ntiles, p->tile_threads, 0,
+                                                         p->stream, (const Rec<double>*)p->recs, p->tile_start,
+                                                         p->tile_count, (const double2*)uv, geo, (double*)uq,
+                                                         (double*)vq, p->rec_cap, nq, p->d_status)));
+    else
+        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32<TILE>, geo.ntiles, p->tile_threads, 0,
+                                                         p->stream, (const Rec<float>*)p->recs, p->tile_start,
+                                                         p->tile_count, (const float2*)uv, geo, (float*)uq,
+                                                         (float*)vq, p->rec_cap, nq, p->d_status)));
+    return PF_OK;
+}
+
 }  // namespace
 
 // the plan's binning scratch (cell records, histograms, status words)
@@ -88,31 +115,24 @@ BinWork plan_binwork_for(pf_plan p) { return plan_binwork(p); }
 // size the plan's vortex buffers for nv vortices ahead of time
 pf_status plan_reserve_vortices(pf_plan p, int64_t nv) { return plan_bin_reserve(p, nv); }
 
-pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w) {
+// R_v in the plan's launch configuration (tile edge, block partition, threads).
+// With dn, the count is read on the device from dn[0] and nv (the capacity)
+// only sizes the launches.
+pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,
+                            const int64_t* dn) {
     pf_status st = plan_bin_reserve(p, nv);
     if (st != PF_OK) return st;
-    const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0);
     const BinWork bw = plan_binwork(p);
-    if (p->prec == PF_FP64) return regularize_launch<double>(p, geo, bw, X, Y, G, nv, (double*)w, p->stream);
-    return regularize_launch<float>(p, geo, bw, X, Y, G, nv, (float*)w, p->stream);
+    if (p->prec == PF_FP64) return regularize_configured<double>(p, bw, X, Y, G, nv, (double*)w, dn);
+    return regularize_configured<float>(p, bw, X, Y, G, nv, (float*)w, dn);
 }
 
-// E_v at the vortices the last vortex_regularize call binned
+// E_v at the vortices the last vortex_regularize call binned (in that call's tiles)
 pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void* uq, void* vq) {
     if (nq == 0) return PF_OK;
-    const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0);
-    if (p->prec == PF_FP64)
-        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles<double>, geo.ntiles, 256, 0, p->stream,
-                                                         (const Rec<double>*)p->recs, p->tile_start, p->tile_count,
-                                                         (const double2*)uv, geo, (double*)uq, (double*)vq, p->rec_cap,
-                                                         nq, p->d_status)));
-    else {
-        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32, geo.ntiles, 256, 0, p->stream,
-                                                         (const Rec<float>*)p->recs, p->tile_start, p->tile_count,
-                                                         (const float2*)uv, geo, (float*)uq, (float*)vq, p->rec_cap,
-                                                         nq, p->d_status)));
-    }
-    return PF_OK;
+    const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0, p->bin_tile);
+    if (p->bin_tile == BIN_TILE_SMALL) return interpolate_tiles<BIN_TILE_SMALL>(p, geo, uv, nq, uq, vq);
+    return interpolate_tiles<BIN_TILE>(p, geo, uv, nq, uq, vq);
 }
 
 pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq) {

@@ -177,9 +177,20 @@ __device__ __forceinline__ bool loc_split(double X, const Geo& g, int axis, int&
 }
 template <typename T> using Frac = typename std::conditional<sizeof(T) == 4, unsigned, double>::type;
 
-template <typename T>
+// The vortex count and block span of a binning pass: the launch's own, or,
+// when dn is given (a captured step replayed at a growing count), dn[0] with
+// the span bin_span computes for it; blocks past the count bin nothing.
+__device__ __forceinline__ void bin_count(const int64_t* dn, int min_span, int64_t& nv, int64_t& span) {
+    if (!dn) return;
+    nv = *dn;
+    const int64_t s = (nv + BIN_MAX_BLOCKS - 1) / BIN_MAX_BLOCKS;
+    span = s < min_span ? min_span : s;
+}
+
+template <typename T, int TILE>
 __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
-                                                       const double* __restrict__ G, int64_t nv, int64_t span, Geo geo,
+                                                       const double* __restrict__ G, int64_t nv, int64_t span,
+                                                       const int64_t* __restrict__ dn, int min_span, Geo geo,
                                                        Pos<T>* __restrict__ pos, int* __restrict__ hist,
                                                        double* __restrict__ gmax_blk, int* __restrict__ status,
                                                        unsigned long long* __restrict__ oob) {
@@ -189,6 +200,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
     double gm = 0.0;
     for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) cnt[i] = 0u;
     pdl_wait();
+    bin_count(dn, min_span, nv, span);
     __syncthreads();
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
@@ -220,8 +232,8 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
             make_pos(p, ci, cj, fx, fy, gs[k]);
             pos[q] = p;
             gm = fmax(gm, fabs((double)p.g));      // |Gamma| as the record carries it
-            const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
-            const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
+            const int tx0 = (ci - 1) / TILE, tx1 = (ci + 2) / TILE;
+            const int ty0 = (cj - 1) / TILE, ty1 = (cj + 2) / TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&cnt[ty * geo.ntx + tx], 1u);
         }
@@ -325,12 +337,14 @@ __global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __res
 // Every block scans the tile totals itself (block 0 publishes the tiles' first
 // slots for the deposit and interpolation passes), adds them to its offsets
 // and places its records.
-constexpr int SCAN_PER = 16;     // tiles per thread in the block scan: 256 * 16 >= 64 * 64 tiles
+constexpr int SCAN_PER = 16;     // tiles per thread in the block scan: 256 * 16 = 64 * 64 tiles at most
 template <typename T> struct ScatterUnroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 static_assert((2048 / BIN_TILE) * (2048 / BIN_TILE) <= BIN_THREADS * SCAN_PER, "scan covers every tile");
+constexpr int MAX_SCAN_TILES = BIN_THREADS * SCAN_PER;   // smaller tiles are offered only up to this count
 
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
+                                                        const int64_t* __restrict__ dn, int min_span,
                                                         Geo geo, const int* __restrict__ off,
                                                         const unsigned* __restrict__ tile_count,
                                                         int* __restrict__ tile_start, Rec<T>* __restrict__ recs,
@@ -339,15 +353,16 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
     __shared__ int wsum[BIN_THREADS / 32];
     unsigned* cnt = sm;
     int* first = (int*)(sm + geo.ntiles);
+    pdl_wait();
+    bin_count(dn, min_span, nv, span);
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
-    pdl_wait();
     // this thread's first records (in flight during the scan)
     Pos<T> p[ScatterUnroll<T>::value];
 #pragma unroll
     for (int k = 0; k < ScatterUnroll<T>::value; ++k) {     // clamped loads; past the end: no vortex
         const int64_t q = lo + k * BIN_THREADS + threadIdx.x;
-        p[k] = pos[q < hi ? q : hi - 1];
+        p[k] = pos[q < hi ? q : (hi > 0 ? hi - 1 : 0)];
         if (q >= hi) make_pos(p[k], 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);
     }
     // exclusive scan of tile_count: thread i owns tiles [i * per, i * per + per)
@@ -394,8 +409,8 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
             const int ci = pos_ci(p[k]), cj = pos_cj(p[k]);
             if (ci == 0xFFFF) continue;
             const int64_t q = base + k * BIN_THREADS + threadIdx.x;
-            const int tx0 = (ci - 1) / BIN_TILE, tx1 = (ci + 2) / BIN_TILE;
-            const int ty0 = (cj - 1) / BIN_TILE, ty1 = (cj + 2) / BIN_TILE;
+            const int tx0 = (ci - 1) / TILE, tx1 = (ci + 2) / TILE;
+            const int ty0 = (cj - 1) / TILE, ty1 = (cj + 2) / TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx) {
                     const int t = ty * geo.ntx + tx;
@@ -404,7 +419,7 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
                         atomicOr(status, ST_INTERNAL);
                         continue;
                     }
-                    recs[slot] = make_rec(p[k], ci - tx * BIN_TILE, cj - ty * BIN_TILE, (int)q);
+                    recs[slot] = make_rec(p[k], ci - tx * TILE, cj - ty * TILE, (int)q);
                 }
         }
     }
@@ -438,14 +453,16 @@ __device__ __forceinline__ void split_hilo(float x, int& hi, int& lo) {
 // node-window bound measured no faster and lost seven bits on clustered
 // vortices; shared adds are not what bounds this kernel.)
 //
-// A record's local cell (lx, ly) lies in [-2, 32], so its nodes lie in
-// [-3, 34]: the accumulator covers that range (ACC_W^2 nodes) and the adds
-// need no bounds tests; only the tile's own 32 x 32 nodes are written out.
-constexpr int ACC_HALO = 3, ACC_W = BIN_TILE + 6;
+// A record's local cell (lx, ly) lies in [-2, TILE], so its nodes lie in
+// [-3, TILE + 2]: the accumulator covers that range (acc_w^2 nodes) and the
+// adds need no bounds tests; only the tile's own TILE x TILE nodes are written
+// out.
+constexpr int ACC_HALO = 3;
+template <int TILE> struct AccW { static constexpr int value = TILE + 6; };
 
 enum { DEP_SPLIT32 = 0, DEP_F32_64 = 1, DEP_F64_64 = 2 };
 
-template <int MODE, typename T>
+template <int MODE, int ACC_W, typename T>
 __device__ __forceinline__ void deposit_one(const Rec<T>& rc, T scale, unsigned long long* acc) {
     int* acc_hi = reinterpret_cast<int*>(acc);
     int* acc_lo = reinterpret_cast<int*>(acc) + ACC_W * ACC_W;
@@ -476,7 +493,7 @@ __device__ __forceinline__ void deposit_one(const Rec<T>& rc, T scale, unsigned 
 }
 
 // every record of the tile, four loads in flight per thread
-template <int MODE, typename T>
+template <int MODE, int ACC_W, typename T>
 __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs, int cnt, T scale,
                                                 unsigned long long* acc) {
     constexpr int U = 4;
@@ -489,15 +506,16 @@ __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs,
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (r0 + u * (int)blockDim.x + (int)threadIdx.x < cnt) deposit_one<MODE, T>(rc[u], scale, acc);
+            if (r0 + u * (int)blockDim.x + (int)threadIdx.x < cnt) deposit_one<MODE, ACC_W, T>(rc[u], scale, acc);
     }
 }
 
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs, const int* __restrict__ tile_start,
                                                  const unsigned* __restrict__ tile_count,
                                                  const double* __restrict__ gmax_all, Geo geo, T* __restrict__ w,
                                                  int64_t rec_cap, int* __restrict__ status) {
+    constexpr int ACC_W = AccW<TILE>::value;
     __shared__ unsigned long long acc[ACC_W * ACC_W];
     const int t = blockIdx.x;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
@@ -512,16 +530,16 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
     const bool split32 = sizeof(T) == 4 && cnt < 65536;
     const int sh = tile_shift_of((unsigned)cnt, *gmax_all) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
     const T scale = pow2<T>(sh);
-    if (sizeof(T) == 8) deposit_records<DEP_F64_64>(recs + start, cnt, scale, acc);
-    else if (split32) deposit_records<DEP_SPLIT32>(recs + start, cnt, scale, acc);
-    else deposit_records<DEP_F32_64>(recs + start, cnt, scale, acc);
+    if (sizeof(T) == 8) deposit_records<DEP_F64_64, ACC_W>(recs + start, cnt, scale, acc);
+    else if (split32) deposit_records<DEP_SPLIT32, ACC_W>(recs + start, cnt, scale, acc);
+    else deposit_records<DEP_F32_64, ACC_W>(recs + start, cnt, scale, acc);
     __syncthreads();
     const int* acc_hi = reinterpret_cast<const int*>(acc);
     const int* acc_lo = reinterpret_cast<const int*>(acc) + ACC_W * ACC_W;
     const float inv_dx2f = (float)geo.inv_dx2;
-    for (int i = threadIdx.x; i < BIN_TILE * BIN_TILE; i += blockDim.x) {
-        const int lx = i % BIN_TILE, ly = i / BIN_TILE;
-        const int gi = tx * BIN_TILE + lx, gj = ty * BIN_TILE + ly;
+    for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
+        const int lx = i % TILE, ly = i / TILE;
+        const int gi = tx * TILE + lx, gj = ty * TILE + ly;
         const int node = (ly + ACC_HALO) * ACC_W + lx + ACC_HALO;
         if (gi < geo.nx && gj < geo.ny) {
             long long a;
@@ -561,15 +579,14 @@ __device__ __forceinline__ void gather16(const T* __restrict__ uv, int nx, int c
 // one node before and two after, per direction) in shared memory, then every
 // record whose cell lies in the tile (each vortex has exactly one such record)
 // gathers its 4x4 stencil there and writes its result at its original index.
-constexpr int PATCH = BIN_TILE + 3;
-
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__ recs,
                                                       const int* __restrict__ tile_start,
                                                       const unsigned* __restrict__ tile_count, const C_t<T>* __restrict__ uv,
                                                       Geo geo, T* __restrict__ uq, T* __restrict__ vq, int64_t rec_cap,
                                                       int64_t nq, int* __restrict__ status) {
     using C = C_t<T>;
+    constexpr int PATCH = TILE + 3;
     __shared__ C patch[PATCH * PATCH];
     const int t = blockIdx.x;
     pdl_wait();
@@ -581,7 +598,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
         return;
     }
     const int tx = t % geo.ntx, ty = t / geo.ntx;
-    const int gi0 = tx * BIN_TILE - 1, gj0 = ty * BIN_TILE - 1;
+    const int gi0 = tx * TILE - 1, gj0 = ty * TILE - 1;
     for (int i = threadIdx.x; i < PATCH * PATCH; i += blockDim.x) {
         const int gi = gi0 + i % PATCH, gj = gj0 + i / PATCH;
         C v = cmake<C>(T(0), T(0));
@@ -603,7 +620,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
         for (int u = 0; u < U; ++u) {
             if (!ok[u]) continue;
             const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
-            if (lx < 0 || lx >= BIN_TILE || ly < 0 || ly >= BIN_TILE) continue;  // not home
+            if (lx < 0 || lx >= TILE || ly < 0 || ly >= TILE) continue;  // not home
             T wx[4], wy[4];
             m4p_weights<T>(rec_fx(rc[u]), wx);
             m4p_weights<T>(rec_fy(rc[u]), wy);
@@ -635,14 +652,14 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
 // shared loads: the patch is staged twice as node pairs, starting at even and
 // at odd local x, so that the four nodes px .. px + 3 of a row are the pairs
 // E[px / 2], E[px / 2 + 1] (px even) or O[(px - 1) / 2], O[(px + 1) / 2].
-constexpr int PAIRS = (PATCH + 1) / 2;   // 18 pairs per patch row
-
+template <int TILE>
 __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __restrict__ recs,
                                                           const int* __restrict__ tile_start,
                                                           const unsigned* __restrict__ tile_count,
                                                           const float2* __restrict__ uv, Geo geo,
                                                           float* __restrict__ uq, float* __restrict__ vq,
                                                           int64_t rec_cap, int64_t nq, int* __restrict__ status) {
+    constexpr int PATCH = TILE + 3, PAIRS = (PATCH + 1) / 2;   // 18 pairs per patch row at TILE 32
     __shared__ float4 pe[PATCH * PAIRS];
     __shared__ float4 po[PATCH * PAIRS];
     const int t = blockIdx.x;
@@ -655,7 +672,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         return;
     }
     const int tx = t % geo.ntx, ty = t / geo.ntx;
-    const int gi0 = tx * BIN_TILE - 1, gj0 = ty * BIN_TILE - 1;
+    const int gi0 = tx * TILE - 1, gj0 = ty * TILE - 1;
     // patch nodes px, py in [0, 2 PAIRS) x [0, PATCH); px = 2 PAIRS - 1 only pads
     for (int i = threadIdx.x; i < PATCH * 2 * PAIRS; i += blockDim.x) {
         const int px = i % (2 * PAIRS), py = i / (2 * PAIRS);
@@ -686,7 +703,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         for (int u = 0; u < U; ++u) {
             if (!ok[u]) continue;
             const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
-            if (lx < 0 || lx >= BIN_TILE || ly < 0 || ly >= BIN_TILE) continue;  // not home
+            if (lx < 0 || lx >= TILE || ly < 0 || ly >= TILE) continue;  // not home
             float wx[4], wy[4];
             m4p_weights<float>(rec_fx(rc[u]), wx);
             m4p_weights<float>(rec_fy(rc[u]), wy);
@@ -745,7 +762,7 @@ struct BinWork {
     int64_t rec_cap;          // record slots in recs
 };
 
-inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
+inline Geo make_geo(int nx, int ny, double dx, double x0, double y0, int tile = BIN_TILE) {
     Geo g;
     g.x0 = x0; g.y0 = y0; g.dx = dx; g.nx = nx; g.ny = ny;
     g.inv_dx = 1.0 / dx;
@@ -755,34 +772,38 @@ inline Geo make_geo(int nx, int ny, double dx, double x0, double y0) {
     const double lx = (double)(nx - 2), ly = (double)(ny - 2);
     memcpy(&g.xlim, &lx, sizeof(double));
     memcpy(&g.ylim, &ly, sizeof(double));
-    g.ntx = ceil_div(nx, BIN_TILE);
-    g.ntiles = g.ntx * ceil_div(ny, BIN_TILE);
+    g.ntx = ceil_div(nx, tile);
+    g.ntiles = g.ntx * ceil_div(ny, tile);
     return g;
 }
 
 // Bin nv vortices by tile (locate, offsets, scatter) into bw; `p` (may be
 // null) only supplies the timing records and the error text.
-template <typename T>
+// With dn (device count, see bin_count), nv is the capacity the launch is sized for.
+template <typename T, int TILE = BIN_TILE>
 pf_status bin_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
-                     const double* G, int64_t nv, cudaStream_t s) {
-    const int nb = bin_blocks(nv);
-    const int64_t span = bin_span(nv);
+                     const double* G, int64_t nv, cudaStream_t s, int min_span = BIN_MIN_SPAN,
+                     const int64_t* dn = nullptr) {
+    if (geo.ntiles > MAX_SCAN_TILES) return PF_ERR_ARG;
+    const int nb = bin_blocks(nv, min_span);
+    const int64_t span = bin_span(nv, min_span);
     const size_t sh_loc = (size_t)geo.ntiles * sizeof(unsigned);
     const size_t sh_sc = 2 * (size_t)geo.ntiles * sizeof(unsigned);
-    if (set_smem(k_locate<T>, sh_loc) != cudaSuccess || set_smem(k_scatter<T>, sh_sc) != cudaSuccess)
+    if (set_smem(k_locate<T, TILE>, sh_loc) != cudaSuccess || set_smem(k_scatter<T, TILE>, sh_sc) != cudaSuccess)
         return PF_ERR_CUDA;
     Pos<T>* pos = (Pos<T>*)bw.pos;
     if (nb > 0) {
-        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T>, nb, BIN_THREADS, sh_loc, s, X, Y, G, nv, span, geo,
-                                                       pos, bw.bin_off, bw.gmax + 1, bw.status, bw.oob)));
+        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T, TILE>, nb, BIN_THREADS, sh_loc, s, X, Y, G, nv,
+                                                       span, dn, min_span, geo, pos, bw.bin_off, bw.gmax + 1,
+                                                       bw.status, bw.oob)));
     }
     PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s,
                                                      geo.ntiles, nb, bw.bin_off, bw.tile_count,
                                                      (const double*)(bw.gmax + 1), bw.gmax)));
     if (nb > 0) {
-        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T>, nb, BIN_THREADS, sh_sc, s, pos, nv, span, geo,
-                                                         bw.bin_off, bw.tile_count, bw.tile_start, (Rec<T>*)bw.recs,
-                                                         bw.rec_cap, bw.status)));
+        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T, TILE>, nb, BIN_THREADS, sh_sc, s, pos, nv,
+                                                         span, dn, min_span, geo, bw.bin_off, bw.tile_count,
+                                                         bw.tile_start, (Rec<T>*)bw.recs, bw.rec_cap, bw.status)));
     } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
         return PF_ERR_CUDA;
     }
@@ -790,22 +811,23 @@ pf_status bin_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double*
 }
 
 // Deposit the binned records of bw into w.
-template <typename T>
+template <typename T, int TILE = BIN_TILE>
 pf_status deposit_launch(pf_plan p, const Geo& geo, const Rec<T>* recs, const int* tile_start,
                          const unsigned* tile_count, const double* gmax, int64_t rec_cap, int* status, T* w,
-                         cudaStream_t s) {
-    PF_KERNEL(p, "regularize", PF_CUDA(p, pf_launch(k_deposit<T>, geo.ntiles, 256, 0, s, recs, tile_start, tile_count,
+                         cudaStream_t s, int threads = 256) {
+    PF_KERNEL(p, "regularize", PF_CUDA(p, pf_launch(k_deposit<T, TILE>, geo.ntiles, threads, 0, s, recs, tile_start, tile_count,
                                                     gmax, geo, w, rec_cap, status)));
     return PF_OK;
 }
 
 // The four regularization kernels.
-template <typename T>
+template <typename T, int TILE = BIN_TILE>
 pf_status regularize_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
-                            const double* G, int64_t nv, T* w, cudaStream_t s) {
-    PF_TRY(bin_launch<T>(p, geo, bw, X, Y, G, nv, s));
-    return deposit_launch<T>(p, geo, (const Rec<T>*)bw.recs, bw.tile_start, bw.tile_count, (const double*)bw.gmax,
-                             bw.rec_cap, bw.status, w, s);
+                            const double* G, int64_t nv, T* w, cudaStream_t s, int min_span = BIN_MIN_SPAN,
+                            int threads = 256, const int64_t* dn = nullptr) {
+    PF_TRY((bin_launch<T, TILE>(p, geo, bw, X, Y, G, nv, s, min_span, dn)));
+    return deposit_launch<T, TILE>(p, geo, (const Rec<T>*)bw.recs, bw.tile_start, bw.tile_count,
+                                   (const double*)bw.gmax, bw.rec_cap, bw.status, w, s, threads);
 }
 
 }  // namespace

@@ -47,6 +47,7 @@ struct pf_vic_state_s {
 namespace {
 
 constexpr int NDIR = 25;               // destinations: tiles (dx, dy) in [-2, 2]^2 around the source
+constexpr int PATCH = BIN_TILE + 3;     // staged (u, v) nodes per tile edge: one before, two after
 constexpr int MOVE_BIAS = 34;          // moved mixed records keep lx + 34, ly + 34 (cells -34 .. 221 of the source tile)
 
 __device__ __forceinline__ int dir_of(int dtx, int dty) { return (dty + 2) * 5 + (dtx + 2); }
@@ -421,8 +422,8 @@ pf_status vic_step_t(pf_vic_state s, double dt, double Uinf, double Vinf, T* uq,
     const Geo geo = make_geo(p->nx, p->ny, p->dx, p->x0, p->y0);
     const int c = s->cur, n = c ^ 1;
     const Rec<T>* rc = (const Rec<T>*)s->recs[c];
-    PF_TRY(deposit_launch<T>(p, geo, rc, s->tstart[c], s->tcount[c], s->gmax, s->rec_cap, p->d_status, (T*)p->w,
-                             p->stream));
+    PF_TRY((deposit_launch<T, BIN_TILE>(p, geo, rc, s->tstart[c], s->tcount[c], s->gmax, s->rec_cap, p->d_status,
+                                        (T*)p->w, p->stream)));
     PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
     PF_CUDA(p, cudaMemsetAsync(s->tcount[n], 0, (size_t)geo.ntiles * sizeof(unsigned), p->stream));
     PF_KERNEL(p, "vic_advect", PF_CUDA(p, pf_launch(k_vic_advect<T>, geo.ntiles, 256, 0, p->stream, rc, s->tstart[c],
