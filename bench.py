@@ -720,47 +720,7 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
                                              "geometry",
                                      "mixed": _steps_per_s(pf, plan, pressure_step, 50)}
         print("workload done: %s" % 'pressure_plate_128', file=sys.stderr, flush=True)
-        # uneven batch: independent instances, one step each per call
-        inst = inputs.batched_instances(n=n_batch)
-        res = {}
-        for prec, name in ((pf.PF_MIXED, "batched_mixed"), (pf.PF_FP64, "unbatched_fp64")):
-            bases, plans, states, bodies = {}, [], [], []
-            for r in inst:
-                gg = r["grid"]
-                key = (gg.nx, gg.ny)
-                if key not in bases:
-                    bases[key] = pf.Plan(gg.nx, gg.ny, gg.dx, gg.x0, gg.y0, prec, stream=stream)
-                p = pf.pf_plan_clone(bases[key], prec, torch.cuda.Stream()) if name.startswith("batched") \
-                    else bases[key]
-                st = pf.State(p, len(r["X"]) + 64)
-                pf.pf_state_set(st, r["X"], r["Y"], r["G"])
-                b = r["body"]
-                plans.append(p)
-                states.append(st)
-                bodies.append(pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=r["Uinf"]))
-            dts = [r["dt"] for r in inst]
-            if name.startswith("batched"):
-                pf.pf_step_batch(plans, states, bodies, dts)          # factorisations
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(3):
-                    pf.pf_step_batch(plans, states, bodies, dts)
-                torch.cuda.synchronize()
-                res[name] = 3 * len(inst) / (time.perf_counter() - t0)
-            else:
-                for p, st, b, dt in zip(plans, states, bodies, dts):
-                    pf.pf_step(p, st, dt, b)
-                    pf.pf_sync(p)
-                t0 = time.perf_counter()
-                for p, st, b, dt in zip(plans, states, bodies, dts):
-                    pf.pf_step(p, st, dt, b)
-                    pf.pf_sync(p)
-                res[name] = len(inst) / (time.perf_counter() - t0)
-            del plans, states, bases
-        out["uneven_batch"] = {"unit": "instance-steps/s", "instances": len(inst),
-                               "desc": "grids 128^2..512^2, plate or ellipse, Ns 32-256, 100-20000 vortices; "
-                                       "batched: one stream per instance, shared tables; unbatched FP64: one "
-                                       "instance at a time", **res}
+        out["uneven_batch"] = bench_uneven_batch(pf, inputs, torch, stream, n_batch)
         print("workload done: %s" % 'uneven_batch', file=sys.stderr, flush=True)
     out["serving"] = bench_serving(pf, inputs, n_requests, (0.3, 0.7, 1.0))
     return out
@@ -771,7 +731,8 @@ def bench_body_profile(pf, inputs, torch, which, K, W):
     circulation sum, sheet solve with release, velocity = R_v + sheet
     deposit + L^-1 + E_v, position update) and of the kernels timed inside
     them, for the 128^2 plate (Euler, factor reused) and the 768x512 pitching
-    plate (Ns 64, RK2, refactored at every stage).  W steps untimed, then K
+    plate (Ns 64, RK2, refactored at every stage) and the 1024^2 plate with
+    1e5 vortices of the served mix (Ns 256, Euler).  W steps untimed, then K
     steps each bracketed by events on the plan stream."""
     import numpy as np
     stream = torch.cuda.Stream()
@@ -791,6 +752,12 @@ def bench_body_profile(pf, inputs, torch, which, K, W):
         cases.append(("pitching_plate_768x512_ns64", g, np.zeros(0), np.zeros(0), np.zeros(0),
                       pf.plate_kinematics(64, pw["chord"], pw["alpha0"], pw["amp"], omega, pw["Uinf"]), pw["dt"], 1,
                       2 * (K + W + 1), None))
+    if which in ("all", "big"):
+        bw = inputs.plate_vortices_1024()
+        b = bw["body"]
+        cases.append(("plate_1024_1e5", bw["grid"], bw["X"], bw["Y"], bw["G"],
+                      pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"], Uinf=bw["Uinf"]),
+                      bw["dt"], 0, len(bw["X"]) + 2 * (K + W + 1), None))
     with torch.cuda.stream(stream):
         for name, g, X, Y, G, body, dt, scheme, cap, reload in cases:
             plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
@@ -825,6 +792,74 @@ def bench_body_profile(pf, inputs, torch, which, K, W):
             state.close()
             plan.close()
     return out
+
+
+def bench_uneven_batch(pf, inputs, torch, stream, n_batch=256):
+    """The uneven batch (256 independent instances), one step each per call."""
+    with torch.cuda.stream(stream):
+        # uneven batch: independent instances, one step each per call, in the
+        # same precision three ways: one CUDA graph of every instance's step
+        # (pf_batch), one stream per instance enqueued per call (pf_step_batch),
+        # and one instance at a time (pf_step, synchronised)
+        inst = inputs.batched_instances(n=n_batch)
+        dts = [r["dt"] for r in inst]
+        res = {}
+        for prec, pname in ((pf.PF_MIXED, "mixed"), (pf.PF_FP64, "fp64")):
+            for mode in ("graph", "streams", "unbatched"):
+                bases, plans, states, bodies = {}, [], [], []
+                for r in inst:
+                    gg = r["grid"]
+                    key = (gg.nx, gg.ny)
+                    if key not in bases:
+                        bases[key] = pf.Plan(gg.nx, gg.ny, gg.dx, gg.x0, gg.y0, prec, stream=stream)
+                    p = pf.pf_plan_clone(bases[key], prec, torch.cuda.Stream())
+                    st = pf.State(p, len(r["X"]) + 64)
+                    pf.pf_state_set(st, r["X"], r["Y"], r["G"])
+                    b = r["body"]
+                    plans.append(p)
+                    states.append(st)
+                    bodies.append(pf.BodyKinematics(b["xb"], b["yb"], b["ds"], b["edges"], b["alpha0"],
+                                                    Uinf=r["Uinf"]))
+                torch.cuda.synchronize()
+                if mode == "graph":
+                    t0 = time.perf_counter()
+                    batch = pf.Batch(plans, states, bodies, dts)       # factorisations and the capture
+                    torch.cuda.synchronize()
+                    res["graph_create_s_" + pname] = time.perf_counter() - t0
+                    batch.step(1)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(3):
+                        batch.step(1)
+                    torch.cuda.synchronize()
+                    res["graph_" + pname] = 3 * len(inst) / (time.perf_counter() - t0)
+                    batch.close()
+                elif mode == "streams":
+                    pf.pf_step_batch(plans, states, bodies, dts)          # factorisations
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(3):
+                        pf.pf_step_batch(plans, states, bodies, dts)
+                    torch.cuda.synchronize()
+                    res["streams_" + pname] = 3 * len(inst) / (time.perf_counter() - t0)
+                else:
+                    for p, st, b, dt in zip(plans, states, bodies, dts):
+                        pf.pf_step(p, st, dt, b)
+                        pf.pf_sync(p)
+                    t0 = time.perf_counter()
+                    for p, st, b, dt in zip(plans, states, bodies, dts):
+                        pf.pf_step(p, st, dt, b)
+                        pf.pf_sync(p)
+                    res["unbatched_" + pname] = len(inst) / (time.perf_counter() - t0)
+                for p in plans:
+                    pf.pf_sync(p)
+                del plans, states, bases
+        return {"unit": "instance-steps/s", "instances": len(inst),
+                "desc": "grids 128^2..512^2, plate or ellipse, Ns 32-256, 100-20000 vortices "
+                        "N(0,1e-3), a CFL step each; per precision: graph = one CUDA graph launch "
+                        "steps every instance (pf_batch, captured once), streams = one stream per "
+                        "instance enqueued every call (pf_step_batch), unbatched = one instance at "
+                        "a time, synchronised", **res}
 
 
 def bench_serving(pf, inputs, n_requests, fractions):
@@ -915,9 +950,18 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 leg and the CPU baseline")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the request server: 4096 requests, Poisson arrivals from 0.1x to 1.2x of saturation")
-    ap.add_argument("--body-profile", choices=["all", "plate", "pitching"],
+    ap.add_argument("--body-profile", choices=["all", "plate", "pitching", "big"],
                     help="only the body steps' phase shares (CUDA events): --warmup steps untimed, --steps timed")
+    ap.add_argument("--uneven-batch", action="store_true",
+                    help="only the uneven batch of 256 instances (graph, streams, unbatched; mixed and FP64)")
     args = ap.parse_args()
+    if args.uneven_batch:
+        import torch
+        import paper_2102_11910_gb300 as pf
+        from paper_2102_11910_gb300 import inputs
+        torch.cuda.set_device(dist_env()[2])
+        print(json.dumps({"uneven_batch": bench_uneven_batch(pf, inputs, torch, torch.cuda.Stream())}))
+        return
     if args.body_profile:
         import torch
         import paper_2102_11910_gb300 as pf

@@ -188,7 +188,9 @@ pf_status pf_interpolate(pf_plan plan, const void* uv, const double* Xq, const d
                          int64_t nq, void* uq, void* vq);
 
 /* The whole body-free step: R_v, psi = -L^{-1} w, curl, E_v at the vortices
- * themselves (plus the uniform flow).  uq, vq: real[nv]. */
+ * themselves (plus the uniform flow).  uq, vq: real[nv]; a vortex whose
+ * stencil leaves the grid is left out of R_v, counted (pf_sync) and gets
+ * uq = vq = 0. */
 pf_status pf_vic_velocity(pf_plan plan, const double* X, const double* Y, const double* Gam,
                           int64_t nv, double Uinf, double Vinf, void* uq, void* vq);
 
@@ -535,6 +537,37 @@ pf_status pf_step_multi(pf_plan plan, pf_state state, int32_t n_bodies, const pf
  * are not stepped. */
 pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
                         const double* dt, int32_t scheme);
+
+/* A batch of independent instances (plan, state, body, step length) whose
+ * steps run as one CUDA graph: pf_step's method for each instance (Sec. 2.4),
+ * captured once, the instances' kernels in parallel branches, so that one
+ * step of every instance is one graph launch and no per-kernel host work.
+ * The captured kernels read each instance's vortex count and last releases
+ * from the state's device counts and are sized by its capacity, so the graph
+ * serves every step until a state is full.
+ * Requirements (else PF_ERR_ARG): n >= 1; plans[i] is the plan states[i] was
+ * created with; plans and states distinct; no plan on the legacy default
+ * stream or with timing on; each body fixed in time (amp = 0 or omega = 0,
+ * or no body); dt[i] > 0; scheme 0 (Euler) or 1 (RK2).
+ * Creation factors S at each body's pose where the state has no factor for
+ * it, reserves every buffer a step of the full capacity uses, synchronises
+ * the plans' streams and captures.  The batch copies dt and the kinematics
+ * structs; the body arrays they point to must outlive it, and while it lives
+ * its states must not be stepped around other bodies.  Each plan's surface
+ * right-hand-side route (pf_plan_set_rhs_route) is chosen once, for the
+ * state's capacity: with the route fixed (not PF_RHS_AUTO) a batch step is
+ * bitwise pf_step's.  PF_ERR_CUDA if the capture or the instantiation fails
+ * (pf_last_error of plans[0] has the text). */
+typedef struct pf_batch_s* pf_batch;
+pf_status pf_batch_create(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
+                          const double* dt, int32_t scheme, pf_batch* out);
+
+/* nsteps steps of every instance: nsteps launches of the graph on the batch's
+ * own stream, ordered after the work enqueued so far on every plan's stream
+ * and before any enqueued there afterwards (pf_sync on a plan waits for them).
+ * PF_ERR_CAPACITY, with nothing launched, if a state would overflow. */
+pf_status pf_batch_step(pf_batch batch, int32_t nsteps);
+pf_status pf_batch_destroy(pf_batch batch);
 
 /* ------------------------------------------------------- request server */
 

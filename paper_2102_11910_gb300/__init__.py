@@ -688,6 +688,49 @@ def pf_step_batch(plans, states, bodies, dt, scheme=0):
     _native.check(_native.lib().pf_step_batch(n, P, S, B, D, int(scheme)), "pf_step_batch")
 
 
+class Batch:
+    """Handle of a pf_batch: independent instances whose steps were captured
+    once into a CUDA graph; step(n) launches it n times.  Keeps the plans,
+    states and bodies alive while it lives."""
+
+    def __init__(self, plans, states, bodies, dt, scheme=0):
+        n = len(plans)
+        self.plans, self.states, self.bodies = list(plans), list(states), list(bodies)
+        P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+        S = (ctypes.c_void_p * n)(*[s.handle.value for s in states])
+        B = (_native.PfBodyKinematics * n)(*[b.struct for b in bodies])
+        dts = [float(dt)] * n if not hasattr(dt, "__len__") else [float(d) for d in dt]
+        if len(dts) != n:
+            raise ValueError("one step length per instance")
+        D = (ctypes.c_double * n)(*dts)
+        h = ctypes.c_void_p()
+        _native.check(_native.lib().pf_batch_create(n, P, S, B, D, int(scheme), ctypes.byref(h)), "pf_batch_create",
+                      plans[0].handle if n else None)
+        self.handle = h
+
+    def step(self, nsteps=1):
+        _native.check(_native.lib().pf_batch_step(self.handle, int(nsteps)), "pf_batch_step", self.plans[0].handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _native.lib().pf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pf_batch_create(plans, states, bodies, dt, scheme=0):
+    return Batch(plans, states, bodies, dt, scheme)
+
+
+def pf_batch_step(batch, nsteps=1):
+    batch.step(nsteps)
+
+
 class Server:
     """Request server (pf_server): continuous batching of time-stepping requests."""
 

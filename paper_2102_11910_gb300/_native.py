@@ -63,6 +63,9 @@ SIGNATURES = {
     "pf_state_get": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_I64), _c.POINTER(_D)]),
     "pf_step": (_c.c_int, [_P, _P, _P, _D, _I32]),
     "pf_step_batch": (_c.c_int, [_I32, _P, _P, _P, _P, _I32]),
+    "pf_batch_create": (_c.c_int, [_I32, _P, _P, _P, _P, _I32, _P]),
+    "pf_batch_step": (_c.c_int, [_P, _I32]),
+    "pf_batch_destroy": (_c.c_int, [_P]),
     "pf_plan_clone": (_c.c_int, [_P, _I32, _P, _c.POINTER(_P)]),
     "pf_server_create": (_c.c_int, [_P, _c.POINTER(_P)]),
     "pf_server_destroy": (_c.c_int, [_P]),
@@ -81,6 +84,7 @@ class GridPfError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
         self.name = STATUS.get(status, str(status))
+        self.detail = detail
         super().__init__("%s returned %s%s" % (where, self.name, (": " + detail) if detail else ""))
 
 

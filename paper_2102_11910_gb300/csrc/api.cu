@@ -322,7 +322,7 @@ pf_status pf_interpolate(pf_plan p, const void* uv, const double* Xq, const doub
 pf_status pf_vic_velocity(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, double Uinf,
                           double Vinf, void* uq, void* vq) {
     if (!p || nv < 0 || (nv > 0 && (!X || !Y || !G || !uq || !vq))) return PF_ERR_ARG;
-    PF_TRY(vortex_regularize(p, X, Y, G, nv, p->w));
+    PF_TRY(vortex_regularize(p, X, Y, G, nv, p->w, nullptr, uq, vq));
     PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
     return vortex_interpolate_located(p, p->uv, nv, uq, vq);
 }

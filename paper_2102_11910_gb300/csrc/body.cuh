@@ -80,6 +80,8 @@ pf_status sheet_solve_device(pf_plan p, pf_schur s, const void* w, const pf_moti
                              int64_t nnz_bound = -1, const VortexSource* vs = nullptr);
 // w += R_s f  (device f of ns doubles, w real[nx*ny])
 pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w);
+// allocate what a sheet solve with this nonzero bound allocates on first use
+pf_status sheet_solve_reserve(pf_plan p, pf_schur s, int64_t nnz_bound);
 
 // step.cu: asynchronous state transfers used by the request server
 pf_status state_load_async(pf_state s, const double* X, const double* Y, const double* G, int64_t nv, double t);

@@ -267,6 +267,7 @@ pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf,
 pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2);           // fft.cu
 enum { CONV_PSI = 0, CONV_UV = 1 };
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,
-                            const int64_t* dn = nullptr);  // transfer.cu
+                            const int64_t* dn = nullptr, void* zu = nullptr, void* zv = nullptr);  // transfer.cu
+pf_status plan_reserve_vortices(pf_plan p, int64_t nv);   // transfer.cu: vortex buffers for nv ahead of time
 pf_status vortex_interpolate(pf_plan p, const void* uv, const double* X, const double* Y, int64_t nq, void* uq, void* vq);
 pf_status vortex_interpolate_located(pf_plan p, const void* uv, int64_t nq, void* uq, void* vq);

@@ -20,7 +20,6 @@
 #include "body.cuh"
 #include "common.cuh"
 
-pf_status plan_reserve_vortices(pf_plan p, int64_t nv);   // transfer.cu
 
 namespace {
 

@@ -342,7 +342,7 @@ Count count_of(pf_state s) { return s->capture ? Count{s->cap, s->dn} : Count{s-
 // optionally with a body sheet f added to the source
 pf_status velocities(pf_plan p, pf_state s, const double* X, const double* Y, Count c, pf_schur sch,
                      const double* f, double Uinf, double Vinf, void* u, void* v) {
-    PF_TRY(vortex_regularize(p, X, Y, s->G, c.n, p->w, c.dn));
+    PF_TRY(vortex_regularize(p, X, Y, s->G, c.n, p->w, c.dn, u, v));
     if (sch) PF_TRY(sheet_deposit(p, sch, f, p->w));
     PF_TRY(conv_solve(p, p->w, p->uv, CONV_UV, Uinf, Vinf));
     return vortex_interpolate_located(p, p->uv, c.n, u, v);
@@ -507,6 +507,74 @@ pf_status state_store_async(pf_state s, double* X, double* Y, double* G, int64_t
 }
 
 int64_t state_capacity(pf_state s) { return s->cap; }
+
+// A captured batch step (pf_batch_create): the graph and its executable, the
+// batch's stream, and what each instance's host counts need after a launch.
+struct pf_batch_s {
+    std::vector<pf_plan> plans;
+    std::vector<pf_state> states;
+    std::vector<pf_body_kinematics> bodies;
+    std::vector<double> dt;
+    std::vector<int> released;          // vortices each instance releases per step
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    std::vector<cudaEvent_t> order;     // one per plan: the plan's earlier work before a launch
+};
+
+namespace {
+
+void free_batch(pf_batch b) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->order)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+bool fixed_in_time(const pf_body_kinematics& k) { return k.ns == 0 || k.amp == 0.0 || k.omega == 0.0; }
+
+// capture one step of every instance into b->graph (the host counts are
+// restored afterwards: the capture runs nothing)
+pf_status capture_batch(pf_batch b, int scheme) {
+    pf_plan p0 = b->plans[0];
+    PF_CUDA(p0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+    pf_status st = PF_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->plans.size() && st == PF_OK && e == cudaSuccess; ++i) {
+        pf_plan p = b->plans[i];
+        pf_state s = b->states[i];
+        e = cudaStreamWaitEvent(p->stream, b->fork, 0);
+        if (e != cudaSuccess) break;
+        const int64_t nv = s->nv;
+        const double t = s->t;
+        int64_t last[2 * PF_MAX_BODIES];
+        std::copy(std::begin(s->last), std::end(s->last), last);
+        s->capture = true;
+        st = pf_step(p, s, &b->bodies[i], b->dt[i], scheme);
+        s->capture = false;
+        s->nv = nv;
+        s->t = t;
+        std::copy(std::begin(last), std::end(last), s->last);
+        if (st != PF_OK && p != p0) snprintf(p0->err, sizeof(p0->err), "instance %zu: %s", i, p->err);
+        // join the plan's stream back (also after an error, so that the capture ends cleanly)
+        e = cudaEventRecord(b->join, p->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &b->graph);
+    if (st != PF_OK) return st;
+    PF_CUDA(p0, e);
+    PF_CUDA(p0, ee);
+    PF_CUDA(p0, cudaGraphInstantiate(&b->exec, b->graph, 0));
+    PF_CUDA(p0, cudaGraphUpload(b->exec, b->stream));
+    return PF_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -721,6 +789,97 @@ pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_bo
     work(false);
     for (auto& t : pool) t.join();
     return (pf_status)first_err.load();
+}
+
+pf_status pf_batch_create(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
+                          const double* dt, int32_t scheme, pf_batch* out) {
+    if (!out) return PF_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !plans || !states || !bodies || !dt || (scheme != 0 && scheme != 1)) return PF_ERR_ARG;
+    std::vector<const void*> own;
+    for (int32_t i = 0; i < n; ++i) {
+        pf_plan p = plans[i];
+        pf_state s = states[i];
+        const pf_body_kinematics& k = bodies[i];
+        if (!p || !s || s->plan != p || !p->stream || p->tm.on || !(dt[i] > 0) || !fixed_in_time(k)) return PF_ERR_ARG;
+        if (k.ns != 0 && (k.ns < 4 || k.ns > PF_MAX_SURFACE_POINTS || !k.xb || !k.yb || !k.ds ||
+                          (k.n_edges != 0 && k.n_edges != 2)))
+            return PF_ERR_ARG;
+        own.push_back(p);
+        own.push_back(s);
+    }
+    std::sort(own.begin(), own.end());
+    if (std::adjacent_find(own.begin(), own.end()) != own.end()) return PF_ERR_ARG;
+    // everything a step of the full capacity allocates, ahead of the capture
+    for (int32_t i = 0; i < n; ++i) {
+        pf_plan p = plans[i];
+        pf_state s = states[i];
+        const pf_body_kinematics& k = bodies[i];
+        PF_TRY(plan_reserve_vortices(p, s->cap));
+        if (k.ns > 0) {
+            PF_TRY(ensure_schur(p, s, surface_of(&k, 1, std::vector<Pose>{body_pose(k, s->t)})));
+            PF_TRY(sheet_solve_reserve(p, s->fac[0].f, 16 * s->cap));
+        }
+        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+    }
+    pf_batch b = new (std::nothrow) pf_batch_s();
+    if (!b) return PF_ERR_OOM;
+    b->plans.assign(plans, plans + n);
+    b->states.assign(states, states + n);
+    b->bodies.assign(bodies, bodies + n);
+    b->dt.assign(dt, dt + n);
+    for (int32_t i = 0; i < n; ++i) b->released.push_back(bodies[i].ns > 0 && bodies[i].n_edges == 2 ? 2 : 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    b->order.assign(n, nullptr);
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->order[i], cudaEventDisableTiming);
+    pf_status st = PF_OK;
+    if (e != cudaSuccess) {
+        snprintf(plans[0]->err, sizeof(plans[0]->err), "pf_batch_create: %s", cudaGetErrorString(e));
+        st = PF_ERR_CUDA;
+    }
+    if (st == PF_OK) st = capture_batch(b, scheme);
+    if (st != PF_OK) {
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return PF_OK;
+}
+
+pf_status pf_batch_step(pf_batch b, int32_t nsteps) {
+    if (!b || nsteps < 0) return PF_ERR_ARG;
+    const size_t n = b->plans.size();
+    for (size_t i = 0; i < n; ++i)
+        if (b->states[i]->nv + (int64_t)nsteps * b->released[i] > b->states[i]->cap) return PF_ERR_CAPACITY;
+    if (nsteps == 0) return PF_OK;
+    pf_plan p0 = b->plans[0];
+    for (size_t i = 0; i < n; ++i) {
+        PF_CUDA(p0, cudaEventRecord(b->order[i], b->plans[i]->stream));
+        PF_CUDA(p0, cudaStreamWaitEvent(b->stream, b->order[i], 0));
+    }
+    for (int32_t k = 0; k < nsteps; ++k) PF_CUDA(p0, cudaGraphLaunch(b->exec, b->stream));
+    PF_CUDA(p0, cudaEventRecord(b->join, b->stream));
+    for (size_t i = 0; i < n; ++i) {
+        PF_CUDA(p0, cudaStreamWaitEvent(b->plans[i]->stream, b->join, 0));
+        pf_state s = b->states[i];
+        for (int32_t k = 0; k < nsteps; ++k) {
+            const int64_t n0 = s->nv;
+            s->nv += b->released[i];
+            for (int e = 0; e < b->released[i]; ++e) s->last[e] = n0 + e;
+            s->t += b->dt[i];
+        }
+    }
+    return PF_OK;
+}
+
+pf_status pf_batch_destroy(pf_batch b) {
+    if (!b) return PF_ERR_ARG;
+    free_batch(b);
+    delete b;
+    return PF_OK;
 }
 
 }  // extern "C"

@@ -117,12 +117,15 @@ pf_status plan_reserve_vortices(pf_plan p, int64_t nv) { return plan_bin_reserve
 
 // R_v in the plan's launch configuration (tile edge, block partition, threads).
 // With dn, the count is read on the device from dn[0] and nv (the capacity)
-// only sizes the launches.
+// only sizes the launches.  With zu, zv (the E_v outputs that follow), every
+// vortex off the grid gets a zero velocity there.
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,
-                            const int64_t* dn) {
+                            const int64_t* dn, void* zu, void* zv) {
     pf_status st = plan_bin_reserve(p, nv);
     if (st != PF_OK) return st;
-    const BinWork bw = plan_binwork(p);
+    BinWork bw = plan_binwork(p);
+    bw.zu = zu;
+    bw.zv = zv;
     if (p->prec == PF_FP64) return regularize_configured<double>(p, bw, X, Y, G, nv, (double*)w, dn);
     return regularize_configured<float>(p, bw, X, Y, G, nv, (float*)w, dn);
 }

@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
                                                        const int64_t* __restrict__ dn, int min_span, Geo geo,
                                                        Pos<T>* __restrict__ pos, int* __restrict__ hist,
                                                        double* __restrict__ gmax_blk, int* __restrict__ status,
-                                                       unsigned long long* __restrict__ oob) {
+                                                       unsigned long long* __restrict__ oob, T* __restrict__ zu,
+                                                       T* __restrict__ zv) {
     extern __shared__ unsigned sm[];
     __shared__ double wmax[BIN_THREADS / 32];
     unsigned* cnt = sm;
@@ -227,6 +228,10 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
                 ++bad;
                 make_pos(p, 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);   // marker: skipped by scatter
                 pos[q] = p;
+                if (zu) {                             // no E_v record: its velocity is zero
+                    zu[q] = T(0);
+                    zv[q] = T(0);
+                }
                 continue;
             }
             make_pos(p, ci, cj, fx, fy, gs[k]);
@@ -760,6 +765,8 @@ struct BinWork {
     void* pos;
     void* recs;
     int64_t rec_cap;          // record slots in recs
+    void* zu = nullptr;       // optional E_v outputs (plan precision): zeroed for every vortex off the grid
+    void* zv = nullptr;
 };
 
 inline Geo make_geo(int nx, int ny, double dx, double x0, double y0, int tile = BIN_TILE) {
@@ -795,7 +802,7 @@ pf_status bin_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double*
     if (nb > 0) {
         PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T, TILE>, nb, BIN_THREADS, sh_loc, s, X, Y, G, nv,
                                                        span, dn, min_span, geo, pos, bw.bin_off, bw.gmax + 1,
-                                                       bw.status, bw.oob)));
+                                                       bw.status, bw.oob, (T*)bw.zu, (T*)bw.zv)));
     }
     PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s,
                                                      geo.ntiles, nb, bw.bin_off, bw.tile_count,

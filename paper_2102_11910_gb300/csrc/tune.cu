@@ -218,13 +218,13 @@ pf_status pf_autotune(pf_plan p, int64_t nv, const char* cache_path, int32_t rep
         const pf_launch_config start = config_of(p);
         std::vector<pf_launch_config> cand;
         for (int tile : {BIN_TILE, BIN_TILE_SMALL})
-            for (int span : SPANS)
-                for (int th : {128, 256})
-                    for (int fft : {0, 1}) {
-                        const pf_launch_config c{tile, span, th, fft};
+            for (int th : {128, 256})
+                for (int fft : {0, 1})
+                    for (int span : SPANS) {
                         // the FFT family is irrelevant where the padded torus is too small
                         // for the register-resident passes: keep one of the two
                         if (fft == 1 && (p->P < 256 || p->Q < 256)) continue;
+                        const pf_launch_config c{tile, span, th, fft};
                         if (config_ok(p, c)) cand.push_back(c);
                     }
         best_t = INFINITY;

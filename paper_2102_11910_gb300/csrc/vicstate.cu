@@ -444,7 +444,6 @@ pf_status vic_step_t(pf_vic_state s, double dt, double Uinf, double Vinf, T* uq,
 
 }  // namespace
 
-pf_status plan_reserve_vortices(pf_plan p, int64_t nv);   // transfer.cu
 BinWork plan_binwork_for(pf_plan p);                       // transfer.cu
 
 extern "C" {

@@ -267,6 +267,30 @@ def batched_instance(rng, shape=None, big=False):
     return dict(grid=grid, body=body, X=X[:nv], Y=Y[:nv], G=G, Uinf=1.0, dt=dt)
 
 
+def plate_vortices_1024(seed=1005, nv=100000, ns=256):
+    """The large served instance with a plate: 1024^2 nodes, dx = 2/1023,
+    centred; a plate of chord 1 at 20 deg with ns = 256 points (dS/dx = 2)
+    releasing at both edges; nv vortices placed and drawn as in
+    batched_instance (outside radius 0.55, upstream-biased box, strengths
+    N(0, 1e-3)) with its CFL step."""
+    rng = np.random.default_rng(seed)
+    nx = ny = 1024
+    dx = 2.0 / (nx - 1)
+    grid = centred_grid(nx, ny, dx)
+    xi = -1.0 + (2.0 * np.arange(1, ns + 1) - 1.0) / ns
+    body = dict(xb=0.5 * xi, yb=np.zeros(ns), ds=np.full(ns, 1.0 / ns), edges=(0, ns - 1), alpha0=math.radians(20.0))
+    hx, hy = 0.5 * (nx - 1) * dx, 0.5 * (ny - 1) * dx - 0.35
+    X, Y = np.empty(0), np.empty(0)
+    while len(X) < nv:
+        x = rng.uniform(-0.8 * hx, 0.4 * hx, 2 * nv)
+        y = rng.uniform(-hy, hy, 2 * nv)
+        keep = np.hypot(x, y) > 0.55
+        X, Y = np.concatenate([X, x[keep]]), np.concatenate([Y, y[keep]])
+    G = rng.normal(0.0, math.sqrt(1e-3), nv)
+    dt = min(0.002, 0.5 * dx / (1.0 + 3.0 * 0.023 * math.sqrt(nv)))
+    return dict(grid=grid, body=body, X=X[:nv], Y=Y[:nv], G=G, Uinf=1.0, dt=dt)
+
+
 def batched_instances(seed=1003, n=256):
     """The uneven batch: n independent instances (seed 1003)."""
     rng = np.random.default_rng(seed)

@@ -256,6 +256,34 @@ def test_odd_count_across_blocks_and_out_of_domain(prec):
     assert rel(w.cpu().numpy(), ref) < (1e-13 if prec == pf.PF_FP64 else 1e-6)
 
 
+@pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
+@pytest.mark.parametrize("tile", [32, 16])
+def test_vortices_off_the_grid_get_zero_velocity(prec, tile):
+    """The 7 vortices off the grid of the test above are left out of R_v and
+    get u = v = 0 (their outputs start as NaN); the others match the oracle
+    run without them.  Both tile edges."""
+    g, X, Y, G = _case(96, 80, 5001, 19, variance=1e-4)
+    X, Y = X.copy(), Y.copy()
+    off = [0, 1, 777, 2048, 4095, 4999, 5000]
+    X[off[:4]] = g.x0 - 3.0 * g.dx
+    Y[off[4:]] = g.y0 + (g.ny + 2) * g.dx
+    keep = np.ones(len(X), bool)
+    keep[off] = False
+    plan = _plan(g, prec)
+    pf.pf_launch_config_set(plan, tile=tile)
+    dtype = torch.float64 if prec == pf.PF_FP64 else torch.float32
+    uq = torch.full((len(X),), float("nan"), dtype=dtype, device="cuda")
+    vq = torch.full_like(uq, float("nan"))
+    pf.pf_vic_velocity(plan, _dev(X), _dev(Y), _dev(G), 0.25, 0.0, uq, vq)
+    with pytest.raises(pf.GridPfError) as e:
+        pf.pf_sync(plan)
+    assert e.value.name == "PF_ERR_OUT_OF_DOMAIN" and "7 points" in str(e.value)
+    u, v = uq.cpu().numpy(), vq.cpu().numpy()
+    assert np.all(u[off] == 0.0) and np.all(v[off] == 0.0)
+    _, _, ru, rv = OV.vortex_velocity(_og(g), X[keep], Y[keep], G[keep], 0.25, 0.0)
+    assert rel(u[keep], ru) < TOL[prec] and rel(v[keep], rv) < TOL[prec]
+
+
 def test_full_size_vic_sampled_against_oracle():
     """1024^2 nodes, 1e6 vortices: w on every node, and psi / velocity at sampled
     nodes and vortices computed one by one by the oracle's direct sums."""
