@@ -81,17 +81,22 @@ pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
  * the free vorticity at the surface stencils (Sec. 2.2.2):
  *   PF_RHS_DIRECT  the FP64 lattice-Green's-function sum over every nonzero
  *                  node of w, each surface point scanning all nx ny nodes;
- *   PF_RHS_FFT     an FP64 zero-padded FFT solve psi = -L^-1 w (FP64 for
- *                  either precision; needs P, Q >= 256), read at the stencils;
+ *   PF_RHS_FFT     a zero-padded FFT solve psi = -L^-1 w (needs P, Q >= 256),
+ *                  read at the stencils: FP64 passes for FP64 plans,
+ *                  double-float passes (pairs of FP32 words, about 48
+ *                  significant bits, run on the FP32 pipe) on the FP32 w of
+ *                  mixed plans;
  *   PF_RHS_SPARSE  the direct sum over a list of the nonzero nodes built once
  *                  per solve (16 ns nnz multiply-adds);
  *   PF_RHS_AUTO    (default) in time stepping, where w holds at most 16 nodes
  *                  per vortex, the sparse route while 16 ns (16 nv) < 2^24;
  *                  otherwise the FFT when ns nx ny > 2^22 and P, Q >= 256,
  *                  else the direct sum.
- * All are FP64; they differ by rounding only.  Mixed-precision plans that
- * take the FFT route allocate 2 nx ny doubles and two FP64 spectra once; the
- * sparse route allocates nx ny ints and doubles once.
+ * All are FP64 or better than FP64 in range and within about 30 FP64 ulps in
+ * rounding; they differ by rounding only.  Mixed-precision plans that take
+ * the FFT route allocate 2 nx ny doubles and two FP64-sized spectra once (and
+ * their grid shape one double-float copy of the LGF spectrum); the sparse
+ * route allocates nx ny ints and doubles once.
  * PF_ERR_ARG for an unknown route or PF_RHS_FFT on a grid with P or Q < 256. */
 enum { PF_RHS_AUTO = 0, PF_RHS_DIRECT = 1, PF_RHS_FFT = 2, PF_RHS_SPARSE = 3 };
 pf_status pf_plan_set_rhs_route(pf_plan plan, int32_t route);

@@ -36,6 +36,7 @@ void free_plan(pf_plan p) {
                           p->twQ32, p->tw256_64, p->tw256_32};
         for (void* q : tables)
             if (q) cudaFree(q);
+        if (p->shared->df) cudaFree(p->shared->df);
         delete p->shared;
     }
 }

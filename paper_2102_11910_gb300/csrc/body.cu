@@ -771,11 +771,6 @@ __global__ void k_surface_from_psi(const double* __restrict__ psi, int nx, int n
     out[p] = -s;
 }
 
-__global__ void k_widen(const float* __restrict__ w, int64_t n, double* __restrict__ w64) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        w64[i] = (double)w[i];
-}
-
 // s'_b = (U - Uinf) y - (V - Vinf) x - Omega/2 (x^2 + y^2)   (Eq. sfsurf with the uniform flow removed)
 __global__ void k_sbprime(const double* __restrict__ x, const double* __restrict__ y, int ns, pf_motion m,
                           double* __restrict__ sb) {
@@ -1220,10 +1215,13 @@ pf_status field_route_buffers(pf_plan p, FieldRoute r) {
         PF_CUDA(p, cudaMalloc(&p->nz_idx, (size_t)M * sizeof(int) + (NZ_BLOCKS + 1) * sizeof(int)));
         PF_CUDA(p, cudaMalloc(&p->nz_val, (size_t)M * sizeof(double)));
     }
-    if (r == ROUTE_FFT && p->prec != PF_FP64 && !p->rhs64) {
-        const size_t spec = (size_t)p->ldK * p->ldT * 2 * sizeof(double);
-        PF_CUDA(p, cudaStreamSynchronize(p->stream));
-        PF_CUDA(p, cudaMalloc(&p->rhs64, 2 * (size_t)M * sizeof(double) + 2 * spec));
+    if (r == ROUTE_FFT && p->prec != PF_FP64) {
+        if (!p->rhs64) {
+            const size_t spec = (size_t)p->ldK * p->ldT * 2 * sizeof(double);
+            PF_CUDA(p, cudaStreamSynchronize(p->stream));
+            PF_CUDA(p, cudaMalloc(&p->rhs64, 2 * (size_t)M * sizeof(double) + 2 * spec));
+        }
+        PF_TRY(df_tables_ready(p));
     }
     return PF_OK;
 }
@@ -1304,15 +1302,14 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
         T2 = p->T2a;
     } else {
         double* b = (double*)p->rhs64;
-        double* wd = b;
         psi = b + M;
         T1 = b + 2 * M;
         T2 = (char*)T1 + spec;
-        k_widen<<<152 * 4, 256, 0, st>>>((const float*)w, M, wd);
-        PF_LAUNCH_CHECK(p);
-        w64 = wd;
+        w64 = nullptr;
     }
-    PF_TRY(conv_psi_f64(p, w64, psi, T1, T2));
+    // FP64 plans: FP64 passes; mixed plans: double-float passes on the FP32 w
+    if (w64) PF_TRY(conv_psi_f64(p, w64, psi, T1, T2));
+    else PF_TRY(conv_psi_df(p, (const float*)w, psi, T1, T2, p->rhs64));
     k_surface_from_psi<<<ceil_div(ns, 128), 128, 0, st>>>(psi, p->nx, ns, s->six, s->siy, s->swx, s->swy, ew);
     PF_LAUNCH_CHECK(p);
     return PF_OK;

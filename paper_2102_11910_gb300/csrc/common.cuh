@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "gridpf.h"
@@ -71,6 +72,11 @@ inline int bin_blocks(int64_t nv, int min_span = BIN_MIN_SPAN) {
 // Read-only tables of one grid shape, shared by a plan and its clones.
 struct PlanTables {
     int refs = 1;
+    // double-float copies of H64 and of the FP64 twiddles (H | twP | twQ, one
+    // allocation) for the mixed plans' FFT route of the surface right-hand
+    // side, built by the first plan that needs them
+    std::mutex mu;
+    void* df = nullptr;
 };
 
 struct pf_plan_s {
@@ -265,6 +271,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 pf_status lgf_build(pf_plan p);                                  // lgf.cu
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf);  // fft.cu
 pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2);           // fft.cu
+pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf);  // fft.cu
+pf_status df_tables_ready(pf_plan p);                                                          // fft.cu
 enum { CONV_PSI = 0, CONV_UV = 1 };
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,
                             const int64_t* dn = nullptr, void* zu = nullptr, void* zv = nullptr);  // transfer.cu

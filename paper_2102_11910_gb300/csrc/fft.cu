@@ -14,8 +14,11 @@
 //   3. rows:    rebuild full Hermitian rows from the half spectra of two real
 //               outputs (psi_j + i psi_{j+1}, or u_j + i v_j), inverse FFT,
 //               keep nodes [0, nx).
+#include "dfloat.cuh"
 #include "fft.cuh"
 #include "fft_reg.cuh"
+
+template <> struct real_of<dfc> { using type = dfl; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx, int ny,
@@ -419,16 +422,16 @@ static pf_status conv_dispatch(pf_plan p, const T* w, T* out, int mode, T Uinf, 
 
 template <typename T>
 static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
-                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ) {
+                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, ConvWs ws) {
     using C = C_t<T>;
     const int P = p->P, Q = p->Q, nx = p->nx, ny = p->ny;
     const size_t sr = 2 * (size_t)P * sizeof(C), sc = 3 * (size_t)Q * sizeof(C);
     PF_CUDA(p, set_smem(k_rows_fwd<T>, sr));
     PF_CUDA(p, set_smem(k_cols<T>, sc));
     PF_CUDA(p, set_smem(k_rows_inv<T>, sr));
-    C* T1 = reinterpret_cast<C*>(p->T1);
-    C* T2a = reinterpret_cast<C*>(p->T2a);
-    C* T2b = reinterpret_cast<C*>(p->T2b);
+    C* T1 = reinterpret_cast<C*>(ws.T1);
+    C* T2a = reinterpret_cast<C*>(ws.T2a);
+    C* T2b = reinterpret_cast<C*>(ws.T2b);
     PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, 256, sr, p->stream>>>(w, T1, nx, ny, P, twP));
     PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ));
     const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
@@ -446,13 +449,13 @@ pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf,
             return conv_dispatch<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
                                          p->twP64, p->twQ64, p->tw256_64, ws);
         return conv_solve_t<double>(p, (const double*)w, (double*)out, mode, Uinf, Vinf, p->H64, p->Hu64, p->Hv64,
-                                    p->twP64, p->twQ64);
+                                    p->twP64, p->twQ64, ws);
     }
     if (reg)
         return conv_dispatch<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
                                     p->Hv32, p->twP32, p->twQ32, p->tw256_32, ws);
     return conv_solve_t<float>(p, (const float*)w, (float*)out, mode, (float)Uinf, (float)Vinf, p->H32, p->Hu32,
-                               p->Hv32, p->twP32, p->twQ32);
+                               p->Hv32, p->twP32, p->twQ32, ws);
 }
 
 // psi = -L^-1 w in FP64 for either precision of plan, on the register-resident
@@ -462,4 +465,89 @@ pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* 
     if (p->P < 256 || p->Q < 256) return PF_ERR_ARG;
     return conv_dispatch<double>(p, w, psi, CONV_PSI, 0.0, 0.0, p->H64, p->Hu64, p->Hv64, p->twP64, p->twQ64,
                                  p->tw256_64, ConvWs{T1, T2, T2});
+}
+
+// ---------------------------------------------------------------- double-float route
+// psi = -L^-1 w for a mixed plan's FP32 w with the shared-memory passes run
+// in double-float (dfloat.cuh): the FP64-class surface right-hand side of the
+// sheet solves at the FP32 pipe's rate.  (The register-resident passes, fully
+// unrolled, grow too large in double-float to compile in reasonable time.)
+// w is widened exactly (lo = 0); psi is returned as doubles (hi + lo).
+
+namespace {
+
+__global__ void k_df_table(const double* __restrict__ src, int64_t n, dfl* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = dfl(src[i]);
+}
+
+__global__ void k_widen_df(const float* __restrict__ w, int64_t n, dfl* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dfl(w[i], 0.0f);
+}
+
+// in place: element i of a dfl array becomes element i of a double array (same size)
+__global__ void k_df_to_double(void* data, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const dfl v = reinterpret_cast<const dfl*>(data)[i];
+        reinterpret_cast<double*>(data)[i] = df_to_double(v);
+    }
+}
+
+struct DfTables {
+    const dfl* H;
+    const dfc *twP, *twQ;
+};
+
+pf_status df_tables(pf_plan p, DfTables& t) {
+    PlanTables* sh = p->shared;
+    const size_t nh = (size_t)(p->P / 2 + 1) * p->Hld;
+    std::lock_guard<std::mutex> lock(sh->mu);
+    if (!sh->df) {
+        const size_t bytes = nh * sizeof(dfl) + (size_t)(p->P + p->Q) * sizeof(dfc);
+        void* d = nullptr;
+        PF_CUDA(p, cudaMalloc(&d, bytes));
+        dfl* h = (dfl*)d;
+        dfc* tp = (dfc*)(h + nh);
+        dfc* tq = tp + p->P;
+        k_df_table<<<152 * 2, 256, 0, p->stream>>>(p->H64, (int64_t)nh, h);
+        k_df_table<<<8, 256, 0, p->stream>>>((const double*)p->twP64, 2 * (int64_t)p->P, (dfl*)tp);
+        k_df_table<<<8, 256, 0, p->stream>>>((const double*)p->twQ64, 2 * (int64_t)p->Q, (dfl*)tq);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);    // complete before any stream reads them
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            snprintf(p->err, sizeof(p->err), "double-float tables: %s", cudaGetErrorString(e));
+            return PF_ERR_CUDA;
+        }
+        sh->df = d;
+    }
+    t.H = (const dfl*)sh->df;
+    t.twP = (const dfc*)(t.H + nh);
+    t.twQ = t.twP + p->P;
+    return PF_OK;
+}
+
+}  // namespace
+
+pf_status df_tables_ready(pf_plan p) {
+    if (p->P < 256 || p->Q < 256) return PF_ERR_ARG;
+    DfTables t;
+    return df_tables(p, t);
+}
+
+// wdf: scratch of nx ny double-floats (8 bytes each); psi: nx ny doubles
+pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf) {
+    if (p->P < 256 || p->Q < 256) return PF_ERR_ARG;
+    DfTables t;
+    PF_TRY(df_tables(p, t));
+    const int64_t M = (int64_t)p->nx * p->ny;
+    const int nb = (int)std::min<int64_t>(ceil_div(M, 256), 152 * 4);
+    k_widen_df<<<nb, 256, 0, p->stream>>>(w, M, (dfl*)wdf);
+    PF_LAUNCH_CHECK(p);
+    PF_TRY(conv_solve_t<dfl>(p, (const dfl*)wdf, (dfl*)psi, CONV_PSI, dfl(0.0), dfl(0.0), t.H, t.H, t.H, t.twP, t.twQ,
+                             ConvWs{T1, T2, T2}));
+    k_df_to_double<<<nb, 256, 0, p->stream>>>(psi, M);
+    PF_LAUNCH_CHECK(p);
+    return PF_OK;
 }

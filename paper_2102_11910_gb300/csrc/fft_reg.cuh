@@ -13,6 +13,7 @@
 template <typename C> struct real_of;
 template <> struct real_of<float2> { using type = float; };
 template <> struct real_of<double2> { using type = double; };
+// (double-float complex: dfloat.cuh)
 
 // cos(2 pi m / 16) for a compile-time m
 template <int M>
@@ -34,7 +35,7 @@ __device__ __forceinline__ C rot16(C x) {
     if (m == 8) { x.x = -x.x; x.y = -x.y; return x; }
     if (m == 12) return INV ? mul_mi(x) : mul_i(x);
     constexpr R c = (R)cos16<m>();
-    constexpr R s = INV ? (R)cos16<m + 12>() : -(R)cos16<m + 12>();   // sin(t) = cos(t - pi/2)
+    constexpr R s = (R)(INV ? cos16<m + 12>() : -cos16<m + 12>());   // sin(t) = cos(t - pi/2)
     C r;
     r.x = x.x * c - x.y * s;
     r.y = x.x * s + x.y * c;

@@ -157,11 +157,12 @@ def test_out_of_grid_body_is_rejected():
 @pytest.mark.parametrize("route", [pf.PF_RHS_FFT, pf.PF_RHS_SPARSE])
 @pytest.mark.parametrize("prec", [pf.PF_FP64, pf.PF_MIXED])
 def test_fft_and_sparse_routes_of_the_surface_rhs_match_the_direct_sum(prec, route):
-    """E_s L^-1 w from an FP64 FFT solve (the route large grids take) or from the
-    list of nonzero nodes (the route time stepping takes with few vortices)
-    against the direct FP64 LGF sum over all nodes (the route pinned to the
-    oracle above): same vorticity, same factor; they differ by FP64 rounding
-    amplified by cond(S)."""
+    """E_s L^-1 w from an FFT solve (the route large grids take: FP64 passes on
+    FP64 plans, double-float passes on mixed ones) or from the list of nonzero
+    nodes (the route time stepping takes with few vortices) against the direct
+    FP64 LGF sum over all nodes (the route pinned to the oracle above): same
+    vorticity, same factor; they differ by FP64-class rounding amplified by
+    cond(S)."""
     n, dx = 256, 2.0 / 255
     g = inputs.centred_grid(n, n, dx)
     b = inputs.plate(96, 1.0, 0.35)                   # dS/dx = 1.33
