@@ -952,9 +952,18 @@ def main():
                     help="only the request server: 4096 requests, Poisson arrivals from 0.1x to 1.2x of saturation")
     ap.add_argument("--body-profile", choices=["all", "plate", "pitching", "big"],
                     help="only the body steps' phase shares (CUDA events): --warmup steps untimed, --steps timed")
+    ap.add_argument("--serving", type=int, default=0, metavar="N",
+                    help="only the request server: N requests at once (the burst), no Poisson rates")
     ap.add_argument("--uneven-batch", action="store_true",
                     help="only the uneven batch of 256 instances (graph, streams, unbatched; mixed and FP64)")
     args = ap.parse_args()
+    if args.serving:
+        import torch
+        import paper_2102_11910_gb300 as pf
+        from paper_2102_11910_gb300 import inputs
+        torch.cuda.set_device(dist_env()[2])
+        print(json.dumps({"serving": bench_serving(pf, inputs, args.serving, ())}))
+        return
     if args.uneven_batch:
         import torch
         import paper_2102_11910_gb300 as pf

@@ -89,8 +89,11 @@ pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
  *   PF_RHS_SPARSE  the direct sum over a list of the nonzero nodes built once
  *                  per solve (16 ns nnz multiply-adds);
  *   PF_RHS_AUTO    (default) in time stepping, where w holds at most 16 nodes
- *                  per vortex, the sparse route while 16 ns (16 nv) < 2^24;
- *                  otherwise the FFT when ns nx ny > 2^22 and P, Q >= 256,
+ *                  per vortex, the sparse route while 16 ns (16 capacity) is
+ *                  below 2^24 for FP64 plans, 2^20 for mixed plans with P,
+ *                  Q >= 256 (capacity: the state's, so that a step's route
+ *                  does not change as vortices are shed); otherwise the FFT
+ *                  when P, Q >= 256 and, for FP64 plans, ns nx ny > 2^22;
  *                  else the direct sum.
  * All are FP64 or better than FP64 in range and within about 30 FP64 ulps in
  * rounding; they differ by rounding only.  Mixed-precision plans that take
@@ -560,9 +563,9 @@ pf_status pf_step_batch(int32_t n, pf_plan* plans, pf_state* states, const pf_bo
  * structs; the body arrays they point to must outlive it, and while it lives
  * its states must not be stepped around other bodies.  Each plan's surface
  * right-hand-side route (pf_plan_set_rhs_route) is chosen once, for the
- * state's capacity: with the route fixed (not PF_RHS_AUTO) a batch step is
- * bitwise pf_step's.  PF_ERR_CUDA if the capture or the instantiation fails
- * (pf_last_error of plans[0] has the text). */
+ * state's capacity, as pf_step chooses it: a batch step is bitwise pf_step's.
+ * PF_ERR_CUDA if the capture or the instantiation fails (pf_last_error of
+ * plans[0] has the text). */
 typedef struct pf_batch_s* pf_batch;
 pf_status pf_batch_create(int32_t n, pf_plan* plans, pf_state* states, const pf_body_kinematics* bodies,
                           const double* dt, int32_t scheme, pf_batch* out);
@@ -580,10 +583,14 @@ pf_status pf_batch_destroy(pf_batch batch);
  * Requests are admitted in submission order while fewer than max_slots are
  * running and the device memory of the resident instances (their grids'
  * LGF tables and spectra, and per instance the plan workspaces, vortex bins,
- * state and Schur factor) stays within hbm_budget_bytes; idle instances are
- * kept for reuse by later requests of the same grid and evicted least
- * recently used first.  Every admitted request runs on its own stream, all of
- * its steps enqueued at admission, so requests overlap on the device.  The
+ * state and Schur factor) stays within hbm_budget_bytes; an instance holds
+ * a power-of-two number of vortices (at least 1024, at least the request's
+ * capacity), and idle instances are kept for reuse by later requests of the
+ * same grid up to that size and evicted least recently used first.  Every
+ * admitted request runs on its own stream, all of its steps enqueued at
+ * admission (for a body fixed in time, every step after the first as a launch
+ * of one step captured into a CUDA graph, as pf_batch_*), so requests overlap
+ * on the device.  The
  * kernels are deterministic and instances share no mutable data: a request's
  * result does not depend on what else is running.  A request waits in the
  * queue only while running requests hold what it needs: one that does not

@@ -1191,17 +1191,24 @@ void schur_free(pf_schur s) {
 // comes from an FP64 FFT solve psi = -L^-1 w (FP64 rounding, far below what
 // the ill-conditioned S amplifies into the sheet) read at the stencils.
 // Route of E_s L^-1 w from the field w (no vortex source): the sparse sum when
-// the caller bounds the nonzero nodes and the sum is small, else the FP64 FFT
-// solve on larger grids, else the direct sum.
+// the caller bounds the nonzero nodes and the sum is small, else the FFT solve
+// where the padded torus allows it, else the direct sum.  The sums run on the
+// FP64 pipe; the FFT of an FP64 plan too, that of a mixed plan in
+// double-float on the FP32 pipe (about sixty times the FP64 rate on this
+// GPU), so mixed plans leave the sparse sum much earlier (2^20 multiply-adds
+// rather than 2^24) and take the FFT whenever it fits.
 enum FieldRoute { ROUTE_SPARSE, ROUTE_DIRECT, ROUTE_FFT };
 
 FieldRoute field_route(pf_plan p, int ns, int64_t nnz_bound) {
     const int64_t M = (int64_t)p->nx * p->ny;
     const bool fft_ok = p->P >= 256 && p->Q >= 256;
+    const bool mixed = p->prec != PF_FP64;
+    const int64_t sparse_max = (int64_t)1 << (mixed && fft_ok ? 20 : 24);
     if (p->rhs_route == PF_RHS_SPARSE ||
-        (p->rhs_route == PF_RHS_AUTO && nnz_bound >= 0 && 16 * (int64_t)ns * nnz_bound < ((int64_t)1 << 24)))
+        (p->rhs_route == PF_RHS_AUTO && nnz_bound >= 0 && 16 * (int64_t)ns * nnz_bound < sparse_max))
         return ROUTE_SPARSE;
-    if (fft_ok && (p->rhs_route == PF_RHS_FFT || (p->rhs_route == PF_RHS_AUTO && (int64_t)ns * M > ((int64_t)1 << 22))))
+    if (fft_ok && (p->rhs_route == PF_RHS_FFT ||
+                   (p->rhs_route == PF_RHS_AUTO && (mixed || (int64_t)ns * M > ((int64_t)1 << 22)))))
         return ROUTE_FFT;
     return ROUTE_DIRECT;
 }

@@ -87,3 +87,12 @@ pf_status sheet_solve_reserve(pf_plan p, pf_schur s, int64_t nnz_bound);
 pf_status state_load_async(pf_state s, const double* X, const double* Y, const double* G, int64_t nv, double t);
 pf_status state_store_async(pf_state s, double* X, double* Y, double* G, int64_t* nv);
 int64_t state_capacity(pf_state s);
+// One pf_step of (p, s, k) captured on the plan's stream and instantiated
+// (the capture runs nothing; s's host counts are left as they were).  The
+// body must be fixed in time; the factor at its pose and every buffer a step
+// of the state's capacity uses are made ready first (this may synchronise the
+// plan's stream).  released: the vortices one step appends.
+pf_status step_graph_create(pf_plan p, pf_state s, const pf_body_kinematics& k, double dt, int scheme,
+                            cudaGraphExec_t* out, int* released);
+// the host counts after one launch of a captured step
+void step_graph_advance(pf_state s, int released, double dt);

@@ -7,9 +7,12 @@
 // plan clone (sharing its grid shape's LGF tables and spectra), a stream and a
 // vortex state; a finished request leaves its slot idle for the next request
 // of the same shape, so grids, spectra and Schur factors stay on the device.
-// All of a request's steps are enqueued on its slot's stream at admission;
-// slots on distinct streams overlap on the device.  Completion is detected
-// with events, without blocking.
+// All of a request's steps are enqueued on its slot's stream at admission:
+// the first as a plain step (it factors S and sizes the buffers), the rest,
+// for a body fixed in time, as launches of one step captured into a CUDA
+// graph (one host call per step instead of a few dozen launches); slots on
+// distinct streams overlap on the device.  Completion is detected with
+// events, without blocking.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -22,6 +25,17 @@
 
 
 namespace {
+
+constexpr int GRAPH_MIN_STEPS = 2;   // remaining steps from which a request's step is captured
+
+// Slot capacities come in powers of two (at least 1024 vortices), so that an
+// idle slot serves any later request of its shape up to that size and slots
+// are created (allocations, page-locked staging) far less often.
+int64_t slot_capacity(int64_t need) {
+    int64_t c = 1024;
+    while (c < need) c *= 2;
+    return c;
+}
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -59,6 +73,7 @@ struct Slot {
     double* pinned = nullptr;    // 3 * cap doubles: X | Y | G
     int64_t nv_out = 0;
     cudaEvent_t done = nullptr;
+    cudaGraphExec_t graph = nullptr;     // the running request's captured step
     Request* req = nullptr;
     double last_used = 0;
 };
@@ -115,6 +130,7 @@ int find_shape(pf_server s, const pf_grid_desc& g) {
 
 void destroy_slot(pf_server s, Slot* sl) {
     if (sl->stream) cudaStreamSynchronize(sl->stream);
+    if (sl->graph) cudaGraphExecDestroy(sl->graph);
     if (sl->state) pf_state_destroy(sl->state);
     if (sl->plan) pf_plan_destroy(sl->plan);
     if (sl->pinned) cudaFreeHost(sl->pinned);
@@ -179,7 +195,21 @@ void launch(Slot* sl, Request* r) {
     std::copy(r->Y.begin(), r->Y.end(), Y);
     std::copy(r->G.begin(), r->G.end(), G);
     pf_status st = state_load_async(sl->state, X, Y, G, nv, 0.0);
-    for (int k = 0; k < r->nsteps && st == PF_OK; ++k) st = pf_step(sl->plan, sl->state, &r->kin, r->dt, r->scheme);
+    int k = 0;
+    if (st == PF_OK && r->nsteps > 0) {
+        st = pf_step(sl->plan, sl->state, &r->kin, r->dt, r->scheme);
+        k = 1;
+    }
+    const bool fixed = r->kin.ns == 0 || r->kin.amp == 0.0 || r->kin.omega == 0.0;
+    if (st == PF_OK && fixed && r->nsteps - k >= GRAPH_MIN_STEPS) {
+        int released = 0;
+        st = step_graph_create(sl->plan, sl->state, r->kin, r->dt, r->scheme, &sl->graph, &released);
+        for (; k < r->nsteps && st == PF_OK; ++k) {
+            if (cudaGraphLaunch(sl->graph, sl->stream) != cudaSuccess) st = PF_ERR_CUDA;
+            else step_graph_advance(sl->state, released, r->dt);
+        }
+    }
+    for (; k < r->nsteps && st == PF_OK; ++k) st = pf_step(sl->plan, sl->state, &r->kin, r->dt, r->scheme);
     if (st == PF_OK) st = state_store_async(sl->state, X, Y, G, &sl->nv_out);
     r->status = st;
     cudaEventRecord(sl->done, sl->stream);
@@ -207,6 +237,10 @@ void retire(pf_server s) {
         s->finished.push_back(r->ticket);
         sl->req = nullptr;
         sl->last_used = now_s();
+        if (sl->graph) {
+            cudaGraphExecDestroy(sl->graph);
+            sl->graph = nullptr;
+        }
     }
 }
 
@@ -267,12 +301,13 @@ pf_status admit(pf_server s) {
                 break;
             }
         if (!sl) {
-            if (!make_room(s, slot_bytes(s->shapes[shape], s->cfg.precision, r->capacity, r->kin.ns))) {
+            const int64_t cap = slot_capacity(r->capacity);
+            if (!make_room(s, slot_bytes(s->shapes[shape], s->cfg.precision, cap, r->kin.ns))) {
                 if (busy > 0) return PF_OK;
                 reject(s, PF_ERR_OOM);
                 continue;
             }
-            const pf_status st = new_slot(s, shape, r->capacity, r->kin.ns, &sl);
+            const pf_status st = new_slot(s, shape, cap, r->kin.ns, &sl);
             if (st == PF_ERR_OOM && busy > 0) return PF_OK;    // wait for memory to free up
             if (st != PF_OK) {
                 reject(s, st);

@@ -331,7 +331,10 @@ pf_status sum_gamma(pf_plan p, pf_state s, int64_t n, const int64_t* dn) {
 }
 
 // Launch size and device count of a stage: the host count, or while the step
-// is captured for replay, the capacity with the count read from s->dn.
+// is captured for replay, the capacity with the count read from s->dn.  (The
+// sheet's right-hand-side route is chosen for the capacity in both cases, 16
+// nodes of w per vortex, so a captured step computes exactly what pf_step
+// does.)
 struct Count {
     int64_t n;
     const int64_t* dn;
@@ -407,7 +410,7 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
                 eb.hi[j] = k.edge_bounds[2 * j + 1];
             }
             PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_KUTTA_SHED, 0.0, s->red, 2, kk, s->newpos,
-                                      s->newpos + MAX_EDGES, s->f, eb, 16 * c.n));
+                                      s->newpos + MAX_EDGES, s->f, eb, 16 * s->cap));
             // release: the new vortices join the arrays X, Y (the caller's position
             // arrays) and G
             k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, c.n, s->newpos,
@@ -416,7 +419,7 @@ pf_status body_stage(pf_plan p, pf_state s, const pf_body_kinematics& k, double 
             if (!c.dn) c.n += 2;
         } else {
             PF_TRY(sheet_solve_device(p, sch, p->w, m, PF_SHEET_CIRCULATION, 0.0, s->red + 1, 0, nullptr, nullptr,
-                                      nullptr, s->f, EdgeBounds(), 16 * c.n));
+                                      nullptr, s->f, EdgeBounds(), 16 * s->cap));
         }
     }
     PhaseSpan ph(p, "phase_velocity");
@@ -459,7 +462,7 @@ pf_status bodies_stage(pf_plan p, pf_state s, const pf_body_kinematics* k, int n
     PF_LAUNCH_CHECK(p);
     double* out = nullptr;
     PF_TRY(sheet_solve_multi_device(p, sch, p->w, mb, ne, s->newpos, s->newpos + MAX_EDGES, s->f, gw, &out,
-                                    16 * c.n));
+                                    16 * s->cap));
     if (ne > 0) {
         k_append<<<1, 32, 0, p->stream>>>(const_cast<double*>(X), const_cast<double*>(Y), s->G, c.n, s->newpos,
                                           out + nb, ne, s->dn, c.dn != nullptr, s->cap, p->d_status);
@@ -538,6 +541,32 @@ void free_batch(pf_batch b) {
 
 bool fixed_in_time(const pf_body_kinematics& k) { return k.ns == 0 || k.amp == 0.0 || k.omega == 0.0; }
 
+// what a captured step of the full capacity needs ready: the vortex buffers,
+// the factor at the (fixed) pose and the buffers of the sheet's route
+pf_status prepare_capture(pf_plan p, pf_state s, const pf_body_kinematics& k) {
+    PF_TRY(plan_reserve_vortices(p, s->cap));
+    if (k.ns > 0) {
+        PF_TRY(ensure_schur(p, s, surface_of(&k, 1, std::vector<Pose>{body_pose(k, s->t)})));
+        PF_TRY(sheet_solve_reserve(p, s->fac[0].f, 16 * s->cap));
+    }
+    return PF_OK;
+}
+
+// one pf_step with the counts read on the device; the host counts are restored
+pf_status step_captured(pf_plan p, pf_state s, const pf_body_kinematics& k, double dt, int scheme) {
+    const int64_t nv = s->nv;
+    const double t = s->t;
+    int64_t last[2 * PF_MAX_BODIES];
+    std::copy(std::begin(s->last), std::end(s->last), last);
+    s->capture = true;
+    const pf_status st = pf_step(p, s, &k, dt, scheme);
+    s->capture = false;
+    s->nv = nv;
+    s->t = t;
+    std::copy(std::begin(last), std::end(last), s->last);
+    return st;
+}
+
 // capture one step of every instance into b->graph (the host counts are
 // restored afterwards: the capture runs nothing)
 pf_status capture_batch(pf_batch b, int scheme) {
@@ -550,16 +579,7 @@ pf_status capture_batch(pf_batch b, int scheme) {
         pf_state s = b->states[i];
         e = cudaStreamWaitEvent(p->stream, b->fork, 0);
         if (e != cudaSuccess) break;
-        const int64_t nv = s->nv;
-        const double t = s->t;
-        int64_t last[2 * PF_MAX_BODIES];
-        std::copy(std::begin(s->last), std::end(s->last), last);
-        s->capture = true;
-        st = pf_step(p, s, &b->bodies[i], b->dt[i], scheme);
-        s->capture = false;
-        s->nv = nv;
-        s->t = t;
-        std::copy(std::begin(last), std::end(last), s->last);
+        st = step_captured(p, s, b->bodies[i], b->dt[i], scheme);
         if (st != PF_OK && p != p0) snprintf(p0->err, sizeof(p0->err), "instance %zu: %s", i, p->err);
         // join the plan's stream back (also after an error, so that the capture ends cleanly)
         e = cudaEventRecord(b->join, p->stream);
@@ -575,6 +595,34 @@ pf_status capture_batch(pf_batch b, int scheme) {
 }
 
 }  // namespace
+
+pf_status step_graph_create(pf_plan p, pf_state s, const pf_body_kinematics& k, double dt, int scheme,
+                            cudaGraphExec_t* out, int* released) {
+    *out = nullptr;
+    if (!fixed_in_time(k) || !p->stream || p->tm.on) return PF_ERR_ARG;
+    PF_TRY(prepare_capture(p, s, k));
+    cudaGraph_t g = nullptr;
+    PF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed));
+    const pf_status st = step_captured(p, s, k, dt, scheme);
+    const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (st != PF_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != PF_OK) return st;
+        PF_CUDA(p, e);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    PF_CUDA(p, ei);
+    *released = k.ns > 0 && k.n_edges == 2 ? 2 : 0;
+    return PF_OK;
+}
+
+void step_graph_advance(pf_state s, int released, double dt) {
+    const int64_t n0 = s->nv;
+    s->nv += released;
+    for (int e = 0; e < released; ++e) s->last[e] = n0 + e;
+    s->t += dt;
+}
 
 extern "C" {
 
@@ -812,15 +860,8 @@ pf_status pf_batch_create(int32_t n, pf_plan* plans, pf_state* states, const pf_
     if (std::adjacent_find(own.begin(), own.end()) != own.end()) return PF_ERR_ARG;
     // everything a step of the full capacity allocates, ahead of the capture
     for (int32_t i = 0; i < n; ++i) {
-        pf_plan p = plans[i];
-        pf_state s = states[i];
-        const pf_body_kinematics& k = bodies[i];
-        PF_TRY(plan_reserve_vortices(p, s->cap));
-        if (k.ns > 0) {
-            PF_TRY(ensure_schur(p, s, surface_of(&k, 1, std::vector<Pose>{body_pose(k, s->t)})));
-            PF_TRY(sheet_solve_reserve(p, s->fac[0].f, 16 * s->cap));
-        }
-        PF_CUDA(p, cudaStreamSynchronize(p->stream));
+        PF_TRY(prepare_capture(plans[i], states[i], bodies[i]));
+        PF_CUDA(plans[i], cudaStreamSynchronize(plans[i]->stream));
     }
     pf_batch b = new (std::nothrow) pf_batch_s();
     if (!b) return PF_ERR_OOM;
@@ -864,13 +905,7 @@ pf_status pf_batch_step(pf_batch b, int32_t nsteps) {
     PF_CUDA(p0, cudaEventRecord(b->join, b->stream));
     for (size_t i = 0; i < n; ++i) {
         PF_CUDA(p0, cudaStreamWaitEvent(b->plans[i]->stream, b->join, 0));
-        pf_state s = b->states[i];
-        for (int32_t k = 0; k < nsteps; ++k) {
-            const int64_t n0 = s->nv;
-            s->nv += b->released[i];
-            for (int e = 0; e < b->released[i]; ++e) s->last[e] = n0 + e;
-            s->t += b->dt[i];
-        }
+        for (int32_t k = 0; k < nsteps; ++k) step_graph_advance(b->states[i], b->released[i], b->dt[i]);
     }
     return PF_OK;
 }

@@ -88,10 +88,11 @@ def test_result_is_the_same_alone_and_in_the_mix(prec):
     for t, r in zip(ts, others):
         X, Y, G, lat = pf.pf_server_result(server, t, _cap(r))
         assert np.all(np.isfinite(X)) and lat > 0
-    # and through pf_step directly
+    # and through pf_step directly, on a state of the server's instance size (a
+    # power of two, at least 1024: the sheet's route is chosen for it)
     g = a["grid"]
     plan = pf.Plan(g[0], g[1], g[2], g[3], g[4], prec)
-    state = pf.State(plan, _cap(a))
+    state = pf.State(plan, 1024)
     pf.pf_state_set(state, a["X"], a["Y"], a["G"], 0.0)
     for _ in range(a["nsteps"]):
         pf.pf_step(plan, state, a["dt"], a["body"], scheme=a["scheme"])
