@@ -467,13 +467,17 @@ def bench_ours(args):
     NPIPE = 4
     hout = [(_t.empty(nv, dtype=_t.float32).pin_memory(), _t.empty(nv, dtype=_t.float32).pin_memory())
             for _ in range(NPIPE)]
-    KE = max(3, min(K, 30))
+    KE = max(3, min(K, 100))
     with _t.cuda.stream(stream):
         pf.pf_vic_velocity_host(plan, hX, hY, hG, 0.0, 0.0, *hout[0])
+        lat_e = []
         t0 = time.perf_counter()
         for _ in range(KE):
+            t1 = time.perf_counter()
             pf.pf_vic_velocity_host(plan, hX, hY, hG, 0.0, 0.0, *hout[0])
+            lat_e.append(time.perf_counter() - t1)
         te = time.perf_counter() - t0
+    lat_e.sort()
     plans = [plan]
     for _ in range(NPIPE - 1):
         sk = torch.cuda.Stream()
@@ -497,7 +501,11 @@ def bench_ours(args):
     te, tp = max_over_ranks(te, world), max_over_ranks(tp, world)
     e2e = {"value": world * KP / tp, "unit": UNIT, "h2d_bytes_per_step": 24 * nv, "d2h_bytes_per_step": 8 * nv,
            "mode": "pf_vic_velocity_host_async on a ring of %d plans (pipelined), %d steps" % (NPIPE, KP),
-           "sync_value": world * KE / te, "sync_mode": "pf_vic_velocity_host, one synchronous call per step"}
+           "sync_value": world * KE / te, "sync_mode": "pf_vic_velocity_host, one synchronous call per step",
+           "sync_latency_ms": {"p50": 1e3 * lat_e[len(lat_e) // 2],
+                               "p99": 1e3 * lat_e[min(len(lat_e) - 1, int(math.ceil(0.99 * len(lat_e))) - 1)],
+                               "calls": KE, "what": "host wall time of one call: inputs in, the step, velocities "
+                                                   "out, synchronised"}}
 
     extras = {}
     if not args.no_extras:
