@@ -14,6 +14,8 @@
 //   3. rows:    rebuild full Hermitian rows from the half spectra of two real
 //               outputs (psi_j + i psi_{j+1}, or u_j + i v_j), inverse FFT,
 //               keep nodes [0, nx).
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "fft.cuh"
 #include "fft_reg.cuh"
@@ -21,7 +23,7 @@
 template <> struct real_of<dfc> { using type = dfl; };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx, int ny,
+__global__ void __launch_bounds__(512) k_rows_fwd(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx, int ny,
                                                   int P, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(256) k_rows_fwd(const T* __restrict__ w, C_t<T
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cols(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
+__global__ void __launch_bounds__(512) k_cols(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
                                               C_t<T>* __restrict__ T2b, int ny, int Q, int mode,
                                               const T* __restrict__ H, const T* __restrict__ Hu,
                                               const T* __restrict__ Hv, int Hld, const C_t<T>* __restrict__ tw) {
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(256) k_cols(const C_t<T>* __restrict__ T1, C_t
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rows_inv(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
+__global__ void __launch_bounds__(512) k_rows_inv(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
                                                   T* __restrict__ out, int nx, int ny, int P, int mode, T Uinf,
                                                   T Vinf, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
@@ -425,17 +427,23 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
                               const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, ConvWs ws) {
     using C = C_t<T>;
     const int P = p->P, Q = p->Q, nx = p->nx, ny = p->ny;
-    const size_t sr = 2 * (size_t)P * sizeof(C), sc = 3 * (size_t)Q * sizeof(C);
+    // the third column buffer holds the second component (mode CONV_UV) only;
+    // the double-float passes of 2048 points and more run 512 threads a block,
+    // one radix-4 butterfly each per pass (their arithmetic, not shared memory,
+    // bounds them; shorter transforms keep 256, which have work for no more)
+    const size_t sr = 2 * (size_t)P * sizeof(C), sc = (mode == CONV_UV ? 3 : 2) * (size_t)Q * sizeof(C);
+    const bool df = std::is_same<T, dfl>::value;
+    const int ntP = df && P >= 2048 ? 512 : 256, ntQ = df && Q >= 2048 ? 512 : 256;
     PF_CUDA(p, set_smem(k_rows_fwd<T>, sr));
     PF_CUDA(p, set_smem(k_cols<T>, sc));
     PF_CUDA(p, set_smem(k_rows_inv<T>, sr));
     C* T1 = reinterpret_cast<C*>(ws.T1);
     C* T2a = reinterpret_cast<C*>(ws.T2a);
     C* T2b = reinterpret_cast<C*>(ws.T2b);
-    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, 256, sr, p->stream>>>(w, T1, nx, ny, P, twP));
-    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, 256, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ));
+    PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, ntP, sr, p->stream>>>(w, T1, nx, ny, P, twP));
+    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, ntQ, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ));
     const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
-    PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, 256, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
+    PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, ntP, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
     return PF_OK;
 }
 
