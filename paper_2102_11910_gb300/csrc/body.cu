@@ -755,6 +755,34 @@ __global__ void k_vortex_entries(const double* __restrict__ X, const double* __r
 }
 
 // The same quantity from an FP64 psi = -L^-1 w on the grid: E_s L^-1 w = -E_s psi.
+// lowest and highest row among n stencil rows (one block)
+__global__ void k_stencil_rows(const int* __restrict__ siy, int n, int* __restrict__ rows) {
+    __shared__ int lo[8], hi[8];
+    int a = 1 << 30, b = -1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a = min(a, siy[i]);
+        b = max(b, siy[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        lo[threadIdx.x >> 5] = a;
+        hi[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = min(a, lo[w]);
+            b = max(b, hi[w]);
+        }
+        rows[0] = a;
+        rows[1] = b;
+    }
+}
+
 __global__ void k_surface_from_psi(const double* __restrict__ psi, int nx, int ns, const int* __restrict__ six,
                                    const int* __restrict__ siy, const double* __restrict__ swx,
                                    const double* __restrict__ swy, double* __restrict__ out) {
@@ -1053,7 +1081,7 @@ pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
 static void free_schur(pf_schur s) {
     void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
                     s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->mwork, s->scal, s->pnx, s->pny,
-                    s->fidx, s->fwt, s->ci, s->cj, s->cw};
+                    s->fidx, s->fwt, s->ci, s->cj, s->cw, s->rows};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->jump) {
@@ -1115,6 +1143,7 @@ pf_status schur_factor_device(pf_plan p, pf_schur s) {
     cudaStream_t st = p->stream;
     k_surface_stencil<<<ceil_div(8 * ns, 32), 32, 0, st>>>(s->x, s->y, ns, p->x0, p->y0, p->dx, p->nx, p->ny, s->six,
                                                             s->siy, s->swx, s->swy, p->d_status);
+    k_stencil_rows<<<1, 256, 0, st>>>(s->siy, 4 * ns, s->rows);
     PF_LAUNCH_CHECK(p);
     if (s->snode) {
         int n2 = 1;
@@ -1173,6 +1202,7 @@ pf_status schur_create(pf_plan p, int ns, pf_schur* out) {
     }
     PF_ALLOC(s->work, 12 * v);
     PF_ALLOC(s->scal, 8 * sizeof(double));
+    PF_ALLOC(s->rows, 2 * sizeof(int));
 #undef PF_ALLOC
     *out = s;
     return PF_OK;
@@ -1316,7 +1346,7 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
     }
     // FP64 plans: FP64 passes; mixed plans: double-float passes on the FP32 w
     if (w64) PF_TRY(conv_psi_f64(p, w64, psi, T1, T2));
-    else PF_TRY(conv_psi_df(p, (const float*)w, psi, T1, T2, p->rhs64));
+    else PF_TRY(conv_psi_df(p, (const float*)w, psi, T1, T2, p->rhs64, s->rows));
     k_surface_from_psi<<<ceil_div(ns, 128), 128, 0, st>>>(psi, p->nx, ns, s->six, s->siy, s->swx, s->swy, ew);
     PF_LAUNCH_CHECK(p);
     return PF_OK;

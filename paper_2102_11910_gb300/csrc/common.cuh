@@ -271,7 +271,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 pf_status lgf_build(pf_plan p);                                  // lgf.cu
 pf_status conv_solve(pf_plan p, const void* w, void* out, int mode, double Uinf, double Vinf);  // fft.cu
 pf_status conv_psi_f64(pf_plan p, const double* w, double* psi, void* T1, void* T2);           // fft.cu
-pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf);  // fft.cu
+pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf,
+                      const int* rows);                                                        // fft.cu
 pf_status df_tables_ready(pf_plan p);                                                          // fft.cu
 enum { CONV_PSI = 0, CONV_UV = 1 };
 pf_status vortex_regularize(pf_plan p, const double* X, const double* Y, const double* G, int64_t nv, void* w,

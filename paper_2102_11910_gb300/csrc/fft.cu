@@ -52,12 +52,18 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_cols(const C_t<T>* __restrict__ T1, C_t<T>* __restrict__ T2a,
                                               C_t<T>* __restrict__ T2b, int ny, int Q, int mode,
                                               const T* __restrict__ H, const T* __restrict__ Hu,
-                                              const T* __restrict__ Hv, int Hld, const C_t<T>* __restrict__ tw) {
+                                              const T* __restrict__ Hv, int Hld, const C_t<T>* __restrict__ tw,
+                                              const int* __restrict__ rows) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* A = reinterpret_cast<C*>(smem_raw);
     C* B = A + Q;
     C* D = B + Q;
+    // rows (nullable, mode CONV_PSI): only output rows rows[0] .. rows[1] are
+    // needed; the row pass takes rows in (even, odd) pairs, so both rows of
+    // every pair that holds a needed one are written (a pair's other row
+    // enters its arithmetic, and must be finite)
+    const int jlo = rows ? max(rows[0], 0) & ~1 : 0, jhi = rows ? min(rows[1] | 1, ny - 1) : ny - 1;
     const int k = blockIdx.x;
     for (int l = threadIdx.x; l < Q; l += blockDim.x)
         A[l] = l < ny ? T1[(size_t)k * ny + l] : cmake<C>(T(0), T(0));
@@ -85,14 +91,15 @@ __global__ void __launch_bounds__(512) k_cols(const C_t<T>* __restrict__ T1, C_t
         for (int l = threadIdx.x; l < Q; l += blockDim.x) Z[l] = Z[l] * H[row + (l <= Q / 2 ? l : Q - l)];
         __syncthreads();
         C* R = block_fft<C, true>(Z, other, Q, tw);
-        for (int j = threadIdx.x; j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = R[j];
+        for (int j = jlo + (int)threadIdx.x; j <= jhi && j < ny; j += blockDim.x) T2a[(size_t)k * ny + j] = R[j];
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_rows_inv(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
                                                   T* __restrict__ out, int nx, int ny, int P, int mode, T Uinf,
-                                                  T Vinf, const C_t<T>* __restrict__ tw) {
+                                                  T Vinf, const C_t<T>* __restrict__ tw,
+                                                  const int* __restrict__ rows) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* A = reinterpret_cast<C*>(smem_raw);
@@ -108,6 +115,8 @@ __global__ void __launch_bounds__(512) k_rows_inv(const C_t<T>* __restrict__ T2a
         jb = ja + 1;
         has_b = jb < ny;
         Sb = T2a;
+        // rows (nullable): blocks whose two rows are not read later do nothing
+        if (rows && (jb < rows[0] || ja > rows[1])) return;
     }
     const int h = P / 2;
     for (int k = threadIdx.x; k <= h; k += blockDim.x) {
@@ -424,7 +433,8 @@ static pf_status conv_dispatch(pf_plan p, const T* w, T* out, int mode, T Uinf, 
 
 template <typename T>
 static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T Vinf, const T* H, const T* Hu,
-                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, ConvWs ws) {
+                              const T* Hv, const C_t<T>* twP, const C_t<T>* twQ, ConvWs ws,
+                              const int* rows = nullptr) {
     using C = C_t<T>;
     const int P = p->P, Q = p->Q, nx = p->nx, ny = p->ny;
     // the third column buffer holds the second component (mode CONV_UV) only;
@@ -441,9 +451,11 @@ static pf_status conv_solve_t(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     C* T2a = reinterpret_cast<C*>(ws.T2a);
     C* T2b = reinterpret_cast<C*>(ws.T2b);
     PF_KERNEL(p, "fft_rows_fwd", k_rows_fwd<T><<<(ny + 1) / 2, ntP, sr, p->stream>>>(w, T1, nx, ny, P, twP));
-    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, ntQ, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ));
+    PF_KERNEL(p, "fft_cols_conv", k_cols<T><<<P / 2 + 1, ntQ, sc, p->stream>>>(T1, T2a, T2b, ny, Q, mode, H, Hu, Hv, p->Hld, twQ,
+                                                                              rows));
     const int nb = mode == CONV_UV ? ny : (ny + 1) / 2;
-    PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, ntP, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP));
+    PF_KERNEL(p, "fft_rows_inv", k_rows_inv<T><<<nb, ntP, sr, p->stream>>>(T2a, T2b, out, nx, ny, P, mode, Uinf, Vinf, twP,
+                                                                               rows));
     return PF_OK;
 }
 
@@ -494,9 +506,11 @@ __global__ void k_widen_df(const float* __restrict__ w, int64_t n, dfl* __restri
         out[i] = dfl(w[i], 0.0f);
 }
 
-// in place: element i of a dfl array becomes element i of a double array (same size)
-__global__ void k_df_to_double(void* data, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// in place: element i of a dfl array becomes element i of a double array (same
+// size), over rows rows[0] .. rows[1] (clamped to [0, ny)) of nx elements
+__global__ void k_df_to_double(void* data, int nx, int ny, const int* __restrict__ rows) {
+    const int64_t i0 = (int64_t)max(rows[0], 0) * nx, i1 = (int64_t)(min(rows[1], ny - 1) + 1) * nx;
+    for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
         const dfl v = reinterpret_cast<const dfl*>(data)[i];
         reinterpret_cast<double*>(data)[i] = df_to_double(v);
     }
@@ -544,8 +558,9 @@ pf_status df_tables_ready(pf_plan p) {
     return df_tables(p, t);
 }
 
-// wdf: scratch of nx ny double-floats (8 bytes each); psi: nx ny doubles
-pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf) {
+// wdf: scratch of nx ny double-floats (8 bytes each); psi: nx ny doubles, of
+// which only rows rows[0] .. rows[1] (device, within [0, ny)) are computed
+pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2, void* wdf, const int* rows) {
     if (p->P < 256 || p->Q < 256) return PF_ERR_ARG;
     DfTables t;
     PF_TRY(df_tables(p, t));
@@ -554,8 +569,8 @@ pf_status conv_psi_df(pf_plan p, const float* w, double* psi, void* T1, void* T2
     k_widen_df<<<nb, 256, 0, p->stream>>>(w, M, (dfl*)wdf);
     PF_LAUNCH_CHECK(p);
     PF_TRY(conv_solve_t<dfl>(p, (const dfl*)wdf, (dfl*)psi, CONV_PSI, dfl(0.0), dfl(0.0), t.H, t.H, t.H, t.twP, t.twQ,
-                             ConvWs{T1, T2, T2}));
-    k_df_to_double<<<nb, 256, 0, p->stream>>>(psi, M);
+                             ConvWs{T1, T2, T2}, rows));
+    k_df_to_double<<<nb, 256, 0, p->stream>>>(psi, p->nx, p->ny, rows);
     PF_LAUNCH_CHECK(p);
     return PF_OK;
 }
