@@ -642,6 +642,15 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
             body = pf.plate_kinematics(64, 1.0, wl["alpha"], Uinf=1.0)
             pf.pf_step(plan, state, 0.002, body)             # includes the one-off factorisation
             res[name] = _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, 0.002, body), 20)
+            # the same step captured once and replayed as a graph (pf_batch of one)
+            gs = torch.cuda.Stream()
+            gplan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, prec, stream=gs)
+            gstate = pf.State(gplan, 256 + 2 * 64)
+            pf.pf_state_set(gstate, wl["X"], wl["Y"], wl["G"])
+            batch = pf.Batch([gplan], [gstate], [body], [0.002])
+            batch.step(1)
+            res[name + "_graph"] = _steps_per_s(pf, gplan, lambda: batch.step(1), 20)
+            batch.close()
         # the same with the generalized edge condition at the leading edge (Sec. 2.5)
         plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
         state = pf.State(plan, 256 + 2 * 64)
@@ -652,8 +661,9 @@ def bench_workloads(pf, inputs, torch, stream, n_batch=256, n_requests=256):
         pf.pf_step(plan, state, 0.002, body)
         res["mixed_edge_bounded"] = _steps_per_s(pf, plan, lambda: pf.pf_step(plan, state, 0.002, body), 20)
         out["plate_128"] = {"unit": "steps/s", "desc": "128^2, plate 20 deg, Ns 64, 256 vortices, Euler, dt 0.002, "
-                            "two-edge release every step (factor reused); edge_bounded: leading edge under "
-                            "|ftilde| <= 0.5 (generalized edge condition), trailing edge Kutta", **res}
+                            "two-edge release every step (factor reused), one pf_step per step or (_graph) one "
+                            "launch of the captured step; edge_bounded: leading edge under |ftilde| <= 0.5 "
+                            "(generalized edge condition), trailing edge Kutta", **res}
         print("workload done: %s" % 'plate_128', file=sys.stderr, flush=True)
         # pitching plate, 768 x 512, RK2, S refactored at every stage.  With the
         # configured Ns = 256 (dS/dx = 0.39, below the paper's 1-4) the released
@@ -960,11 +970,39 @@ def main():
                     help="only the request server: 4096 requests, Poisson arrivals from 0.1x to 1.2x of saturation")
     ap.add_argument("--body-profile", choices=["all", "plate", "pitching", "big"],
                     help="only the body steps' phase shares (CUDA events): --warmup steps untimed, --steps timed")
+    ap.add_argument("--vic", type=int, nargs=2, metavar=("N", "NV"),
+                    help="only the body-free step on N^2 nodes with NV vortices (the benchmark recipe scaled; "
+                         "--warmup untimed, --steps timed), for profiling smaller cases")
     ap.add_argument("--serving", type=int, default=0, metavar="N",
                     help="only the request server: N requests at once (the burst), no Poisson rates")
     ap.add_argument("--uneven-batch", action="store_true",
                     help="only the uneven batch of 256 instances (graph, streams, unbatched; mixed and FP64)")
     args = ap.parse_args()
+    if args.vic:
+        import torch
+        import paper_2102_11910_gb300 as pf
+        from paper_2102_11910_gb300 import inputs
+        torch.cuda.set_device(dist_env()[2])
+        n, nvv = args.vic
+        wl = inputs.vic_1024(nv=nvv, n=n)
+        g = wl["grid"]
+        stream = torch.cuda.Stream()
+        X, Y, G = (torch.from_numpy(a).cuda() for a in (wl["X"], wl["Y"], wl["G"]))
+        with torch.cuda.stream(stream):
+            plan = pf.Plan(g.nx, g.ny, g.dx, g.x0, g.y0, pf.PF_MIXED, stream=stream)
+            uq = torch.empty(nvv, dtype=torch.float32, device="cuda")
+            vq = torch.empty_like(uq)
+            flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+            def step():
+                pf.pf_vic_velocity(plan, X, Y, G, 0.0, 0.0, uq, vq)
+            for _ in range(args.warmup):
+                step()
+            pf.pf_sync(plan)
+            per = time_events(step, args.steps, stream, flush)
+            pf.pf_sync(plan)
+        print(json.dumps({"vic": {"n": n, "nv": nvv, "ms_per_step": statistics.mean(per), "steps": args.steps}}))
+        return
     if args.serving:
         import torch
         import paper_2102_11910_gb300 as pf
