@@ -8,8 +8,8 @@
  *   - array arguments are DEVICE pointers owned by the caller;
  *   - work is enqueued asynchronously on the plan's CUDA stream, so a call
  *     returning PF_OK means "enqueued"; errors found by kernels (out-of-domain
- *     vortices, a timed-out wait) are recorded in a sticky device status word
- *     and reported by pf_sync;
+ *     vortices, a full state, a failed binning check) are recorded in a sticky
+ *     device status word and reported by pf_sync;
  *   - node fields are row-major nx*ny arrays, index j*nx + i for node (i, j) at
  *     (x0 + i dx, y0 + j dx);  their element type is double for PF_FP64 plans and
  *     float for PF_MIXED plans ("real" below);
@@ -37,7 +37,8 @@ typedef enum {
     PF_ERR_CUDA = 3,           /* a CUDA runtime call failed; pf_last_error has the text   */
     PF_ERR_OUT_OF_DOMAIN = 4,  /* a point's 4x4 stencil left the grid; it was not used    */
     PF_ERR_SINGULAR = 5,       /* a pivot of the Schur factorisation vanished              */
-    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                            */
+    PF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (no kernel here waits on
+                                  another: reserved, never returned)                     */
     PF_ERR_NOT_FACTORED = 7,   /* a sheet solve was asked of a body without a factor       */
     PF_ERR_CAPACITY = 8,       /* a state's vortex capacity would be exceeded              */
     PF_ERR_INTERNAL = 9        /* a device-side consistency check of the vortex binning
@@ -90,7 +91,7 @@ pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
  *                  per solve (16 ns nnz multiply-adds);
  *   PF_RHS_AUTO    (default) in time stepping, where w holds at most 16 nodes
  *                  per vortex, the sparse route while 16 ns (16 capacity) is
- *                  below 2^24 for FP64 plans, 2^20 for mixed plans with P,
+ *                  below 2^24 for FP64 plans, 2^22 for mixed plans with P,
  *                  Q >= 256 (capacity: the state's, so that a step's route
  *                  does not change as vortices are shed); otherwise the FFT
  *                  when P, Q >= 256 and, for FP64 plans, ns nx ny > 2^22;
