@@ -91,8 +91,7 @@ pf_status pf_plan_fft_size(pf_plan plan, int32_t* P, int32_t* Q);
  *                  per solve (16 ns nnz multiply-adds);
  *   PF_RHS_AUTO    (default) in time stepping, where w holds at most 16 nodes
  *                  per vortex, the sparse route while 16 ns (16 capacity) is
- *                  below 2^24 for FP64 plans, 2^22 for mixed plans with P,
- *                  Q >= 256 (capacity: the state's, so that a step's route
+ *                  below 2^24 (capacity: the state's, so that a step's route
  *                  does not change as vortices are shed); otherwise the FFT
  *                  when P, Q >= 256 and, for FP64 plans, ns nx ny > 2^22;
  *                  else the direct sum.
