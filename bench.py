@@ -325,6 +325,28 @@ def kernel_table(rep, nsteps, g, nv, esz, hbm_peak):
     return kern
 
 
+# FP32 FMA lanes: 152 SMs x 128 lanes x 2 flops at the 2070 MHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def fft_flop_roofline(kern, nx, ny, P, Q):
+    """The three FFT passes of the velocity solve against the FP32 ALU peak,
+    with the radix-2 count 5 n log2 n flops per complex transform of length n:
+    ny/2 forward row transforms (two real rows each) of length P, P/2 + 1
+    columns of one forward and two inverse length-Q transforms plus the two
+    spectral products, ny inverse row transforms (u + i v) of length P."""
+    names = ("fft_rows_fwd", "fft_cols_conv", "fft_rows_inv")
+    if not all(n in kern for n in names):
+        return None
+    lp, lq = math.log2(P), math.log2(Q)
+    flops = (ny / 2) * 5 * P * lp + (P / 2 + 1) * (3 * 5 * Q * lq + 2 * 6 * Q) + ny * 5 * P * lp
+    us = 1e3 * sum(kern[n]["avg_ms"] for n in names)
+    achieved = flops / (us * 1e-6) / 1e12
+    return {"bound": "alu", "flops": flops, "us": us, "achieved": achieved, "unit": "TFLOP/s",
+            "peak": FP32_PEAK_TFLOPS, "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.070 GHz"}
+
+
 def roofline_of(kern, hbm_peak, peak_note, traffic_rec):
     """The dominant kernel (most time among those with algorithmic bytes)."""
     dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["avg_ms"] * kern[k]["launches_per_step"])
@@ -423,6 +445,7 @@ def bench_ours(args):
                  "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
                  "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak, "peak": hbm_peak,
                  "dram_bytes_measured": (traffic_rec or {}).get("step_dram_bytes", {}).get("pf_vic_velocity")}
+    fft_roof = fft_flop_roofline(kern, g.nx, g.ny, plan.P, plan.Q)
 
     # the same workload as a tile-ordered vortex state, stepped in time (forward
     # Euler): deposit, node velocity, E_v with the move, incremental re-bin
@@ -609,7 +632,7 @@ def bench_ours(args):
                        "launch_config": dict(tuned_cfg, source="pf_autotune (%.2f s, best %.1f us on its synthetic "
                                              "vortices, L2 warm)" % (tune_s, tuned_us))},
             "latency_ms": {"p50": p50, "p99": p99},
-            "roofline": roof, "step_roofline": step_roof,
+            "roofline": roof, "step_roofline": step_roof, "fft_flop_roofline": fft_roof,
             "kernels": kern, "gpu_launches": int(round(launches_per_step * K)),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed_loop": t_wall,
             "vic_state_step": vic_state,
