@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
                                                        unsigned long long* __restrict__ oob, T* __restrict__ zu,
                                                        T* __restrict__ zv) {
     extern __shared__ unsigned sm[];
-    __shared__ double wmax[BIN_THREADS / 32];
+    __shared__ T wmax[BIN_THREADS / 32];
     unsigned* cnt = sm;
-    double gm = 0.0;
+    T gm = T(0);          // in the record's precision: no FP64 instruction per vortex in the mixed path
     for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) cnt[i] = 0u;
     pdl_wait();
     bin_count(dn, min_span, nv, span);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
             }
             make_pos(p, ci, cj, fx, fy, gs[k]);
             pos[q] = p;
-            gm = fmax(gm, fabs((double)p.g));      // |Gamma| as the record carries it
+            gm = fmax(gm, (T)fabs(p.g));           // |Gamma| as the record carries it
             const int tx0 = (ci - 1) / TILE, tx1 = (ci + 2) / TILE;
             const int ty0 = (cj - 1) / TILE, ty1 = (cj + 2) / TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gm;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
+        T m = T(0);
         for (int i = 0; i < BIN_THREADS / 32; ++i) m = fmax(m, wmax[i]);
-        gmax_blk[blockIdx.x] = m;
+        gmax_blk[blockIdx.x] = (double)m;
     }
     int* row = hist + (size_t)blockIdx.x * geo.ntiles;
     for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) row[i] = (int)cnt[i];
