@@ -191,17 +191,45 @@ __device__ __forceinline__ size_t spec_at(int j, int k, int nk) {
     return ((size_t)(j >> 2) * nk + k) * 4 + (j & 3);
 }
 
+// Two consecutive rows j, j + 1 (j even) of a half spectrum are adjacent in
+// this layout: one 16-byte access in FP32, two in FP64.
+template <typename C>
+__device__ __forceinline__ void ld_pair(const C* p, C& a, C& b) { a = p[0]; b = p[1]; }
+template <>
+__device__ __forceinline__ void ld_pair<float2>(const float2* p, float2& a, float2& b) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    a = make_float2(q.x, q.y);
+    b = make_float2(q.z, q.w);
+}
+template <typename C>
+__device__ __forceinline__ void st_pair(C* p, C a, C b) { p[0] = a; p[1] = b; }
+template <>
+__device__ __forceinline__ void st_pair<float2>(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Row groups (one complex transform of two real rows, or of one row of u + i v)
+// per block of the inverse row pass: one for P >= 1024 (a 1024-row grid's
+// velocity then runs as 1024 blocks of 128 threads, eight an SM, in one wave),
+// two for shorter rows (a whole warp or more a block).  The forward pass keeps
+// two (four rows a block: its 32-byte sectors of T1 written whole by one
+// block measured faster than twice the blocks writing halves).
+template <int R3> struct RowGroups { static constexpr int value = R3 >= 4 ? 1 : 2; };
+constexpr int FWD_GROUPS = 2;
+
 template <typename T, int R3>
-__global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w, C_t<T>* __restrict__ T1, int nx,
-                                                        int ny, const C_t<T>* __restrict__ tw256,
-                                                        const C_t<T>* __restrict__ twP) {
+__global__ void __launch_bounds__(16 * R3 * FWD_GROUPS) k_rows_fwd_r(const T* __restrict__ w,
+                                                                                C_t<T>* __restrict__ T1, int nx,
+                                                                                int ny, const C_t<T>* __restrict__ tw256,
+                                                                                const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
-    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1, G = FWD_GROUPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufs = reinterpret_cast<C*>(smem_raw);
     const int g = threadIdx.x / TP, t = threadIdx.x % TP;
     C* buf = bufs + g * SB;
-    const int j0 = 4 * blockIdx.x + 2 * g;
+    const int r0 = 2 * G * blockIdx.x;          // the block's first row (even)
+    const int j0 = r0 + 2 * g;
     const bool h0 = j0 < ny, h1 = j0 + 1 < ny;
     pdl_wait();
     C v[16];
@@ -217,13 +245,14 @@ __global__ void __launch_bounds__(32 * R3) k_rows_fwd_r(const T* __restrict__ w,
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf[spad(t + TP * r)] = v[r];
     __syncthreads();
-    // the block's four rows are one contiguous run of NK * 4 elements
-    C* dst = T1 + (size_t)blockIdx.x * NK * 4;
-    for (int e = threadIdx.x; e < NK * 4; e += blockDim.x) {
-        const int k = e >> 2, jj = e & 3;
-        const C* bz = bufs + (jj >> 1) * SB;
+    // per k, the half spectra of the rows j0, j0 + 1 of each group are adjacent
+    // (rows past ny get the zero spectrum of their zero input)
+    C* dst = T1 + (size_t)(r0 >> 2) * NK * 4 + (r0 & 3);
+    for (int e = threadIdx.x; e < NK * G; e += blockDim.x) {
+        const int k = e / G, gg = e % G;
+        const C* bz = bufs + gg * SB;
         const C z1 = bz[spad(k)], z2 = conjc(bz[spad((P - k) & (P - 1))]);
-        dst[e] = (jj & 1) ? mul_mi(z1 - z2) * T(0.5) : (z1 + z2) * T(0.5);
+        st_pair(dst + 4 * k + 2 * gg, (z1 + z2) * T(0.5), mul_mi(z1 - z2) * T(0.5));
     }
 }
 
@@ -308,54 +337,73 @@ __global__ void __launch_bounds__(16 * R3, sizeof(T) == 4 ? 32 / R3 : 1) k_cols_
     }
 }
 
-// FP32 at P = 2048: at most 64 registers, so four blocks fit an SM and the
-// 512 blocks of a 1024-row grid run in one wave (three at 76 registers took
-// 1.12 waves: 18.2 -> 15.3 us)
+// Inverse row pass.  A group's complex row is u_j + i v_j (node velocity: one
+// row, half spectra from T2a and T2b) or psi_j + i psi_{j+1} (two rows of
+// T2a).  Where the block's rows start at an even row, each k's values of two
+// rows come as one 16-byte pair.  FP32 at P = 2048: one group (128 threads) a
+// block at most 64 registers, eight blocks an SM, so a 1024-row grid's 1024
+// blocks run in one wave.
 template <typename T, int R3>
-__global__ void __launch_bounds__(32 * R3, sizeof(T) == 4 && R3 == 8 ? 4 : 1) k_rows_inv_r(const C_t<T>* __restrict__ T2a, const C_t<T>* __restrict__ T2b,
-                                                        T* __restrict__ out, int nx, int ny, int mode, T Uinf,
-                                                        T Vinf, const C_t<T>* __restrict__ tw256,
-                                                        const C_t<T>* __restrict__ twP) {
+__global__ void __launch_bounds__(16 * R3 * RowGroups<R3>::value,
+                                  sizeof(T) == 4 && R3 == 8 ? 8 : 1) k_rows_inv_r(const C_t<T>* __restrict__ T2a,
+                                                                             const C_t<T>* __restrict__ T2b,
+                                                                             T* __restrict__ out, int nx, int ny,
+                                                                             int mode, T Uinf, T Vinf,
+                                                                             const C_t<T>* __restrict__ tw256,
+                                                                             const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
-    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1;
+    constexpr int P = 256 * R3, TP = P / 16, SB = SBuf<P>::size, NK = P / 2 + 1, G = RowGroups<R3>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufs = reinterpret_cast<C*>(smem_raw);
     const int g = threadIdx.x / TP, t = threadIdx.x % TP;
-    C* buf = reinterpret_cast<C*>(smem_raw) + g * SB;
-    int ja, jb;
-    const C* Sb;
-    bool ha, hb;
-    if (mode == CONV_UV) {
-        ja = jb = 2 * blockIdx.x + g;
-        Sb = T2b;
-        ha = hb = ja < ny;
-    } else {
-        ja = 4 * blockIdx.x + 2 * g;
-        jb = ja + 1;
-        Sb = T2a;
-        ha = ja < ny;
-        hb = jb < ny;
-    }
+    const bool uv = mode == CONV_UV;
+    const int rows = uv ? G : 2 * G;                 // rows of the block
+    const int r0 = rows * blockIdx.x;                // <= ny - 1: every row read lies in a stored group of four
     const int h = P / 2;
     pdl_wait();
-    const int jla = ha ? ja : ny - 1, jlb = hb ? jb : ny - 1;       // clamped rows: loads never branch
-    for (int k = t; k <= h; k += TP) {
-        C a = T2a[spec_at(jla, k, NK)];
-        C b = Sb[spec_at(jlb, k, NK)];
-        if (!ha) a = cmake<C>(T(0), T(0));
-        if (!hb) b = cmake<C>(T(0), T(0));
-        if (k == 0 || k == h) { a.y = 0; b.y = 0; }
-        buf[spad(k)] = a + mul_i(b);
-        if (k > 0 && k < h) buf[spad(P - k)] = conjc(a) + mul_i(conjc(b));
+#pragma unroll 2
+    for (int k = threadIdx.x; k <= h; k += blockDim.x) {
+        C a[2], b[2];
+        const size_t at = spec_at(r0, k, NK);
+        if (uv) {                                     // group gg takes row r0 + gg
+            if (G == 2) {
+                ld_pair(T2a + at, a[0], a[1]);
+                ld_pair(T2b + at, b[0], b[1]);
+            } else {                                  // one row a block: r0 may be odd
+                a[0] = T2a[at];
+                b[0] = T2b[at];
+            }
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg)
+                if (r0 + gg >= ny) a[gg] = b[gg] = cmake<C>(T(0), T(0));
+        } else {                                      // group gg takes rows r0 + 2 gg, r0 + 2 gg + 1
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg) {
+                ld_pair(T2a + at + 2 * gg, a[gg], b[gg]);
+                if (r0 + 2 * gg >= ny) a[gg] = cmake<C>(T(0), T(0));
+                if (r0 + 2 * gg + 1 >= ny) b[gg] = cmake<C>(T(0), T(0));
+            }
+        }
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            C x = a[gg], y = b[gg];
+            if (k == 0 || k == h) { x.y = 0; y.y = 0; }
+            C* buf = bufs + gg * SB;
+            buf[spad(k)] = x + mul_i(y);
+            if (k > 0 && k < h) buf[spad(P - k)] = conjc(x) + mul_i(conjc(y));
+        }
     }
     __syncthreads();
+    C* buf = bufs + g * SB;
     C v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = buf[spad(t + TP * r)];
     __syncthreads();
     fft_strided<C, true, R3>(v, buf, t, tw256, twP);
-    if (mode == CONV_UV) {
-        if (ha) {
-            C* o = reinterpret_cast<C*>(out) + (size_t)ja * nx;
+    if (uv) {
+        const int j = r0 + g;
+        if (j < ny) {
+            C* o = reinterpret_cast<C*>(out) + (size_t)j * nx;
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 const int n = t + TP * r;
@@ -363,12 +411,13 @@ __global__ void __launch_bounds__(32 * R3, sizeof(T) == 4 && R3 == 8 ? 4 : 1) k_
             }
         }
     } else {
+        const int ja = r0 + 2 * g, jb = ja + 1;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int n = t + TP * r;
             if (n < nx) {
-                if (ha) out[(size_t)ja * nx + n] = v[r].x;
-                if (hb) out[(size_t)jb * nx + n] = v[r].y;
+                if (ja < ny) out[(size_t)ja * nx + n] = v[r].x;
+                if (jb < ny) out[(size_t)jb * nx + n] = v[r].y;
             }
         }
     }
@@ -387,20 +436,21 @@ static pf_status conv_solve_r(pf_plan p, const T* w, T* out, int mode, T Uinf, T
     using C = C_t<T>;
     constexpr int P = 256 * R3P, Q = 256 * R3Q;
     const int nx = p->nx, ny = p->ny;
-    const size_t sr = 2 * (size_t)SBuf<P>::size * sizeof(C);
+    constexpr int G = RowGroups<R3P>::value;
+    const size_t sf = FWD_GROUPS * (size_t)SBuf<P>::size * sizeof(C), sr = G * (size_t)SBuf<P>::size * sizeof(C);
     const size_t sc = 2 * (size_t)SBuf<Q>::size * sizeof(C) + 2 * (size_t)((Q / 2 + 1 + 3) / 4 * 4) * sizeof(T);
-    PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sr));
+    PF_CUDA(p, set_smem(k_rows_fwd_r<T, R3P>, sf));
     PF_CUDA(p, set_smem(k_cols_r<T, R3Q>, sc));
     PF_CUDA(p, set_smem(k_rows_inv_r<T, R3P>, sr));
     C* T1 = reinterpret_cast<C*>(ws.T1);
     C* T2a = reinterpret_cast<C*>(ws.T2a);
     C* T2b = reinterpret_cast<C*>(ws.T2b);
-    PF_KERNEL(p, "fft_rows_fwd", PF_CUDA(p, pf_launch(k_rows_fwd_r<T, R3P>, (ny + 3) / 4, 32 * R3P, sr, p->stream, w, T1,
+    PF_KERNEL(p, "fft_rows_fwd", PF_CUDA(p, pf_launch(k_rows_fwd_r<T, R3P>, ceil_div(ny, 2 * FWD_GROUPS), 16 * R3P * FWD_GROUPS, sf, p->stream, w, T1,
                                                       nx, ny, tw256, twP)));
     PF_KERNEL(p, "fft_cols_conv", PF_CUDA(p, pf_launch(k_cols_r<T, R3Q>, P / 2 + 1, 16 * R3Q, sc, p->stream, T1, T2a,
                                                        T2b, ny, P / 2 + 1, mode, H, Hu, Hv, p->Hld, tw256, twQ)));
-    const int nb = mode == CONV_UV ? (ny + 1) / 2 : (ny + 3) / 4;
-    PF_KERNEL(p, "fft_rows_inv", PF_CUDA(p, pf_launch(k_rows_inv_r<T, R3P>, nb, 32 * R3P, sr, p->stream, T2a, T2b, out,
+    const int nb = mode == CONV_UV ? ceil_div(ny, G) : ceil_div(ny, 2 * G);
+    PF_KERNEL(p, "fft_rows_inv", PF_CUDA(p, pf_launch(k_rows_inv_r<T, R3P>, nb, 16 * R3P * G, sr, p->stream, T2a, T2b, out,
                                                       nx, ny, mode, Uinf, Vinf, tw256, twP)));
     return PF_OK;
 }

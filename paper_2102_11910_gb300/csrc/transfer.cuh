@@ -273,7 +273,7 @@ __device__ __forceinline__ int tile_shift_of(unsigned count, double gmax) {
 // k_offsets: a block covers OFF_TILES tiles; its OFF_SEGS x OFF_TILES threads
 // each own a run of at most OFF_RUN consecutive vortex blocks of one tile.
 constexpr int OFF_TILES = 8, OFF_SEGS = 128, OFF_RUN = 5;
-static_assert(OFF_SEGS * OFF_RUN >= BIN_MAX_BLOCKS, "k_offsets covers every block");
+static_assert(OFF_SEGS * OFF_RUN >= BIN_MAX_BLOCKS && BIN_MAX_BLOCKS <= 1024, "k_offsets covers every block");
 static_assert(OFF_TILES * OFF_SEGS == 1024, "k_offsets runs 1024 threads");
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
@@ -292,12 +292,16 @@ __global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __res
                                                   unsigned* __restrict__ tile_count, const double* __restrict__ gmax_blk,
                                                   double* __restrict__ gmax_all) {
     __shared__ int part[OFF_SEGS][OFF_TILES + 1];
+    __shared__ double wmax[32];
     const int tx = threadIdx.x % OFF_TILES, ty = threadIdx.x / OFF_TILES;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int t0 = blockIdx.x * OFF_TILES, t = t0 + tx;
     const int S = (nb + OFF_SEGS - 1) / OFF_SEGS;   // <= OFF_RUN
     const int b0 = ty * S;
     pdl_wait();
+    // block 0: the largest |Gamma| over the locate blocks, one load a thread
+    // (nb <= 1024), issued with the histogram loads and reduced after them
+    double gm = blockIdx.x == 0 && (int)threadIdx.x < nb ? gmax_blk[threadIdx.x] : 0.0;
     int v[OFF_RUN];
     int seg = 0;
 #pragma unroll
@@ -307,15 +311,19 @@ __global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __res
         v[k] = in ? v[k] : 0;
         seg += v[k];
     }
-    if (blockIdx.x == 0 && wid == OFF_TILES) {       // largest |Gamma| over the locate blocks
-        double m = 0.0;
-        for (int b = lane; b < nb; b += 32) m = fmax(m, gmax_blk[b]);
+    if (blockIdx.x == 0) {                           // block-uniform
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if (lane == 0) wmax[wid] = gm;
+    }
+    part[ty][tx] = seg;
+    __syncthreads();
+    if (blockIdx.x == 0 && wid == OFF_TILES) {       // OFF_TILES < 32: a warp that scans nothing
+        double m = wmax[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) *gmax_all = m;
     }
-    part[ty][tx] = seg;
-    __syncthreads();
     if (wid < OFF_TILES) {                            // exclusive scan over the runs of tile t0 + wid
         const int a0 = part[4 * lane][wid], a1 = part[4 * lane + 1][wid];
         const int a2 = part[4 * lane + 2][wid], a3 = part[4 * lane + 3][wid];
@@ -497,21 +505,31 @@ __device__ __forceinline__ void deposit_one(const Rec<T>& rc, T scale, unsigned 
     }
 }
 
-// every record of the tile, four loads in flight per thread
+// U records per thread at a time, the next U loaded while these are used (a
+// thread past the end reloads the last record, which it then skips)
+constexpr int REC_U = 4;
+template <typename T>
+__device__ __forceinline__ void load_recs(const Rec<T>* __restrict__ recs, int r0, int cnt, Rec<T> (&rc)[REC_U]) {
+#pragma unroll
+    for (int u = 0; u < REC_U; ++u) {
+        const int r = r0 + u * (int)blockDim.x + (int)threadIdx.x;
+        rc[u] = recs[r < cnt ? r : cnt - 1];
+    }
+}
+
+// every record of the tile; rc holds this thread's first REC_U (load_recs at 0)
 template <int MODE, int ACC_W, typename T>
 __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs, int cnt, T scale,
-                                                unsigned long long* acc) {
-    constexpr int U = 4;
-    for (int r0 = 0; r0 < cnt; r0 += U * (int)blockDim.x) {
-        Rec<T> rc[U];
+                                                unsigned long long* acc, Rec<T> (&rc)[REC_U]) {
+    const int stride = REC_U * (int)blockDim.x;
+    for (int r0 = 0; r0 < cnt; r0 += stride) {
+        Rec<T> cur[REC_U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {      // a thread past the end reloads the last record (not deposited)
-            const int r = r0 + u * (int)blockDim.x + (int)threadIdx.x;
-            rc[u] = recs[r < cnt ? r : cnt - 1];
-        }
+        for (int u = 0; u < REC_U; ++u) cur[u] = rc[u];
+        if (r0 + stride < cnt) load_recs(recs, r0 + stride, cnt, rc);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (r0 + u * (int)blockDim.x + (int)threadIdx.x < cnt) deposit_one<MODE, ACC_W, T>(rc[u], scale, acc);
+        for (int u = 0; u < REC_U; ++u)
+            if (r0 + u * (int)blockDim.x + (int)threadIdx.x < cnt) deposit_one<MODE, ACC_W, T>(cur[u], scale, acc);
     }
 }
 
@@ -526,18 +544,20 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     for (int i = threadIdx.x; i < ACC_W * ACC_W; i += blockDim.x) acc[i] = 0ull;
     pdl_wait();
-    __syncthreads();
     int start = tile_start[t], cnt = (int)tile_count[t];
     if (start < 0 || cnt < 0 || (int64_t)start + cnt > rec_cap) {     // block-uniform
         if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
         start = cnt = 0;
     }
+    Rec<T> rc[REC_U];
+    if (cnt > 0) load_recs(recs + start, 0, cnt, rc);               // in flight across the barrier
     const bool split32 = sizeof(T) == 4 && cnt < 65536;
     const int sh = tile_shift_of((unsigned)cnt, *gmax_all) - (split32 ? 23 : 0);   // 2^61 -> 2^38 when split
     const T scale = pow2<T>(sh);
-    if (sizeof(T) == 8) deposit_records<DEP_F64_64, ACC_W>(recs + start, cnt, scale, acc);
-    else if (split32) deposit_records<DEP_SPLIT32, ACC_W>(recs + start, cnt, scale, acc);
-    else deposit_records<DEP_F32_64, ACC_W>(recs + start, cnt, scale, acc);
+    __syncthreads();
+    if (sizeof(T) == 8) deposit_records<DEP_F64_64, ACC_W>(recs + start, cnt, scale, acc, rc);
+    else if (split32) deposit_records<DEP_SPLIT32, ACC_W>(recs + start, cnt, scale, acc, rc);
+    else deposit_records<DEP_F32_64, ACC_W>(recs + start, cnt, scale, acc, rc);
     __syncthreads();
     const int* acc_hi = reinterpret_cast<const int*>(acc);
     const int* acc_lo = reinterpret_cast<const int*>(acc) + ACC_W * ACC_W;
@@ -676,6 +696,8 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
         return;
     }
+    Rec<float> rc[REC_U];
+    load_recs(recs + start, 0, cnt, rc);          // in flight while the patch is staged
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     const int gi0 = tx * TILE - 1, gj0 = ty * TILE - 1;
     // patch nodes px, py in [0, 2 PAIRS) x [0, PATCH); px = 2 PAIRS - 1 only pads
@@ -694,24 +716,21 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         }
     }
     __syncthreads();
-    constexpr int U = 4;
-    for (int r0 = 0; r0 < cnt; r0 += U * blockDim.x) {
-        Rec<float> rc[U];
-        bool ok[U];
+    const int stride = REC_U * (int)blockDim.x;
+    for (int r0 = 0; r0 < cnt; r0 += stride) {
+        Rec<float> cur[REC_U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {           // loads first (clamped index)
-            const int r = r0 + u * blockDim.x + threadIdx.x;
-            ok[u] = r < cnt;
-            rc[u] = recs[start + (ok[u] ? r : cnt - 1)];
-        }
+        for (int u = 0; u < REC_U; ++u) cur[u] = rc[u];
+        if (r0 + stride < cnt) load_recs(recs + start, r0 + stride, cnt, rc);   // the next ones in flight
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
+        for (int u = 0; u < REC_U; ++u) {
+            if (r0 + u * (int)blockDim.x + (int)threadIdx.x >= cnt) continue;
+            const Rec<float>& rcu = cur[u];
+            const int lx = rec_lx(rcu), ly = rec_ly(rcu);
             if (lx < 0 || lx >= TILE || ly < 0 || ly >= TILE) continue;  // not home
             float wx[4], wy[4];
-            m4p_weights<float>(rec_fx(rc[u]), wx);
-            m4p_weights<float>(rec_fy(rc[u]), wy);
+            m4p_weights<float>(rec_fx(rcu), wx);
+            m4p_weights<float>(rec_fy(rcu), wy);
             const float4* rows = (lx & 1) ? po + (lx - 1) / 2 : pe + lx / 2;   // node px = lx is the first
             float su = 0.f, sv = 0.f;
 #pragma unroll
@@ -722,12 +741,12 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
                 su += wy[b] * ru;
                 sv += wy[b] * rv;
             }
-            if (rc[u].q < 0 || rc[u].q >= nq) {
+            if (rcu.q < 0 || rcu.q >= nq) {
                 atomicOr(status, ST_INTERNAL);
                 continue;
             }
-            uq[rc[u].q] = su;
-            vq[rc[u].q] = sv;
+            uq[rcu.q] = su;
+            vq[rcu.q] = sv;
         }
     }
 }
