@@ -100,7 +100,8 @@ pf_status interpolate_tiles(pf_plan p, const Geo& geo, const void* uv, int64_t n
                                                          p->tile_count, (const double2*)uv, geo, (double*)uq,
                                                          (double*)vq, p->rec_cap, nq, p->d_status)));
     else
-        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32<TILE>, geo.ntiles, p->tile_threads, 0,
+        PF_KERNEL(p, "interpolate", PF_CUDA(p, pf_launch(k_interp_tiles_f32<TILE>, geo.ntiles, p->tile_threads,
+                                                         (size_t)(REC_U * p->tile_threads + 32) * sizeof(Rec<float>),
                                                          p->stream, (const Rec<float>*)p->recs, p->tile_start,
                                                          p->tile_count, (const float2*)uv, geo, (float*)uq,
                                                          (float*)vq, p->rec_cap, nq, p->d_status)));

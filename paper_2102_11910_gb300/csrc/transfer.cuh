@@ -732,6 +732,13 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
 // shared loads: the patch is staged twice as node pairs, starting at even and
 // at odd local x, so that the four nodes px .. px + 3 of a row are the pairs
 // E[px / 2], E[px / 2 + 1] (px even) or O[(px - 1) / 2], O[(px + 1) / 2].
+//
+// The home records of each chunk of REC_U x blockDim records are counting-
+// sorted by the shared-memory bank of their first patch row (as the deposit's
+// records are, same transposed layout), so the eight lanes of each quarter-
+// warp, whose 16-byte loads are served together, read eight different bank
+// groups; non-home records (a vortex's other tiles) drop out in the same pass.
+// Dynamic shared memory: (REC_U x blockDim + 32) records.
 template <int TILE>
 __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __restrict__ recs,
                                                           const int* __restrict__ tile_start,
@@ -742,6 +749,9 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     constexpr int PATCH = TILE + 3, PAIRS = (PATCH + 1) / 2;   // 18 pairs per patch row at TILE 32
     __shared__ float4 pe[PATCH * PAIRS];
     __shared__ float4 po[PATCH * PAIRS];
+    __shared__ int bcnt[32], bstart[32], nhome;
+    extern __shared__ __align__(16) unsigned char interp_dyn[];
+    Rec<float>* srt = reinterpret_cast<Rec<float>*>(interp_dyn);
     const int t = blockIdx.x;
     pdl_wait();
     const int cnt = (int)tile_count[t];
@@ -753,6 +763,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     }
     Rec<float> rc[REC_U];
     load_recs(recs + start, 0, cnt, rc);          // in flight while the patch is staged
+    if (threadIdx.x < 32) bcnt[threadIdx.x] = 0;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
     const int gi0 = tx * TILE - 1, gj0 = ty * TILE - 1;
     // patch nodes px, py in [0, 2 PAIRS) x [0, PATCH); px = 2 PAIRS - 1 only pads
@@ -771,18 +782,43 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         }
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
     const int stride = REC_U * (int)blockDim.x;
     for (int r0 = 0; r0 < cnt; r0 += stride) {
-        Rec<float> cur[REC_U];
-#pragma unroll
-        for (int u = 0; u < REC_U; ++u) cur[u] = rc[u];
-        if (r0 + stride < cnt) load_recs(recs + start, r0 + stride, cnt, rc);   // the next ones in flight
+        const int n = cnt - r0 < stride ? cnt - r0 : stride;
+        int key[REC_U], pos[REC_U];
 #pragma unroll
         for (int u = 0; u < REC_U; ++u) {
-            if (r0 + u * (int)blockDim.x + (int)threadIdx.x >= cnt) continue;
-            const Rec<float>& rcu = cur[u];
+            const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
+            const bool home = u * (int)blockDim.x + (int)threadIdx.x < n && lx >= 0 && lx < TILE && ly >= 0 &&
+                              ly < TILE;
+            const float4* row = ((lx & 1) ? po + (lx - 1) / 2 : pe + lx / 2) + ly * PAIRS;
+            key[u] = home ? (int)((__cvta_generic_to_shared(row) >> 4) & 31) : -1;
+            pos[u] = home ? atomicAdd(&bcnt[key[u]], 1) : 0;
+        }
+        __syncthreads();
+        if (wid == 0) {                               // bucket starts; counters cleared for the next chunk
+            const int c = bcnt[lane];
+            const int incl = warp_incl_scan(c, lane);
+            bstart[lane] = incl - c;
+            bcnt[lane] = 0;
+            if (lane == 31) nhome = incl;
+        }
+        __syncthreads();
+        const int nh = nhome, R = (nh + 31) >> 5;
+#pragma unroll
+        for (int u = 0; u < REC_U; ++u) {
+            if (key[u] >= 0) {
+                const int idx = bstart[key[u]] + pos[u];
+                srt[(idx % R) * 32 + idx / R] = rc[u];
+            }
+        }
+        if (r0 + stride < cnt) load_recs(recs + start, r0 + stride, cnt, rc);   // the next chunk in flight
+        __syncthreads();
+        for (int i = wid; i < R; i += nw) {
+            if (lane * R + i >= nh) continue;
+            const Rec<float> rcu = srt[i * 32 + lane];
             const int lx = rec_lx(rcu), ly = rec_ly(rcu);
-            if (lx < 0 || lx >= TILE || ly < 0 || ly >= TILE) continue;  // not home
             float wx[4], wy[4];
             m4p_weights<float>(rec_fx(rcu), wx);
             m4p_weights<float>(rec_fy(rcu), wy);
@@ -803,6 +839,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
             uq[rcu.q] = su;
             vq[rcu.q] = sv;
         }
+        __syncthreads();                              // srt and the counters are reused
     }
 }
 
