@@ -383,7 +383,7 @@ def bench_ours(args):
         # launch configuration picked by the library's autotuner for this grid
         # and vortex count (before the warm-up; not part of any timed step)
         t0 = time.perf_counter()
-        tuned_cfg, tuned_us = pf.pf_autotune(plan, nv, None, reps=5)
+        tuned_cfg, tuned_us = pf.pf_autotune(plan, nv, None, reps=15)
         tune_s = time.perf_counter() - t0
         uq = torch.empty(nv, dtype=torch.float32, device="cuda")
         vq = torch.empty(nv, dtype=torch.float32, device="cuda")
@@ -630,7 +630,7 @@ def bench_ours(args):
                        "l2": "flushed between timed steps (256 MB write, outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "launch_config": dict(tuned_cfg, source="pf_autotune (%.2f s, best %.1f us on its synthetic "
-                                             "vortices, L2 warm)" % (tune_s, tuned_us))},
+                                             "vortices, L2 flushed before each timed call)" % (tune_s, tuned_us))},
             "latency_ms": {"p50": p50, "p99": p99},
             "roofline": roof, "step_roofline": step_roof, "fft_flop_roofline": fft_roof,
             "kernels": kern, "gpu_launches": int(round(launches_per_step * K)),

@@ -508,10 +508,10 @@ __device__ __forceinline__ void deposit_one(const Rec<T>& rc, T scale, unsigned 
 // U records per thread at a time, the next U loaded while these are used (a
 // thread past the end reloads the last record, which it then skips)
 constexpr int REC_U = 4;
-template <typename T>
-__device__ __forceinline__ void load_recs(const Rec<T>* __restrict__ recs, int r0, int cnt, Rec<T> (&rc)[REC_U]) {
+template <typename T, int U>
+__device__ __forceinline__ void load_recs(const Rec<T>* __restrict__ recs, int r0, int cnt, Rec<T> (&rc)[U]) {
 #pragma unroll
-    for (int u = 0; u < REC_U; ++u) {
+    for (int u = 0; u < U; ++u) {
         const int r = r0 + u * (int)blockDim.x + (int)threadIdx.x;
         rc[u] = recs[r < cnt ? r : cnt - 1];
     }
@@ -738,8 +738,9 @@ __global__ void __launch_bounds__(256) k_interp_tiles(const Rec<T>* __restrict__
 // records are, same transposed layout), so the eight lanes of each quarter-
 // warp, whose 16-byte loads are served together, read eight different bank
 // groups; non-home records (a vortex's other tiles) drop out in the same pass.
-// Dynamic shared memory: (REC_U x blockDim + 32) records.
-template <int TILE>
+// U records a thread a chunk.  Dynamic shared memory: (U x blockDim + 32)
+// records.
+template <int TILE, int U>
 __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __restrict__ recs,
                                                           const int* __restrict__ tile_start,
                                                           const unsigned* __restrict__ tile_count,
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
         return;
     }
-    Rec<float> rc[REC_U];
+    Rec<float> rc[U];
     load_recs(recs + start, 0, cnt, rc);          // in flight while the patch is staged
     if (threadIdx.x < 32) bcnt[threadIdx.x] = 0;
     const int tx = t % geo.ntx, ty = t / geo.ntx;
@@ -783,12 +784,12 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
-    const int stride = REC_U * (int)blockDim.x;
+    const int stride = U * (int)blockDim.x;
     for (int r0 = 0; r0 < cnt; r0 += stride) {
         const int n = cnt - r0 < stride ? cnt - r0 : stride;
-        int key[REC_U], pos[REC_U];
+        int key[U], pos[U];
 #pragma unroll
-        for (int u = 0; u < REC_U; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int lx = rec_lx(rc[u]), ly = rec_ly(rc[u]);
             const bool home = u * (int)blockDim.x + (int)threadIdx.x < n && lx >= 0 && lx < TILE && ly >= 0 &&
                               ly < TILE;
@@ -807,7 +808,7 @@ __global__ void __launch_bounds__(256) k_interp_tiles_f32(const Rec<float>* __re
         __syncthreads();
         const int nh = nhome, R = (nh + 31) >> 5;
 #pragma unroll
-        for (int u = 0; u < REC_U; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (key[u] >= 0) {
                 const int idx = bstart[key[u]] + pos[u];
                 srt[(idx % R) * 32 + idx / R] = rc[u];
