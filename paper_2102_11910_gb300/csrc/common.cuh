@@ -57,10 +57,9 @@ constexpr int PF_DIAG_DOUBLES = 4 * 2048 + 3 + 5 * 4096;   // impulse scratch: r
 
 // Vortex partition of the binning passes: block b owns vortices
 // [b * span, min(nv, (b + 1) * span)).  Large sets use exactly BIN_MAX_BLOCKS
-// blocks of 1024 threads (one per SM, all resident at once, equal work per
-// SM: a block's fixed work, its 1024-tile histogram and scan, is paid once an
-// SM); small sets use fewer blocks of at least min_span vortices.
-constexpr int BIN_MAX_BLOCKS = 152;
+// blocks (four per SM, all resident at once, equal work per SM); small sets
+// use fewer blocks of at least 1024 vortices.
+constexpr int BIN_MAX_BLOCKS = 608;
 constexpr int BIN_MIN_SPAN = 1024;   // default fewest vortices per block (a tuned plan may use another)
 inline int64_t bin_span(int64_t nv, int min_span = BIN_MIN_SPAN) {
     const int64_t s = (nv + BIN_MAX_BLOCKS - 1) / BIN_MAX_BLOCKS;

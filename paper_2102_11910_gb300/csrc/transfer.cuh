@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int BIN_THREADS = 1024;
+constexpr int BIN_THREADS = 256;
 constexpr int BIN_UNROLL = 4;        // vortices per thread whose loads are issued together
 
 // Per-vortex cell record (original order).  Mixed path: packed cell and the
@@ -351,12 +351,12 @@ __global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __res
 // slots for the deposit and interpolation passes), adds them to its offsets
 // and places its records.
 constexpr int SCAN_PER = 16;     // tiles per thread in the block scan: 256 * 16 = 64 * 64 tiles at most
-template <typename T> struct ScatterUnroll { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
+template <typename T> struct ScatterUnroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 static_assert((2048 / BIN_TILE) * (2048 / BIN_TILE) <= BIN_THREADS * SCAN_PER, "scan covers every tile");
 constexpr int MAX_SCAN_TILES = BIN_THREADS * SCAN_PER;   // smaller tiles are offered only up to this count
 
 template <typename T, int TILE>
-__global__ void __launch_bounds__(BIN_THREADS, 1) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
+__global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
                                                         const int64_t* __restrict__ dn, int min_span,
                                                         Geo geo, const int* __restrict__ off,
                                                         const unsigned* __restrict__ tile_count,
