@@ -544,6 +544,7 @@ __device__ __forceinline__ void deposit_records(const Rec<T>* __restrict__ recs,
 // 32 i + l) so a row reads 32 consecutive records.  Only the order of the
 // integer adds changes, so the sums are those of the unsorted deposit.
 constexpr int DEP_MAX_THREADS = 256;
+constexpr int DEP_SORT_MIN = 256;     // fewer records: too few adds for the sort's three barriers to pay
 constexpr int DEP_SORT_SLOTS = REC_U * DEP_MAX_THREADS + 32;
 
 template <int ACC_W, typename T>
@@ -611,7 +612,9 @@ __global__ void __launch_bounds__(256) k_deposit(const Rec<T>* __restrict__ recs
     const T scale = pow2<T>(sh);
     __syncthreads();
     if (sizeof(T) == 8) deposit_records<DEP_F64_64, ACC_W>(recs + start, cnt, scale, acc, rc);
-    else if (split32) deposit_records_banked<ACC_W>(recs + start, cnt, scale, acc, rc, srt, bcnt, bstart);
+    else if (split32 && cnt >= DEP_SORT_MIN)        // block-uniform
+        deposit_records_banked<ACC_W>(recs + start, cnt, scale, acc, rc, srt, bcnt, bstart);
+    else if (split32) deposit_records<DEP_SPLIT32, ACC_W>(recs + start, cnt, scale, acc, rc);
     else deposit_records<DEP_F32_64, ACC_W>(recs + start, cnt, scale, acc, rc);
     __syncthreads();
     const int* acc_hi = reinterpret_cast<const int*>(acc);
