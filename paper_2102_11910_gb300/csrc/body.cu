@@ -692,15 +692,22 @@ __global__ void __launch_bounds__(256) k_nz_write(const T* __restrict__ w, int M
     }
 }
 
+// The nonzero entries are split into gridDim.y chunks, so that few surface
+// points still fill the GPU (64 points made 64 blocks); each block writes its
+// chunk's partial sum, and the last block of a point to finish (a counter per
+// point, reset by that block) adds the partials in chunk order: the result
+// does not depend on which block finishes last.
 __global__ void __launch_bounds__(256) k_surface_einvlw_sparse(const int* __restrict__ idx, const double* __restrict__ val,
                                                                const int* __restrict__ total, int nx,
                                                                const int* __restrict__ six, const int* __restrict__ siy,
                                                                const double* __restrict__ swx,
                                                                const double* __restrict__ swy,
                                                                const double* __restrict__ G, double dx2,
+                                                               double* __restrict__ part, unsigned* __restrict__ done,
                                                                double* __restrict__ out) {
     __shared__ double sh[256];
-    const int p = blockIdx.x;
+    __shared__ bool last;
+    const int p = blockIdx.x, c = blockIdx.y, nc = gridDim.y;
     int ix[4], iy[4];
     double wx[4], wy[4];
 #pragma unroll
@@ -711,8 +718,10 @@ __global__ void __launch_bounds__(256) k_surface_einvlw_sparse(const int* __rest
         wy[a] = swy[4 * p + a];
     }
     const int n = *total;
+    const int chunk = (n + nc - 1) / nc;
+    const int q0 = c * chunk, q1 = q0 + chunk < n ? q0 + chunk : n;
     double acc = 0.0;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         const int m = idx[q];
         const int i = m % nx, j = m / nx;
         double s = 0.0;
@@ -726,8 +735,30 @@ __global__ void __launch_bounds__(256) k_surface_einvlw_sparse(const int* __rest
         acc += val[q] * s;
     }
     const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[p] = dx2 * tot;
+    if (nc == 1) {
+        if (threadIdx.x == 0) out[p] = dx2 * tot;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        part[(size_t)p * nc + c] = tot;
+        __threadfence();
+        last = atomicAdd(&done[p], 1u) == (unsigned)(nc - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (int k = 0; k < nc; ++k) t += __ldcg(&part[(size_t)p * nc + k]);
+        out[p] = dx2 * t;
+        done[p] = 0u;                                 // ready for the next call (and a graph's next replay)
+    }
 }
+
+// chunks of the sparse surface sum per surface point: about one block an SM
+// (a function of ns alone, so a captured step and pf_step split alike; more
+// chunks cost the batched instances, which fill the GPU together, more than
+// they gave one instance)
+inline int ew_split(int ns) { return std::max(1, std::min(EW_SPLIT_MAX, ceil_div(152, ns))); }
 
 // Vortex route of the same sum: the node entries of R_v Gamma listed straight
 // from the FP64 positions, sixteen per vortex (M4' weights in FP64, Eq.
@@ -1081,7 +1112,7 @@ pf_status sheet_deposit(pf_plan p, pf_schur s, const double* f, void* w) {
 static void free_schur(pf_schur s) {
     void* ptrs[] = {s->x, s->y, s->ds, s->six, s->siy, s->swx, s->swy, s->S, s->A, s->Sinv, s->f0, s->f0hat,
                     s->dgamma0, s->sorder, s->snode, s->gj, s->work, s->mwork, s->scal, s->pnx, s->pny,
-                    s->fidx, s->fwt, s->ci, s->cj, s->cw, s->rows};
+                    s->fidx, s->fwt, s->ci, s->cj, s->cw, s->rows, s->ewpart, s->ewdone};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->jump) {
@@ -1203,6 +1234,9 @@ pf_status schur_create(pf_plan p, int ns, pf_schur* out) {
     PF_ALLOC(s->work, 12 * v);
     PF_ALLOC(s->scal, 8 * sizeof(double));
     PF_ALLOC(s->rows, 2 * sizeof(int));
+    PF_ALLOC(s->ewpart, (size_t)EW_SPLIT_MAX * v);
+    PF_ALLOC(s->ewdone, (size_t)ns * sizeof(unsigned));
+    if (cudaMemsetAsync(s->ewdone, 0, (size_t)ns * sizeof(unsigned), p->stream) != cudaSuccess) return fail(PF_ERR_CUDA);
 #undef PF_ALLOC
     *out = s;
     return PF_OK;
@@ -1293,8 +1327,9 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
         const int nb = (int)std::min<int64_t>(ceil_div(vs->n, 256), 152 * 8);
         k_vortex_entries<<<nb, 256, 0, st>>>(vs->X, vs->Y, vs->G, vs->n, p->nx, p->ny, p->x0, p->y0, p->dx,
                                              p->vent_idx, p->vent_val, total);
-        k_surface_einvlw_sparse<<<ns, 256, 0, st>>>(p->vent_idx, p->vent_val, total, p->nx, s->six, s->siy, s->swx,
-                                                    s->swy, p->G, p->dx * p->dx, ew);
+        k_surface_einvlw_sparse<<<dim3(ns, ew_split(ns)), 256, 0, st>>>(p->vent_idx, p->vent_val, total, p->nx, s->six,
+                                                                        s->siy, s->swx, s->swy, p->G, p->dx * p->dx,
+                                                                        s->ewpart, s->ewdone, ew);
         PF_LAUNCH_CHECK(p);
         return PF_OK;
     }
@@ -1313,8 +1348,9 @@ pf_status surface_rhs(pf_plan p, pf_schur s, const void* w, double* ew, int64_t 
             k_nz_write<float><<<NZ_BLOCKS, 256, 0, st>>>((const float*)w, (int)M, chunk, counts, p->nz_idx, p->nz_val,
                                                          total);
         }
-        k_surface_einvlw_sparse<<<ns, 256, 0, st>>>(p->nz_idx, p->nz_val, total, p->nx, s->six, s->siy, s->swx, s->swy,
-                                                    p->G, p->dx * p->dx, ew);
+        k_surface_einvlw_sparse<<<dim3(ns, ew_split(ns)), 256, 0, st>>>(p->nz_idx, p->nz_val, total, p->nx, s->six,
+                                                                        s->siy, s->swx, s->swy, p->G, p->dx * p->dx,
+                                                                        s->ewpart, s->ewdone, ew);
         PF_LAUNCH_CHECK(p);
         return PF_OK;
     }

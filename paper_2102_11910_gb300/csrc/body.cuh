@@ -39,7 +39,10 @@ struct pf_schur_s {
     int pbox[4] = {0, -1, 0, -1};   // cell-centre box (i0, i1, j0, j1) the surface faces can reach
     double* scal = nullptr;   // device scalars: s0, Gamma1, Gamma2, -, new-vortex x[2], y[2]
     int* rows = nullptr;      // lowest and highest grid row of the stencils (device): the rows psi is read at
+    double* ewpart = nullptr; // sparse surface sum: partial sums (ns x EW_SPLIT_MAX) and a done counter per point
+    unsigned* ewdone = nullptr;
 };
+constexpr int EW_SPLIT_MAX = 16;
 
 pf_status schur_create(pf_plan p, int ns, pf_schur* out);
 void schur_free(pf_schur s);
