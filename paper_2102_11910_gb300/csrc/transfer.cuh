@@ -180,38 +180,41 @@ template <typename T> using Frac = typename std::conditional<sizeof(T) == 4, uns
 // The vortex count and block span of a binning pass: the launch's own, or,
 // when dn is given (a captured step replayed at a growing count), dn[0] with
 // the span bin_span computes for it; blocks past the count bin nothing.
-__device__ __forceinline__ void bin_count(const int64_t* dn, int min_span, int64_t& nv, int64_t& span) {
+// (max_blocks: the launch's partition mode, BIN_MAX_BLOCKS or BIN_WIDE_BLOCKS,
+// chosen on the host for the capacity.)
+__device__ __forceinline__ void bin_count(const int64_t* dn, int min_span, int max_blocks, int64_t& nv,
+                                          int64_t& span) {
     if (!dn) return;
     nv = *dn;
-    const int64_t s = (nv + BIN_MAX_BLOCKS - 1) / BIN_MAX_BLOCKS;
+    const int64_t s = (nv + max_blocks - 1) / max_blocks;
     span = s < min_span ? min_span : s;
 }
 
-template <typename T, int TILE>
-__global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
+template <typename T, int TILE, int NT>
+__global__ void __launch_bounds__(NT) k_locate(const double* __restrict__ X, const double* __restrict__ Y,
                                                        const double* __restrict__ G, int64_t nv, int64_t span,
-                                                       const int64_t* __restrict__ dn, int min_span, Geo geo,
+                                                       const int64_t* __restrict__ dn, int min_span, int max_blocks, Geo geo,
                                                        Pos<T>* __restrict__ pos, int* __restrict__ hist,
                                                        double* __restrict__ gmax_blk, int* __restrict__ status,
                                                        unsigned long long* __restrict__ oob, T* __restrict__ zu,
                                                        T* __restrict__ zv) {
     extern __shared__ unsigned sm[];
-    __shared__ T wmax[BIN_THREADS / 32];
+    __shared__ T wmax[NT / 32];
     unsigned* cnt = sm;
     T gm = T(0);          // in the record's precision: no FP64 instruction per vortex in the mixed path
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) cnt[i] = 0u;
+    for (int i = threadIdx.x; i < geo.ntiles; i += NT) cnt[i] = 0u;
     pdl_wait();
-    bin_count(dn, min_span, nv, span);
+    bin_count(dn, min_span, max_blocks, nv, span);
     __syncthreads();
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
     int bad = 0;
-    for (int64_t base = lo; base < hi; base += BIN_THREADS * BIN_UNROLL) {
+    for (int64_t base = lo; base < hi; base += NT * BIN_UNROLL) {
         // issue the loads of BIN_UNROLL vortices before using any of them
         double xs[BIN_UNROLL], ys[BIN_UNROLL], gs[BIN_UNROLL];
 #pragma unroll
         for (int k = 0; k < BIN_UNROLL; ++k) {   // clamped: a thread past the end reloads the last vortex
-            int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            int64_t q = base + k * NT + threadIdx.x;
             q = q < hi ? q : hi - 1;
             xs[k] = X[q];
             ys[k] = Y[q];
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
         }
 #pragma unroll
         for (int k = 0; k < BIN_UNROLL; ++k) {
-            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            const int64_t q = base + k * NT + threadIdx.x;
             if (q >= hi) break;
             int ci = 0, cj = 0;
             Frac<T> fx = 0, fy = 0;
@@ -253,11 +256,11 @@ __global__ void __launch_bounds__(BIN_THREADS) k_locate(const double* __restrict
     __syncthreads();
     if (threadIdx.x == 0) {
         T m = T(0);
-        for (int i = 0; i < BIN_THREADS / 32; ++i) m = fmax(m, wmax[i]);
+        for (int i = 0; i < NT / 32; ++i) m = fmax(m, wmax[i]);
         gmax_blk[blockIdx.x] = (double)m;
     }
     int* row = hist + (size_t)blockIdx.x * geo.ntiles;
-    for (int i = threadIdx.x; i < geo.ntiles; i += BIN_THREADS) row[i] = (int)cnt[i];
+    for (int i = threadIdx.x; i < geo.ntiles; i += NT) row[i] = (int)cnt[i];
 }
 
 // Fixed-point exponent of a tile: every node sum is bounded by
@@ -351,35 +354,39 @@ __global__ void __launch_bounds__(1024) k_offsets(int ntiles, int nb, int* __res
 // slots for the deposit and interpolation passes), adds them to its offsets
 // and places its records.
 constexpr int SCAN_PER = 16;     // tiles per thread in the block scan: 256 * 16 = 64 * 64 tiles at most
-template <typename T> struct ScatterUnroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+// vortices a thread loads at a time: at 1024 threads the eight FP32 records
+// spill (64 registers at most), so four (FP64: four and two)
+template <typename T, int NT> struct ScatterUnroll {
+    static constexpr int value = (sizeof(T) == 4 ? 8 : 4) / (NT == 1024 ? 2 : 1);
+};
 static_assert((2048 / BIN_TILE) * (2048 / BIN_TILE) <= BIN_THREADS * SCAN_PER, "scan covers every tile");
 constexpr int MAX_SCAN_TILES = BIN_THREADS * SCAN_PER;   // smaller tiles are offered only up to this count
 
-template <typename T, int TILE>
-__global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
-                                                        const int64_t* __restrict__ dn, int min_span,
+template <typename T, int TILE, int NT>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 4) k_scatter(const Pos<T>* __restrict__ pos, int64_t nv, int64_t span,
+                                                        const int64_t* __restrict__ dn, int min_span, int max_blocks,
                                                         Geo geo, const int* __restrict__ off,
                                                         const unsigned* __restrict__ tile_count,
                                                         int* __restrict__ tile_start, Rec<T>* __restrict__ recs,
                                                         int64_t rec_cap, int* __restrict__ status) {
     extern __shared__ unsigned sm[];
-    __shared__ int wsum[BIN_THREADS / 32];
+    __shared__ int wsum[NT / 32];
     unsigned* cnt = sm;
     int* first = (int*)(sm + geo.ntiles);
     pdl_wait();
-    bin_count(dn, min_span, nv, span);
+    bin_count(dn, min_span, max_blocks, nv, span);
     const int64_t lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < nv ? lo + span : nv;
     // this thread's first records (in flight during the scan)
-    Pos<T> p[ScatterUnroll<T>::value];
+    Pos<T> p[ScatterUnroll<T, NT>::value];
 #pragma unroll
-    for (int k = 0; k < ScatterUnroll<T>::value; ++k) {     // clamped loads; past the end: no vortex
-        const int64_t q = lo + k * BIN_THREADS + threadIdx.x;
+    for (int k = 0; k < ScatterUnroll<T, NT>::value; ++k) {     // clamped loads; past the end: no vortex
+        const int64_t q = lo + k * NT + threadIdx.x;
         p[k] = pos[q < hi ? q : (hi > 0 ? hi - 1 : 0)];
         if (q >= hi) make_pos(p[k], 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);
     }
     // exclusive scan of tile_count: thread i owns tiles [i * per, i * per + per)
-    const int per = (geo.ntiles + BIN_THREADS - 1) / BIN_THREADS;   // <= SCAN_PER
+    const int per = (geo.ntiles + NT - 1) / NT;   // <= SCAN_PER
     const int t0 = threadIdx.x * per;
     int mine = 0;
 #pragma unroll
@@ -408,20 +415,20 @@ __global__ void __launch_bounds__(BIN_THREADS, 4) k_scatter(const Pos<T>* __rest
         }
     }
     __syncthreads();
-    for (int64_t base = lo; base < hi; base += BIN_THREADS * ScatterUnroll<T>::value) {
+    for (int64_t base = lo; base < hi; base += NT * ScatterUnroll<T, NT>::value) {
         if (base != lo) {
 #pragma unroll
-            for (int k = 0; k < ScatterUnroll<T>::value; ++k) {     // loads first (clamped)
-                const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            for (int k = 0; k < ScatterUnroll<T, NT>::value; ++k) {     // loads first (clamped)
+                const int64_t q = base + k * NT + threadIdx.x;
                 p[k] = pos[q < hi ? q : hi - 1];
                 if (q >= hi) make_pos(p[k], 0xFFFF, 0xFFFF, Frac<T>(0), Frac<T>(0), 0.0);
             }
         }
 #pragma unroll
-        for (int k = 0; k < ScatterUnroll<T>::value; ++k) {
+        for (int k = 0; k < ScatterUnroll<T, NT>::value; ++k) {
             const int ci = pos_ci(p[k]), cj = pos_cj(p[k]);
             if (ci == 0xFFFF) continue;
-            const int64_t q = base + k * BIN_THREADS + threadIdx.x;
+            const int64_t q = base + k * NT + threadIdx.x;
             const int tx0 = (ci - 1) / TILE, tx1 = (ci + 2) / TILE;
             const int ty0 = (cj - 1) / TILE, ty1 = (cj + 2) / TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
@@ -902,34 +909,43 @@ inline Geo make_geo(int nx, int ny, double dx, double x0, double y0, int tile = 
 // Bin nv vortices by tile (locate, offsets, scatter) into bw; `p` (may be
 // null) only supplies the timing records and the error text.
 // With dn (device count, see bin_count), nv is the capacity the launch is sized for.
-template <typename T, int TILE = BIN_TILE>
-pf_status bin_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
-                     const double* G, int64_t nv, cudaStream_t s, int min_span = BIN_MIN_SPAN,
-                     const int64_t* dn = nullptr) {
-    if (geo.ntiles > MAX_SCAN_TILES) return PF_ERR_ARG;
+template <typename T, int TILE, int NT>
+pf_status bin_launch_nt(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
+                        const double* G, int64_t nv, cudaStream_t s, int min_span, const int64_t* dn) {
     const int nb = bin_blocks(nv, min_span);
     const int64_t span = bin_span(nv, min_span);
+    const int mb = bin_max_blocks(nv);
     const size_t sh_loc = (size_t)geo.ntiles * sizeof(unsigned);
     const size_t sh_sc = 2 * (size_t)geo.ntiles * sizeof(unsigned);
-    if (set_smem(k_locate<T, TILE>, sh_loc) != cudaSuccess || set_smem(k_scatter<T, TILE>, sh_sc) != cudaSuccess)
+    if (set_smem(k_locate<T, TILE, NT>, sh_loc) != cudaSuccess || set_smem(k_scatter<T, TILE, NT>, sh_sc) != cudaSuccess)
         return PF_ERR_CUDA;
     Pos<T>* pos = (Pos<T>*)bw.pos;
     if (nb > 0) {
-        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T, TILE>, nb, BIN_THREADS, sh_loc, s, X, Y, G, nv,
-                                                       span, dn, min_span, geo, pos, bw.bin_off, bw.gmax + 1,
+        PF_KERNEL(p, "bin_locate", PF_CUDA(p, pf_launch(k_locate<T, TILE, NT>, nb, NT, sh_loc, s, X, Y, G, nv,
+                                                       span, dn, min_span, mb, geo, pos, bw.bin_off, bw.gmax + 1,
                                                        bw.status, bw.oob, (T*)bw.zu, (T*)bw.zv)));
     }
     PF_KERNEL(p, "bin_offsets", PF_CUDA(p, pf_launch(k_offsets, ceil_div(geo.ntiles, OFF_TILES), 1024, 0, s,
                                                      geo.ntiles, nb, bw.bin_off, bw.tile_count,
                                                      (const double*)(bw.gmax + 1), bw.gmax)));
     if (nb > 0) {
-        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T, TILE>, nb, BIN_THREADS, sh_sc, s, pos, nv,
-                                                         span, dn, min_span, geo, bw.bin_off, bw.tile_count,
+        PF_KERNEL(p, "bin_scatter", PF_CUDA(p, pf_launch(k_scatter<T, TILE, NT>, nb, NT, sh_sc, s, pos, nv,
+                                                         span, dn, min_span, mb, geo, bw.bin_off, bw.tile_count,
                                                          bw.tile_start, (Rec<T>*)bw.recs, bw.rec_cap, bw.status)));
     } else if (cudaMemsetAsync(bw.tile_start, 0, (size_t)geo.ntiles * sizeof(int), s) != cudaSuccess) {
         return PF_ERR_CUDA;
     }
     return PF_OK;
+}
+
+template <typename T, int TILE = BIN_TILE>
+pf_status bin_launch(pf_plan p, const Geo& geo, const BinWork& bw, const double* X, const double* Y,
+                     const double* G, int64_t nv, cudaStream_t s, int min_span = BIN_MIN_SPAN,
+                     const int64_t* dn = nullptr) {
+    if (geo.ntiles > MAX_SCAN_TILES) return PF_ERR_ARG;
+    if (bin_max_blocks(nv) == BIN_WIDE_BLOCKS)
+        return bin_launch_nt<T, TILE, 1024>(p, geo, bw, X, Y, G, nv, s, min_span, dn);
+    return bin_launch_nt<T, TILE, BIN_THREADS>(p, geo, bw, X, Y, G, nv, s, min_span, dn);
 }
 
 // Deposit the binned records of bw into w.
