@@ -135,7 +135,8 @@ pf_status pf_timing_report(pf_plan plan, char* buf, int64_t buflen);
  *                 rounding (within the plan precision's tolerance).
  *   min_span      fewest vortices per binning block: 256, 512, 1024, 2048 or
  *                 4096.  Results are bitwise the same for every value.
- *   tile_threads  threads per tile block of the deposit and E_v: 128 or 256.
+ *   tile_threads  threads per tile block of the deposit (and of E_v in FP64
+ *                 plans; mixed plans' E_v always runs 256): 128 or 256.
  *                 Results are bitwise the same for both.
  *   fft           0: register-resident radix-16 Stockham passes (grids whose
  *                 padded torus is at least 256 x 256; smaller ones always take
